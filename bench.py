@@ -1,0 +1,491 @@
+#!/usr/bin/env python
+"""Throughput of the per-timestep render-and-backprop path on GB300.
+
+One step = one training step of the batched multi-camera path at one
+timestep: temporal selection, instance-matrix projection with EWA covariance,
+frustum mask and point-life update (Eq. 5), LOD cull, SH colour, tile|depth
+duplication and radix sort, 16x16-tile alpha blending (Eq. 2), an L1
+photometric loss against a synthetic target, and the hand-written backward to
+every Gaussian parameter and instance pose. All cameras of the rig run in one
+call sequence captured as a CUDA graph.
+
+Printed (rank 0, one JSON line): views/s (value), Mpix/s, the plain per-view
+comparator (the same library, one camera per call sequence, eager, no graph),
+per-kernel device times, the roofline of the dominant kernel, the FP64 CPU
+oracle timed on a bounded sample on this host, an end-to-end figure through
+the public API with host buffers, and the SM clocks seen while timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rig|mid|large|tiny|small-rig]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM roofline"
+
+# workload name -> (scene spec, overrides, LOD threshold, description)
+WORKLOADS = {
+    "rig": ("rig", {}, 1.0, "batched surround rig on the large corridor: 8M static + 80 instances "
+            "of U{5k..20k}, SH3, 5x 1920x1080 + 2x 1280x960 cameras at one timestep"),
+    "mid": ("mid", {}, 1.0, "mid corridor: 1M static + 20x5k dynamic, SH3, one 1920x1080 camera"),
+    "large": ("large", {}, 1.0, "large corridor: 8M static + 80 instances, SH3, one 1920x1280 camera"),
+    "tiny": ("tiny", {}, 0.0, "tiny corridor: 20k static + 2x1k dynamic, SH0, one 320x192 camera"),
+    "small-rig": ("rig", {"n_static": 1_500_000, "n_inst": 16, "n_steps": 60}, 1.0,
+                  "profiling case: the surround rig on a 1.5M-Gaussian corridor"),
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    p.add_argument("--workload", default="rig", choices=tuple(WORKLOADS))
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-plain", action="store_true", help="skip the plain per-view comparator")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured", float(d.get("sm_max_mhz", 2070.0))
+    return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"s3r_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_workload(name: str, seed: int):
+    from paper_2503_08217_gb300 import scenegen
+    spec, over, lod, desc = WORKLOADS[name]
+    scene = scenegen.generate(spec, seed=seed, **over)
+    return scene, lod, desc
+
+
+def step_index(scene, rank: int) -> int:
+    return min(scene.n_steps - 1, scene.n_steps // 2 + rank)
+
+
+def tile_passes(tiles: int) -> int:
+    """8-bit radix passes over the view-tile ids (as the library plans them)."""
+    bits = 0
+    while bits < 32 and (1 << bits) < tiles:
+        bits += 1
+    return (bits + 7) // 8
+
+
+def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: int,
+                  tile_passes: int):
+    """Algorithmic bytes (or FP32 ops) per launch of each kernel."""
+    n, nsel, S, K = scene.n, counts["n_selected"], counts["n_splats"], counts["n_duplicates"]
+    nfr = counts["n_frustum"]
+    kk = (scene.sh_degree + 1) ** 2 * 3 * 4
+    geo = 12 + 12 + 16 + 4
+    m = {
+        "temporal_compact": ("hbm", 8 * n + 4 * nsel),
+        "project": ("hbm", nsel * (4 + geo + 12) + 8 * nfr + n_kept_gaussians * (4 + kk)
+                    + S * (8 + 16 + 16 + 8 + 1 + 4)),
+        "sort_depth_pass0": ("hbm", S * (4 + 8)),
+        "sort_depth_pass1": ("hbm", S * 16),
+        "sort_depth_pass2": ("hbm", S * 16),
+        "sort_depth_pass3": ("hbm", S * 16),
+        "duplicate": ("hbm", S * (4 + 8 + 1) + K * 8),
+        "tile_ranges": ("hbm", K * 4 + tiles * 8),
+        "zero_splat_grads": ("hbm", S * 48),
+        "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + 2 * (geo + kk)) + S * 48),
+        "blend_fwd": ("alu", counts["n_blend_pairs"] * 22),
+    }
+    for p in range(tile_passes):
+        m[f"sort_tile_pass{p}"] = ("hbm", K * 16)
+    return m
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2503_08217_gb300 import binding, build
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer, pixel_count, tile_count
+
+    build.build()
+    binding.load()
+    torch.cuda.set_device(local)
+    dev_name = f"cuda:{local}"
+    scene, lod, desc = make_workload(args.workload, args.seed)
+    k = step_index(scene, rank)
+    cams = scene.cams[k]
+    n_views = len(cams)
+    P = pixel_count(cams)
+    dev = DeviceScene.from_host(scene, dev_name)
+    cs = dev.c_scene()
+    n = scene.n
+    max_splats = max(4096, int(n * min(n_views, 3)))
+    r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
+
+    # --- first-epoch sweep: Eq. 5 over all timesteps, then Eq. 6
+    vis = torch.empty((n, 2), device=dev_name)
+    life = torch.empty((n, 2), device=dev_name)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
+    all_vis = vis.clone()
+    bg = torch.zeros(3, device=dev_name)
+    sweep_t0 = time.time()
+    for kk in range(scene.n_steps):
+        iq = torch.from_numpy(scene.inst_quat[kk]).to(dev_name)
+        it = torch.from_numpy(scene.inst_trans[kk]).to(dev_name)
+        r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
+                     life, lod)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    torch.cuda.synchronize()
+    sweep_s = time.time() - sweep_t0
+    r.counts()  # clears any capacity flag raised while sweeping
+
+    iq = torch.from_numpy(scene.inst_quat[k]).to(dev_name)
+    it = torch.from_numpy(scene.inst_trans[k]).to(dev_name)
+    t = float(scene.times[k])
+    gen = torch.Generator(device=dev_name)
+    gen.manual_seed(1234 + rank)
+    target = torch.rand(3 * P, device=dev_name, generator=gen)
+    out = torch.empty(3 * P, device=dev_name)
+    dL = torch.empty(3 * P, device=dev_name)
+    loss = torch.zeros(1, device=dev_name)
+    grads = {"means": torch.zeros_like(dev.means), "log_scales": torch.zeros_like(dev.log_scales),
+             "quats": torch.zeros_like(dev.quats), "opacity_logits": torch.zeros_like(dev.opacity_logits),
+             "sh": torch.zeros_like(dev.sh), "inst_quat": torch.zeros_like(iq),
+             "inst_trans": torch.zeros_like(it)}
+
+    def step():
+        for g in grads.values():
+            g.zero_()
+        loss.zero_()
+        r.forward(dev, iq, it, cams, t, vis, life, lod, bg, out=out, c_scene=cs)
+        binding.l1_loss(out, target, dL, loss)
+        r.backward(dev, iq, it, bg, dL, grads, c_scene=cs)
+
+    step()
+    torch.cuda.synchronize()
+    r.sync_status()
+    counts = r.counts()
+    r.ws.set_timing(True)
+    graph = r.capture(step)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device=dev_name)
+
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    ktimes = {}
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.fill_(float(i))                     # L2 flush, outside the timed events
+            ev[i][0].record()
+            graph.replay()
+            ev[i][1].record()
+            torch.cuda.synchronize()
+            for name, ms in r.ws.kernel_times().items():
+                ktimes.setdefault(name, []).append(ms)
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev_name)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    r.ws.set_timing(False)
+    r.sync_status()
+    clock = clocks.summary()
+    ms_per_step = total_ms / args.steps
+    views_s = world * n_views * args.steps / (total_ms / 1e3)
+    mpix_s = world * P * args.steps / (total_ms / 1e3) / 1e6
+
+    # --- kernel table and roofline of the dominant kernel
+    keep = r.ws.debug("keep_mask", torch.int32, counts["n_selected"])
+    n_kept_g = int((keep != 0).sum().item())
+    kmean = {name: float(np.mean(v)) for name, v in ktimes.items()}
+    models = kernel_models(counts, scene, n_kept_g, P, tile_count(cams), tile_passes(tile_count(cams)))
+    hbm_peak, peak_kind, sm_max = measured_peaks()
+    alu_peak_gops = 152 * 128 * sm_max * 1e6 / 1e9     # FP32 lanes x clock, one op per lane-cycle
+    table = {}
+    for name, ms in sorted(kmean.items(), key=lambda kv: -kv[1]):
+        row = {"ms": round(ms, 4)}
+        if name in models and ms > 0:
+            bound, amount = models[name]
+            if bound == "hbm":
+                gbs = amount / (ms / 1e3) / 1e9
+                row.update(bound="hbm", bytes=int(amount), gbs=round(gbs, 1), frac=round(gbs / hbm_peak, 3))
+            else:
+                gops = amount / (ms / 1e3) / 1e9
+                row.update(bound="alu", ops=int(amount), gops=round(gops, 1),
+                           frac=round(gops / alu_peak_gops, 3))
+        table[name] = row
+    dom = max(kmean, key=kmean.get)
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+    if dom in models:
+        bound, amount = models[dom]
+        if bound == "hbm":
+            roof.update(bound="hbm", achieved=table[dom]["gbs"], peak=hbm_peak, unit="GB/s",
+                        frac=table[dom]["frac"], peak_source=f"{peak_kind} hbm_gbs")
+        else:
+            roof.update(bound="alu", achieved=table[dom]["gops"], peak=round(alu_peak_gops, 1),
+                        unit="Gop/s (FP32)", frac=table[dom]["frac"],
+                        peak_source="152 SMs x 128 FP32 lanes x max SM clock")
+    launches_per_step = len(kmean) + 1      # + the L1 loss kernel
+
+    # --- plain per-view comparator: the same library, one camera per call, eager
+    plain = None
+    if not args.no_plain:
+        r1 = Renderer(n, scene.n_inst, [max(cams, key=lambda c: c.width * c.height)],
+                      max_splats=max(4096, n), max_duplicates=min(2**31 - 1, 6 * max(4096, n)))
+        offs = np.cumsum([0] + [3 * c.width * c.height for c in cams])
+
+        def plain_sweep():
+            for g in grads.values():
+                g.zero_()
+            for v, cam in enumerate(cams):
+                o = out[offs[v]:offs[v + 1]]
+                d = dL[offs[v]:offs[v + 1]]
+                loss.zero_()
+                r1.forward(dev, iq, it, [cam], t, vis, life, lod, bg, out=o, c_scene=cs)
+                binding.l1_loss(o, target[offs[v]:offs[v + 1]], d, loss)
+                r1.backward(dev, iq, it, bg, d, grads, c_scene=cs)
+
+        for _ in range(max(1, args.warmup)):
+            plain_sweep()
+        torch.cuda.synchronize()
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            pev[i][0].record()
+            plain_sweep()
+            pev[i][1].record()
+        torch.cuda.synchronize()
+        r1.sync_status()
+        pms = float(np.mean([a.elapsed_time(b) for a, b in pev]))
+        plain = {"value": round(n_views / (pms / 1e3), 3), "unit": "views/s", "ms_per_step": round(pms, 3),
+                 "batched_speedup": round(pms / ms_per_step, 3),
+                 "how": "one camera per project/sort/render_fwd/l1/render_bwd sequence, eager launches, no graph"}
+        del r1
+
+    # --- end to end through the public API, host buffers in the timed region
+    e2e = None
+    if not args.no_e2e:
+        tgt_host = target.cpu().pin_memory()
+        iq_host = iq.cpu().pin_memory()
+        it_host = it.cpu().pin_memory()
+        loss_host = torch.zeros(1).pin_memory()
+        st = torch.cuda.current_stream()
+        for _ in range(2):
+            target.copy_(tgt_host, non_blocking=True)
+            graph.replay()
+            loss_host.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(args.steps):
+            target.copy_(tgt_host, non_blocking=True)
+            iq.copy_(iq_host, non_blocking=True)
+            it.copy_(it_host, non_blocking=True)
+            graph.replay()
+            loss_host.copy_(loss, non_blocking=True)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            tt = torch.tensor([ems], device=dev_name)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ems = float(tt.item())
+        bi = tgt_host.numel() * 4 + iq_host.numel() * 4 + it_host.numel() * 4
+        e2e = {"value": round(world * n_views / (ems / 1e3), 3), "unit": "views/s",
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": 4, "ms_per_step": round(ems, 3)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_sample(scene, k, lod, vis.cpu().numpy())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(views_s, 3), "unit": "views/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}", "gaussians": n, "instances": scene.n_inst,
+                       "cameras": n_views, "pixels_per_view_batch": P, "timestep": k,
+                       "sh_degree": scene.sh_degree, "lod_px": lod,
+                       "l2": "flushed (512 MiB write) between timed steps, outside the timed events",
+                       "graph": "whole step captured as one CUDA graph",
+                       "parallelism": f"replicas x{world}, one timestep per rank, no collective"},
+            "mpix_per_s": round(mpix_s, 3),
+            "plain_per_view": plain,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clock,
+            "kernels": table,
+            "counts": {k2: int(v) for k2, v in counts.items()},
+            "visibility_sweep_s": round(sweep_s, 3),
+            "workspace_gb": round(r.ws.nbytes / 1e9, 3),
+        }
+        print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_sample(scene, k, lod, vis_np):
+    """The FP64 oracle, as it stands, on a bounded sample of the same
+    workload: one camera (the smallest of the rig) at the same timestep over
+    the full scene, forward (tiled blend) and backward."""
+    import oracle
+    cams = scene.cams[k]
+    cam = min(cams, key=lambda c: c.width * c.height)
+    t0 = time.time()
+    f = oracle.step_forward(scene, k, vis_np, None, lod, cams=[cam], tiled=True)
+    rng = np.random.default_rng(0)
+    dL = [rng.standard_normal((3, cam.height, cam.width))]
+    oracle.step_backward(scene, k, f, dL, lod, cams=[cam])
+    dt = time.time() - t0
+    return {"value": round(1.0 / dt, 5), "unit": "views/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"1 view ({cam.width}x{cam.height}) of the same workload and timestep, fwd+bwd, "
+                      f"full scene; {dt:.1f} s"}
+
+
+def run_reference(args, rank, world, local):
+    """The FP64 CPU oracle on this host's cores, each step a bounded sample
+    of the workload (one camera, same timestep, full scene)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    scene, lod, desc = make_workload(args.workload, args.seed)
+    k = step_index(scene, 0)
+    vis, _ = oracle.vis_reset(scene.n)
+    cams = scene.cams[k]
+    cam = min(cams, key=lambda c: c.width * c.height)
+    rng = np.random.default_rng(0)
+    dL = [rng.standard_normal((3, cam.height, cam.width))]
+
+    def one():
+        f = oracle.step_forward(scene, k, vis, None, lod, cams=[cam], tiled=True)
+        oracle.step_backward(scene, k, f, dL, lod, cams=[cam])
+
+    budget = 150.0
+    t_first = time.time()
+    one()
+    per = time.time() - t_first
+    steps = max(1, min(args.steps, int(budget / max(per, 1e-3))))
+    warm = min(args.warmup, max(0, int(30.0 / max(per, 1e-3))))
+    for _ in range(warm):
+        one()
+    t0 = time.time()
+    for _ in range(steps):
+        one()
+    dt = (time.time() - t0) / steps
+    v = 1.0 / dt
+    sample = (f"1 view ({cam.width}x{cam.height}) of the {args.workload} workload at timestep {k}, "
+              f"full scene, fwd (tiled blend) + bwd per step; {steps} timed steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "views/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": round(dt * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "timestep": k},
+        "cpu_baseline": {"value": round(v, 5), "unit": "views/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 5), "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

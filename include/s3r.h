@@ -1,0 +1,270 @@
+/*
+ * s3r.h -- C ABI of the GB300 (sm_103a) S3R-GS render-and-backprop hot path.
+ *
+ * One timestep of the streamlined pipeline of S3R-GS (Sec. 3.3, "Streamlined
+ * Reconstruction Stage"):
+ *   1. temporal selection of the Gaussians whose visibility window contains t
+ *      (Sec. 3.3, "Temporal separation");
+ *   2. projection of each selected Gaussian straight into every camera through
+ *      one composed matrix per instance, W_{t,i} = W_t W_{t,i2g} (Sec. 3.3,
+ *      "Instance-specific projection"), with the EWA 2D covariance of Eq. 1;
+ *   3. the frustum mask M_t and the point-life update of Eq. 5;
+ *   4. the adaptive-LOD cull of Gaussians whose 2D scale is below r
+ *      (Sec. 3.3, "Adaptive LOD", deterministic threshold form);
+ *   5. SH colour, tile|depth key duplication, radix sort, and 16x16-tile
+ *      front-to-back alpha blending (Eq. 2);
+ *   6. the exact gradient of the images w.r.t. all Gaussian parameters and the
+ *      per-instance poses (the training step the paper's reconstruction runs);
+ *   7. Eq. 6 and the periodic reset of the visibility record.
+ *
+ * Conventions (every entry point):
+ *   - All array arguments are DEVICE pointers on the workspace's device,
+ *     caller-owned, FP32/uint32/int64 as stated, C-contiguous, and 16-byte
+ *     aligned where a 128-bit load is used (marked "16-B"). A misaligned or
+ *     null required pointer returns S3R_ERR_INVALID and launches nothing.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream). They perform no host synchronisation
+ *     and allocate nothing, so a sequence of them can be captured into a CUDA
+ *     graph. Only s3r_workspace_create/destroy allocate and free, and only
+ *     s3r_query_counts / s3r_sync_status synchronise.
+ *   - Data-dependent sizes (selected Gaussians, splats, duplicates) stay on
+ *     the device; every kernel reads its own extent from there.
+ *   - Device-side failures (a capacity overflow, an exhausted spin budget) are
+ *     latched into a status word in the workspace; the work that overflowed is
+ *     dropped, never written out of bounds. The next s3r_sync_status (or
+ *     s3r_query_counts) returns S3R_ERR_CAPACITY / S3R_ERR_TIMEOUT and clears it.
+ *   - Nothing aborts. s3r_last_error() returns a thread-local message for the
+ *     most recent non-OK status of the calling thread.
+ *
+ * Camera model: OpenCV pinhole (x right, y down, z forward). Pixel (x, y) is
+ * sampled at (x + 0.5, y + 0.5). Tiles are 16x16 pixels. Gaussian i of
+ * segment k (k = 0 static, k >= 1 instance k) is expressed in that segment's
+ * local frame; instance k's pose at time t maps local to world coordinates.
+ */
+#ifndef S3R_H_
+#define S3R_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  S3R_OK = 0,
+  S3R_ERR_INVALID = 1,   /* bad argument: null, misaligned, out of range */
+  S3R_ERR_CAPACITY = 2,  /* a device count exceeded the workspace capacity */
+  S3R_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  S3R_ERR_TIMEOUT = 4,   /* a bounded device-side wait gave up */
+  S3R_ERR_STATE = 5      /* calls out of order (e.g. sort before project) */
+} s3r_status;
+
+#define S3R_MAX_VIEWS 32
+#define S3R_TILE 16
+
+/* Pinhole camera. world_to_cam is the 3x4 row-major matrix [R | t] of the
+ * world-to-camera transform W_t (Eq. 1). near_z <= 0 means 0.2. */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy, near_z;
+  float world_to_cam[12];
+} s3r_camera;
+
+/* The Gaussians (Sec. 3.3: position, covariance as scale + rotation, opacity;
+ * colour as SH coefficients). Device pointers, all of length n along dim 0:
+ *   means          [n,3]  FP32
+ *   log_scales     [n,3]  FP32  (scale = exp(log_scale))
+ *   quats          [n,4]  FP32  (w, x, y, z), any norm > 0; 16-B
+ *   opacity_logits [n]    FP32  (opacity = sigmoid(logit))
+ *   sh             [n,K,3] FP32, K = (sh_degree+1)^2; 16-B
+ *   inst_offsets   [n_inst+2] int64: segment k covers [off[k], off[k+1]),
+ *                  off[0] = 0, off[n_inst+1] = n; segment 0 is static.
+ * The library never writes these. */
+typedef struct {
+  int64_t n;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  int32_t sh_degree;
+  const int64_t* inst_offsets;
+  int32_t n_inst;
+} s3r_scene;
+
+/* Per-instance pose at time t, the W_{t,i2g} of Sec. 3.3 (local -> world):
+ * rotation R(q/|q|) and translation. Device pointers [n_inst,4] (16-B) and
+ * [n_inst,3]. */
+typedef struct {
+  const float* quat;
+  const float* trans;
+} s3r_poses;
+
+/* Gradient outputs, ACCUMULATED (+=) into caller-zeroed device buffers with
+ * the layouts of s3r_scene / s3r_poses. Any pointer may be NULL to skip it
+ * (its work is still done where other outputs need it). */
+typedef struct {
+  float* means;           /* [n,3] */
+  float* log_scales;      /* [n,3] */
+  float* quats;           /* [n,4] */
+  float* opacity_logits;  /* [n]   */
+  float* sh;              /* [n,K,3] */
+  float* inst_quat;       /* [n_inst,4] */
+  float* inst_trans;      /* [n_inst,3] */
+} s3r_grads;
+
+typedef struct {
+  int64_t max_gaussians;   /* n of the largest scene */
+  int64_t max_splats;      /* kept (Gaussian, view) pairs per call */
+  int64_t max_duplicates;  /* (tile, splat) pairs per call, < 2^31 */
+  int32_t max_views;       /* cameras per call, <= S3R_MAX_VIEWS */
+  int32_t max_instances;   /* dynamic instances (static segment not counted) */
+  int64_t max_tiles;       /* 16x16 tiles summed over the cameras of a call */
+  int64_t max_pixels;      /* pixels summed over the cameras of a call */
+} s3r_capacity;
+
+typedef struct {
+  int64_t n_selected;      /* Gaussians whose window contains t */
+  int64_t n_splats;        /* kept (Gaussian, view) pairs */
+  int64_t n_duplicates;    /* (tile, splat) pairs */
+  int64_t n_frustum;       /* selected Gaussians inside at least one frustum */
+  int64_t n_blend_pairs;   /* (pixel, splat) pairs the last forward blend evaluated */
+  uint32_t device_status;  /* latched bits: 1 capacity, 2 timeout */
+} s3r_counts;
+
+typedef struct s3r_workspace s3r_workspace;
+
+/* Allocate a workspace for the given capacities on `device` (the current
+ * device is restored afterwards). The workspace owns every intermediate of a
+ * call sequence: the selected index list, the projected splats, keys, tile
+ * ranges, the final transmittance and contributor counts of each pixel, and
+ * per-splat gradients. Returns S3R_ERR_CUDA if the allocation fails. */
+s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspace** out);
+s3r_status s3r_workspace_destroy(s3r_workspace* ws);
+/* Bytes of device memory held by the workspace. */
+int64_t s3r_workspace_bytes(const s3r_workspace* ws);
+
+/*
+ * Steps 1-4 + colour for one timestep over n_views cameras (Sec. 3.3).
+ *   cams        HOST array [n_views] (copied into kernel parameters).
+ *   t           normalised rendering time in [-1, 1] (Sec. 3.3).
+ *   vis_window  [n,2] FP32 (v_s, v_e); selected iff v_s <= t <= v_e (FP32).
+ *   point_life  [n,2] FP32 (l_s, l_e), updated in place by Eq. 5 for every
+ *               selected Gaussian inside at least one camera's frustum
+ *               (M_t, before the LOD cull); NULL skips the update.
+ *   lod_threshold  r in pixels: a Gaussian is culled from a view iff the
+ *               square root of the largest eigenvalue of its 2D covariance
+ *               (before the 0.3 px^2 dilation) is < r. r <= 0 culls nothing.
+ * Writes only workspace state. Sizes: n <= max_gaussians, n_views <=
+ * max_views, n_inst <= max_instances, tiles/pixels within capacity. */
+s3r_status s3r_project(s3r_workspace* ws, const s3r_scene* scene, const s3r_poses* poses,
+                       const s3r_camera* cams, int32_t n_views, float t,
+                       const float* vis_window, float* point_life, float lod_threshold,
+                       void* stream);
+
+/* Step 5a: duplicate every kept splat into one (tile, splat) pair per 16x16
+ * tile its 3-sigma rectangle touches, and sort the pairs by the 64-bit key
+ * (view-tile id << 32 | FP32 depth bits), stably in projection order (a
+ * least-significant-digit radix sort: the depth digits run on the splats
+ * before duplication, the tile digits on the pairs). Then the [start, end)
+ * range of every tile. Reads and writes workspace state only. */
+s3r_status s3r_sort(s3r_workspace* ws, void* stream);
+
+/* Step 5b: front-to-back alpha blending of every tile (Eq. 2) with the 3DGS
+ * thresholds (alpha = min(0.99, o G), skipped below 1/255, stop before T
+ * would fall under 1e-4).
+ *   background  [3] FP32 composited with the final transmittance.
+ *   out_rgb     [sum_v 3*H_v*W_v] FP32: view v's planar [3,H_v,W_v] image
+ *               at offset 3 * (sum of the pixel counts of views < v).
+ * Keeps the final T and the contributor count of each pixel for the
+ * backward pass. */
+s3r_status s3r_render_fwd(s3r_workspace* ws, const float* background, float* out_rgb, void* stream);
+
+/* Step 6: gradient of sum(dL_drgb * rgb) w.r.t. all parameters and poses.
+ * Must follow s3r_render_fwd on the same workspace with the same scene and
+ * poses. Walks each tile back to front from its stored final transmittance
+ * (no per-pixel lists), reduces per warp before global atomics, then chains
+ * the 2D gradients through Eq. 1 to the parameters and through the composed
+ * matrices W_t W_{t,i2g} to every instance pose.
+ *   dL_drgb     same layout as out_rgb.
+ *   grads       accumulated (+=).
+ * Adjoints of clamped quantities (alpha at 0.99, the x/z and y/z clamp of the
+ * Jacobian, negative colours) are zero, as in the exact derivative. */
+s3r_status s3r_render_bwd(s3r_workspace* ws, const s3r_scene* scene, const s3r_poses* poses,
+                          const float* background, const float* dL_drgb,
+                          const s3r_grads* grads, void* stream);
+
+enum {
+  S3R_VIS_RECORD = 0,    /* Eq. 5 on the Gaussians whose mask bit is set */
+  S3R_VIS_FINALIZE = 1,  /* Eq. 6: v = (l_s - 0.1, l_e + 0.1), FP32 */
+  S3R_VIS_RESET = 2      /* v = (-1, 1), l = (1, -1): visible at all times */
+};
+
+/* The temporal-visibility record (Sec. 3.3, Eqs. 5-6) over n Gaussians.
+ *   mask        RECORD only: [ceil(n/32)] uint32 bitmask, bit i = M_t[i].
+ *   point_life  [n,2] FP32 (l_s, l_e); vis_window [n,2] FP32 (v_s, v_e).
+ * RECORD updates point_life; FINALIZE writes vis_window from point_life;
+ * RESET writes both (new Gaussians appended at the end are reset by passing
+ * pointers offset to their first index). */
+s3r_status s3r_update_visibility(int64_t n, float t, const uint32_t* mask, float* point_life,
+                                 float* vis_window, int32_t mode, void* stream);
+
+/* Photometric L1 loss of a rendered batch (the paper does not state its
+ * loss; this is the plain mean absolute error a training step can use):
+ *   loss = sum |pred - target| / n   (added to *loss_out, one FP32 scalar)
+ *   dL_dpred[i] = sign(pred[i] - target[i]) / n   (written)
+ * pred, target, dL_dpred: [n] FP32 device arrays; loss_out: device FP32. */
+s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float* dL_dpred,
+                       float* loss_out, void* stream);
+
+/* Per-kernel device timing (tracing). With timing enabled, every kernel the
+ * workspace's calls launch is bracketed by a pair of CUDA events owned by the
+ * workspace (recorded on the caller's stream, so this also works inside a
+ * captured CUDA graph). After the stream has been synchronised,
+ * s3r_kernel_times writes the duration in milliseconds of the most recent
+ * launch of each kernel id into ms[0..n) (-1 where it never ran).
+ * s3r_kernel_name gives the name of an id in [0, s3r_kernel_count()). */
+s3r_status s3r_set_timing(s3r_workspace* ws, int32_t enable);
+int32_t s3r_kernel_count(void);
+const char* s3r_kernel_name(int32_t id);
+s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n);
+
+/* Synchronise `stream`, then return the device counts of the last call
+ * sequence and the latched device status (which it clears). Tests and logs
+ * only. */
+s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out);
+/* Synchronise `stream` and convert the latched device status into a return
+ * value (S3R_ERR_CAPACITY / S3R_ERR_TIMEOUT), clearing it. */
+s3r_status s3r_sync_status(s3r_workspace* ws, void* stream);
+
+/* Read-only views of workspace intermediates, for tests and tools (device
+ * pointers, valid until the next s3r_project on the workspace).
+ *   name: "selected" u32[n_selected] ascending Gaussian ids;
+ *         "frustum_mask" u32[n_selected] bit v = inside camera v's frustum;
+ *         "keep_mask" u32[n_selected] bit v = kept (frustum and LOD) in v;
+ *         "splat_start" u32[n_selected] first splat of each selected Gaussian;
+ *         "splat_xy" float2[n_splats]; "splat_conic_opacity" float4;
+ *         "splat_rgb_depth" float4; "splat_rect" uint2 (x0|y0<<16, x1|y1<<16,
+ *         tiles, half-open); "splat_view" uint8;
+ *         "sorted_splats" u32[n_duplicates] splat id per pair in key order;
+ *         "sorted_tiles" u32[n_duplicates] view-tile id per pair;
+ *         "tile_ranges" uint2[tiles]; "final_T" float[pixels];
+ *         "n_contrib" u32[pixels]; "splat_grads" float[n_splats*12]
+ *         (du, dv, dA, dB, dC, dopacity, dr, dg, db, 0, 0, 0);
+ *         "pose_grad_matrix" float[n_views*(n_inst+1)*12] dL/dW_{t,i}.
+ * Returns NULL for an unknown name. */
+const void* s3r_debug_buffer(const s3r_workspace* ws, const char* name);
+
+/* Thread-local message of the last non-OK status returned on this thread. */
+const char* s3r_last_error(void);
+
+/* Library version and the compute capability it was built for (e.g. 103). */
+int32_t s3r_version(void);
+int32_t s3r_built_arch(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S3R_H_ */

@@ -1,0 +1,486 @@
+// Backward of the instance-specific projection (Eq. 1 through the composed
+// matrices W_t W_{t,i2g} of Sec. 3.3) and of the SH colour: from the per-splat
+// 2D adjoints written by the blend backward to the Gaussian parameters and to
+// every instance pose.
+//
+// One thread per selected Gaussian loops over its kept views (its splats are
+// contiguous), recomputes the forward intermediates of each view, and
+// accumulates the parameter adjoints in registers; the owning thread then adds
+// them to the caller's buffers (no atomics: a Gaussian has one thread).
+// Adjoints of the composed 3x4 matrices are summed per (view, instance) in
+// shared memory and flushed once per CTA; a tiny kernel then maps them to the
+// pose: dP = V_rot^T dW, and through R(q) to (dq, dt).
+#include "s3r_math.cuh"
+
+namespace s3r {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct BwdArgs {
+  const float* means;
+  const float* log_scales;
+  const float4* quats;
+  const float* opac_logits;
+  const float4* sh;
+  const float* sh_f;
+  const int64_t* inst_off;
+  int n_inst;
+  const float4* pose_q;
+  const float* pose_t;
+  const uint32_t* selected;
+  const uint32_t* keep_mask;
+  const uint32_t* splat_start;
+  const float4* sp_grad;   // [S][3] float4
+  int64_t cap_splats;
+  uint32_t* ctr;
+  float* pose_dM;          // [n_views][n_inst+1][12]
+  s3r_grads g;
+};
+
+// d/d(direction) of sum_k w_k Y_k(d) for the real SH basis of sh_basis<DEG>.
+template <int DEG>
+__device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const float w[16],
+                                            float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if (DEG >= 1) {
+    const float k1 = 0.48860251190291992f;
+    g[1] -= k1 * w[1];
+    g[2] += k1 * w[2];
+    g[0] -= k1 * w[3];
+  }
+  if (DEG >= 2) {
+    const float k2a = 1.0925484305920792f, k2c = 0.31539156525252005f, k2e = 0.54627421529603959f;
+    g[0] += k2a * y * w[4];                    g[1] += k2a * x * w[4];
+    g[1] -= k2a * z * w[5];                    g[2] -= k2a * y * w[5];
+    g[0] -= 2.f * k2c * x * w[6];              g[1] -= 2.f * k2c * y * w[6];
+    g[2] += 4.f * k2c * z * w[6];
+    g[0] -= k2a * z * w[7];                    g[2] -= k2a * x * w[7];
+    g[0] += 2.f * k2e * x * w[8];              g[1] -= 2.f * k2e * y * w[8];
+    if (DEG >= 3) {
+      const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f,
+                  k3c = 0.45704579946446572f, k3d = 0.37317633259011546f,
+                  k3e = 1.4453057213202769f;
+      const float xx = x * x, yy = y * y, zz = z * z;
+      g[0] -= 6.f * k3a * x * y * w[9];
+      g[1] -= k3a * (3.f * xx - 3.f * yy) * w[9];
+      g[0] += k3b * y * z * w[10]; g[1] += k3b * x * z * w[10]; g[2] += k3b * x * y * w[10];
+      g[0] += 2.f * k3c * x * y * w[11];
+      g[1] -= k3c * (4.f * zz - xx - 3.f * yy) * w[11];
+      g[2] -= 8.f * k3c * y * z * w[11];
+      g[0] -= 6.f * k3d * x * z * w[12];
+      g[1] -= 6.f * k3d * y * z * w[12];
+      g[2] += k3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      g[0] -= k3c * (4.f * zz - 3.f * xx - yy) * w[13];
+      g[1] += 2.f * k3c * x * y * w[13];
+      g[2] -= 8.f * k3c * x * z * w[13];
+      g[0] += 2.f * k3e * x * z * w[14];
+      g[1] -= 2.f * k3e * y * z * w[14];
+      g[2] += k3e * (xx - yy) * w[14];
+      g[0] -= k3a * (3.f * xx - 3.f * yy) * w[15];
+      g[1] += 6.f * k3a * x * y * w[15];
+    }
+  }
+}
+
+// Adjoint of the raw quaternion q (w, x, y, z) given dL/dR for R(q/|q|).
+__device__ __forceinline__ float4 quat_backward(float4 q, const float dR[9]) {
+  const float n2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  const float inv = rsqrtf(n2);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  // partials of the nine entries of R w.r.t. the unit quaternion
+  float gw = 2.f * (x * (dR[7] - dR[5]) + y * (dR[2] - dR[6]) + z * (dR[3] - dR[1]));
+  float gx = 2.f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5])) -
+             4.f * x * (dR[4] + dR[8]);
+  float gy = 2.f * (x * (dR[1] + dR[3]) + z * (dR[5] + dR[7]) + w * (dR[2] - dR[6])) -
+             4.f * y * (dR[0] + dR[8]);
+  float gz = 2.f * (x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) + w * (dR[3] - dR[1])) -
+             4.f * z * (dR[0] + dR[4]);
+  const float dot = gw * w + gx * x + gy * y + gz * z;
+  return make_float4((gw - w * dot) * inv, (gx - x * dot) * inv, (gy - y * dot) * inv,
+                     (gz - z * dot) * inv);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(kThreads) k_project_bwd(const __grid_constant__ ViewSet vs,
+                                                          BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nk = a.n_inst + 1;
+  InstMat* mats = reinterpret_cast<InstMat*>(smem_raw);
+  float* s_dM = reinterpret_cast<float*>(mats + vs.n_views * nk);      // [views][nk][12]
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dM + vs.n_views * nk * 12);
+  __shared__ uint32_t s_tile;
+  constexpr int K = sh_count(DEG);
+
+  compose_all(vs, a.pose_q, a.pose_t, a.n_inst, mats);
+  for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) s_dM[i] = 0.f;
+  for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
+  __syncthreads();
+
+  const uint32_t n_sel = a.ctr[kCtrSelected];
+  const int64_t n_tiles = ((int64_t)n_sel + kThreads - 1) / kThreads;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageProjectBwd, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    __syncthreads();
+    if (tile >= n_tiles) break;
+    const int64_t j = tile * kThreads + threadIdx.x;
+    if (j >= (int64_t)n_sel) continue;
+    const uint32_t kmask = a.keep_mask[j];
+    if (!kmask) continue;
+    const uint32_t gid = a.selected[j];
+    const int k = segment_of(s_off, a.n_inst, gid);
+    uint32_t s = a.splat_start[j];
+
+    const float mu[3] = {a.means[3 * (size_t)gid], a.means[3 * (size_t)gid + 1],
+                         a.means[3 * (size_t)gid + 2]};
+    const float sc[3] = {__expf(a.log_scales[3 * (size_t)gid]),
+                         __expf(a.log_scales[3 * (size_t)gid + 1]),
+                         __expf(a.log_scales[3 * (size_t)gid + 2])};
+    const float4 q = a.quats[gid];
+    float R[9], RS[9];
+    quat_to_rot(q, R);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) RS[3 * r + c] = R[3 * r + c] * sc[c];
+    const float opac = 1.f / (1.f + __expf(-a.opac_logits[gid]));
+    float sh[K * 3];
+    if constexpr ((K * 3) % 4 == 0) {
+      const float4* src = a.sh + (size_t)gid * (K * 3 / 4);
+#pragma unroll
+      for (int i = 0; i < K * 3 / 4; ++i) {
+        const float4 v4 = __ldg(src + i);
+        sh[4 * i] = v4.x; sh[4 * i + 1] = v4.y; sh[4 * i + 2] = v4.z; sh[4 * i + 3] = v4.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < K * 3; ++i) sh[i] = __ldg(a.sh_f + (size_t)gid * K * 3 + i);
+    }
+
+    float g_mu[3] = {0.f, 0.f, 0.f}, g_RS[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g_RS[i] = 0.f;
+    float g_ol = 0.f;
+    float g_sh[K * 3];
+#pragma unroll
+    for (int i = 0; i < K * 3; ++i) g_sh[i] = 0.f;
+
+    uint32_t m = kmask;
+    while (m) {
+      const int v = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t si = s++;
+      if (si >= a.cap_splats) break;
+      const float4 ga = a.sp_grad[3 * si], gb = a.sp_grad[3 * si + 1], gc = a.sp_grad[3 * si + 2];
+      const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gO = gb.y;
+      const float grgb[3] = {gb.z, gb.w, gc.x};
+      const InstMat& M = mats[v * nk + k];
+      const ViewInfo& vi = vs.v[v];
+      const float* A = M.m;   // rows at 0, 4, 8; translation at 3, 7, 11
+
+      // ---- forward recompute (the same arithmetic as project_view)
+      const float x = fmaf(A[0], mu[0], fmaf(A[1], mu[1], fmaf(A[2], mu[2], A[3])));
+      const float y = fmaf(A[4], mu[0], fmaf(A[5], mu[1], fmaf(A[6], mu[2], A[7])));
+      const float z = fmaf(A[8], mu[0], fmaf(A[9], mu[1], fmaf(A[10], mu[2], A[11])));
+      float B[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          B[3 * r + c] = fmaf(A[4 * r], RS[c], fmaf(A[4 * r + 1], RS[3 + c], A[4 * r + 2] * RS[6 + c]));
+      const float iz = 1.f / z;
+      const float rx = x * iz, ry = y * iz;
+      const bool clx = rx < -vi.limx || rx > vi.limx;
+      const bool cly = ry < -vi.limy || ry > vi.limy;
+      const float txr = fminf(vi.limx, fmaxf(-vi.limx, rx));
+      const float tyr = fminf(vi.limy, fmaxf(-vi.limy, ry));
+      const float j00 = vi.fx * iz, j02 = -vi.fx * txr * iz;
+      const float j11 = vi.fy * iz, j12 = -vi.fy * tyr * iz;
+      float C0[3], C1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        C0[c] = fmaf(j00, B[c], j02 * B[6 + c]);
+        C1[c] = fmaf(j11, B[3 + c], j12 * B[6 + c]);
+      }
+      const float sa = fmaf(C0[0], C0[0], fmaf(C0[1], C0[1], C0[2] * C0[2]));
+      const float sb = fmaf(C0[0], C1[0], fmaf(C0[1], C1[1], C0[2] * C1[2]));
+      const float scc = fmaf(C1[0], C1[0], fmaf(C1[1], C1[1], C1[2] * C1[2]));
+      const float ad = sa + kDilation, cd = scc + kDilation;
+      const float idet = 1.f / (ad * cd - sb * sb);
+      const float qa = cd * idet, qb = -sb * idet, qc = ad * idet;
+
+      float dA[9], db[3], dp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dA[i] = 0.f;
+      db[0] = db[1] = db[2] = 0.f;
+
+      // ---- opacity = sigmoid(logit)
+      g_ol += gO * opac * (1.f - opac);
+
+      // ---- colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir from the camera centre
+      {
+        const float vx = mu[0] - M.c[0], vy = mu[1] - M.c[1], vz = mu[2] - M.c[2];
+        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
+        float Y[16];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float graw[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float acc = 0.5f;
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc = fmaf(sh[3 * i + ch], Y[i], acc);
+          graw[ch] = acc < 0.f ? 0.f : grgb[ch];
+        }
+        float wk[16];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          g_sh[3 * i] += Y[i] * graw[0];
+          g_sh[3 * i + 1] += Y[i] * graw[1];
+          g_sh[3 * i + 2] += Y[i] * graw[2];
+          wk[i] = sh[3 * i] * graw[0] + sh[3 * i + 1] * graw[1] + sh[3 * i + 2] * graw[2];
+        }
+        if (DEG > 0) {
+          float gd[3];
+          sh_dir_grad<DEG>(dx, dy, dz, wk, gd);
+          const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+          const float gv3[3] = {(gd[0] - dx * dd) * inv, (gd[1] - dy * dd) * inv,
+                                (gd[2] - dz * dd) * inv};
+          g_mu[0] += gv3[0]; g_mu[1] += gv3[1]; g_mu[2] += gv3[2];
+          // camera centre c = -A^{-1} b with gc = -gv3: dA = (A gv3) c^T, db = A gv3
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float t = A[4 * r] * gv3[0] + A[4 * r + 1] * gv3[1] + A[4 * r + 2] * gv3[2];
+            dA[3 * r] += t * M.c[0]; dA[3 * r + 1] += t * M.c[1]; dA[3 * r + 2] += t * M.c[2];
+            db[r] += t;
+          }
+        }
+      }
+
+      // ---- conic = inverse of the dilated 2D covariance
+      const float hb = 0.5f * gB;
+      const float m00 = qa * gA + qb * hb, m01 = qa * hb + qb * gC;
+      const float m10 = qb * gA + qc * hb, m11 = qb * hb + qc * gC;
+      const float g_a = -(m00 * qa + m01 * qb);
+      const float g_b = -2.f * (m00 * qb + m01 * qc);
+      const float g_c = -(m10 * qb + m11 * qc);
+      // ---- Sigma2 = C C^T
+      float dC0[3], dC1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dC0[c] = 2.f * g_a * C0[c] + g_b * C1[c];
+        dC1[c] = 2.f * g_c * C1[c] + g_b * C0[c];
+      }
+      // ---- C = J B
+      const float dj00 = dC0[0] * B[0] + dC0[1] * B[1] + dC0[2] * B[2];
+      const float dj02 = dC0[0] * B[6] + dC0[1] * B[7] + dC0[2] * B[8];
+      const float dj11 = dC1[0] * B[3] + dC1[1] * B[4] + dC1[2] * B[5];
+      const float dj12 = dC1[0] * B[6] + dC1[1] * B[7] + dC1[2] * B[8];
+      float dB[9];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dB[c] = j00 * dC0[c];
+        dB[3 + c] = j11 * dC1[c];
+        dB[6 + c] = j02 * dC0[c] + j12 * dC1[c];
+      }
+      // ---- B = A RS
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          dA[3 * r + c] += dB[3 * r] * RS[3 * c] + dB[3 * r + 1] * RS[3 * c + 1] + dB[3 * r + 2] * RS[3 * c + 2];
+          g_RS[3 * r + c] += A[r] * dB[c] + A[4 + r] * dB[3 + c] + A[8 + r] * dB[6 + c];
+        }
+      // ---- J(p), with the field-of-view clamp
+      dp[2] -= (dj00 * j00 + dj11 * j11) * iz;
+      if (!clx) {
+        dp[0] -= dj02 * vi.fx * iz * iz;
+        dp[2] -= 2.f * dj02 * j02 * iz;
+      } else {
+        dp[2] -= dj02 * j02 * iz;
+      }
+      if (!cly) {
+        dp[1] -= dj12 * vi.fy * iz * iz;
+        dp[2] -= 2.f * dj12 * j12 * iz;
+      } else {
+        dp[2] -= dj12 * j12 * iz;
+      }
+      // ---- (u, v) = (fx x/z + cx, fy y/z + cy)
+      dp[0] += gu * vi.fx * iz;
+      dp[1] += gv * vi.fy * iz;
+      dp[2] -= (gu * vi.fx * rx + gv * vi.fy * ry) * iz;
+      // ---- p = A mu + b
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g_mu[c] += A[c] * dp[0] + A[4 + c] * dp[1] + A[8 + c] * dp[2];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        dA[3 * r] += dp[r] * mu[0]; dA[3 * r + 1] += dp[r] * mu[1]; dA[3 * r + 2] += dp[r] * mu[2];
+        db[r] += dp[r];
+      }
+      if (k > 0) {
+        float* dst = s_dM + (v * nk + k) * 12;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          atomicAdd(dst + 4 * r, dA[3 * r]);
+          atomicAdd(dst + 4 * r + 1, dA[3 * r + 1]);
+          atomicAdd(dst + 4 * r + 2, dA[3 * r + 2]);
+          atomicAdd(dst + 4 * r + 3, db[r]);
+        }
+      }
+    }
+
+    // ---- RS = R diag(s), s = exp(log s), R = R(q/|q|)
+    float dR[9], g_ls[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      g_ls[c] = (R[c] * g_RS[c] + R[3 + c] * g_RS[3 + c] + R[6 + c] * g_RS[6 + c]) * sc[c];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) dR[3 * r + c] = g_RS[3 * r + c] * sc[c];
+    }
+    const float4 g_q = quat_backward(q, dR);
+
+    if (a.g.means) {
+      float* p = a.g.means + 3 * (size_t)gid;
+      p[0] += g_mu[0]; p[1] += g_mu[1]; p[2] += g_mu[2];
+    }
+    if (a.g.log_scales) {
+      float* p = a.g.log_scales + 3 * (size_t)gid;
+      p[0] += g_ls[0]; p[1] += g_ls[1]; p[2] += g_ls[2];
+    }
+    if (a.g.quats) {
+      float4* p = reinterpret_cast<float4*>(a.g.quats) + gid;
+      float4 o = *p;
+      o.x += g_q.x; o.y += g_q.y; o.z += g_q.z; o.w += g_q.w;
+      *p = o;
+    }
+    if (a.g.opacity_logits) a.g.opacity_logits[gid] += g_ol;
+    if (a.g.sh) {
+      if constexpr ((K * 3) % 4 == 0) {
+        float4* p = reinterpret_cast<float4*>(a.g.sh) + (size_t)gid * (K * 3 / 4);
+#pragma unroll
+        for (int i = 0; i < K * 3 / 4; ++i) {
+          float4 o = p[i];
+          o.x += g_sh[4 * i]; o.y += g_sh[4 * i + 1]; o.z += g_sh[4 * i + 2]; o.w += g_sh[4 * i + 3];
+          p[i] = o;
+        }
+      } else {
+        float* p = a.g.sh + (size_t)gid * K * 3;
+#pragma unroll
+        for (int i = 0; i < K * 3; ++i) p[i] += g_sh[i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) {
+    const int k = (i / 12) % nk;
+    if (k > 0 && s_dM[i] != 0.f) atomicAdd(a.pose_dM + i, s_dM[i]);
+  }
+}
+
+// dL/dP_k = V_rot^T dL/dW_{v,k} summed over views, then (q, t) of the pose.
+__global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __restrict__ dM,
+                             int n_inst, const float4* __restrict__ pose_q, float* g_q,
+                             float* g_t) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (k > n_inst) return;
+  const int nk = n_inst + 1;
+  float dPr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dPt[3] = {0.f, 0.f, 0.f};
+  for (int v = 0; v < vs.n_views; ++v) {
+    const float* V = vs.v[v].V;
+    const float* d = dM + (v * nk + k) * 12;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        dPr[3 * r + c] += V[r] * d[c] + V[4 + r] * d[4 + c] + V[8 + r] * d[8 + c];
+      dPt[r] += V[r] * d[3] + V[4 + r] * d[7] + V[8 + r] * d[11];
+    }
+  }
+  if (g_t) {
+    g_t[3 * (k - 1)] += dPt[0];
+    g_t[3 * (k - 1) + 1] += dPt[1];
+    g_t[3 * (k - 1) + 2] += dPt[2];
+  }
+  if (g_q) {
+    const float4 gq = quat_backward(pose_q[k - 1], dPr);
+    g_q[4 * (k - 1)] += gq.x;
+    g_q[4 * (k - 1) + 1] += gq.y;
+    g_q[4 * (k - 1) + 2] += gq.z;
+    g_q[4 * (k - 1) + 3] += gq.w;
+  }
+}
+
+template <int DEG>
+cudaError_t launch_deg(s3r_workspace* ws, const BwdArgs& a, cudaStream_t st) {
+  const int nk = ws->n_inst + 1;
+  const size_t smem = (size_t)ws->n_views * nk * (sizeof(InstMat) + 12 * sizeof(float)) +
+                      sizeof(uint32_t) * (nk + 1) + 16;
+  static thread_local size_t cached_smem = 0;
+  static thread_local int cached_per_sm = 0;
+  if (smem != cached_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_project_bwd<DEG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project_bwd<DEG>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    cached_smem = smem;
+    cached_per_sm = per_sm;
+  }
+  const int per_sm = cached_per_sm;
+  KernelTimer timer(ws, kKProjectBwd, st);
+  k_project_bwd<DEG><<<ws->num_sms * per_sm, kThreads, smem, st>>>(ws->views, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
+                               const s3r_grads* g, cudaStream_t st) {
+  BwdArgs a;
+  a.means = sc->means;
+  a.log_scales = sc->log_scales;
+  a.quats = reinterpret_cast<const float4*>(sc->quats);
+  a.opac_logits = sc->opacity_logits;
+  a.sh = reinterpret_cast<const float4*>(sc->sh);
+  a.sh_f = sc->sh;
+  a.inst_off = sc->inst_offsets;
+  a.n_inst = sc->n_inst;
+  a.pose_q = reinterpret_cast<const float4*>(poses ? poses->quat : nullptr);
+  a.pose_t = poses ? poses->trans : nullptr;
+  a.selected = ws->selected;
+  a.keep_mask = ws->keep_mask;
+  a.splat_start = ws->splat_start;
+  a.sp_grad = reinterpret_cast<const float4*>(ws->sp_grad);
+  a.cap_splats = ws->cap.max_splats;
+  a.ctr = ws->ctr;
+  a.pose_dM = ws->pose_dM;
+  a.g = *g;
+  const int nk = ws->n_inst + 1;
+  cudaError_t e = cudaMemsetAsync(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)ws->n_views * nk, st);
+  if (e != cudaSuccess) return e;
+  // the tile counter of this stage is reset per call (several backward calls
+  // may follow one forward)
+  if ((e = cudaMemsetAsync(ws->ctr + kCtrTileBase + kStageProjectBwd, 0, sizeof(uint32_t), st)) !=
+      cudaSuccess)
+    return e;
+  switch (sc->sh_degree) {
+    case 0: e = launch_deg<0>(ws, a, st); break;
+    case 1: e = launch_deg<1>(ws, a, st); break;
+    case 2: e = launch_deg<2>(ws, a, st); break;
+    default: e = launch_deg<3>(ws, a, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  if (ws->n_inst > 0 && (g->inst_quat || g->inst_trans)) {
+    KernelTimer timer(ws, kKPoseChain, st);
+    k_pose_chain<<<(ws->n_inst + 127) / 128, 128, 0, st>>>(ws->views, ws->pose_dM, ws->n_inst,
+                                                          a.pose_q, g->inst_quat, g->inst_trans);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace s3r

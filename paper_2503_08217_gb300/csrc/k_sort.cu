@@ -1,0 +1,339 @@
+// Tile|depth key duplication and the radix sort that orders every tile's
+// splats front to back (the rasteriser of Eq. 2), then per-tile ranges.
+//
+// The sorted order is the one of a stable LSD radix sort on the 64-bit key
+// (view-tile id << 32 | FP32 depth bits) over the duplicated pairs in
+// projection order. Duplicates of one splat share its depth, so the four
+// depth-digit passes run on the splats BEFORE duplication (S keys instead of
+// K); the splats are then expanded into (tile, splat) pairs in depth order,
+// and the one or two tile-digit passes finish the sort. Every pass is a
+// single-pass "onesweep" kernel: persistent CTAs take 3840-key tiles from an
+// atomic counter, rank digits with warp match.any, get each digit's global
+// offset from a precomputed histogram plus a decoupled look-back over tiles,
+// reorder the tile in shared memory and write it out coalesced.
+#include "s3r_internal.cuh"
+
+namespace s3r {
+namespace {
+
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kWarpKeys = kSortItems * 32;   // 480 keys per warp per tile
+
+struct PassArgs {
+  const uint32_t* keys_in;
+  const uint32_t* vals_in;   // null: values are the input positions
+  uint32_t* keys_out;
+  uint32_t* vals_out;
+  const uint32_t* count;     // device count of keys
+  int64_t cap;
+  int shift;
+  const uint32_t* hist;      // [256] global digit histogram of this pass
+  uint32_t* ctr;
+  unsigned long long* lookback;
+  int stage;
+};
+
+// Exclusive scan of one value per thread across a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_tmp /*[8]*/,
+                                                    uint32_t* total) {
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
+  }
+  if (lane == 31) s_tmp[warp] = incl;
+  __syncthreads();
+  uint32_t wbase = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = s_tmp[w];
+    if (w < warp) wbase += c;
+    tot += c;
+  }
+  __syncthreads();
+  if (total) *total = tot;
+  return wbase + incl - x;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
+  __shared__ uint32_t s_keys[kSortTileKeys];
+  __shared__ uint32_t s_vals[kSortTileKeys];
+  __shared__ uint32_t s_cnt[kWarps][kRadix];   // per-warp digit counts -> exclusive offsets
+  __shared__ uint32_t s_gbase[kRadix];         // exclusive scan of the global histogram
+  __shared__ uint32_t s_dst[kRadix];           // global start of each digit for this tile
+  __shared__ uint32_t s_loc[kRadix];           // tile-local start of each digit
+  __shared__ uint32_t s_tmp[kWarps];
+  __shared__ uint32_t s_tile;
+
+  const int64_t n = min((int64_t)*a.count, a.cap);
+  const int64_t n_tiles = (n + kSortTileKeys - 1) / kSortTileKeys;
+  const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], a.stage);
+  const int warp = threadIdx.x >> 5;
+  const uint32_t lane = lane_id();
+  const uint32_t lt = lanemask_lt();
+  const int d_me = threadIdx.x;   // the digit this thread scans / looks back on
+
+  s_gbase[d_me] = block_excl_scan(a.hist[d_me], s_tmp, nullptr);
+
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + a.stage, 1u);
+    for (int i = lane; i < kRadix; i += 32) s_cnt[warp][i] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const int64_t base = tile * kSortTileKeys + (int64_t)warp * kWarpKeys;
+
+    uint32_t key[kSortItems], val[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t idx = base + r * 32 + lane;
+      const bool valid = idx < n;
+      key[r] = valid ? __ldcs(a.keys_in + idx) : 0xffffffffu;
+      val[r] = valid ? (a.vals_in ? __ldcs(a.vals_in + idx) : (uint32_t)idx) : 0u;
+      const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
+      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : kRadix);
+      uint32_t before = 0;
+      if (valid) before = s_cnt[warp][d];
+      rank[r] = before + __popc(peers & lt);
+      __syncwarp();
+      if (valid && (peers & lt) == 0) s_cnt[warp][d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit: exclusive offsets over warps, tile count, look-back
+    uint32_t tile_cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = s_cnt[w][d_me];
+      s_cnt[w][d_me] = tile_cnt;
+      tile_cnt += c;
+    }
+    const uint32_t prefix =
+        lookback_prefix(a.lookback + d_me, kRadix, tile, tag, tile_cnt, a.ctr);
+    s_dst[d_me] = s_gbase[d_me] + prefix;
+    s_loc[d_me] = block_excl_scan(tile_cnt, s_tmp, nullptr);
+    __syncthreads();
+
+    // reorder in shared memory by digit (stable)
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t idx = base + r * 32 + lane;
+      if (idx < n) {
+        const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
+        const uint32_t pos = s_loc[d] + s_cnt[warp][d] + rank[r];
+        s_keys[pos] = key[r];
+        s_vals[pos] = val[r];
+      }
+    }
+    __syncthreads();
+    const int64_t tile_n = min((int64_t)kSortTileKeys, n - tile * kSortTileKeys);
+    for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
+      const uint32_t k = s_keys[i];
+      const uint32_t d = (k >> a.shift) & (kRadix - 1);
+      const uint32_t dst = s_dst[d] + (uint32_t)i - s_loc[d];
+      __stcs(a.keys_out + dst, k);
+      __stcs(a.vals_out + dst, s_vals[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// Expand depth-sorted splats into (view-tile id, splat) pairs. Each tile of
+// 256 consecutive sorted splats owns one contiguous output range (block scan
+// of tile counts + decoupled look-back); the range is written with one
+// thread per output element (binary search for its splat), so writes are
+// coalesced and balanced however many tiles a splat covers.
+struct DupArgs {
+  const uint32_t* sorted_splats;
+  const uint2* sp_rect;
+  const uint8_t* sp_view;
+  uint32_t* dup_key;
+  uint32_t* dup_val;
+  uint32_t* hist;        // tile-digit histograms (kHistTile...)
+  int tile_passes;
+  int64_t cap_splats, cap_dups;
+  uint32_t* ctr;
+  unsigned long long* lookback;
+};
+
+__global__ void __launch_bounds__(256) k_duplicate(const __grid_constant__ ViewSet vs, DupArgs a) {
+  __shared__ uint32_t s_excl[257];
+  __shared__ uint32_t s_splat[256];
+  __shared__ uint2 s_rect[256];
+  __shared__ int s_view[256];
+  __shared__ uint32_t s_hist[4][kRadix];
+  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_tile, s_base;
+  __shared__ int s_gx[S3R_MAX_VIEWS], s_tb[S3R_MAX_VIEWS];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  if (threadIdx.x < vs.n_views) {
+    s_gx[threadIdx.x] = vs.v[threadIdx.x].gx;
+    s_tb[threadIdx.x] = vs.v[threadIdx.x].tile_base;
+  }
+  const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
+  const int64_t n_tiles = (n + 255) / 256;
+  const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
+  bool overflow = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const int64_t i = tile * 256 + threadIdx.x;
+    uint32_t cnt = 0;
+    if (i < n) {
+      const uint32_t s = a.sorted_splats[i];
+      const uint2 r = a.sp_rect[s];
+      const uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
+      const uint32_t h = (r.y >> 16) - (r.x >> 16);
+      cnt = w * h;
+      s_splat[threadIdx.x] = s;
+      s_rect[threadIdx.x] = r;
+      s_view[threadIdx.x] = a.sp_view[s];
+    }
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(cnt, s_tmp, &total);
+    s_excl[threadIdx.x] = ex;
+    if (threadIdx.x == 0) {
+      s_excl[256] = total;
+      const uint32_t prefix = lookback_prefix(a.lookback, 1, tile, tag, total, a.ctr);
+      s_base = prefix;
+      if (tile == n_tiles - 1) a.ctr[kCtrDups] = prefix + total;
+    }
+    __syncthreads();
+    const uint32_t base = s_base;
+    for (uint32_t o = threadIdx.x; o < total; o += 256) {
+      // last q with s_excl[q] <= o
+      int lo = 0, hi = 256;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_excl[mid] <= o) lo = mid; else hi = mid;
+      }
+      const uint32_t rr = o - s_excl[lo];
+      const uint2 r = s_rect[lo];
+      const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16;
+      const uint32_t w = (r.y & 0xffffu) - x0;
+      const uint32_t ty = y0 + rr / w, tx = x0 + rr % w;
+      const int v = s_view[lo];
+      const uint32_t tile_id = (uint32_t)s_tb[v] + ty * (uint32_t)s_gx[v] + tx;
+      const int64_t pos = (int64_t)base + o;
+      if (pos < a.cap_dups) {
+        __stcs(a.dup_key + pos, tile_id);
+        __stcs(a.dup_val + pos, s_splat[lo]);
+        for (int p = 0; p < a.tile_passes; ++p)
+          atomicAdd(&s_hist[p][(tile_id >> (8 * p)) & 0xffu], 1u);
+      } else {
+        overflow = true;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.tile_passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(a.hist + kHistTile * kRadix + i, c);
+  }
+  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
+}
+
+// [start, end) of every tile in the tile-sorted pair array.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* ctr, int64_t cap,
+                         uint2* __restrict__ ranges) {
+  const int64_t n = min((int64_t)ctr[kCtrDups], cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
+    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+  }
+}
+
+int per_sm_for(const void* fn, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
+}
+
+}  // namespace
+
+cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
+  cudaError_t e;
+  // occupancy is queried once (outside any graph capture: the first call)
+  static thread_local int sweep_per_sm = 0, dup_per_sm = 0;
+  if (!sweep_per_sm) sweep_per_sm = per_sm_for((const void*)k_onesweep, kSortThreads);
+  if (!dup_per_sm) dup_per_sm = per_sm_for((const void*)k_duplicate, 256);
+  const int g_sweep = ws->num_sms * sweep_per_sm;
+  // depth digits on the splats: 4 passes, result back in buffer 0
+  for (int p = 0; p < 4; ++p) {
+    PassArgs a;
+    a.keys_in = ws->depth_key[p & 1];
+    a.vals_in = p == 0 ? nullptr : ws->depth_val[p & 1];
+    a.keys_out = ws->depth_key[(p + 1) & 1];
+    a.vals_out = ws->depth_val[(p + 1) & 1];
+    a.count = ws->ctr + kCtrSplats;
+    a.cap = ws->cap.max_splats;
+    a.shift = 8 * p;
+    a.hist = ws->hist + (kHistDepth + p) * kRadix;
+    a.ctr = ws->ctr;
+    a.lookback = ws->lookback;
+    a.stage = kStageDepth0 + p;
+    KernelTimer timer(ws, kKDepth0 + p, st);
+    k_onesweep<<<g_sweep, kSortThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  ws->depth_final = 0;
+  // expand into (tile, splat) pairs in depth order
+  DupArgs d;
+  d.sorted_splats = ws->depth_val[0];
+  d.sp_rect = ws->sp_rect;
+  d.sp_view = ws->sp_view;
+  d.dup_key = ws->dup_key[0];
+  d.dup_val = ws->dup_val[0];
+  d.hist = ws->hist;
+  d.tile_passes = ws->tile_passes;
+  d.cap_splats = ws->cap.max_splats;
+  d.cap_dups = ws->cap.max_duplicates;
+  d.ctr = ws->ctr;
+  d.lookback = ws->lookback;
+  const int g_dup = ws->num_sms * dup_per_sm;
+  {
+    KernelTimer timer(ws, kKDuplicate, st);
+    k_duplicate<<<g_dup, 256, 0, st>>>(ws->views, d);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // tile digits on the pairs
+  for (int p = 0; p < ws->tile_passes; ++p) {
+    PassArgs a;
+    a.keys_in = ws->dup_key[p & 1];
+    a.vals_in = ws->dup_val[p & 1];
+    a.keys_out = ws->dup_key[(p + 1) & 1];
+    a.vals_out = ws->dup_val[(p + 1) & 1];
+    a.count = ws->ctr + kCtrDups;
+    a.cap = ws->cap.max_duplicates;
+    a.shift = 8 * p;
+    a.hist = ws->hist + (kHistTile + p) * kRadix;
+    a.ctr = ws->ctr;
+    a.lookback = ws->lookback;
+    a.stage = kStageTile0 + p;
+    KernelTimer timer(ws, kKTile0 + p, st);
+    k_onesweep<<<g_sweep, kSortThreads, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  ws->dup_final = ws->tile_passes & 1;
+  if ((e = cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->views.total_tiles, st)) !=
+      cudaSuccess)
+    return e;
+  KernelTimer timer(ws, kKRanges, st);
+  k_ranges<<<ws->num_sms * 4, 256, 0, st>>>(ws->dup_key[ws->dup_final], ws->ctr,
+                                            ws->cap.max_duplicates, ws->ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace s3r

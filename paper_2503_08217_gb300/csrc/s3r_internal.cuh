@@ -1,0 +1,232 @@
+// Internal declarations shared by the CUDA translation units of libs3r.
+// Not part of the public ABI (that is include/s3r.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "s3r.h"
+
+namespace s3r {
+
+constexpr int kTile = S3R_TILE;            // 16x16 pixel tiles
+constexpr int kTilePixels = kTile * kTile;
+
+// ---- device counters (uint32 slots of ws->ctr) -----------------------------
+enum Ctr : int {
+  kCtrSelected = 0,   // Gaussians whose window contains t
+  kCtrSplats = 1,     // kept (Gaussian, view) pairs (may exceed capacity)
+  kCtrDups = 2,       // (tile, splat) pairs (may exceed capacity)
+  kCtrStatus = 3,     // latched error bits
+  kCtrEpoch = 4,      // bumped once per s3r_project; tags look-back words
+  kCtrFrustum = 5,    // selected Gaussians inside >= 1 frustum
+  kCtrTileBase = 8,   // 16 dynamic tile-acquisition counters, one per stage
+  kCtrPairs = 24,     // 64-bit: (pixel, splat) pairs evaluated by the forward blend
+  kCtrCount = 32
+};
+constexpr uint32_t kStatusCapacity = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+
+// Look-back stages (each has its own tile counter and status tag).
+enum Stage : int {
+  kStageCompact = 0,
+  kStageProject = 1,
+  kStageDup = 2,
+  kStageDepth0 = 3,   // 3..6: depth radix passes
+  kStageTile0 = 7,    // 7..10: tile radix passes
+  kStageProjectBwd = 11,
+  kStageCount = 12
+};
+
+// Bounded spin: after this many polls a wait gives up, latches
+// kStatusTimeout and carries on (results are then invalid, nothing hangs).
+constexpr int kSpinLimit = 1 << 22;
+
+// ---- per-call camera set, passed by value in kernel parameters -------------
+struct ViewInfo {
+  int32_t width, height, gx, gy;
+  int32_t tile_base, pix_base;
+  float fx, fy, cx, cy, near_z, limx, limy;
+  float V[12];
+};
+
+struct ViewSet {
+  int32_t n_views;
+  int32_t total_tiles;
+  int32_t total_pixels;
+  int32_t pad;
+  ViewInfo v[S3R_MAX_VIEWS];
+};
+
+// ---- radix sort geometry ----------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 15;                       // keys per thread per tile
+constexpr int kSortTileKeys = kSortThreads * kSortItems;  // 3840
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+// digit histograms: 4 depth passes + up to 4 tile passes
+constexpr int kHistDepth = 0;
+constexpr int kHistTile = 4;
+constexpr int kHistCount = 8;
+
+// Kernel ids for the per-kernel timing hook.
+enum KernelId : int {
+  kKBegin = 0, kKCompact, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
+  kKTile0, kKTile1, kKTile2, kKTile3, kKRanges, kKBlendFwd, kKZeroGrads, kKBlendBwd,
+  kKProjectBwd, kKPoseChain, kKCount
+};
+
+}  // namespace s3r
+
+// The workspace: every intermediate of one call sequence, allocated once.
+struct s3r_workspace {
+  int device;
+  s3r_capacity cap;
+  int num_sms;
+  // device buffers
+  uint32_t* ctr;            // [kCtrCount]
+  uint32_t* hist;           // [kHistCount][256]
+  unsigned long long* lookback;  // tagged look-back words
+  int64_t lookback_words;
+  uint32_t* selected;       // [N]
+  uint32_t* frustum_mask;   // [N]
+  uint32_t* keep_mask;      // [N]
+  uint32_t* splat_start;    // [N]
+  float2* sp_xy;            // [S]
+  float4* sp_conic_o;       // [S]
+  float4* sp_rgb_d;         // [S]
+  uint2* sp_rect;           // [S]
+  uint8_t* sp_view;         // [S]
+  uint32_t* depth_key[2];   // [S]
+  uint32_t* depth_val[2];   // [S]
+  uint32_t* dup_key[2];     // [K]
+  uint32_t* dup_val[2];     // [K]
+  uint2* ranges;            // [tiles]
+  float* final_T;           // [P]
+  uint32_t* n_contrib;      // [P]
+  float* sp_grad;           // [S*12]
+  float* pose_dM;           // [views*(inst+1)*12]
+  int64_t bytes;
+  // host-side state of the current call sequence
+  s3r::ViewSet views;
+  int n_views;
+  int n_inst;
+  int sh_degree;
+  int64_t n;
+  int stage_done;           // 0 none, 1 projected, 2 sorted, 3 rendered
+  int depth_final;          // which buffer holds the depth-sorted splats
+  int dup_final;            // which buffer holds the tile-sorted pairs
+  int tile_passes;
+  // per-kernel timing hook
+  int timing;
+  cudaEvent_t ev[2 * s3r::kKCount];
+  int ev_used[s3r::kKCount];
+};
+
+namespace s3r {
+// Records a CUDA event before a kernel launch and another after it when the
+// workspace's timing hook is on.
+struct KernelTimer {
+  s3r_workspace* ws;
+  int id;
+  cudaStream_t st;
+  KernelTimer(s3r_workspace* w, int kid, cudaStream_t s) : ws(w), id(kid), st(s) {
+    if (ws->timing) cudaEventRecord(ws->ev[2 * id], st);
+  }
+  ~KernelTimer() {
+    if (ws->timing) {
+      cudaEventRecord(ws->ev[2 * id + 1], st);
+      ws->ev_used[id] = 1;
+    }
+  }
+};
+}  // namespace s3r
+
+namespace s3r {
+
+// ---- launchers (one translation unit each) ---------------------------------
+cudaError_t launch_begin(s3r_workspace* ws, cudaStream_t st);
+cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float t,
+                           cudaStream_t st);
+cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
+                           float t, float* life, float lod, cudaStream_t st);
+cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st);
+cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cudaStream_t st);
+cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* dL,
+                              cudaStream_t st);
+cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
+                               const s3r_grads* g, cudaStream_t st);
+cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
+                           float* loss, cudaStream_t st);
+cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
+                              int mode, cudaStream_t st);
+
+// ---- small device helpers ----------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Tagged look-back word: [tag:30][flag:2][value:32]. flag 1 = this tile's
+// aggregate only, 2 = inclusive prefix through this tile.
+__device__ __forceinline__ unsigned long long lb_word(uint32_t tag, uint32_t flag, uint32_t v) {
+  return ((unsigned long long)tag << 34) | ((unsigned long long)flag << 32) | v;
+}
+__device__ __forceinline__ uint32_t stage_tag(uint32_t epoch, int stage) {
+  return ((epoch << 4) | (uint32_t)stage) & 0x3fffffffu;
+}
+
+// Exclusive prefix for `tile` of one running sum (one digit). `words` points
+// at digit d's word of tile 0; consecutive tiles are `stride` words apart.
+// Publishes the inclusive value on exit. Bounded: on give-up latches
+// kStatusTimeout into ctr and returns the partial sum.
+__device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, int64_t stride,
+                                                     int64_t tile, uint32_t tag, uint32_t aggregate,
+                                                     uint32_t* ctr) {
+  unsigned long long* mine = words + tile * stride;
+  if (tile == 0) {
+    st_relaxed(mine, lb_word(tag, 2, aggregate));
+    return 0;
+  }
+  st_relaxed(mine, lb_word(tag, 1, aggregate));
+  uint32_t prefix = 0;
+  int64_t k = tile - 1;
+  int spins = 0;
+  while (k >= 0) {
+    unsigned long long w = ld_relaxed(words + k * stride);
+    uint32_t wtag = (uint32_t)(w >> 34);
+    uint32_t flag = (uint32_t)(w >> 32) & 3u;
+    if (wtag != tag || flag == 0) {
+      if (++spins > kSpinLimit) {
+        atomicOr(ctr + kCtrStatus, kStatusTimeout);
+        break;
+      }
+      __nanosleep(20);
+      continue;
+    }
+    prefix += (uint32_t)w;
+    if (flag == 2) break;
+    --k;
+  }
+  st_relaxed(mine, lb_word(tag, 2, prefix + aggregate));
+  return prefix;
+}
+
+__device__ __forceinline__ uint32_t lane_id() {
+  uint32_t l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+#endif
+
+}  // namespace s3r

@@ -1,0 +1,178 @@
+// FP32 device math of the instance-specific projection (Sec. 3.3 with Eq. 1)
+// and of the SH colour, shared by the forward and backward projection
+// kernels of libs3r.
+#pragma once
+
+#include "s3r_internal.cuh"
+
+namespace s3r {
+
+// Composed instance matrix W_{t,i} = W_t W_{t,i2g} (3x4, row-major) and the
+// camera centre expressed in the instance's frame, -A^T b (A is a rotation).
+struct __align__(16) InstMat {
+  float m[12];
+  float c[3];
+  float pad;
+};
+
+constexpr float kDilation = 0.3f;
+constexpr float kMinEig = 0.1f;
+
+// Rotation of the unit quaternion q/|q| (w, x, y, z), row-major.
+__device__ __forceinline__ void quat_to_rot(float4 q, float R[9]) {
+  const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+  R[0] = 1.f - 2.f * (yy + zz); R[1] = 2.f * (xy - wz); R[2] = 2.f * (xz + wy);
+  R[3] = 2.f * (xy + wz); R[4] = 1.f - 2.f * (xx + zz); R[5] = 2.f * (yz - wx);
+  R[6] = 2.f * (xz - wy); R[7] = 2.f * (yz + wx); R[8] = 1.f - 2.f * (xx + yy);
+}
+
+// Compose W_v * P_k for all views v and segments k (k = 0: identity pose)
+// into `mats` ([n_views][n_inst+1]), cooperatively over the CTA.
+__device__ __forceinline__ void compose_all(const ViewSet& vs, const float4* pose_q,
+                                            const float* pose_t, int n_inst, InstMat* mats) {
+  const int nk = n_inst + 1;
+  for (int i = threadIdx.x; i < vs.n_views * nk; i += blockDim.x) {
+    const int v = i / nk, k = i - v * nk;
+    const float* V = vs.v[v].V;
+    float P[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
+    if (k > 0) {
+      float R[9];
+      quat_to_rot(pose_q[k - 1], R);
+      for (int r = 0; r < 3; ++r) {
+        P[4 * r] = R[3 * r];
+        P[4 * r + 1] = R[3 * r + 1];
+        P[4 * r + 2] = R[3 * r + 2];
+        P[4 * r + 3] = pose_t[3 * (k - 1) + r];
+      }
+    }
+    InstMat m;
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 4; ++c)
+        m.m[4 * r + c] = fmaf(V[4 * r], P[c], fmaf(V[4 * r + 1], P[4 + c], V[4 * r + 2] * P[8 + c]));
+      m.m[4 * r + 3] += V[4 * r + 3];
+    }
+    // camera centre in the instance frame: -A^T b
+    for (int c = 0; c < 3; ++c)
+      m.c[c] = -(m.m[c] * m.m[3] + m.m[4 + c] * m.m[7] + m.m[8 + c] * m.m[11]);
+    m.pad = 0.f;
+    mats[i] = m;
+  }
+}
+
+// Segment (0 = static, k = instance k) of Gaussian `gid` from the offsets.
+__device__ __forceinline__ int segment_of(const uint32_t* off, int n_inst, uint32_t gid) {
+  int lo = 0, hi = n_inst + 1;  // off[lo] <= gid < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= gid) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Result of projecting one Gaussian into one view.
+struct Proj2D {
+  float x, y, z;        // camera-space position
+  float u, v;           // pixel position
+  float ca, cb, cc;     // conic: power = -0.5 (ca dx^2 + cc dy^2) - cb dx dy
+  float sigma;          // sqrt(largest eigenvalue) before dilation (LOD scale)
+  float radius;
+  int x0, y0, x1, y1;   // tile rectangle, half-open
+  bool infrustum;
+};
+
+// Project a Gaussian with local mean mu and RS = R(q) diag(s) through the
+// composed matrix M. Follows Eq. 1 with the 3DGS conventions: near plane,
+// the 1.3x field-of-view clamp of the Jacobian, 0.3 px^2 dilation, 3-sigma
+// radius and a 16x16-tile bounding rectangle.
+__device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[3],
+                                               const float RS[9], const ViewInfo& vi) {
+  Proj2D o;
+  o.infrustum = false;
+  o.x = fmaf(M.m[0], mu[0], fmaf(M.m[1], mu[1], fmaf(M.m[2], mu[2], M.m[3])));
+  o.y = fmaf(M.m[4], mu[0], fmaf(M.m[5], mu[1], fmaf(M.m[6], mu[2], M.m[7])));
+  o.z = fmaf(M.m[8], mu[0], fmaf(M.m[9], mu[1], fmaf(M.m[10], mu[2], M.m[11])));
+  if (!(o.z > vi.near_z)) return o;
+  // B = A * RS (A = rotation part of M): camera-space covariance is B B^T
+  float B[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      B[3 * r + c] = fmaf(M.m[4 * r], RS[c], fmaf(M.m[4 * r + 1], RS[3 + c], M.m[4 * r + 2] * RS[6 + c]));
+  const float iz = 1.f / o.z;
+  const float rx = o.x * iz, ry = o.y * iz;
+  const float txr = fminf(vi.limx, fmaxf(-vi.limx, rx));
+  const float tyr = fminf(vi.limy, fmaxf(-vi.limy, ry));
+  const float j00 = vi.fx * iz, j02 = -vi.fx * txr * iz;
+  const float j11 = vi.fy * iz, j12 = -vi.fy * tyr * iz;
+  // C = J B (2x3); Sigma2 = C C^T
+  float C0[3], C1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C0[c] = fmaf(j00, B[c], j02 * B[6 + c]);
+    C1[c] = fmaf(j11, B[3 + c], j12 * B[6 + c]);
+  }
+  const float a = fmaf(C0[0], C0[0], fmaf(C0[1], C0[1], C0[2] * C0[2]));
+  const float b = fmaf(C0[0], C1[0], fmaf(C0[1], C1[1], C0[2] * C1[2]));
+  const float c = fmaf(C1[0], C1[0], fmaf(C1[1], C1[1], C1[2] * C1[2]));
+  const float mid0 = 0.5f * (a + c);
+  const float det0 = a * c - b * b;
+  o.sigma = sqrtf(mid0 + sqrtf(fmaxf(0.f, mid0 * mid0 - det0)));
+  const float ad = a + kDilation, cd = c + kDilation;
+  const float det = ad * cd - b * b;
+  if (!(det > 0.f)) return o;
+  const float idet = 1.f / det;
+  o.ca = cd * idet;
+  o.cb = -b * idet;
+  o.cc = ad * idet;
+  const float mid = 0.5f * (ad + cd);
+  const float lam = mid + sqrtf(fmaxf(kMinEig, mid * mid - det));
+  o.radius = ceilf(3.f * sqrtf(lam));
+  o.u = fmaf(vi.fx, rx, vi.cx);
+  o.v = fmaf(vi.fy, ry, vi.cy);
+  const float inv_tile = 1.f / kTile;
+  o.x0 = (int)fminf((float)vi.gx, fmaxf(0.f, floorf((o.u - o.radius) * inv_tile)));
+  o.x1 = (int)fminf((float)vi.gx, fmaxf(0.f, floorf((o.u + o.radius + (kTile - 1)) * inv_tile)));
+  o.y0 = (int)fminf((float)vi.gy, fmaxf(0.f, floorf((o.v - o.radius) * inv_tile)));
+  o.y1 = (int)fminf((float)vi.gy, fmaxf(0.f, floorf((o.v + o.radius + (kTile - 1)) * inv_tile)));
+  o.infrustum = (o.x1 > o.x0) && (o.y1 > o.y0);
+  return o;
+}
+
+// Real SH basis (orthonormal, Condon-Shortley sign) at a unit direction d,
+// degrees 0..DEG. Band constants: sqrt((2l+1)/(4 pi) * (l-|m|)!/(l+|m|)!)
+// times the usual factor 2 for m != 0, folded into one number per term.
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float dx, float dy, float dz, float Y[16]) {
+  Y[0] = 0.28209479177387814f;
+  if (DEG >= 1) {
+    const float k1 = 0.48860251190291992f;
+    Y[1] = -k1 * dy;
+    Y[2] = k1 * dz;
+    Y[3] = -k1 * dx;
+  }
+  if (DEG >= 2) {
+    const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    Y[4] = 1.0925484305920792f * dx * dy;
+    Y[5] = -1.0925484305920792f * dy * dz;
+    Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * dx * dz;
+    Y[8] = 0.54627421529603959f * (xx - yy);
+    if (DEG >= 3) {
+      Y[9] = -0.59004358992664352f * dy * (3.f * xx - yy);
+      Y[10] = 2.8906114426405538f * dx * dy * dz;
+      Y[11] = -0.45704579946446572f * dy * (4.f * zz - xx - yy);
+      Y[12] = 0.37317633259011546f * dz * (2.f * zz - 3.f * xx - 3.f * yy);
+      Y[13] = -0.45704579946446572f * dx * (4.f * zz - xx - yy);
+      Y[14] = 1.4453057213202769f * dz * (xx - yy);
+      Y[15] = -0.59004358992664352f * dx * (xx - 3.f * yy);
+    }
+  }
+}
+
+__host__ __device__ constexpr int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+
+}  // namespace s3r

@@ -1,0 +1,127 @@
+"""Helpers for the GPU parity tests: run one timestep through the C ABI and
+copy the workspace intermediates out; build the oracle's per-splat view of
+the same inputs; and mark the pixels and Gaussians whose integer decisions
+sit within rounding distance of a threshold (where FP32 and FP64 may
+legitimately differ)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2503_08217_gb300 import binding
+from paper_2503_08217_gb300.render import DeviceScene, Renderer, pixel_count, split_views
+
+
+def gpu_step(scene, step, cams, vis, life=None, lod=0.0, bg=(0.0, 0.0, 0.0), dL=None,
+             renderer=None, max_splats=None, max_duplicates=None, dev=None):
+    """Run project/sort/fwd (and bwd if dL is given) on cuda:0."""
+    dev = DeviceScene.from_host(scene) if dev is None else dev
+    r = renderer or Renderer(scene.n, scene.n_inst, cams, max_splats=max_splats,
+                             max_duplicates=max_duplicates)
+    vis_t = torch.from_numpy(np.ascontiguousarray(vis, np.float32)).cuda()
+    life_t = None if life is None else torch.from_numpy(np.ascontiguousarray(life, np.float32)).cuda()
+    iq = torch.from_numpy(np.ascontiguousarray(scene.inst_quat[step], np.float32)).cuda()
+    it = torch.from_numpy(np.ascontiguousarray(scene.inst_trans[step], np.float32)).cuda()
+    bg_t = torch.tensor(bg, dtype=torch.float32, device="cuda")
+    t = float(scene.times[step])
+    out = r.forward(dev, iq, it, cams, t, vis_t, life_t, lod, bg_t)
+    res = {"renderer": r, "out": out, "images": [v.double().cpu().numpy() for v in split_views(out, cams)]}
+    c = r.counts()
+    res["counts"] = c
+    _raise_status(c)
+    n_sel, n_sp, n_dup = c["n_selected"], c["n_splats"], c["n_duplicates"]
+    ws = r.ws
+    res["selected"] = ws.debug("selected", torch.int32, n_sel).cpu().numpy().astype(np.int64)
+    res["frustum_mask"] = ws.debug("frustum_mask", torch.int32, n_sel).cpu().numpy().view(np.uint32)
+    res["keep_mask"] = ws.debug("keep_mask", torch.int32, n_sel).cpu().numpy().view(np.uint32)
+    res["splat_start"] = ws.debug("splat_start", torch.int32, n_sel).cpu().numpy().view(np.uint32)
+    sp = min(n_sp, r.ws.capacity.max_splats)
+    res["xy"] = ws.debug("splat_xy", torch.float32, 2 * sp).cpu().numpy().reshape(-1, 2)
+    res["conic_o"] = ws.debug("splat_conic_opacity", torch.float32, 4 * sp).cpu().numpy().reshape(-1, 4)
+    res["rgb_d"] = ws.debug("splat_rgb_depth", torch.float32, 4 * sp).cpu().numpy().reshape(-1, 4)
+    rect = ws.debug("splat_rect", torch.int32, 2 * sp).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    res["rect"] = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16],
+                           1).astype(np.int32)
+    res["view"] = ws.debug("splat_view", torch.uint8, sp).cpu().numpy().astype(np.int32)
+    nd = min(n_dup, r.ws.capacity.max_duplicates)
+    res["sorted_splats"] = ws.debug("sorted_splats", torch.int32, nd).cpu().numpy().view(np.uint32)
+    res["sorted_tiles"] = ws.debug("sorted_tiles", torch.int32, nd).cpu().numpy().view(np.uint32)
+    n_tiles = sum(((cm.width + 15) // 16) * ((cm.height + 15) // 16) for cm in cams)
+    res["ranges"] = ws.debug("tile_ranges", torch.int32, 2 * n_tiles).cpu().numpy().view(np.uint32).reshape(-1, 2)
+    P = pixel_count(cams)
+    res["final_T"] = ws.debug("final_T", torch.float32, P).cpu().numpy()
+    res["n_contrib"] = ws.debug("n_contrib", torch.int32, P).cpu().numpy()
+    if life_t is not None:
+        res["life"] = life_t.cpu().numpy()
+    if dL is not None:
+        grads = {"means": torch.zeros_like(dev.means), "log_scales": torch.zeros_like(dev.log_scales),
+                 "quats": torch.zeros_like(dev.quats), "opacity_logits": torch.zeros_like(dev.opacity_logits),
+                 "sh": torch.zeros_like(dev.sh), "inst_quat": torch.zeros_like(iq),
+                 "inst_trans": torch.zeros_like(it)}
+        dL_t = torch.from_numpy(np.concatenate([np.asarray(d, np.float32).reshape(-1) for d in dL])).cuda()
+        r.backward(dev, iq, it, bg_t, dL_t, grads)
+        torch.cuda.synchronize()
+        res["grads"] = {k: v.double().cpu().numpy() for k, v in grads.items()}
+        res["splat_grads"] = ws.debug("splat_grads", torch.float32, 12 * sp).cpu().numpy().reshape(-1, 12)
+    _raise_status(r.counts())
+    return res
+
+
+def _raise_status(c):
+    if c["device_status"] & 2:
+        raise binding.S3RError(4, "a bounded device-side wait gave up")
+    if c["device_status"] & 1:
+        raise binding.S3RError(2, f"capacity exceeded ({c})")
+
+
+def splat_gids(res):
+    """Gaussian id and view of every GPU splat (from the per-Gaussian masks)."""
+    gids = np.zeros(len(res["view"]), np.int64)
+    for j, g in enumerate(res["selected"]):
+        m = int(res["keep_mask"][j])
+        s = int(res["splat_start"][j])
+        while m:
+            gids[s] = g
+            s += 1
+            m &= m - 1
+    return gids
+
+
+def sweep_visibility(scene, cams_fn=None, lod=0.0):
+    """Oracle forward-only sweep over every timestep, then Eq. 6: the
+    visibility record a first training epoch would produce."""
+    vis, life = oracle.vis_reset(scene.n)
+    for k in range(scene.n_steps):
+        cams = scene.cams[k] if cams_fn is None else cams_fn(k)
+        sel = oracle.select(vis, float(scene.times[k]))
+        mt = np.zeros(sel.shape[0], bool)
+        for cam in cams:
+            mt |= oracle.project(scene, sel, k, cam, lod)["infrustum"]
+        full = np.zeros(scene.n, bool)
+        full[sel[mt]] = True
+        oracle.vis_record(life, full, np.float32(scene.times[k]))
+    return oracle.vis_finalize(life), life
+
+
+def bad_pixels(cam, rec, flag):
+    """Pixels to leave out of an image comparison: the blend flagged them, or
+    they lie in a tile that a Gaussian with a near-threshold projection
+    decision may or may not cover (its rectangle grown by one tile)."""
+    bad = flag.copy()
+    H, W = cam.height, cam.width
+    gx, gy = (W + 15) // 16, (H + 15) // 16
+    near = rec["near"] & (rec["infrustum"] | (rec["p"][:, 2] > 0))
+    for i in np.nonzero(near)[0]:
+        x0, y0, x1, y1 = rec["rect"][i]
+        if x1 <= x0 or y1 <= y0:
+            # decision flipped near an edge of the image: grow around the centre
+            u, v = rec["uv"][i]
+            x0 = x1 = int(np.clip(u // 16, 0, gx - 1))
+            y0 = y1 = int(np.clip(v // 16, 0, gy - 1))
+            x1 += 1
+            y1 += 1
+        x0, y0 = max(0, x0 - 1), max(0, y0 - 1)
+        x1, y1 = min(gx, x1 + 1), min(gy, y1 + 1)
+        bad[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
+    return bad

@@ -1,0 +1,47 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point that include/s3r.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "s3r.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(s3r_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("s3r_project", "s3r_sort", "s3r_render_fwd", "s3r_render_bwd",
+                     "s3r_update_visibility"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2503_08217_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    lib.s3r_built_arch.restype = ctypes.c_int32
+    assert lib.s3r_built_arch() == 103
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2503_08217_gb300 import binding
+    assert set(binding.EXPORTS) == set(declared_functions())
+
+
+def test_invalid_calls_fail_without_a_gpu():
+    """Argument checks run before any CUDA call: NULL handles are rejected."""
+    from paper_2503_08217_gb300 import binding
+    L = binding.load()
+    assert L.s3r_sort(None, None) == 1
+    assert L.s3r_render_fwd(None, None, None, None) == 1
+    assert L.s3r_update_visibility(-1, 0.0, None, None, None, 0, None) == 1
+    assert L.s3r_update_visibility(10, 0.0, None, None, None, 7, None) == 1
+    assert b"mode" in L.s3r_last_error()

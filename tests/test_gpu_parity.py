@@ -1,0 +1,449 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (FP32 kernels vs FP64 oracle):
+  * integer / index stages (selection, masks, rectangles, sort order, tile
+    ranges, visibility record): bit-exact, except on Gaussians whose FP64
+    decision quantity lies within 1e-5 (relative) of its threshold, which the
+    oracle flags and the test counts;
+  * images: max |GPU - oracle| <= 1e-4 on every pixel outside the tiles of
+    flagged Gaussians and pixels whose blend has a near-threshold decision;
+  * gradients: per tensor ||g - g*||_2 <= 1e-3 ||g*||_2, and per element
+    |g - g*| <= 1e-3 |g*| + 1e-5 max|g*|.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_08217_gb300 import scenegen
+from paper_2503_08217_gb300.scenegen import make_camera
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2503_08217_gb300 import build, binding
+    build.build()
+    binding.load()
+    return True
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return scenegen.generate("tiny", seed=0)
+
+
+@pytest.fixture(scope="module")
+def tiny_vis(tiny):
+    import gpu_helpers
+    return gpu_helpers.sweep_visibility(tiny)
+
+
+def _oracle_views(scene, step, cams, vis, lod, bg=(0.0, 0.0, 0.0)):
+    f = oracle.step_forward(scene, step, vis, None, lod, cams=cams, bg=bg)
+    return f
+
+
+def _compare_selection_and_masks(res, f, n_views):
+    np.testing.assert_array_equal(res["selected"], f["sel"])
+    near = np.zeros(f["sel"].shape[0], bool)
+    fm = np.zeros(f["sel"].shape[0], np.uint32)
+    km = np.zeros(f["sel"].shape[0], np.uint32)
+    for v in range(n_views):
+        rec = f["views"][v]["rec"]
+        near |= rec["near"]
+        fm |= rec["infrustum"].astype(np.uint32) << np.uint32(v)
+        km |= rec["kept"].astype(np.uint32) << np.uint32(v)
+    ok = ~near
+    np.testing.assert_array_equal(res["frustum_mask"][ok], fm[ok])
+    np.testing.assert_array_equal(res["keep_mask"][ok], km[ok])
+    return near
+
+
+def _compare_splats(res, f, scene, cams):
+    """GPU splat records vs the oracle's FP64 projection of the same pairs."""
+    import gpu_helpers
+    gids = gpu_helpers.splat_gids(res)
+    checked = 0
+    for v, cam in enumerate(cams):
+        rec = f["views"][v]["rec"]
+        idx = {int(g): i for i, g in enumerate(rec["gid"])}
+        mine = np.nonzero(res["view"] == v)[0]
+        for s in mine:
+            i = idx[int(gids[s])]
+            if rec["near"][i] or not rec["kept"][i]:
+                continue
+            u, vv = rec["uv"][i]
+            assert abs(res["xy"][s, 0] - u) <= 1e-5 * abs(u) + 2e-4
+            assert abs(res["xy"][s, 1] - vv) <= 1e-5 * abs(vv) + 2e-4
+            np.testing.assert_allclose(res["conic_o"][s, :3], rec["conic"][i], rtol=2e-4,
+                                       atol=2e-5 * np.abs(rec["conic"][i]).max())
+            assert abs(res["conic_o"][s, 3] - rec["opacity"][i]) <= 2e-6
+            np.testing.assert_allclose(res["rgb_d"][s, :3], rec["rgb"][i], atol=2e-5)
+            z32 = np.float32(res["rgb_d"][s, 3])
+            zo = rec["depth32"][i]
+            ulp = np.spacing(np.float32(max(abs(z32), abs(zo))))
+            assert abs(float(z32) - float(zo)) <= 4 * ulp
+            np.testing.assert_array_equal(res["rect"][s], rec["rect"][i])
+            checked += 1
+    return checked
+
+
+def _stage_isolated_sort(res, cams):
+    """Feed the GPU's FP32 splats to the oracle's key construction + stable
+    sort + ranges; the GPU's sorted pairs and ranges must match exactly."""
+    tile_base = 0
+    all_vals, all_tiles, all_ranges = [], [], []
+    for v, cam in enumerate(cams):
+        mine = np.nonzero(res["view"] == v)[0]
+        depth = res["rgb_d"][mine, 3].astype(np.float32)
+        keys, vals, ranges = oracle.tile_keys(cam.width, cam.height, depth, res["rect"][mine],
+                                              tile_base=tile_base)
+        all_vals.append(mine[vals])
+        all_tiles.append((keys >> np.uint64(32)).astype(np.int64))
+        nz = ranges[:, 1] > ranges[:, 0]
+        ranges = ranges.copy()
+        off = sum(len(a) for a in all_vals[:-1])
+        ranges[nz] += off
+        all_ranges.append(ranges)
+        tile_base += ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+    vals = np.concatenate(all_vals)
+    tiles = np.concatenate(all_tiles)
+    ranges = np.concatenate(all_ranges)
+    np.testing.assert_array_equal(res["sorted_splats"].astype(np.int64), vals)
+    np.testing.assert_array_equal(res["sorted_tiles"].astype(np.int64), tiles)
+    np.testing.assert_array_equal(res["ranges"].astype(np.int64), ranges)
+
+
+def _compare_images(res, f, cams, bg=(0.0, 0.0, 0.0)):
+    import gpu_helpers
+    worst, n_bad = 0.0, 0
+    for v, cam in enumerate(cams):
+        view = f["views"][v]
+        bad = gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])
+        diff = np.abs(res["images"][v] - view["image"]).max(axis=0)
+        worst = max(worst, float(diff[~bad].max()) if (~bad).any() else 0.0)
+        n_bad += int(bad.sum())
+        assert diff[~bad].max() <= 1e-4, (v, float(diff[~bad].max()))
+    return worst, n_bad
+
+
+def _stage_isolated_blend(res, cams, bg=(0.0, 0.0, 0.0)):
+    """Oracle blend (FP64) on the GPU's FP32 splat records."""
+    P0 = 0
+    for v, cam in enumerate(cams):
+        mine = np.nonzero(res["view"] == v)[0]
+        sp = {"uv": res["xy"][mine].astype(np.float64),
+              "conic": res["conic_o"][mine, :3].astype(np.float64),
+              "opacity": res["conic_o"][mine, 3].astype(np.float64),
+              "rgb": res["rgb_d"][mine, :3].astype(np.float64),
+              "depth32": res["rgb_d"][mine, 3].astype(np.float32),
+              "rect": res["rect"][mine], "order": np.arange(mine.size)}
+        o = oracle.render(cam.width, cam.height, sp, bg)
+        ok = ~o["flag"]
+        diff = np.abs(res["images"][v] - o["image"]).max(axis=0)
+        assert diff[ok].max() <= 2e-5, (v, float(diff[ok].max()))
+        P = cam.width * cam.height
+        nc = res["n_contrib"][P0:P0 + P].reshape(cam.height, cam.width)
+        np.testing.assert_array_equal(nc[ok], o["n_contrib"][ok])
+        T = res["final_T"][P0:P0 + P].reshape(cam.height, cam.width)
+        np.testing.assert_allclose(T[ok], o["T"][ok], rtol=1e-4, atol=1e-6)
+        P0 += P
+
+
+def _compare_grads(g_gpu, g_orc, names):
+    for k in names:
+        a, b = np.asarray(g_gpu[k], np.float64), np.asarray(g_orc[k], np.float64).reshape(np.shape(g_gpu[k]))
+        scale = np.abs(b).max()
+        assert scale > 0, k
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 1e-3, (k, rel)
+        bad = np.abs(a - b) > 1e-3 * np.abs(b) + 1e-5 * scale
+        assert not bad.any(), (k, int(bad.sum()), float(np.abs(a - b)[bad].max()), scale)
+
+
+# ---------------------------------------------------------------------- tests
+def test_tiny_forward_stages(built, tiny, tiny_vis):
+    import gpu_helpers
+    vis, _ = tiny_vis
+    for step in (0, 5, 9):
+        cams = tiny.cams[step]
+        res = gpu_helpers.gpu_step(tiny, step, cams, vis)
+        f = _oracle_views(tiny, step, cams, vis, 0.0)
+        near = _compare_selection_and_masks(res, f, len(cams))
+        assert near.sum() <= 3
+        assert _compare_splats(res, f, tiny, cams) > 1000
+        _stage_isolated_sort(res, cams)
+        _stage_isolated_blend(res, cams)
+        worst, n_bad = _compare_images(res, f, cams)
+        assert n_bad <= 0.05 * 320 * 192
+
+
+def test_tiny_gradients(built, tiny, tiny_vis):
+    import gpu_helpers
+    vis, _ = tiny_vis
+    step = 4
+    cams = tiny.cams[step]
+    f = _oracle_views(tiny, step, cams, vis, 0.0)
+    rng = np.random.default_rng(7)
+    dL = []
+    for v, cam in enumerate(cams):
+        d = rng.standard_normal((3, cam.height, cam.width))
+        view = f["views"][v]
+        d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+        dL.append(d)
+    g_orc = oracle.step_backward(tiny, step, f, dL, 0.0, cams=cams)
+    for v in range(len(cams)):
+        for d in dL:
+            d[:, g_orc["pixel_flags"][v]] = 0.0
+    g_orc = oracle.step_backward(tiny, step, f, dL, 0.0, cams=cams)
+    res = gpu_helpers.gpu_step(tiny, step, cams, vis, dL=dL)
+    _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                         "inst_quat", "inst_trans"))
+
+
+def test_temporal_sweep_record_matches(built, tiny):
+    """Eq. 5 over all timesteps then Eq. 6 on the GPU equals the oracle's
+    record (the same first-epoch sweep)."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    vis_o, life_o = gpu_helpers.sweep_visibility(tiny)
+    n = tiny.n
+    vis = torch.full((n, 2), 0.0, device="cuda")
+    life = torch.zeros((n, 2), device="cuda")
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
+    vis_np0 = vis.cpu().numpy()
+    np.testing.assert_array_equal(vis_np0, np.tile([-1.0, 1.0], (n, 1)).astype(np.float32))
+    r = None
+    from paper_2503_08217_gb300.render import DeviceScene
+    dev = DeviceScene.from_host(tiny)
+    near_any = np.zeros(n, bool)
+    for k in range(tiny.n_steps):
+        res = gpu_helpers.gpu_step(tiny, k, tiny.cams[k], vis_np0, life=life.cpu().numpy(), dev=dev,
+                                   renderer=r)
+        r = res["renderer"]
+        life = torch.from_numpy(res["life"]).cuda()
+        sel = oracle.select(vis_np0, float(tiny.times[k]))
+        for cam in tiny.cams[k]:
+            near_any[sel[oracle.project(tiny, sel, k, cam, 0.0)["near"]]] = True
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    v = vis.cpu().numpy()
+    ok = ~near_any
+    np.testing.assert_array_equal(v[ok], vis_o[ok])
+    np.testing.assert_array_equal(life.cpu().numpy()[ok], life_o[ok])
+    assert near_any.sum() <= 10
+
+
+def test_visibility_modes_match_oracle(built):
+    from paper_2503_08217_gb300 import binding
+    rng = np.random.default_rng(3)
+    n = 1001
+    life_np = rng.uniform(-1, 1, (n, 2)).astype(np.float32)
+    mask = rng.random(n) < 0.4
+    words = np.zeros((n + 31) // 32, np.uint32)
+    for i in np.nonzero(mask)[0]:
+        words[i >> 5] |= np.uint32(1) << np.uint32(i & 31)
+    life = torch.from_numpy(life_np.copy()).cuda()
+    vis = torch.zeros((n, 2), device="cuda")
+    t = np.float32(0.37)
+    binding.update_visibility(n, float(t), torch.from_numpy(words.view(np.int32)).cuda(), life, vis,
+                              binding.VIS_RECORD)
+    ref = life_np.copy()
+    oracle.vis_record(ref, mask, t)
+    np.testing.assert_array_equal(life.cpu().numpy(), ref)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    np.testing.assert_array_equal(vis.cpu().numpy(), oracle.vis_finalize(ref))
+    # reset of a sub-range starting at an odd index (newly added Gaussians)
+    binding.update_visibility(n - 7, 0.0, None, life[7:], vis[7:], binding.VIS_RESET)
+    np.testing.assert_array_equal(vis.cpu().numpy()[7:], np.tile([-1.0, 1.0], (n - 7, 1)))
+    np.testing.assert_array_equal(life.cpu().numpy()[7:], np.tile([1.0, -1.0], (n - 7, 1)))
+    np.testing.assert_array_equal(life.cpu().numpy()[:7], ref[:7])
+
+
+def _rig_crop(seed=1):
+    sc = scenegen.generate("mid", seed=seed, n_static=30_000, n_inst=4, n_steps=12)
+    # instances near the rig so that dynamic Gaussians are visible
+    sc.inst_trans[:, :, 2] = np.linspace(8, 40, 4)[None, :] + sc.inst_trans[:, :, 2] * 0.0 + \
+        np.arange(sc.n_steps)[:, None] * 0.5
+    sc.inst_trans[:, :, 0] = np.array([-4.0, 3.0, -2.0, 5.0])[None, :]
+    sc.means[: sc.inst_offsets[1], 2] *= 0.2      # pull the static strip closer (z in [0, 60])
+    cams = []
+    for k in range(sc.n_steps):
+        pos = (0.0, 0.0, 6.0 + 0.5 * k)
+        cams.append([make_camera(160, 96, 90.0, pos, 0.0), make_camera(96, 80, 60.0, pos, 2.1),
+                     make_camera(128, 64, 70.0, pos, -1.3)])
+    return scenegen.with_cameras(sc, cams)
+
+
+def test_multiview_rig_sh3_lod(built):
+    """Three cameras of uneven size in one call, SH degree 3, LOD r = 1 px,
+    dynamic instances: forward stages, images and gradients."""
+    import gpu_helpers
+    sc = _rig_crop()
+    vis, _ = gpu_helpers.sweep_visibility(sc, lod=1.0)
+    step = 6
+    cams = sc.cams[step]
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3))
+    f = _oracle_views(sc, step, cams, vis, 1.0, bg=(0.2, 0.1, 0.3))
+    _compare_selection_and_masks(res, f, len(cams))
+    assert _compare_splats(res, f, sc, cams) > 500
+    _stage_isolated_sort(res, cams)
+    _stage_isolated_blend(res, cams, bg=(0.2, 0.1, 0.3))
+    _compare_images(res, f, cams)
+    rng = np.random.default_rng(11)
+    dL = []
+    for v, cam in enumerate(cams):
+        d = rng.standard_normal((3, cam.height, cam.width))
+        view = f["views"][v]
+        d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+        dL.append(d)
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=(0.2, 0.1, 0.3))
+    for v in range(len(cams)):
+        dL[v][:, g_orc["pixel_flags"][v]] = 0.0
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=(0.2, 0.1, 0.3))
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3), dL=dL)
+    _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                         "inst_quat", "inst_trans"))
+
+
+def test_empty_selection_renders_background(built, tiny):
+    import gpu_helpers
+    vis = np.tile(np.array([[0.9, -0.9]], np.float32), (tiny.n, 1))   # empty windows
+    cams = tiny.cams[3]
+    rng = np.random.default_rng(0)
+    dL = [rng.standard_normal((3, 192, 320))]
+    res = gpu_helpers.gpu_step(tiny, 3, cams, vis, bg=(0.25, 0.5, 0.75), dL=dL)
+    assert res["counts"]["n_selected"] == 0 and res["counts"]["n_splats"] == 0
+    for ch, val in enumerate((0.25, 0.5, 0.75)):
+        assert np.all(res["images"][0][ch] == np.float32(val))
+    for k, g in res["grads"].items():
+        assert np.all(g == 0), k
+
+
+def test_lod_culls_everything(built, tiny, tiny_vis):
+    import gpu_helpers
+    vis, _ = tiny_vis
+    res = gpu_helpers.gpu_step(tiny, 2, tiny.cams[2], vis, lod=1e6)
+    assert res["counts"]["n_splats"] == 0 and res["counts"]["n_frustum"] > 0
+    assert np.all(res["images"][0] == 0)
+
+
+def test_lod_zero_equals_no_culling(built, tiny, tiny_vis):
+    import gpu_helpers
+    vis, _ = tiny_vis
+    a = gpu_helpers.gpu_step(tiny, 7, tiny.cams[7], vis, lod=0.0)
+    b = gpu_helpers.gpu_step(tiny, 7, tiny.cams[7], vis, lod=-5.0)
+    np.testing.assert_array_equal(a["images"][0], b["images"][0])
+    np.testing.assert_array_equal(a["keep_mask"], a["frustum_mask"])
+
+
+def test_single_gaussian_and_ragged_sizes(built):
+    """One Gaussian; image sizes that are not multiples of 16."""
+    import gpu_helpers
+    g = scenegen.generate("fd", seed=2, n_static=1, n_inst=0, n_steps=2)
+    g.means[0] = (0.1, -0.2, 5.0)
+    cams = [make_camera(37, 23, 30.0, (0.0, 0.0, 0.0), 0.0)]
+    g = scenegen.with_cameras(g, [cams, cams])
+    vis, _ = oracle.vis_reset(1)
+    res = gpu_helpers.gpu_step(g, 0, cams, vis)
+    f = _oracle_views(g, 0, cams, vis, 0.0)
+    assert res["counts"]["n_splats"] == 1
+    np.testing.assert_allclose(res["images"][0], f["views"][0]["image"], atol=1e-5)
+
+
+def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    vis, _ = tiny_vis
+    with pytest.raises(binding.S3RError) as e:
+        gpu_helpers.gpu_step(tiny, 3, tiny.cams[3], vis, max_splats=100, max_duplicates=50)
+    assert e.value.status == 2   # S3R_ERR_CAPACITY
+
+
+def test_invalid_arguments_are_rejected(built, tiny):
+    from paper_2503_08217_gb300 import binding
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer
+    dev = DeviceScene.from_host(tiny)
+    r = Renderer(tiny.n, tiny.n_inst, tiny.cams[0])
+    with pytest.raises(binding.S3RError) as e:
+        r.ws.sort()
+    assert e.value.status == 5   # S3R_ERR_STATE: sort before project
+    vis = torch.zeros((tiny.n + 1, 2), device="cuda")
+    iq = torch.from_numpy(tiny.inst_quat[0]).cuda()
+    it = torch.from_numpy(tiny.inst_trans[0]).cuda()
+    bg = torch.zeros(3, device="cuda")
+    with pytest.raises(binding.S3RError) as e:   # misaligned visibility window
+        r.forward(dev, iq, it, tiny.cams[0], 0.0, vis[1:].reshape(-1)[1:-1].reshape(-1, 2), None, 0.0, bg)
+    assert e.value.status == 1
+    too_many = tiny.cams[0] * 2
+    with pytest.raises(binding.S3RError) as e:
+        r.forward(dev, iq, it, too_many, 0.0, vis[:tiny.n], None, 0.0, bg)
+    assert e.value.status == 1
+
+
+def test_autograd_function_matches_direct_calls(built, tiny, tiny_vis):
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer, render
+    vis, _ = tiny_vis
+    dev = DeviceScene.from_host(tiny)
+    cams = tiny.cams[5]
+    r = Renderer(tiny.n, tiny.n_inst, cams)
+    params = [p.clone().requires_grad_(True) for p in dev.params()]
+    iq = torch.from_numpy(tiny.inst_quat[5]).cuda().requires_grad_(True)
+    it = torch.from_numpy(tiny.inst_trans[5]).cuda().requires_grad_(True)
+    bg = torch.zeros(3, device="cuda")
+    vis_t = torch.from_numpy(vis).cuda()
+    out = render(r, dev, cams, float(tiny.times[5]), 0.0, bg, vis_t, None, iq, it, params=params)
+    w = torch.randn_like(out)
+    (out * w).sum().backward()
+    assert params[0].grad is not None and iq.grad is not None
+    # the same through the raw calls
+    grads = {k: torch.zeros_like(v) for k, v in zip(("means", "log_scales", "quats", "opacity_logits", "sh"),
+                                                   dev.params())}
+    grads["inst_quat"] = torch.zeros_like(iq)
+    grads["inst_trans"] = torch.zeros_like(it)
+    out2 = r.forward(dev, iq.detach(), it.detach(), cams, float(tiny.times[5]), vis_t, None, 0.0, bg)
+    r.backward(dev, iq.detach(), it.detach(), bg, w, grads)
+    torch.testing.assert_close(out, out2, rtol=0, atol=0)
+    for p, k in zip(params, ("means", "log_scales", "quats", "opacity_logits", "sh")):
+        torch.testing.assert_close(p.grad, grads[k], rtol=1e-5, atol=1e-6)
+
+
+def test_cuda_graph_replay_matches_eager(built, tiny, tiny_vis):
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer
+    vis, _ = tiny_vis
+    dev = DeviceScene.from_host(tiny)
+    cams = tiny.cams[6]
+    r = Renderer(tiny.n, tiny.n_inst, cams)
+    iq = torch.from_numpy(tiny.inst_quat[6]).cuda()
+    it = torch.from_numpy(tiny.inst_trans[6]).cuda()
+    bg = torch.zeros(3, device="cuda")
+    vis_t = torch.from_numpy(vis).cuda()
+    out = torch.empty(3 * 320 * 192, device="cuda")
+    dL = torch.randn(3 * 320 * 192, device="cuda")
+    grads = {k: torch.zeros_like(v) for k, v in zip(("means", "log_scales", "quats", "opacity_logits", "sh"),
+                                                   dev.params())}
+    grads["inst_quat"] = torch.zeros_like(iq)
+    grads["inst_trans"] = torch.zeros_like(it)
+    cs = dev.c_scene()
+
+    def step():
+        for g in grads.values():
+            g.zero_()
+        r.forward(dev, iq, it, cams, float(tiny.times[6]), vis_t, None, 0.0, bg, out=out, c_scene=cs)
+        r.backward(dev, iq, it, bg, dL, grads, c_scene=cs)
+
+    step()
+    torch.cuda.synchronize()
+    ref_out = out.clone()
+    ref_g = {k: v.clone() for k, v in grads.items()}
+    g = r.capture(step)
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    torch.testing.assert_close(out, ref_out, rtol=0, atol=0)
+    for k in ref_g:
+        torch.testing.assert_close(grads[k], ref_g[k], rtol=1e-5, atol=1e-6)
