@@ -68,6 +68,10 @@ def lib():
         L.orc_project_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp,
                                            f64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_sh_basis.argtypes = [vp, vp, vp]
+        L.orc_render_pixels.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32,
+                                        vp, vp, vp, vp, vp, vp]
+        L.orc_render_backward_pixels.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp,
+                                                 vp, vp, vp, vp, vp, vp]
         L.orc_num_threads.restype = i32
         L.orc_set_margins.argtypes = [f64, f64, f64]
         _lib = L
@@ -121,7 +125,20 @@ def cam_array(cam) -> np.ndarray:
 
 
 def _scene_arrays(scene):
-    """Parameters widened (exactly) to float64; the oracle computes in FP64."""
+    """Parameters widened (exactly) to float64; the oracle computes in FP64.
+    The widened copies are kept on the scene object (large scenes)."""
+    cache = getattr(scene, "_oracle_f64", None)
+    if cache is not None and cache[0] is scene.means:
+        return cache[1]
+    arrays = _widen(scene)
+    try:
+        object.__setattr__(scene, "_oracle_f64", (scene.means, arrays))
+    except (AttributeError, TypeError):
+        pass
+    return arrays
+
+
+def _widen(scene):
     return (np.ascontiguousarray(scene.means, np.float64),
             np.ascontiguousarray(scene.log_scales, np.float64),
             np.ascontiguousarray(scene.quats, np.float64),
@@ -147,6 +164,7 @@ def project(scene, sel: np.ndarray, step: int, cam, lod_r: float, *, conventiona
 def unpack_records(rec: np.ndarray) -> dict:
     return {
         "infrustum": rec[:, 0] > 0.5, "kept": rec[:, 1] > 0.5, "near": rec[:, 2] > 0.5,
+        "near_bits": rec[:, 2].astype(np.int32),
         "p": rec[:, 3:6], "uv": rec[:, 6:8], "conic": rec[:, 8:11], "opacity": rec[:, 11],
         "rgb": rec[:, 12:15], "radius": rec[:, 15], "rect": rec[:, 16:20].astype(np.int32),
         "sigma_lod": rec[:, 20], "depth32": rec[:, 21].astype(np.float32),
@@ -191,6 +209,40 @@ def render(width: int, height: int, sp: dict, bg=(0.0, 0.0, 0.0), *, tiled=False
         lib().orc_render(width, height, n, _P(u), _P(v), _P(conic), _P(opac), _P(rgb), _P(depth),
                          _P(order), _P(rect), _P(bgv), _P(img), _P(T), _P(nc), _P(flag))
     return {"image": img, "T": T, "n_contrib": nc, "flag": flag.astype(bool)}
+
+
+def render_pixels(sp: dict, px, py, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Eq. 2 at chosen pixels only (rgb [n,3], T, n_contrib, flag)."""
+    u, v, conic, opac, rgb, depth, order, rect = _splat_args(sp)
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    m = px.shape[0]
+    out = np.zeros((m, 3))
+    T = np.zeros(m)
+    nc = np.zeros(m, np.int32)
+    flag = np.zeros(m, np.int32)
+    bgv = np.asarray(bg, np.float64)
+    lib().orc_render_pixels(0, 0, u.shape[0], _P(u), _P(v), _P(conic), _P(opac), _P(rgb), _P(depth),
+                            _P(order), _P(rect), _P(bgv), m, _P(px), _P(py), _P(out), _P(T), _P(nc),
+                            _P(flag))
+    return {"rgb": out, "T": T, "n_contrib": nc, "flag": flag.astype(bool)}
+
+
+def render_backward_pixels(sp: dict, px, py, dL, bg=(0.0, 0.0, 0.0)) -> dict:
+    """Per-splat gradients of sum_q dL[q] . image(px[q], py[q])."""
+    u, v, conic, opac, rgb, depth, order, rect = _splat_args(sp)
+    n = u.shape[0]
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    d = np.ascontiguousarray(dL, np.float64)
+    g = {"uv": np.zeros((n, 2)), "conic": np.zeros((n, 3)), "opacity": np.zeros(n),
+         "rgb": np.zeros((n, 3))}
+    bgv = np.asarray(bg, np.float64)
+    lib().orc_render_backward_pixels(n, _P(u), _P(v), _P(conic), _P(opac), _P(rgb), _P(depth),
+                                     _P(order), _P(rect), _P(bgv), px.shape[0], _P(px), _P(py),
+                                     _P(d), _P(g["uv"]), _P(g["conic"]), _P(g["opacity"]),
+                                     _P(g["rgb"]))
+    return g
 
 
 def tile_keys(width: int, height: int, depth32, rect, tile_base: int = 0):

@@ -170,7 +170,9 @@ void sh_basis(const double d[3], double Y[16], double dY[16][3]) {
 struct Proj {
   int infrustum;   // M_t bit: z > near, det > 0, non-empty tile rectangle
   int kept;        // infrustum and sigma_lod >= r
-  int near_boundary;  // some integer decision lies within a tiny margin of its boundary
+  int near_boundary;  // bits set when a decision lies within a tiny margin of its
+                      // threshold: 1 near plane, 2 left, 4 right, 8 top, 16 bottom
+                      // rect edge, 32 radius ceil, 64 LOD threshold
   double p[3];     // camera-space position
   double u, v;
   double conic[3]; // (A, B, C): power = -0.5 (A dx^2 + C dy^2) - B dx dy
@@ -224,8 +226,8 @@ void project_core(const Cam& cam, const double A[3][3], const double b[3], const
   for (int i = 0; i < 3; ++i) o.b[i] = b[i];
   for (int r = 0; r < 3; ++r) o.p[r] = A[r][0] * mu[0] + A[r][1] * mu[1] + A[r][2] * mu[2] + b[r];
   const double x = o.p[0], y = o.p[1], z = o.p[2];
-  const double margin = 1e-5;
-  if (std::fabs(z - cam.near_z) < margin * cam.near_z) o.near_boundary = 1;
+  const double margin = 3e-6;
+  if (std::fabs(z - cam.near_z) < margin * cam.near_z) o.near_boundary |= 1;
   if (!(z > cam.near_z)) return;
 
   // 3D covariance Sigma = R S S^T R^T
@@ -291,7 +293,7 @@ void project_core(const Cam& cam, const double A[3][3], const double b[3], const
   const double lam = mid + std::sqrt(std::max(0.1, mid * mid - det));
   const double r3 = 3.0 * std::sqrt(lam);
   o.radius = std::ceil(r3);
-  if (near_int(r3, margin * r3)) o.near_boundary = 1;
+  if (near_int(r3, margin * r3)) o.near_boundary |= 32;
   o.u = cam.fx * x / z + cam.cx;
   o.v = cam.fy * y / z + cam.cy;
   const int gx = (cam.w + kTile - 1) / kTile, gy = (cam.h + kTile - 1) / kTile;
@@ -303,13 +305,15 @@ void project_core(const Cam& cam, const double A[3][3], const double b[3], const
   const double qy0 = (o.v - o.radius) / kTile, qy1 = (o.v + o.radius + kTile - 1) / kTile;
   const double tol_x = margin * (std::fabs(o.u) + o.radius + kTile) / kTile;
   const double tol_y = margin * (std::fabs(o.v) + o.radius + kTile) / kTile;
-  if (near_int(qx0, tol_x) || near_int(qx1, tol_x) || near_int(qy0, tol_y) || near_int(qy1, tol_y))
-    o.near_boundary = 1;
+  if (near_int(qx0, tol_x)) o.near_boundary |= 2;
+  if (near_int(qx1, tol_x)) o.near_boundary |= 4;
+  if (near_int(qy0, tol_y)) o.near_boundary |= 8;
+  if (near_int(qy1, tol_y)) o.near_boundary |= 16;
   o.rect[0] = edge(qx0, gx); o.rect[1] = edge(qy0, gy);
   o.rect[2] = edge(qx1, gx); o.rect[3] = edge(qy1, gy);
   if ((o.rect[2] - o.rect[0]) * (o.rect[3] - o.rect[1]) <= 0) return;
   o.infrustum = 1;
-  if (lod_r > 0 && std::fabs(o.sigma_lod - lod_r) < margin * lod_r) o.near_boundary = 1;
+  if (lod_r > 0 && std::fabs(o.sigma_lod - lod_r) < margin * lod_r) o.near_boundary |= 64;
   o.kept = (o.sigma_lod >= lod_r);
   o.opacity = 1.0 / (1.0 + std::exp(-opac_logit));
   // colour: SH evaluated on the direction from the camera centre, expressed in
@@ -885,6 +889,81 @@ void orc_render_backward(int W, int H, int n, const double* u, const double* v,
       g_opac[i] += a[5];
       g_rgb[3 * i] += a[6]; g_rgb[3 * i + 1] += a[7]; g_rgb[3 * i + 2] += a[8];
     }
+}
+
+// The same blend for a chosen set of pixels only: the tile lists are built
+// just for the tiles those pixels lie in. For spot checks at full size.
+void orc_render_pixels(int W, int H, int n, const double* u, const double* v, const double* conic,
+                       const double* opac, const double* rgb, const float* depth32,
+                       const int64_t* order, const int32_t* rect, const double* bg, int n_pix,
+                       const int32_t* px, const int32_t* py, double* out_rgb /*[n_pix,3]*/,
+                       double* out_T, int32_t* out_ncontrib, int32_t* out_flag) {
+  SplatView s{n, u, v, conic, opac, rgb, depth32, order, rect};
+  const std::vector<int> all = depth_order(s);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int q = 0; q < n_pix; ++q) {
+    const int tx = px[q] / kTile, ty = py[q] / kTile;
+    std::vector<int> list;
+    for (int i : all)
+      if (covers(rect + 4 * i, tx, ty)) list.push_back(i);
+    PixelTrace tr;
+    blend_pixel(s, list, px[q] + 0.5, py[q] + 0.5, tr);
+    double C[3] = {0, 0, 0};
+    for (size_t c = 0; c < tr.contrib.size(); ++c) {
+      const int i = tr.list[tr.contrib[c]];
+      for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * tr.alpha[c] * tr.T[c];
+    }
+    for (int ch = 0; ch < 3; ++ch) out_rgb[3 * q + ch] = C[ch] + tr.Tfinal * bg[ch];
+    out_T[q] = tr.Tfinal;
+    out_ncontrib[q] = tr.n_contrib;
+    out_flag[q] = tr.flag;
+  }
+  (void)W; (void)H;
+}
+
+// Gradient of sum_q dL[q] . image(px[q], py[q]) w.r.t. the splats, for a
+// chosen set of pixels (accumulated, same layout as orc_render_backward).
+void orc_render_backward_pixels(int n, const double* u, const double* v, const double* conic,
+                                const double* opac, const double* rgb, const float* depth32,
+                                const int64_t* order, const int32_t* rect, const double* bg,
+                                int n_pix, const int32_t* px, const int32_t* py,
+                                const double* dL /*[n_pix,3]*/, double* g_uv, double* g_conic,
+                                double* g_opac, double* g_rgb) {
+  SplatView s{n, u, v, conic, opac, rgb, depth32, order, rect};
+  const std::vector<int> all = depth_order(s);
+  for (int q = 0; q < n_pix; ++q) {
+    const int tx = px[q] / kTile, ty = py[q] / kTile;
+    std::vector<int> list;
+    for (int i : all)
+      if (covers(rect + 4 * i, tx, ty)) list.push_back(i);
+    PixelTrace tr;
+    const double fx = px[q] + 0.5, fy = py[q] + 0.5;
+    blend_pixel(s, list, fx, fy, tr);
+    const double* dC = dL + 3 * q;
+    const int m = (int)tr.contrib.size();
+    double suffix[3] = {0, 0, 0};
+    for (int c = m - 1; c >= 0; --c) {
+      const int i = tr.list[tr.contrib[c]];
+      const double al = tr.alpha[c], T = tr.T[c];
+      double dalpha = 0;
+      for (int ch = 0; ch < 3; ++ch) {
+        dalpha += dC[ch] * (rgb[3 * i + ch] * T - suffix[ch] / (1.0 - al) - tr.Tfinal * bg[ch] / (1.0 - al));
+        g_rgb[3 * i + ch] += al * T * dC[ch];
+      }
+      for (int ch = 0; ch < 3; ++ch) suffix[ch] += rgb[3 * i + ch] * al * T;
+      if (tr.capped[c]) continue;
+      const double G = tr.G[c];
+      g_opac[i] += G * dalpha;
+      const double dpow = opac[i] * dalpha * G;
+      const double dx = u[i] - fx, dy = v[i] - fy;
+      const double A = conic[3 * i], B = conic[3 * i + 1], C = conic[3 * i + 2];
+      g_uv[2 * i] += dpow * (-A * dx - B * dy);
+      g_uv[2 * i + 1] += dpow * (-C * dy - B * dx);
+      g_conic[3 * i] += dpow * (-0.5 * dx * dx);
+      g_conic[3 * i + 1] += dpow * (-dx * dy);
+      g_conic[3 * i + 2] += dpow * (-0.5 * dy * dy);
+    }
+  }
 }
 
 // Projection backward for one view: from the splat gradients of the kept

@@ -263,12 +263,12 @@ _TYPESTR = {torch.float32: "<f4", torch.int32: "<i4", torch.uint8: "|u1", torch.
 
 
 class _DeviceArray:
-    """A read-only view of device memory for torch.as_tensor (CUDA array
-    interface); used only to copy workspace intermediates out for tests."""
+    """A view of device memory for torch.as_tensor (CUDA array interface);
+    used only to copy workspace intermediates out, never written through."""
 
     def __init__(self, ptr: int, count: int, dtype: torch.dtype):
         self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": _TYPESTR[dtype],
-                                         "data": (int(ptr), True), "version": 3,
+                                         "data": (int(ptr), False), "version": 3,
                                          "strides": None}
 
 

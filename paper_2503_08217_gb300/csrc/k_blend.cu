@@ -118,6 +118,33 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
   }
 }
 
+// Sum eight values over the warp with 9 shuffles instead of 8 x 5: at each
+// butterfly level every lane keeps half of its remaining values and sends the
+// other half to its partner. On return, lane l holds the warp total of value
+// index 4*bit4(l) + 2*bit3(l) + bit2(l); lanes 4m (m = 0..7) hold value m.
+__device__ __forceinline__ float warp_sum8_transposed(const float v[8], uint32_t lane) {
+  const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u;
+  float k4[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float send = b4 ? v[j] : v[j + 4];
+    const float keep = b4 ? v[j + 4] : v[j];
+    k4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float k2[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float send = b3 ? k4[j] : k4[j + 2];
+    const float keep = b3 ? k4[j + 2] : k4[j];
+    k2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b2 ? k2[0] : k2[1];
+  float k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
+  k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
+  return k1;
+}
+
 __device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z),
                "f"(w)
@@ -222,30 +249,12 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
         }
       }
       if (__any_sync(0xffffffffu, act)) {
+        const float eight[8] = {g_u, g_v, g_a, g_b, g_c, g_o, g_r, g_g};
+        const float tot = warp_sum8_transposed(eight, lane);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          g_u += __shfl_xor_sync(0xffffffffu, g_u, o);
-          g_v += __shfl_xor_sync(0xffffffffu, g_v, o);
-          g_a += __shfl_xor_sync(0xffffffffu, g_a, o);
-          g_b += __shfl_xor_sync(0xffffffffu, g_b, o);
-          g_c += __shfl_xor_sync(0xffffffffu, g_c, o);
-          g_o += __shfl_xor_sync(0xffffffffu, g_o, o);
-          g_r += __shfl_xor_sync(0xffffffffu, g_r, o);
-          g_g += __shfl_xor_sync(0xffffffffu, g_g, o);
-          g_bl += __shfl_xor_sync(0xffffffffu, g_bl, o);
-        }
-        if (lane == 0) {
-          float* sg = s_g[j];
-          atomicAdd(sg + 0, g_u);
-          atomicAdd(sg + 1, g_v);
-          atomicAdd(sg + 2, g_a);
-          atomicAdd(sg + 3, g_b);
-          atomicAdd(sg + 4, g_c);
-          atomicAdd(sg + 5, g_o);
-          atomicAdd(sg + 6, g_r);
-          atomicAdd(sg + 7, g_g);
-          atomicAdd(sg + 8, g_bl);
-        }
+        for (int o = 16; o > 0; o >>= 1) g_bl += __shfl_xor_sync(0xffffffffu, g_bl, o);
+        if ((lane & 3u) == 0) atomicAdd(&s_g[j][lane >> 2], tot);
+        if (lane == 0) atomicAdd(&s_g[j][8], g_bl);
       }
     }
     __syncthreads();

@@ -102,7 +102,7 @@ __device__ __forceinline__ float4 quat_backward(float4 q, const float dR[9]) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(kThreads) k_project_bwd(const __grid_constant__ ViewSet vs,
+__global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_constant__ ViewSet vs,
                                                           BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nk = a.n_inst + 1;

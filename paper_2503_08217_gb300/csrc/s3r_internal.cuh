@@ -125,17 +125,24 @@ struct s3r_workspace {
 
 namespace s3r {
 // Records a CUDA event before a kernel launch and another after it when the
-// workspace's timing hook is on.
+// workspace's timing hook is on. The events are recorded as external events,
+// so under stream capture they become event-record nodes of the graph and
+// time every replay.
 struct KernelTimer {
   s3r_workspace* ws;
   int id;
   cudaStream_t st;
+  unsigned flags = 0;
   KernelTimer(s3r_workspace* w, int kid, cudaStream_t s) : ws(w), id(kid), st(s) {
-    if (ws->timing) cudaEventRecord(ws->ev[2 * id], st);
+    if (!ws->timing) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags(ws->ev[2 * id], st, flags);
   }
   ~KernelTimer() {
     if (ws->timing) {
-      cudaEventRecord(ws->ev[2 * id + 1], st);
+      cudaEventRecordWithFlags(ws->ev[2 * id + 1], st, flags);
       ws->ev_used[id] = 1;
     }
   }

@@ -75,17 +75,19 @@ def _raise_status(c):
         raise binding.S3RError(2, f"capacity exceeded ({c})")
 
 
+def popcount32(a):
+    a = np.asarray(a, np.uint32)
+    if hasattr(np, "bitwise_count"):
+        return np.bitwise_count(a).astype(np.int64)
+    return np.unpackbits(a.view(np.uint8).reshape(-1, 4), axis=1).sum(1).astype(np.int64)
+
+
 def splat_gids(res):
-    """Gaussian id and view of every GPU splat (from the per-Gaussian masks)."""
-    gids = np.zeros(len(res["view"]), np.int64)
-    for j, g in enumerate(res["selected"]):
-        m = int(res["keep_mask"][j])
-        s = int(res["splat_start"][j])
-        while m:
-            gids[s] = g
-            s += 1
-            m &= m - 1
-    return gids
+    """Gaussian id of every GPU splat: a selected Gaussian's splats are
+    contiguous from its splat_start, one per kept view."""
+    counts = popcount32(res["keep_mask"])
+    assert np.array_equal(np.cumsum(counts) - counts, res["splat_start"].astype(np.int64))
+    return np.repeat(res["selected"], counts)
 
 
 def sweep_visibility(scene, cams_fn=None, lod=0.0):
@@ -106,22 +108,41 @@ def sweep_visibility(scene, cams_fn=None, lod=0.0):
 
 def bad_pixels(cam, rec, flag):
     """Pixels to leave out of an image comparison: the blend flagged them, or
-    they lie in a tile that a Gaussian with a near-threshold projection
-    decision may or may not cover (its rectangle grown by one tile)."""
+    they lie in a tile whose membership in a flagged Gaussian's list may flip
+    between FP32 and FP64: the tile column/row on either side of a flagged
+    rectangle edge, the whole ring for a flagged radius, the whole rectangle
+    (grown by one tile) for a near-plane or LOD flag."""
     bad = flag.copy()
     H, W = cam.height, cam.width
     gx, gy = (W + 15) // 16, (H + 15) // 16
-    near = rec["near"] & (rec["infrustum"] | (rec["p"][:, 2] > 0))
-    for i in np.nonzero(near)[0]:
-        x0, y0, x1, y1 = rec["rect"][i]
-        if x1 <= x0 or y1 <= y0:
-            # decision flipped near an edge of the image: grow around the centre
-            u, v = rec["uv"][i]
-            x0 = x1 = int(np.clip(u // 16, 0, gx - 1))
-            y0 = y1 = int(np.clip(v // 16, 0, gy - 1))
-            x1 += 1
-            y1 += 1
-        x0, y0 = max(0, x0 - 1), max(0, y0 - 1)
-        x1, y1 = min(gx, x1 + 1), min(gy, y1 + 1)
-        bad[y0 * 16:y1 * 16, x0 * 16:x1 * 16] = True
+    bits = rec.get("near_bits", rec["near"].astype(np.int32) * 1)
+    cand = np.nonzero((bits != 0) & (rec["infrustum"] | (rec["p"][:, 2] > 0)))[0]
+
+    def mark(xa, ya, xb, yb):
+        xa, ya = max(0, xa), max(0, ya)
+        xb, yb = min(gx, xb), min(gy, yb)
+        if xb > xa and yb > ya:
+            bad[ya * 16:yb * 16, xa * 16:xb * 16] = True
+
+    for i in cand:
+        b = int(bits[i])
+        x0, y0, x1, y1 = (int(q) for q in rec["rect"][i])
+        if (b & (1 | 64)) or x1 <= x0 or y1 <= y0:
+            if x1 <= x0 or y1 <= y0:   # a rect that may be empty on one side: around the centre
+                u, v = rec["uv"][i]
+                r = int(rec["radius"][i]) // 16 + 2
+                x0, x1 = int(u // 16) - r, int(u // 16) + r + 1
+                y0, y1 = int(v // 16) - r, int(v // 16) + r + 1
+            mark(x0 - 1, y0 - 1, x1 + 1, y1 + 1)
+            continue
+        if b & 32:
+            b |= 2 | 4 | 8 | 16
+        if b & 2:
+            mark(x0 - 1, y0 - 1, x0 + 1, y1 + 1)
+        if b & 4:
+            mark(x1 - 1, y0 - 1, x1 + 1, y1 + 1)
+        if b & 8:
+            mark(x0 - 1, y0 - 1, x1 + 1, y0 + 1)
+        if b & 16:
+            mark(x0 - 1, y1 - 1, x1 + 1, y1 + 1)
     return bad
