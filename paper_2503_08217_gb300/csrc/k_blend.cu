@@ -21,7 +21,8 @@
 namespace s3r {
 namespace {
 
-constexpr int kThreads = kTilePixels;   // 256
+constexpr int kThreads = kTilePixels / 2;   // 128: two pixels per thread
+constexpr int kBatch = 256;                   // splats staged per batch
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
@@ -47,74 +48,187 @@ __device__ __forceinline__ int view_of_tile(const ViewSet& vs, int tile) {
   return v;
 }
 
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.69314718055994531f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Shared-memory form of a splat for the blend: the conic is pre-scaled so that
+// the exponent is evaluated directly in base 2:
+//   a = (u, v, A2, B2), b = (C2, opacity, r, g), c = b-channel, with
+//   A2 = -A/2 log2(e), B2 = -B log2(e), C2 = -C/2 log2(e)
+// so that power * log2(e) = dx (A2 dx + B2 dy) + C2 dy^2 and G = 2^that.
+__device__ __forceinline__ void stage_splat(const float2 xy, const float4 co, const float4 rgb,
+                                            float4& a, float4& b, float& c) {
+  a = make_float4(xy.x, xy.y, -0.5f * kLog2e * co.x, -kLog2e * co.y);
+  b = make_float4(-0.5f * kLog2e * co.z, co.w, rgb.x, rgb.y);
+  c = rgb.z;
+}
+
+// Exponent (base 2) and alpha of a staged splat at pixel centre (fx, fy).
+// The forward and the backward call this same function, so both take the
+// same FP32 decisions.
+struct SplatEval {
+  float dx, dy, p, G, raw, alpha;
+};
+__device__ __forceinline__ SplatEval eval_splat(const float4 a, const float4 b, float fx, float fy) {
+  SplatEval e;
+  e.dx = a.x - fx;
+  e.dy = a.y - fy;
+  e.p = fmaf(e.dx, fmaf(a.z, e.dx, a.w * e.dy), b.x * e.dy * e.dy);
+  e.G = ex2_approx(e.p);
+  e.raw = b.y * e.G;
+  e.alpha = fminf(kAlphaMax, e.raw);
+  return e;
+}
+
+// Bounding box of the region where a staged splat can reach alpha >= 1/255:
+// the ellipse d^T Q d <= 2 ln(255 o) (Q the conic), grown by a small relative
+// and absolute margin so that FP32 rounding of the exact test can never fall
+// outside it. Empty (xmin = +inf) when o < 1/255.
+__device__ __forceinline__ float4 alpha_box(const float2 xy, const float4 co) {
+  const float o = co.w;
+  if (!(o * 255.f > 1.f)) return make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+  const float L2 = 2.f * __logf(255.f * o);
+  const float det = co.x * co.z - co.y * co.y;
+  const float ex = sqrtf(fmaxf(L2 * co.z / det, 0.f)) * 1.002f + 0.02f;
+  const float ey = sqrtf(fmaxf(L2 * co.x / det, 0.f)) * 1.002f + 0.02f;
+  return make_float4(xy.x - ex, xy.x + ex, xy.y - ey, xy.y + ey);
+}
+
+// Pixel layout: a tile is four 8x8 blocks, one per warp; lane (x = l & 7,
+// y = l >> 3) owns the pixels (x, y) and (x, y + 4) of its warp's block.
+struct TilePixels {
+  int px, py0, py1;
+  bool in0, in1;
+  float fx, fy0, fy1;
+  float bx0, bx1, by0, by1;   // pixel-centre extent of the warp's block
+};
+__device__ __forceinline__ TilePixels tile_pixels(const ViewInfo& vi, int tx, int ty, int warp,
+                                                  uint32_t lane) {
+  TilePixels t;
+  const int X0 = tx * kTile + (warp & 1) * 8, Y0 = ty * kTile + (warp >> 1) * 8;
+  t.px = X0 + (int)(lane & 7u);
+  t.py0 = Y0 + (int)(lane >> 3);
+  t.py1 = t.py0 + 4;
+  t.in0 = t.px < vi.width && t.py0 < vi.height;
+  t.in1 = t.px < vi.width && t.py1 < vi.height;
+  t.fx = t.px + 0.5f;
+  t.fy0 = t.py0 + 0.5f;
+  t.fy1 = t.py1 + 0.5f;
+  t.bx0 = X0 + 0.5f;
+  t.bx1 = X0 + 7.5f;
+  t.by0 = Y0 + 0.5f;
+  t.by1 = Y0 + 7.5f;
+  return t;
+}
+
+__device__ __forceinline__ bool box_misses(const float4 b, const TilePixels& t) {
+  return b.x > t.bx1 || b.y < t.bx0 || b.z > t.by1 || b.w < t.by0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
                                                         BlendArgs a) {
-  __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_co[kThreads];
-  __shared__ float4 s_rgb[kThreads];
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float4 s_box[kBatch];
+  __shared__ float s_c[kBatch];
   const int tile = blockIdx.x;
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
   const int lt = tile - vi.tile_base;
-  const int tx = lt % vi.gx, ty = lt / vi.gx;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = px < vi.width && py < vi.height;
-  const float fx = px + 0.5f, fy = py + 0.5f;
+  const uint32_t lane = lane_id();
+  const TilePixels P = tile_pixels(vi, lt % vi.gx, lt / vi.gx, threadIdx.x >> 5, lane);
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
 
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  uint32_t contributor = 0, last = 0;
-  bool done = !inside;
-  for (int b0 = 0; b0 < n; b0 += kThreads) {
-    if (__syncthreads_count(done) == kThreads) break;
-    const int i = b0 + threadIdx.x;
-    if (i < n) {
-      const uint32_t s = a.sorted_splats[range.x + i];
-      s_xy[threadIdx.x] = a.sp_xy[s];
-      s_co[threadIdx.x] = a.sp_conic_o[s];
-      s_rgb[threadIdx.x] = a.sp_rgb_d[s];
+  float T0 = 1.f, T1 = 1.f;
+  float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
+  int last0 = 0, last1 = 0, end0 = n, end1 = n;   // end: positions visited
+  bool done0 = !P.in0, done1 = !P.in1;
+  if (done0) end0 = 0;
+  if (done1) end1 = 0;
+  for (int b0 = 0; b0 < n; b0 += kBatch) {
+    if (__syncthreads_count(done0 && done1) == kThreads) break;
+    for (int i = threadIdx.x; i < kBatch && b0 + i < n; i += kThreads) {
+      const uint32_t s = a.sorted_splats[range.x + b0 + i];
+      const float2 xy = a.sp_xy[s];
+      const float4 co = a.sp_conic_o[s];
+      stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
+      s_box[i] = alpha_box(xy, co);
     }
     __syncthreads();
-    const int m = min(kThreads, n - b0);
-    for (int j = 0; j < m && !done; ++j) {
-      ++contributor;
-      const float2 xy = s_xy[j];
-      const float4 co = s_co[j];
-      const float dx = xy.x - fx, dy = xy.y - fy;
-      const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-      if (power > 0.f) continue;
-      const float alpha = fminf(kAlphaMax, co.w * __expf(power));
-      if (alpha < kAlphaMin) continue;
-      const float nT = T * (1.f - alpha);
-      if (nT < kTStop) {
-        done = true;
-        break;
+    const int m = min(kBatch, n - b0);
+    for (int j = 0; j < m; ++j) {
+      if (done0 && done1) break;
+      if (box_misses(s_box[j], P)) continue;          // warp-uniform
+      const float4 sa = s_a[j], sb = s_b[j];
+      const float cb = s_c[j];
+      const int pos = b0 + j + 1;
+      {
+        const SplatEval e = eval_splat(sa, sb, P.fx, P.fy0);
+        const bool ok = !done0 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
+        const float nT = T0 * (1.f - e.alpha);
+        const bool stop = ok && (nT < kTStop);
+        const bool blend = ok && !stop;
+        const float w = blend ? e.alpha * T0 : 0.f;
+        C00 = fmaf(sb.z, w, C00);
+        C01 = fmaf(sb.w, w, C01);
+        C02 = fmaf(cb, w, C02);
+        T0 = blend ? nT : T0;
+        last0 = blend ? pos : last0;
+        end0 = stop ? pos : end0;
+        done0 = done0 || stop;
       }
-      const float4 c = s_rgb[j];
-      const float w = alpha * T;
-      C0 = fmaf(c.x, w, C0);
-      C1 = fmaf(c.y, w, C1);
-      C2 = fmaf(c.z, w, C2);
-      T = nT;
-      last = contributor;
+      {
+        const SplatEval e = eval_splat(sa, sb, P.fx, P.fy1);
+        const bool ok = !done1 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
+        const float nT = T1 * (1.f - e.alpha);
+        const bool stop = ok && (nT < kTStop);
+        const bool blend = ok && !stop;
+        const float w = blend ? e.alpha * T1 : 0.f;
+        C10 = fmaf(sb.z, w, C10);
+        C11 = fmaf(sb.w, w, C11);
+        C12 = fmaf(cb, w, C12);
+        T1 = blend ? nT : T1;
+        last1 = blend ? pos : last1;
+        end1 = stop ? pos : end1;
+        done1 = done1 || stop;
+      }
     }
   }
-  // work accounting: one 64-bit atomic per warp
-  unsigned long long visited = contributor;
+  // work accounting: (pixel, splat) pairs visited, one 64-bit atomic per warp
+  unsigned long long visited = (unsigned long long)end0 + (unsigned long long)end1;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) visited += __shfl_xor_sync(0xffffffffu, visited, o);
-  if ((threadIdx.x & 31) == 0 && visited) atomicAdd(a.pairs, visited);
-  if (inside) {
-    const int64_t plane = (int64_t)vi.width * vi.height;
-    const int64_t pix = (int64_t)py * vi.width + px;
+  if (lane == 0 && visited) atomicAdd(a.pairs, visited);
+  const int64_t plane = (int64_t)vi.width * vi.height;
+  if (P.in0) {
+    const int64_t pix = (int64_t)P.py0 * vi.width + P.px;
     float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
-    o[0] = fmaf(T, a.bg[0], C0);
-    o[plane] = fmaf(T, a.bg[1], C1);
-    o[2 * plane] = fmaf(T, a.bg[2], C2);
-    a.final_T[vi.pix_base + pix] = T;
-    a.n_contrib[vi.pix_base + pix] = last;
+    o[0] = fmaf(T0, a.bg[0], C00);
+    o[plane] = fmaf(T0, a.bg[1], C01);
+    o[2 * plane] = fmaf(T0, a.bg[2], C02);
+    a.final_T[vi.pix_base + pix] = T0;
+    a.n_contrib[vi.pix_base + pix] = (uint32_t)last0;
+  }
+  if (P.in1) {
+    const int64_t pix = (int64_t)P.py1 * vi.width + P.px;
+    float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
+    o[0] = fmaf(T1, a.bg[0], C10);
+    o[plane] = fmaf(T1, a.bg[1], C11);
+    o[2 * plane] = fmaf(T1, a.bg[2], C12);
+    a.final_T[vi.pix_base + pix] = T1;
+    a.n_contrib[vi.pix_base + pix] = (uint32_t)last1;
   }
 }
 
@@ -145,126 +259,151 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], uint32_t
   return k1;
 }
 
+// red.shared.add.f32 executed only where `pred` holds, without a branch.
+__device__ __forceinline__ void red_shared_if(float* addr, float v, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.f32 [%0], %1;\n\t}" ::"r"(sa),
+      "f"(v), "r"((int)pred)
+      : "memory");
+}
+
 __device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z),
                "f"(w)
                : "memory");
 }
 
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ ViewSet vs,
-                                                        BlendArgs a) {
-  __shared__ float2 s_xy[kThreads];
-  __shared__ float4 s_co[kThreads];
-  __shared__ float4 s_rgb[kThreads];
-  __shared__ uint32_t s_id[kThreads];
-  __shared__ float s_g[kThreads][9];
-  __shared__ uint32_t s_max;
-  const int tile = blockIdx.x;
-  const int v = view_of_tile(vs, tile);
-  const ViewInfo& vi = vs.v[v];
-  const int lt = tile - vi.tile_base;
-  const int tx = lt % vi.gx, ty = lt / vi.gx;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = px < vi.width && py < vi.height;
-  const float fx = px + 0.5f, fy = py + 0.5f;
-  const uint2 range = a.ranges[tile];
+// Per-pixel state of the reverse walk.
+struct BwdPixel {
+  float T, T_final, bg_dot, d0, d1, d2;
+  float acc0, acc1, acc2, last_alpha, lc0, lc1, lc2;
+  int last;
+};
 
-  float T = 1.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
-  uint32_t last = 0;
-  if (threadIdx.x == 0) s_max = 0;
+// One splat's contribution to the adjoints at one pixel (reverse order),
+// accumulated into g[0..8]; updates the pixel's recovered transmittance and
+// the colour behind it only where the splat was blended in the forward.
+__device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sa,
+                                          const float4 sb, float cb, bool act, float g[9]) {
+  const float inv = rcp_approx(1.f - e.alpha);
+  q.T = act ? q.T * inv : q.T;
+  const float w = e.alpha * q.T;
+  const float la = q.last_alpha;
+  q.acc0 = act ? fmaf(la, q.lc0, (1.f - la) * q.acc0) : q.acc0;
+  q.acc1 = act ? fmaf(la, q.lc1, (1.f - la) * q.acc1) : q.acc1;
+  q.acc2 = act ? fmaf(la, q.lc2, (1.f - la) * q.acc2) : q.acc2;
+  q.lc0 = act ? sb.z : q.lc0;
+  q.lc1 = act ? sb.w : q.lc1;
+  q.lc2 = act ? cb : q.lc2;
+  q.last_alpha = act ? e.alpha : q.last_alpha;
+  float dalpha = ((sb.z - q.acc0) * q.d0 + (sb.w - q.acc1) * q.d1 + (cb - q.acc2) * q.d2) * q.T;
+  dalpha = fmaf(-q.T_final * inv, q.bg_dot, dalpha);
+  const bool live = act && !(e.raw > kAlphaMax);         // alpha = 0.99 is constant
+  const float dpow = live ? sb.y * e.G * dalpha : 0.f;    // dL/d(power), natural units
+  const float dpl = dpow * kLn2;
+  g[0] += dpl * fmaf(2.f * sa.z, e.dx, sa.w * e.dy);     // d/du
+  g[1] += dpl * fmaf(sa.w, e.dx, 2.f * sb.x * e.dy);     // d/dv
+  g[2] -= 0.5f * dpow * e.dx * e.dx;                     // d/dA
+  g[3] -= dpow * e.dx * e.dy;                            // d/dB
+  g[4] -= 0.5f * dpow * e.dy * e.dy;                     // d/dC
+  g[5] += live ? e.G * dalpha : 0.f;                     // d/dopacity
+  g[6] += act ? w * q.d0 : 0.f;                          // d/drgb
+  g[7] += act ? w * q.d1 : 0.f;
+  g[8] += act ? w * q.d2 : 0.f;
+}
+
+__device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const ViewInfo& vi,
+                                         int px, int py, bool inside) {
+  q.T = 1.f; q.d0 = q.d1 = q.d2 = 0.f; q.last = 0;
   if (inside) {
     const int64_t plane = (int64_t)vi.width * vi.height;
     const int64_t pix = (int64_t)py * vi.width + px;
     const float* g = a.dL + 3 * (int64_t)vi.pix_base + pix;
-    d0 = g[0];
-    d1 = g[plane];
-    d2 = g[2 * plane];
-    T = a.final_T[vi.pix_base + pix];
-    last = a.n_contrib[vi.pix_base + pix];
+    q.d0 = g[0];
+    q.d1 = g[plane];
+    q.d2 = g[2 * plane];
+    q.T = a.final_T[vi.pix_base + pix];
+    q.last = (int)a.n_contrib[vi.pix_base + pix];
   }
-  __syncthreads();
-  if (last) atomicMax(&s_max, last);
-  const float T_final = T;
-  const float bg_dot = a.bg[0] * d0 + a.bg[1] * d1 + a.bg[2] * d2;
-  float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;          // colour behind the current splat
-  float last_alpha = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
-  __syncthreads();
-  const int n = (int)s_max;
-  const uint32_t lane = lane_id();
+  q.T_final = q.T;
+  q.bg_dot = a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2;
+  q.acc0 = q.acc1 = q.acc2 = 0.f;
+  q.last_alpha = q.lc0 = q.lc1 = q.lc2 = 0.f;
+}
 
-  for (int hi = n; hi > 0; hi -= kThreads) {
-    const int lo = max(0, hi - kThreads);
+__global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ ViewSet vs,
+                                                        BlendArgs a) {
+  __shared__ float4 s_a[kBatch];
+  __shared__ float4 s_b[kBatch];
+  __shared__ float4 s_box[kBatch];
+  __shared__ float s_c[kBatch];
+  __shared__ uint32_t s_id[kBatch];
+  __shared__ float s_g[kBatch][9];
+  __shared__ int s_max;
+  const int tile = blockIdx.x;
+  const int v = view_of_tile(vs, tile);
+  const ViewInfo& vi = vs.v[v];
+  const int lt = tile - vi.tile_base;
+  const uint32_t lane = lane_id();
+  const TilePixels P = tile_pixels(vi, lt % vi.gx, lt / vi.gx, threadIdx.x >> 5, lane);
+  const uint2 range = a.ranges[tile];
+
+  BwdPixel q0, q1;
+  bwd_init(q0, a, vi, P.px, P.py0, P.in0);
+  bwd_init(q1, a, vi, P.px, P.py1, P.in1);
+  if (threadIdx.x == 0) s_max = 0;
+  __syncthreads();
+  int wlast = max(q0.last, q1.last);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+  if (lane == 0 && wlast) atomicMax(&s_max, wlast);
+  __syncthreads();
+  const int n = s_max;
+
+  for (int hi = n; hi > 0; hi -= kBatch) {
+    const int lo = max(0, hi - kBatch);
     const int m = hi - lo;
     __syncthreads();
-    if (threadIdx.x < m) {
-      const uint32_t s = a.sorted_splats[range.x + lo + threadIdx.x];
-      s_id[threadIdx.x] = s;
-      s_xy[threadIdx.x] = a.sp_xy[s];
-      s_co[threadIdx.x] = a.sp_conic_o[s];
-      s_rgb[threadIdx.x] = a.sp_rgb_d[s];
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const uint32_t s = a.sorted_splats[range.x + lo + i];
+      s_id[i] = s;
+      const float2 xy = a.sp_xy[s];
+      const float4 co = a.sp_conic_o[s];
+      stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
+      s_box[i] = alpha_box(xy, co);
     }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) s_g[threadIdx.x][q] = 0.f;
+    for (int i = threadIdx.x; i < kBatch * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
-    for (int j = m - 1; j >= 0; --j) {
+    // this warp's splats end at its own last contributor
+    for (int j = min(m, wlast - lo) - 1; j >= 0; --j) {
+      if (box_misses(s_box[j], P)) continue;                 // warp-uniform
+      const float4 sa = s_a[j], sb = s_b[j];
+      const float cb = s_c[j];
       const int pos = lo + j;
-      bool act = inside && pos < (int)last;
-      float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f;
-      float g_r = 0.f, g_g = 0.f, g_bl = 0.f;
-      if (act) {
-        const float2 xy = s_xy[j];
-        const float4 co = s_co[j];
-        const float dx = xy.x - fx, dy = xy.y - fy;
-        const float power = -0.5f * (co.x * dx * dx + co.z * dy * dy) - co.y * dx * dy;
-        const float G = __expf(power);
-        const float raw = co.w * G;
-        const float alpha = fminf(kAlphaMax, raw);
-        act = !(power > 0.f) && !(alpha < kAlphaMin);
-        if (act) {
-          const float4 c = s_rgb[j];
-          const float one_m = 1.f - alpha;
-          T = T / one_m;
-          const float w = alpha * T;
-          g_r = w * d0;
-          g_g = w * d1;
-          g_bl = w * d2;
-          acc0 = last_alpha * lc0 + (1.f - last_alpha) * acc0;
-          acc1 = last_alpha * lc1 + (1.f - last_alpha) * acc1;
-          acc2 = last_alpha * lc2 + (1.f - last_alpha) * acc2;
-          lc0 = c.x; lc1 = c.y; lc2 = c.z;
-          float dalpha = (c.x - acc0) * d0 + (c.y - acc1) * d1 + (c.z - acc2) * d2;
-          dalpha *= T;
-          last_alpha = alpha;
-          dalpha -= T_final / one_m * bg_dot;
-          if (!(raw > kAlphaMax)) {
-            g_o = G * dalpha;
-            const float dpow = co.w * G * dalpha;
-            g_u = dpow * (-co.x * dx - co.y * dy);
-            g_v = dpow * (-co.z * dy - co.y * dx);
-            g_a = dpow * (-0.5f * dx * dx);
-            g_b = dpow * (-dx * dy);
-            g_c = dpow * (-0.5f * dy * dy);
-          }
-        }
-      }
-      if (__any_sync(0xffffffffu, act)) {
-        const float eight[8] = {g_u, g_v, g_a, g_b, g_c, g_o, g_r, g_g};
-        const float tot = warp_sum8_transposed(eight, lane);
+      const SplatEval e0 = eval_splat(sa, sb, P.fx, P.fy0);
+      const SplatEval e1 = eval_splat(sa, sb, P.fx, P.fy1);
+      const bool act0 = (pos < q0.last) && !(e0.p > 0.f) && !(e0.alpha < kAlphaMin);
+      const bool act1 = (pos < q1.last) && !(e1.p > 0.f) && !(e1.alpha < kAlphaMin);
+      if (!__any_sync(0xffffffffu, act0 || act1)) continue;  // warp-uniform
+      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bwd_pixel(q0, e0, sa, sb, cb, act0, g);
+      bwd_pixel(q1, e1, sa, sb, cb, act1, g);
+      const float tot = warp_sum8_transposed(g, lane);
+      float g8 = g[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g_bl += __shfl_xor_sync(0xffffffffu, g_bl, o);
-        if ((lane & 3u) == 0) atomicAdd(&s_g[j][lane >> 2], tot);
-        if (lane == 0) atomicAdd(&s_g[j][8], g_bl);
-      }
+      for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
+      red_shared_if(&s_g[j][lane >> 2], tot, (lane & 3u) == 0);
+      red_shared_if(&s_g[j][8], g8, lane == 0);
     }
     __syncthreads();
-    if (threadIdx.x < m) {
-      const float* sg = s_g[threadIdx.x];
+    for (int i = threadIdx.x; i < m; i += kThreads) {
+      const float* sg = s_g[i];
       bool any = false;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) any |= sg[q] != 0.f;
+      for (int r = 0; r < 9; ++r) any |= sg[r] != 0.f;
       if (any) {
-        float* dst = a.sp_grad + 12 * (size_t)s_id[threadIdx.x];
+        float* dst = a.sp_grad + 12 * (size_t)s_id[i];
         red_v4(dst, sg[0], sg[1], sg[2], sg[3]);
         red_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
         atomicAdd(dst + 8, sg[8]);

@@ -65,16 +65,21 @@ __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ 
     }
     if (lane == 0) s_warp[warp] = count;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t total = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_warp[w];
-        s_warp[w] = total;
-        total += c;
+    if (warp == 0) {
+      const uint32_t c = lane < kWarps ? s_warp[lane] : 0u;
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
       }
-      const uint32_t prefix = lookback_prefix(lookback, 1, tile, tag, total, ctr);
-      s_base = prefix;
-      if (tile == n_tiles - 1) ctr[kCtrSelected] = prefix + total;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t prefix = warp_lookback(lookback, tile, tag, total, ctr);
+      if (lane < kWarps) s_warp[lane] = incl - c;
+      if (lane == 0) {
+        s_base = prefix;
+        if (tile == n_tiles - 1) ctr[kCtrSelected] = prefix + total;
+      }
     }
     __syncthreads();
     uint32_t out = s_base + s_warp[warp];

@@ -48,7 +48,56 @@ struct ProjArgs {
   uint32_t* ctr;
   unsigned long long* lookback;
   int64_t cap_splats;
+  const InstMat* mats;      // [n_views][n_inst+1], from k_compose
 };
+
+// W_v * P_k for every view v and segment k (k = 0: identity pose), and the
+// camera centre in the segment's frame, computed in FP64 once per call. One
+// block per view, one thread per segment.
+__global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __restrict__ pose_q,
+                          const float* __restrict__ pose_t, int n_inst, InstMat* __restrict__ out) {
+  const int v = blockIdx.x;
+  const int nk = n_inst + 1;
+  const float* Vf = vs.v[v].V;
+  double V[12];
+  for (int i = 0; i < 12; ++i) V[i] = Vf[i];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[3] = {0, 0, 0};
+    if (k > 0) {
+      const float4 qf = pose_q[k - 1];
+      double w = qf.x, x = qf.y, y = qf.z, z = qf.w;
+      const double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+      w *= inv; x *= inv; y *= inv; z *= inv;
+      R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+      R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+      R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+      for (int r = 0; r < 3; ++r) t[r] = pose_t[3 * (k - 1) + r];
+    }
+    double A[9], b[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c)
+        A[3 * r + c] = V[4 * r] * R[c] + V[4 * r + 1] * R[3 + c] + V[4 * r + 2] * R[6 + c];
+      b[r] = V[4 * r] * t[0] + V[4 * r + 1] * t[1] + V[4 * r + 2] * t[2] + V[4 * r + 3];
+    }
+    // c = -A^{-1} b by cofactors
+    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8],
+                 c02 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    const double Ai[9] = {c00 / det, (A[2] * A[7] - A[1] * A[8]) / det, (A[1] * A[5] - A[2] * A[4]) / det,
+                          c01 / det, (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                          c02 / det, (A[1] * A[6] - A[0] * A[7]) / det, (A[0] * A[4] - A[1] * A[3]) / det};
+    InstMat m;
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) m.m[4 * r + c] = (float)A[3 * r + c];
+      m.m[4 * r + 3] = (float)b[r];
+      const double cr = -(Ai[3 * r] * b[0] + Ai[3 * r + 1] * b[1] + Ai[3 * r + 2] * b[2]);
+      m.c[r] = (float)cr;
+      m.c_lo[r] = (float)(cr - (double)m.c[r]);
+    }
+    m.pad[0] = m.pad[1] = 0.f;
+    out[v * nk + k] = m;
+  }
+}
 
 template <int DEG>
 __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ ViewSet vs, ProjArgs a) {
@@ -61,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
   __shared__ uint32_t s_tile, s_base, s_frustum;
   constexpr int K = sh_count(DEG);
 
-  compose_all(vs, a.pose_q, a.pose_t, a.n_inst, mats);
+  load_mats(a.mats, mats, vs.n_views * nk);
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   if (threadIdx.x == 0) s_frustum = 0;
@@ -135,16 +184,21 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
     if (lane == 31) s_warp[warp] = incl;
     if (lane == 0 && nfr) atomicAdd(&s_frustum, nfr);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t total = 0;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_warp[w];
-        s_warp[w] = total;
-        total += c;
+    if (warp == 0) {
+      const uint32_t c = lane < kWarps ? s_warp[lane] : 0u;
+      uint32_t wincl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wincl, o);
+        if (lane >= (uint32_t)o) wincl += y;
       }
-      const uint32_t prefix = lookback_prefix(a.lookback, 1, tile, tag, total, a.ctr);
-      s_base = prefix;
-      if (tile == n_tiles - 1) a.ctr[kCtrSplats] = prefix + total;
+      const uint32_t total = __shfl_sync(0xffffffffu, wincl, 31);
+      const uint32_t prefix = warp_lookback(a.lookback, tile, tag, total, a.ctr);
+      if (lane < kWarps) s_warp[lane] = wincl - c;
+      if (lane == 0) {
+        s_base = prefix;
+        if (tile == n_tiles - 1) a.ctr[kCtrSplats] = prefix + total;
+      }
     }
     __syncthreads();
     uint32_t s = s_base + s_warp[warp] + incl - nkept;
@@ -176,7 +230,9 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
         m &= m - 1;
         const InstMat& M = mats[v * nk + k];
         const Proj2D p = project_view(M, mu, RS, vs.v[v]);
-        float dx = mu[0] - M.c[0], dy = mu[1] - M.c[1], dz = mu[2] - M.c[2];
+        float rp[3];
+        rel_pos(M, mu, rp);
+        float dx = rp[0], dy = rp[1], dz = rp[2];
         const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= inv; dy *= inv; dz *= inv;
         float Y[16];
@@ -279,6 +335,14 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.ctr = ws->ctr;
   a.lookback = ws->lookback;
   a.cap_splats = ws->cap.max_splats;
+  a.mats = reinterpret_cast<const InstMat*>(ws->mats);
+  {
+    KernelTimer timer(ws, kKCompose, st);
+    k_compose<<<ws->n_views, 128, 0, st>>>(ws->views, a.pose_q, a.pose_t, sc->n_inst,
+                                           reinterpret_cast<InstMat*>(ws->mats));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   switch (sc->sh_degree) {
     case 0: return launch_deg<0>(ws, a, st);
     case 1: return launch_deg<1>(ws, a, st);

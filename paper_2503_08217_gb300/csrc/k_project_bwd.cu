@@ -36,6 +36,7 @@ struct BwdArgs {
   uint32_t* ctr;
   float* pose_dM;          // [n_views][n_inst+1][12]
   s3r_grads g;
+  const InstMat* mats;     // from the forward's k_compose (same poses)
 };
 
 // d/d(direction) of sum_k w_k Y_k(d) for the real SH basis of sh_basis<DEG>.
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
   __shared__ uint32_t s_tile;
   constexpr int K = sh_count(DEG);
 
-  compose_all(vs, a.pose_q, a.pose_t, a.n_inst, mats);
+  load_mats(a.mats, mats, vs.n_views * nk);
   for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) s_dM[i] = 0.f;
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   __syncthreads();
@@ -181,9 +182,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       const float* A = M.m;   // rows at 0, 4, 8; translation at 3, 7, 11
 
       // ---- forward recompute (the same arithmetic as project_view)
-      const float x = fmaf(A[0], mu[0], fmaf(A[1], mu[1], fmaf(A[2], mu[2], A[3])));
-      const float y = fmaf(A[4], mu[0], fmaf(A[5], mu[1], fmaf(A[6], mu[2], A[7])));
-      const float z = fmaf(A[8], mu[0], fmaf(A[9], mu[1], fmaf(A[10], mu[2], A[11])));
+      float rp[3], x, y, z;
+      rel_pos(M, mu, rp);
+      cam_pos(M, rp, x, y, z);
       float B[9];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 
       // ---- colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir from the camera centre
       {
-        const float vx = mu[0] - M.c[0], vy = mu[1] - M.c[1], vz = mu[2] - M.c[2];
+        const float vx = rp[0], vy = rp[1], vz = rp[2];
         const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
         const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
         float Y[16];
@@ -459,6 +460,7 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.ctr = ws->ctr;
   a.pose_dM = ws->pose_dM;
   a.g = *g;
+  a.mats = reinterpret_cast<const InstMat*>(ws->mats);
   const int nk = ws->n_inst + 1;
   cudaError_t e = cudaMemsetAsync(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)ws->n_views * nk, st);
   if (e != cudaSuccess) return e;

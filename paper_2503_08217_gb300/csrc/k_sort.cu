@@ -143,11 +143,18 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
   }
 }
 
-// Expand depth-sorted splats into (view-tile id, splat) pairs. Each tile of
-// 256 consecutive sorted splats owns one contiguous output range (block scan
-// of tile counts + decoupled look-back); the range is written with one
-// thread per output element (binary search for its splat), so writes are
-// coalesced and balanced however many tiles a splat covers.
+// Expand depth-sorted splats into (view-tile id, splat) pairs. A CTA takes
+// 1024 consecutive sorted splats (4 per thread): a block scan of their tile
+// counts and a decoupled look-back give the CTA one contiguous output range.
+// Each thread then writes 8 consecutive outputs, locating its first splat by
+// binary search and advancing an incremental cursor after that; the tile id of
+// output r of a splat with rectangle width w is base + (r / w) * gx + r % w,
+// with r / w taken from a float reciprocal and one integer correction step.
+constexpr int kDupThreads = 256;
+constexpr int kDupPer = 4;                            // splats per thread
+constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per tile
+constexpr int kDupItems = 8;                          // outputs per thread per step
+
 struct DupArgs {
   const uint32_t* sorted_splats;
   const uint2* sp_rect;
@@ -161,22 +168,16 @@ struct DupArgs {
   unsigned long long* lookback;
 };
 
-__global__ void __launch_bounds__(256) k_duplicate(const __grid_constant__ ViewSet vs, DupArgs a) {
-  __shared__ uint32_t s_excl[257];
-  __shared__ uint32_t s_splat[256];
-  __shared__ uint2 s_rect[256];
-  __shared__ int s_view[256];
+__global__ void __launch_bounds__(kDupThreads) k_duplicate(const __grid_constant__ ViewSet vs,
+                                                           DupArgs a) {
+  __shared__ uint32_t s_excl[kDupSplats + 1];
+  __shared__ uint4 s_meta[kDupSplats];   // (splat, first tile id, gx | w << 16, 1/w bits)
   __shared__ uint32_t s_hist[4][kRadix];
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile, s_base;
-  __shared__ int s_gx[S3R_MAX_VIEWS], s_tb[S3R_MAX_VIEWS];
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-  if (threadIdx.x < vs.n_views) {
-    s_gx[threadIdx.x] = vs.v[threadIdx.x].gx;
-    s_tb[threadIdx.x] = vs.v[threadIdx.x].tile_base;
-  }
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
-  const int64_t n_tiles = (n + 255) / 256;
+  const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
   const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
   bool overflow = false;
   for (;;) {
@@ -184,52 +185,92 @@ __global__ void __launch_bounds__(256) k_duplicate(const __grid_constant__ ViewS
     __syncthreads();
     const int64_t tile = s_tile;
     if (tile >= n_tiles) break;
-    const int64_t i = tile * 256 + threadIdx.x;
-    uint32_t cnt = 0;
-    if (i < n) {
-      const uint32_t s = a.sorted_splats[i];
-      const uint2 r = a.sp_rect[s];
-      const uint32_t w = (r.y & 0xffffu) - (r.x & 0xffffu);
-      const uint32_t h = (r.y >> 16) - (r.x >> 16);
-      cnt = w * h;
-      s_splat[threadIdx.x] = s;
-      s_rect[threadIdx.x] = r;
-      s_view[threadIdx.x] = a.sp_view[s];
+    // ---- counts of this thread's 4 splats
+    const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
+    uint32_t cnt[kDupPer], run = 0;
+#pragma unroll
+    for (int k = 0; k < kDupPer; ++k) {
+      const int64_t i = i0 + k;
+      cnt[k] = 0;
+      uint4 meta = make_uint4(0u, 0u, 1u << 16, __float_as_uint(1.f));
+      if (i < n) {
+        const uint32_t sp = a.sorted_splats[i];
+        const uint2 r = a.sp_rect[sp];
+        const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16;
+        const uint32_t w = (r.y & 0xffffu) - x0, h = (r.y >> 16) - y0;
+        const ViewInfo& vi = vs.v[a.sp_view[sp]];
+        cnt[k] = w * h;
+        const uint32_t first = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
+        meta = make_uint4(sp, first, (uint32_t)vi.gx | (w << 16),
+                          __float_as_uint(w ? 1.f / (float)w : 1.f));
+      }
+      s_meta[threadIdx.x * kDupPer + k] = meta;
+      run += cnt[k];
     }
     uint32_t total;
-    const uint32_t ex = block_excl_scan(cnt, s_tmp, &total);
-    s_excl[threadIdx.x] = ex;
-    if (threadIdx.x == 0) {
-      s_excl[256] = total;
-      const uint32_t prefix = lookback_prefix(a.lookback, 1, tile, tag, total, a.ctr);
-      s_base = prefix;
-      if (tile == n_tiles - 1) a.ctr[kCtrDups] = prefix + total;
+    uint32_t ex = block_excl_scan(run, s_tmp, &total);
+#pragma unroll
+    for (int k = 0; k < kDupPer; ++k) {
+      s_excl[threadIdx.x * kDupPer + k] = ex;
+      ex += cnt[k];
+    }
+    if (threadIdx.x < 32) {
+      const uint32_t prefix = warp_lookback(a.lookback, tile, tag, total, a.ctr);
+      if (threadIdx.x == 0) {
+        s_excl[kDupSplats] = total;
+        s_base = prefix;
+        if (tile == n_tiles - 1) a.ctr[kCtrDups] = prefix + total;
+      }
     }
     __syncthreads();
     const uint32_t base = s_base;
-    for (uint32_t o = threadIdx.x; o < total; o += 256) {
-      // last q with s_excl[q] <= o
-      int lo = 0, hi = 256;
+    // ---- expansion: 8 consecutive outputs per thread
+    for (uint32_t c0 = 0; c0 < total; c0 += kDupThreads * kDupItems) {
+      const uint32_t o0 = c0 + threadIdx.x * kDupItems;
+      if (o0 >= total) continue;
+      int lo = 0, hi = kDupSplats;          // last q with s_excl[q] <= o0
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
-        if (s_excl[mid] <= o) lo = mid; else hi = mid;
+        if (s_excl[mid] <= o0) lo = mid; else hi = mid;
       }
-      const uint32_t rr = o - s_excl[lo];
-      const uint2 r = s_rect[lo];
-      const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16;
-      const uint32_t w = (r.y & 0xffffu) - x0;
-      const uint32_t ty = y0 + rr / w, tx = x0 + rr % w;
-      const int v = s_view[lo];
-      const uint32_t tile_id = (uint32_t)s_tb[v] + ty * (uint32_t)s_gx[v] + tx;
-      const int64_t pos = (int64_t)base + o;
-      if (pos < a.cap_dups) {
-        __stcs(a.dup_key + pos, tile_id);
-        __stcs(a.dup_val + pos, s_splat[lo]);
-        for (int p = 0; p < a.tile_passes; ++p)
-          atomicAdd(&s_hist[p][(tile_id >> (8 * p)) & 0xffu], 1u);
-      } else {
-        overflow = true;
+      int q = lo;
+      uint32_t q_end = s_excl[q + 1];
+      uint4 meta = s_meta[q];
+      uint32_t hi_digit = 0xffffffffu, hi_count = 0;
+      const uint32_t o_end = min(o0 + kDupItems, total);
+      for (uint32_t o = o0; o < o_end; ++o) {
+        while (o >= q_end) {
+          ++q;
+          q_end = s_excl[q + 1];
+          meta = s_meta[q];
+        }
+        const uint32_t rr = o - s_excl[q];
+        const uint32_t w = meta.z >> 16, gx = meta.z & 0xffffu;
+        uint32_t row = (uint32_t)(((float)rr + 0.5f) * __uint_as_float(meta.w));
+        row -= (row * w > rr) ? 1u : 0u;          // one correction step keeps it exact
+        row += ((row + 1u) * w <= rr) ? 1u : 0u;  // for any rectangle size
+        const uint32_t tile_id = meta.y + row * gx + (rr - row * w);
+        const int64_t pos = (int64_t)base + o;
+        if (pos < a.cap_dups) {
+          __stcs(a.dup_key + pos, tile_id);
+          __stcs(a.dup_val + pos, meta.x);
+          atomicAdd(&s_hist[0][tile_id & 0xffu], 1u);
+          if (a.tile_passes > 1) {           // higher digits change rarely along a run
+            const uint32_t d = (tile_id >> 8) & 0xffu;
+            if (d != hi_digit) {
+              if (hi_count) atomicAdd(&s_hist[1][hi_digit], hi_count);
+              hi_digit = d;
+              hi_count = 0;
+            }
+            ++hi_count;
+            for (int p = 2; p < a.tile_passes; ++p)
+              atomicAdd(&s_hist[p][(tile_id >> (8 * p)) & 0xffu], 1u);
+          }
+        } else {
+          overflow = true;
+        }
       }
+      if (hi_count) atomicAdd(&s_hist[1][hi_digit], hi_count);
     }
     __syncthreads();
   }
@@ -268,7 +309,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   // occupancy is queried once (outside any graph capture: the first call)
   static thread_local int sweep_per_sm = 0, dup_per_sm = 0;
   if (!sweep_per_sm) sweep_per_sm = per_sm_for((const void*)k_onesweep, kSortThreads);
-  if (!dup_per_sm) dup_per_sm = per_sm_for((const void*)k_duplicate, 256);
+  if (!dup_per_sm) dup_per_sm = per_sm_for((const void*)k_duplicate, kDupThreads);
   const int g_sweep = ws->num_sms * sweep_per_sm;
   // depth digits on the splats: 4 passes, result back in buffer 0
   for (int p = 0; p < 4; ++p) {
@@ -305,7 +346,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   const int g_dup = ws->num_sms * dup_per_sm;
   {
     KernelTimer timer(ws, kKDuplicate, st);
-    k_duplicate<<<g_dup, 256, 0, st>>>(ws->views, d);
+    k_duplicate<<<g_dup, kDupThreads, 0, st>>>(ws->views, d);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // tile digits on the pairs

@@ -61,7 +61,7 @@ cudaError_t alloc(s3r_workspace* ws, T** p, int64_t count) {
 }
 
 const char* const kKernelNames[kKCount] = {
-    "begin", "temporal_compact", "project", "sort_depth_pass0", "sort_depth_pass1",
+    "begin", "temporal_compact", "compose", "project", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
     "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "blend_fwd", "zero_splat_grads",
     "blend_bwd", "project_bwd", "pose_chain"};
@@ -74,14 +74,14 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM};
+                  ws->sp_grad, ws->pose_dM, ws->mats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
 // Dynamic shared memory the projection kernels need for n_views x segments.
 size_t proj_smem_bytes(int n_views, int n_inst) {
-  return (size_t)n_views * (n_inst + 1) * (64 + 48) + 4 * (size_t)(n_inst + 2) + 16;
+  return (size_t)n_views * (n_inst + 1) * (80 + 48) + 4 * (size_t)(n_inst + 2) + 16;
 }
 
 s3r_status check_scene(const s3r_workspace* ws, const s3r_scene* sc) {
@@ -184,6 +184,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->n_contrib, cap->max_pixels);
   S3R_ALLOC(ws->sp_grad, 12 * S);
   S3R_ALLOC(ws->pose_dM, (int64_t)cap->max_views * nk * 12);
+  S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
 #undef S3R_ALLOC
   for (int i = 0; i < 2 * kKCount; ++i) {
     if ((e = cudaEventCreate(&ws->ev[i])) != cudaSuccess) {

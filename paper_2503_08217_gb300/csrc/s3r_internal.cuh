@@ -71,7 +71,7 @@ constexpr int kHistCount = 8;
 
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
-  kKBegin = 0, kKCompact, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
+  kKBegin = 0, kKCompact, kKCompose, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
   kKTile0, kKTile1, kKTile2, kKTile3, kKRanges, kKBlendFwd, kKZeroGrads, kKBlendBwd,
   kKProjectBwd, kKPoseChain, kKCount
 };
@@ -106,6 +106,7 @@ struct s3r_workspace {
   uint32_t* n_contrib;      // [P]
   float* sp_grad;           // [S*12]
   float* pose_dM;           // [views*(inst+1)*12]
+  float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   int64_t bytes;
   // host-side state of the current call sequence
   s3r::ViewSet views;
@@ -221,6 +222,58 @@ __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, i
     --k;
   }
   st_relaxed(mine, lb_word(tag, 2, prefix + aggregate));
+  return prefix;
+}
+
+__device__ __forceinline__ uint32_t lane_id_() {
+  uint32_t l;
+  asm("mov.u32 %0, %%laneid;" : "=r"(l));
+  return l;
+}
+
+// Warp-cooperative form of lookback_prefix for one running sum over tiles at
+// stride 1: all 32 lanes of ONE warp call it with the same arguments. Each
+// step reads 32 predecessors at once and stops at the nearest one that has
+// published its inclusive prefix, so a walk over w unfinished predecessors
+// takes ceil(w/32) dependent loads instead of w. Returns the exclusive
+// prefix in every lane; lane 0 publishes the inclusive value.
+__device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int64_t tile,
+                                                  uint32_t tag, uint32_t aggregate, uint32_t* ctr) {
+  const uint32_t lane = lane_id_();
+  if (lane == 0) st_relaxed(words + tile, lb_word(tag, tile == 0 ? 2u : 1u, aggregate));
+  if (tile == 0) return 0;
+  uint32_t prefix = 0;
+  int64_t base = tile - 1;
+  int spins = 0;
+  for (;;) {
+    const int64_t k = base - (int64_t)lane;
+    uint32_t flag = 2, val = 0;   // before tile 0: an inclusive zero
+    if (k >= 0) {
+      const unsigned long long w = ld_relaxed(words + k);
+      const bool ok = (uint32_t)(w >> 34) == tag;
+      flag = ok ? (uint32_t)(w >> 32) & 3u : 0u;
+      val = (uint32_t)w;
+    }
+    const uint32_t incl = __ballot_sync(0xffffffffu, flag == 2u);
+    const uint32_t waiting = __ballot_sync(0xffffffffu, flag == 0u);
+    const int first = incl ? __ffs(incl) - 1 : 32;          // nearest inclusive
+    const uint32_t need = first == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first));
+    if (waiting & need) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(ctr + kCtrStatus, kStatusTimeout);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    uint32_t part = ((int)lane <= first) ? val : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    prefix += part;
+    if (first < 32) break;
+    base -= 32;
+  }
+  if (lane == 0) st_relaxed(words + tile, lb_word(tag, 2u, prefix + aggregate));
   return prefix;
 }
 

@@ -7,12 +7,18 @@
 
 namespace s3r {
 
-// Composed instance matrix W_{t,i} = W_t W_{t,i2g} (3x4, row-major) and the
-// camera centre expressed in the instance's frame, -A^T b (A is a rotation).
+// Composed instance matrix W_{t,i} = W_t W_{t,i2g} (3x4, row-major, rows
+// [A | b]) and the camera centre in the instance's frame, c = -A^{-1} b, as an
+// unevaluated sum c_hi + c_lo of two floats. Both are computed in FP64 once per
+// call (k_compose). Camera-space positions are evaluated as
+// A ((mu - c_hi) - c_lo): for Gaussians near the camera mu - c_hi is exact
+// (Sterbenz), so positions far from the world origin do not lose their
+// camera-relative precision the way A mu + b does.
 struct __align__(16) InstMat {
   float m[12];
-  float c[3];
-  float pad;
+  float c[3];     // c_hi
+  float c_lo[3];
+  float pad[2];
 };
 
 constexpr float kDilation = 0.3f;
@@ -29,37 +35,26 @@ __device__ __forceinline__ void quat_to_rot(float4 q, float R[9]) {
   R[6] = 2.f * (xz - wy); R[7] = 2.f * (yz + wx); R[8] = 1.f - 2.f * (xx + yy);
 }
 
-// Compose W_v * P_k for all views v and segments k (k = 0: identity pose)
-// into `mats` ([n_views][n_inst+1]), cooperatively over the CTA.
-__device__ __forceinline__ void compose_all(const ViewSet& vs, const float4* pose_q,
-                                            const float* pose_t, int n_inst, InstMat* mats) {
-  const int nk = n_inst + 1;
-  for (int i = threadIdx.x; i < vs.n_views * nk; i += blockDim.x) {
-    const int v = i / nk, k = i - v * nk;
-    const float* V = vs.v[v].V;
-    float P[12] = {1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 0.f, 1.f, 0.f};
-    if (k > 0) {
-      float R[9];
-      quat_to_rot(pose_q[k - 1], R);
-      for (int r = 0; r < 3; ++r) {
-        P[4 * r] = R[3 * r];
-        P[4 * r + 1] = R[3 * r + 1];
-        P[4 * r + 2] = R[3 * r + 2];
-        P[4 * r + 3] = pose_t[3 * (k - 1) + r];
-      }
-    }
-    InstMat m;
-    for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < 4; ++c)
-        m.m[4 * r + c] = fmaf(V[4 * r], P[c], fmaf(V[4 * r + 1], P[4 + c], V[4 * r + 2] * P[8 + c]));
-      m.m[4 * r + 3] += V[4 * r + 3];
-    }
-    // camera centre in the instance frame: -A^T b
-    for (int c = 0; c < 3; ++c)
-      m.c[c] = -(m.m[c] * m.m[3] + m.m[4 + c] * m.m[7] + m.m[8 + c] * m.m[11]);
-    m.pad = 0.f;
-    mats[i] = m;
-  }
+// Camera-relative position d = (mu - c_hi) - c_lo in the instance frame.
+__device__ __forceinline__ void rel_pos(const InstMat& M, const float mu[3], float d[3]) {
+  d[0] = (mu[0] - M.c[0]) - M.c_lo[0];
+  d[1] = (mu[1] - M.c[1]) - M.c_lo[1];
+  d[2] = (mu[2] - M.c[2]) - M.c_lo[2];
+}
+
+// Camera-space position p = A d.
+__device__ __forceinline__ void cam_pos(const InstMat& M, const float d[3], float& x, float& y,
+                                        float& z) {
+  x = fmaf(M.m[0], d[0], fmaf(M.m[1], d[1], M.m[2] * d[2]));
+  y = fmaf(M.m[4], d[0], fmaf(M.m[5], d[1], M.m[6] * d[2]));
+  z = fmaf(M.m[8], d[0], fmaf(M.m[9], d[1], M.m[10] * d[2]));
+}
+
+// Copy the composed matrices of the call from global to shared memory.
+__device__ __forceinline__ void load_mats(const InstMat* __restrict__ g, InstMat* s, int count) {
+  const float4* src = reinterpret_cast<const float4*>(g);
+  float4* dst = reinterpret_cast<float4*>(s);
+  for (int i = threadIdx.x; i < count * (int)(sizeof(InstMat) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
 // Segment (0 = static, k = instance k) of Gaussian `gid` from the offsets.
@@ -91,9 +86,9 @@ __device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[
                                                const float RS[9], const ViewInfo& vi) {
   Proj2D o;
   o.infrustum = false;
-  o.x = fmaf(M.m[0], mu[0], fmaf(M.m[1], mu[1], fmaf(M.m[2], mu[2], M.m[3])));
-  o.y = fmaf(M.m[4], mu[0], fmaf(M.m[5], mu[1], fmaf(M.m[6], mu[2], M.m[7])));
-  o.z = fmaf(M.m[8], mu[0], fmaf(M.m[9], mu[1], fmaf(M.m[10], mu[2], M.m[11])));
+  float d[3];
+  rel_pos(M, mu, d);
+  cam_pos(M, d, o.x, o.y, o.z);
   if (!(o.z > vi.near_z)) return o;
   // B = A * RS (A = rotation part of M): camera-space covariance is B B^T
   float B[9];
