@@ -168,9 +168,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
     }
     __syncthreads();
     const int m = min(kBatch, n - b0);
-    for (int j = 0; j < m; ++j) {
-      if (done0 && done1) break;
-      if (box_misses(s_box[j], P)) continue;          // warp-uniform
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      if (__all_sync(0xffffffffu, done0 && done1)) break;
+      // which of the next 32 splats can reach this warp's 8x8 block
+      uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane < m && !box_misses(s_box[c0 + lane], P));
+      while (todo) {
+      const int j = c0 + __ffs(todo) - 1;
+      todo &= todo - 1;
       const float4 sa = s_a[j], sb = s_b[j];
       const float cb = s_c[j];
       const int pos = b0 + j + 1;
@@ -203,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         last1 = blend ? pos : last1;
         end1 = stop ? pos : end1;
         done1 = done1 || stop;
+      }
       }
     }
   }
@@ -375,9 +380,16 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
     }
     for (int i = threadIdx.x; i < kBatch * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
-    // this warp's splats end at its own last contributor
-    for (int j = min(m, wlast - lo) - 1; j >= 0; --j) {
-      if (box_misses(s_box[j], P)) continue;                 // warp-uniform
+    // this warp's splats end at its own last contributor; walk them back to
+    // front, 32 at a time, visiting only those whose footprint box meets the
+    // warp's 8x8 block
+    for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
+      const int c0 = max(0, c1 - 31);
+      uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane <= c1 && !box_misses(s_box[c0 + lane], P));
+      while (todo) {
+      const int bit = 31 - __clz(todo);
+      todo &= ~(1u << bit);
+      const int j = c0 + bit;
       const float4 sa = s_a[j], sb = s_b[j];
       const float cb = s_c[j];
       const int pos = lo + j;
@@ -395,6 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
       for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
       red_shared_if(&s_g[j][lane >> 2], tot, (lane & 3u) == 0);
       red_shared_if(&s_g[j][8], g8, lane == 0);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += kThreads) {

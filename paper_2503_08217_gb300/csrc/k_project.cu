@@ -49,6 +49,7 @@ struct ProjArgs {
   unsigned long long* lookback;
   int64_t cap_splats;
   const InstMat* mats;      // [n_views][n_inst+1], from k_compose
+  int32_t* tile_diff;       // per-tile pair counts as a difference array
 };
 
 // W_v * P_k for every view v and segment k (k = 0: identity pose), and the
@@ -102,15 +103,16 @@ __global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __re
 template <int DEG>
 __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ ViewSet vs, ProjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  InstMat* mats = reinterpret_cast<InstMat*>(smem_raw);
+  // composed matrices are read through L1: a CTA's Gaussians are contiguous,
+  // so they touch the matrices of very few instances
+  const InstMat* __restrict__ mats = a.mats;
   const int nk = a.n_inst + 1;
-  uint32_t* s_off = reinterpret_cast<uint32_t*>(mats + vs.n_views * nk);   // [n_inst+2]
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(smem_raw);   // [n_inst+2]
   __shared__ uint32_t s_hist[4][kRadix];
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_tile, s_base, s_frustum;
   constexpr int K = sh_count(DEG);
 
-  load_mats(a.mats, mats, vs.n_views * nk);
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   if (threadIdx.x == 0) s_frustum = 0;
@@ -212,18 +214,8 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
     // ---- pass 2: kept views -> splats
     if (kmask) {
       const float opac = 1.f / (1.f + __expf(-a.opac_logits[gid]));
-      float sh[K * 3];
-      if constexpr ((K * 3) % 4 == 0) {
-        const float4* src = a.sh + (size_t)gid * (K * 3 / 4);
-#pragma unroll
-        for (int i = 0; i < K * 3 / 4; ++i) {
-          const float4 q = __ldg(src + i);
-          sh[4 * i] = q.x; sh[4 * i + 1] = q.y; sh[4 * i + 2] = q.z; sh[4 * i + 3] = q.w;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < K * 3; ++i) sh[i] = __ldg(a.sh_f + (size_t)gid * K * 3 + i);
-      }
+      const float4* sh4 = a.sh + (size_t)gid * (K * 3 / 4);   // K*3 % 4 == 0 for K = 4, 16
+      const float* sh1 = a.sh_f + (size_t)gid * K * 3;
       uint32_t m = kmask;
       while (m) {
         const int v = __ffs(m) - 1;
@@ -237,14 +229,27 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
         dx *= inv; dy *= inv; dz *= inv;
         float Y[16];
         sh_basis<DEG>(dx, dy, dz, Y);
-        float rgb[3];
+        float rgb[3] = {0.5f, 0.5f, 0.5f};
+        if constexpr ((K * 3) % 4 == 0) {
+          // 128-bit loads: coefficient 4q+e of the [K][3] row
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          float acc = 0.5f;
+          for (int qd = 0; qd < K * 3 / 4; ++qd) {
+            const float4 c4 = __ldg(sh4 + qd);
+            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-          for (int i = 0; i < K; ++i) acc = fmaf(sh[3 * i + ch], Y[i], acc);
-          rgb[ch] = fmaxf(acc, 0.f);
+            for (int e = 0; e < 4; ++e) {
+              const int f = 4 * qd + e;
+              rgb[f % 3] = fmaf(cv[e], Y[f / 3], rgb[f % 3]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(__ldg(sh1 + 3 * i + ch), Y[i], rgb[ch]);
         }
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
         if ((int64_t)s < a.cap_splats) {
           a.sp_xy[s] = make_float2(p.u, p.v);
           a.sp_conic_o[s] = make_float4(p.ca, p.cb, p.cc, opac);
@@ -258,6 +263,13 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
           atomicAdd(&s_hist[1][(key >> 8) & 0xffu], 1u);
           atomicAdd(&s_hist[2][(key >> 16) & 0xffu], 1u);
           atomicAdd(&s_hist[3][key >> 24], 1u);
+          // pairs per tile: +1 / -1 at the ends of each covered tile row
+          const int gx = vs.v[v].gx, w = p.x1 - p.x0;
+          int32_t* row = a.tile_diff + vs.v[v].tile_base + p.y0 * gx + p.x0;
+          for (int ty = p.y0; ty < p.y1; ++ty, row += gx) {
+            atomicAdd(row, 1);
+            atomicAdd(row + w, -1);
+          }
         } else {
           overflow = true;
         }
@@ -279,8 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
 
 template <int DEG>
 cudaError_t launch_deg(s3r_workspace* ws, const ProjArgs& a, cudaStream_t st) {
-  const size_t smem = (size_t)ws->n_views * (ws->n_inst + 1) * sizeof(InstMat) +
-                      sizeof(uint32_t) * (ws->n_inst + 2) + 16;
+  const size_t smem = sizeof(uint32_t) * (ws->n_inst + 2) + 16;
   // attribute and occupancy are queried once per shared-memory size, so that a
   // launch inside CUDA-graph capture issues nothing but the kernel
   static thread_local size_t cached_smem = 0;
@@ -336,6 +347,11 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.lookback = ws->lookback;
   a.cap_splats = ws->cap.max_splats;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
+  a.tile_diff = ws->tile_diff;
+  {
+    cudaError_t e0 = cudaMemsetAsync(ws->tile_diff, 0, sizeof(int32_t) * ((size_t)ws->views.total_tiles + 1), st);
+    if (e0 != cudaSuccess) return e0;
+  }
   {
     KernelTimer timer(ws, kKCompose, st);
     k_compose<<<ws->n_views, 128, 0, st>>>(ws->views, a.pose_q, a.pose_t, sc->n_inst,

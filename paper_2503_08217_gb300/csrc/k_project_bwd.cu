@@ -107,13 +107,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
                                                           BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nk = a.n_inst + 1;
-  InstMat* mats = reinterpret_cast<InstMat*>(smem_raw);
-  float* s_dM = reinterpret_cast<float*>(mats + vs.n_views * nk);      // [views][nk][12]
+  // the composed matrices are read through L1 (a CTA touches few instances);
+  // shared memory holds only the per-(view, instance) matrix adjoints
+  const InstMat* __restrict__ mats = a.mats;
+  float* s_dM = reinterpret_cast<float*>(smem_raw);                      // [views][nk][12]
   uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dM + vs.n_views * nk * 12);
   __shared__ uint32_t s_tile;
   constexpr int K = sh_count(DEG);
 
-  load_mats(a.mats, mats, vs.n_views * nk);
   for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) s_dM[i] = 0.f;
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   __syncthreads();
@@ -416,7 +417,7 @@ __global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __
 template <int DEG>
 cudaError_t launch_deg(s3r_workspace* ws, const BwdArgs& a, cudaStream_t st) {
   const int nk = ws->n_inst + 1;
-  const size_t smem = (size_t)ws->n_views * nk * (sizeof(InstMat) + 12 * sizeof(float)) +
+  const size_t smem = (size_t)ws->n_views * nk * 12 * sizeof(float) +
                       sizeof(uint32_t) * (nk + 1) + 16;
   static thread_local size_t cached_smem = 0;
   static thread_local int cached_per_sm = 0;

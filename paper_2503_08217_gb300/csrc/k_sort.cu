@@ -88,12 +88,18 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
 
     uint32_t key[kSortItems], val[kSortItems];
     uint32_t rank[kSortItems];
+    // all loads first, so that each thread has 2 x 15 requests in flight
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       const int64_t idx = base + r * 32 + lane;
       const bool valid = idx < n;
       key[r] = valid ? __ldcs(a.keys_in + idx) : 0xffffffffu;
       val[r] = valid ? (a.vals_in ? __ldcs(a.vals_in + idx) : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+      const int64_t idx = base + r * 32 + lane;
+      const bool valid = idx < n;
       const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : kRadix);
       uint32_t before = 0;
@@ -172,10 +178,8 @@ __global__ void __launch_bounds__(kDupThreads) k_duplicate(const __grid_constant
                                                            DupArgs a) {
   __shared__ uint32_t s_excl[kDupSplats + 1];
   __shared__ uint4 s_meta[kDupSplats];   // (splat, first tile id, gx | w << 16, 1/w bits)
-  __shared__ uint32_t s_hist[4][kRadix];
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile, s_base;
-  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
   const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
   const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
@@ -236,7 +240,6 @@ __global__ void __launch_bounds__(kDupThreads) k_duplicate(const __grid_constant
       int q = lo;
       uint32_t q_end = s_excl[q + 1];
       uint4 meta = s_meta[q];
-      uint32_t hi_digit = 0xffffffffu, hi_count = 0;
       const uint32_t o_end = min(o0 + kDupItems, total);
       for (uint32_t o = o0; o < o_end; ++o) {
         while (o >= q_end) {
@@ -254,44 +257,81 @@ __global__ void __launch_bounds__(kDupThreads) k_duplicate(const __grid_constant
         if (pos < a.cap_dups) {
           __stcs(a.dup_key + pos, tile_id);
           __stcs(a.dup_val + pos, meta.x);
-          atomicAdd(&s_hist[0][tile_id & 0xffu], 1u);
-          if (a.tile_passes > 1) {           // higher digits change rarely along a run
-            const uint32_t d = (tile_id >> 8) & 0xffu;
-            if (d != hi_digit) {
-              if (hi_count) atomicAdd(&s_hist[1][hi_digit], hi_count);
-              hi_digit = d;
-              hi_count = 0;
-            }
-            ++hi_count;
-            for (int p = 2; p < a.tile_passes; ++p)
-              atomicAdd(&s_hist[p][(tile_id >> (8 * p)) & 0xffu], 1u);
-          }
         } else {
           overflow = true;
         }
       }
-      if (hi_count) atomicAdd(&s_hist[1][hi_digit], hi_count);
     }
     __syncthreads();
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < a.tile_passes * kRadix; i += blockDim.x) {
-    const uint32_t c = (&s_hist[0][0])[i];
-    if (c) atomicAdd(a.hist + kHistTile * kRadix + i, c);
   }
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
 }
 
-// [start, end) of every tile in the tile-sorted pair array.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* ctr, int64_t cap,
-                         uint2* __restrict__ ranges) {
-  const int64_t n = min((int64_t)ctr[kCtrDups], cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = keys[i];
-    if (i == 0 || keys[i - 1] != k) ranges[k].x = (uint32_t)i;
-    if (i == n - 1 || keys[i + 1] != k) ranges[k].y = (uint32_t)(i + 1);
+// Per-tile pair counts from the projection's difference array (+1 / -1 at
+// the two ends of every covered tile row), their exclusive scan (the [start,
+// end) range of every tile in the sorted pair array, clamped to capacity),
+// and the digit histograms of the tile-id radix passes. One CTA; three walks
+// over the tiles (sum of differences, sum of counts, output).
+constexpr int kCountThreads = 1024;
+
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t x, uint32_t* s_tmp /*[32]*/) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl += y;
   }
+  if (lane == 31) s_tmp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = s_tmp[lane];
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= (uint32_t)o) wi += y;
+    }
+    s_tmp[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t r = s_tmp[warp] + incl - x;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kCountThreads) k_tile_counts(const int32_t* __restrict__ diff,
+                                                               int tiles, int passes, int64_t cap,
+                                                               uint2* __restrict__ ranges,
+                                                               uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_hist[4][kRadix];
+  __shared__ uint32_t s_tmp[32];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  const int per = (tiles + kCountThreads - 1) / kCountThreads;
+  const int t0 = min(tiles, (int)threadIdx.x * per), t1 = min(tiles, t0 + per);
+  int32_t dsum = 0;
+  for (int t = t0; t < t1; ++t) dsum += diff[t];
+  const int32_t enter = (int32_t)block_excl_scan_1024((uint32_t)dsum, s_tmp);   // count entering t0
+  uint32_t csum = 0;
+  int32_t c = enter;
+  for (int t = t0; t < t1; ++t) {
+    c += diff[t];
+    csum += (uint32_t)c;
+  }
+  uint32_t start = block_excl_scan_1024(csum, s_tmp);
+  c = enter;
+  for (int t = t0; t < t1; ++t) {
+    c += diff[t];
+    const uint32_t cnt = (uint32_t)c;
+    const uint32_t b = (uint32_t)min((int64_t)start, cap), e = (uint32_t)min((int64_t)start + cnt, cap);
+    ranges[t] = cnt ? make_uint2(b, e) : make_uint2(0u, 0u);   // empty tiles: [0, 0)
+    start += cnt;
+    if (cnt)
+      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][((uint32_t)t >> (8 * p)) & 0xffu], cnt);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) hist[i] = (&s_hist[0][0])[i];
 }
 
 int per_sm_for(const void* fn, int threads) {
@@ -336,6 +376,13 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.sp_rect = ws->sp_rect;
   d.sp_view = ws->sp_view;
   d.dup_key = ws->dup_key[0];
+  {
+    KernelTimer timer(ws, kKTileCounts, st);
+    k_tile_counts<<<1, kCountThreads, 0, st>>>(ws->tile_diff, ws->views.total_tiles, ws->tile_passes,
+                                               ws->cap.max_duplicates, ws->ranges,
+                                               ws->hist + kHistTile * kRadix);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   d.dup_val = ws->dup_val[0];
   d.hist = ws->hist;
   d.tile_passes = ws->tile_passes;
@@ -368,13 +415,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   ws->dup_final = ws->tile_passes & 1;
-  if ((e = cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->views.total_tiles, st)) !=
-      cudaSuccess)
-    return e;
-  KernelTimer timer(ws, kKRanges, st);
-  k_ranges<<<ws->num_sms * 4, 256, 0, st>>>(ws->dup_key[ws->dup_final], ws->ctr,
-                                            ws->cap.max_duplicates, ws->ranges);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace s3r

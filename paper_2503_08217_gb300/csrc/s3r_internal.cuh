@@ -72,7 +72,7 @@ constexpr int kHistCount = 8;
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
   kKBegin = 0, kKCompact, kKCompose, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
-  kKTile0, kKTile1, kKTile2, kKTile3, kKRanges, kKBlendFwd, kKZeroGrads, kKBlendBwd,
+  kKTile0, kKTile1, kKTile2, kKTile3, kKTileCounts, kKBlendFwd, kKZeroGrads, kKBlendBwd,
   kKProjectBwd, kKPoseChain, kKCount
 };
 
@@ -107,6 +107,7 @@ struct s3r_workspace {
   float* sp_grad;           // [S*12]
   float* pose_dM;           // [views*(inst+1)*12]
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
+  int32_t* tile_diff;       // [tiles+1] difference array of per-tile pair counts
   int64_t bytes;
   // host-side state of the current call sequence
   s3r::ViewSet views;
@@ -168,6 +169,7 @@ cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, fl
                            float* loss, cudaStream_t st);
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
                               int mode, cudaStream_t st);
+
 
 // ---- small device helpers ----------------------------------------------------
 #ifdef __CUDACC__
