@@ -230,6 +230,29 @@ int32_t s3r_kernel_count(void);
 const char* s3r_kernel_name(int32_t id);
 s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n);
 
+/* Allocation-free temporal selection. The paper has no counterpart: this is
+ * a convenience for callers that cannot allocate device memory at all, e.g.
+ * code running inside a host framework whose caching allocator owns the
+ * whole device, or a real-time loop that may not call cudaMalloc after
+ * start-up. It computes the same list as the selection step of s3r_project
+ * (ascending ids i with vis_window[i] = (v_s, v_e), v_s <= t <= v_e, FP32)
+ * without a workspace:
+ *   n           number of Gaussians, 0 <= n <= S3R_STATIC_MAX_GAUSSIANS;
+ *               larger n returns S3R_ERR_INVALID (nothing is launched).
+ *   vis_window  [n,2] FP32 device array, 16-byte aligned.
+ *   out_idx     [n] uint32 device array (caller-owned), receives the list.
+ *   out_count   one uint32 in device memory, receives its length.
+ * The look-back scratch is a fixed array in the library's device image
+ * (about 128 KB, held by every GPU that loads the library until the process
+ * exits); every call shares it and clears the part it uses on entry, so
+ * calls that overlap on the GPU (e.g. on two streams at once) race and must
+ * be serialised by the caller. The first call on a device looks up the
+ * array's device address (once per device); make that first call before any
+ * stream capture. No allocation or free happens in any call. */
+#define S3R_STATIC_MAX_GAUSSIANS (1LL << 26)
+s3r_status s3r_select_visible_static(int64_t n, float t, const float* vis_window, uint32_t* out_idx,
+                                     uint32_t* out_count, void* stream);
+
 /* Synchronise `stream`, then return the device counts of the last call
  * sequence and the latched device status (which it clears). Tests and logs
  * only. */

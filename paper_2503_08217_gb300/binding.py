@@ -25,7 +25,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_sort", "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
-           "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times")
+           "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static")
 
 
 class S3RError(RuntimeError):
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
     L.s3r_query_counts.argtypes = [vp, vp, P(Counts)]
     L.s3r_l1_loss.argtypes = [i64, vp, vp, vp, vp, vp]
     L.s3r_set_timing.argtypes = [vp, i32]
+    L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_kernel_count.restype = i32
     L.s3r_kernel_name.argtypes = [i32]
     L.s3r_kernel_name.restype = ctypes.c_char_p
@@ -110,7 +111,7 @@ def load(path: str = LIB_PATH):
     for name in ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_project", "s3r_sort",
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
-                 "s3r_kernel_times"):
+                 "s3r_kernel_times", "s3r_select_visible_static"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -276,6 +277,16 @@ def l1_loss(pred, target, dL_dpred, loss_out, stream=None):
     """loss_out += mean|pred - target|; dL_dpred = sign(pred - target) / n."""
     _check(load().s3r_l1_loss(int(pred.numel()), _ptr(pred), _ptr(target), _ptr(dL_dpred),
                               _ptr(loss_out), _stream(stream)))
+
+
+def select_visible_static(vis_window, t: float, out_idx, out_count, stream=None):
+    """Temporal selection without any device allocation by the library: the
+    ids i with v_s <= t <= v_e go to out_idx (uint32, caller-owned) and their
+    number to out_count (one uint32 on the device). For callers that may not
+    allocate; see s3r_select_visible_static in include/s3r.h."""
+    n = int(vis_window.shape[0]) if vis_window is not None else 0
+    _check(load().s3r_select_visible_static(n, float(t), _ptr(vis_window), _ptr(out_idx),
+                                            _ptr(out_count), _stream(stream)))
 
 
 def update_visibility(n: int, t: float, mask, point_life, vis_window, mode: int, stream=None):

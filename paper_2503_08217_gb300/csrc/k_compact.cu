@@ -7,6 +7,9 @@
 // per round gives every selected Gaussian its rank; a block scan over the 8
 // warps and a single-pass decoupled look-back over tiles give the global
 // offset, so the output is written once, in order, coalesced.
+#include <mutex>
+#include <string>
+
 #include "s3r_internal.cuh"
 
 namespace s3r {
@@ -118,3 +121,86 @@ cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float
 }
 
 }  // namespace s3r
+
+namespace s3r {
+
+// ---- allocation-free variant --------------------------------------------
+// The same k_compact kernel, run on scratch that lives in a fixed array of
+// the library's device image instead of a workspace: look-back words for up
+// to S3R_STATIC_MAX_GAUSSIANS / 4096 tiles and the counters the kernel uses.
+namespace {
+
+constexpr int64_t kStaticTiles = S3R_STATIC_MAX_GAUSSIANS / kTileSpan;   // 16,384
+
+struct StaticScratch {
+  unsigned long long lookback[kStaticTiles];   // 128 KB
+  uint32_t ctr[kCtrCount];
+};
+
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+StaticScratch* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+s3r_status static_scratch(StaticScratch** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_last_error(S3R_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_last_error(S3R_ERR_INVALID, "s3r_select_visible_static: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) {
+      const std::string msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return set_last_error(S3R_ERR_CUDA, msg.c_str());
+    }
+    g_static_ptr[dev] = static_cast<StaticScratch*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return S3R_OK;
+}
+
+}  // namespace
+}  // namespace s3r
+
+extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float* vis_window,
+                                                uint32_t* out_idx, uint32_t* out_count,
+                                                void* stream) {
+  using namespace s3r;
+  if (n < 0 || n > S3R_STATIC_MAX_GAUSSIANS)
+    return set_last_error(S3R_ERR_INVALID,
+                          "s3r_select_visible_static: n must be in [0, 2^26] (the fixed scratch "
+                          "holds look-back words for at most 67,108,864 Gaussians)");
+  if (!out_count || ((uintptr_t)out_count & 3u))
+    return set_last_error(S3R_ERR_INVALID, "s3r_select_visible_static: out_count must be a device uint32");
+  if (n > 0 && (!vis_window || !out_idx || ((uintptr_t)vis_window & 15u) || ((uintptr_t)out_idx & 3u)))
+    return set_last_error(S3R_ERR_INVALID,
+                          "s3r_select_visible_static: vis_window (16-byte aligned) and out_idx are required");
+  if (!(t == t)) return set_last_error(S3R_ERR_INVALID, "s3r_select_visible_static: t is NaN");
+  StaticScratch* sc = nullptr;
+  s3r_status st = static_scratch(&sc);
+  if (st != S3R_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
+  // the array keeps the previous call's contents: clear the counters and the
+  // look-back words this call will use
+  cudaError_t e = cudaMemsetAsync(sc->ctr, 0, sizeof(sc->ctr), s);
+  if (e == cudaSuccess && n_tiles > 0)
+    e = cudaMemsetAsync(sc->lookback, 0, sizeof(unsigned long long) * (size_t)n_tiles, s);
+  if (e == cudaSuccess) {
+    int64_t grid = 152 * 8;
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid < 1) grid = 1;
+    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(vis_window, n, t, out_idx, sc->ctr, sc->lookback);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out_count, sc->ctr + kCtrSelected, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return set_last_error(S3R_ERR_CUDA, cudaGetErrorString(e));
+  return S3R_OK;
+}

@@ -118,6 +118,13 @@ s3r_status check_poses(const s3r_scene* sc, const s3r_poses* poses) {
 
 }  // namespace
 
+namespace s3r {
+s3r_status set_last_error(s3r_status st, const char* msg) {
+  g_last_error = msg;
+  return st;
+}
+}  // namespace s3r
+
 extern "C" {
 
 const char* s3r_last_error(void) { return g_last_error.c_str(); }

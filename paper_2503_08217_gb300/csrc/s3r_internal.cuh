@@ -169,7 +169,8 @@ cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, fl
                            float* loss, cudaStream_t st);
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
                               int mode, cudaStream_t st);
-
+// Record `msg` as the calling thread's last error and return `st`.
+s3r_status set_last_error(s3r_status st, const char* msg);
 
 // ---- small device helpers ----------------------------------------------------
 #ifdef __CUDACC__
