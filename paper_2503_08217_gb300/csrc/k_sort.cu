@@ -149,17 +149,26 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
   }
 }
 
-// Expand depth-sorted splats into (view-tile id, splat) pairs. A CTA takes
-// 1024 consecutive sorted splats (4 per thread): a block scan of their tile
-// counts and a decoupled look-back give the CTA one contiguous output range.
-// Each thread then writes 8 consecutive outputs, locating its first splat by
-// binary search and advancing an incremental cursor after that; the tile id of
-// output r of a splat with rectangle width w is base + (r / w) * gx + r % w,
-// with r / w taken from a float reciprocal and one integer correction step.
+// Expand depth-sorted splats into (view-tile id, splat) pairs, in two kernels
+// so that the work is balanced by OUTPUT count: the nearest splats come first
+// in depth order and may each cover hundreds of tiles.
+//  k_dup_scan:   per sorted splat, its tile count and a compact descriptor
+//                (splat id, first tile id, grid width | rect width << 16,
+//                1/width); a block scan + decoupled look-back over 1024-splat
+//                tiles gives every splat its first output position.
+//  k_dup_expand: persistent CTAs take fixed chunks of 4096 outputs; a warp
+//                finds the chunk's first splat by a 32-ary search of the
+//                offsets, each thread expands 16 consecutive outputs (binary
+//                search in shared memory, then an incremental cursor), the
+//                pairs are staged in shared memory and written coalesced. The
+//                tile id of output r of a splat of rectangle width w is
+//                first + (r / w) * gx + r % w, r / w from a float reciprocal
+//                with one integer correction step.
 constexpr int kDupThreads = 256;
-constexpr int kDupPer = 4;                            // splats per thread
-constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per tile
-constexpr int kDupItems = 8;                          // outputs per thread per step
+constexpr int kDupPer = 4;                            // splats per thread in the scan
+constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per scan tile
+constexpr int kExpItems = 16;                         // outputs per thread per chunk
+constexpr int kExpChunk = kDupThreads * kExpItems;    // 4096 outputs per chunk
 
 struct DupArgs {
   const uint32_t* sorted_splats;
@@ -167,104 +176,146 @@ struct DupArgs {
   const uint8_t* sp_view;
   uint32_t* dup_key;
   uint32_t* dup_val;
-  uint32_t* hist;        // tile-digit histograms (kHistTile...)
-  int tile_passes;
+  uint32_t* dup_excl;    // [S+1] first output of each sorted splat
+  uint4* dup_meta;       // [S] descriptors
   int64_t cap_splats, cap_dups;
   uint32_t* ctr;
   unsigned long long* lookback;
 };
 
-__global__ void __launch_bounds__(kDupThreads) k_duplicate(const __grid_constant__ ViewSet vs,
-                                                           DupArgs a) {
-  __shared__ uint32_t s_excl[kDupSplats + 1];
-  __shared__ uint4 s_meta[kDupSplats];   // (splat, first tile id, gx | w << 16, 1/w bits)
+__global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant__ ViewSet vs,
+                                                          DupArgs a) {
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile, s_base;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
   const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
   const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
-  bool overflow = false;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
     if (tile >= n_tiles) break;
-    // ---- counts of this thread's 4 splats
     const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
-    uint32_t cnt[kDupPer], run = 0;
+    uint32_t sp[kDupPer], cnt[kDupPer], run = 0;
+#pragma unroll
+    for (int k = 0; k < kDupPer; ++k) sp[k] = i0 + k < n ? a.sorted_splats[i0 + k] : 0u;
+    uint2 rect[kDupPer];
+    int view[kDupPer];
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
-      const int64_t i = i0 + k;
-      cnt[k] = 0;
-      uint4 meta = make_uint4(0u, 0u, 1u << 16, __float_as_uint(1.f));
-      if (i < n) {
-        const uint32_t sp = a.sorted_splats[i];
-        const uint2 r = a.sp_rect[sp];
-        const uint32_t x0 = r.x & 0xffffu, y0 = r.x >> 16;
-        const uint32_t w = (r.y & 0xffffu) - x0, h = (r.y >> 16) - y0;
-        const ViewInfo& vi = vs.v[a.sp_view[sp]];
-        cnt[k] = w * h;
-        const uint32_t first = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
-        meta = make_uint4(sp, first, (uint32_t)vi.gx | (w << 16),
-                          __float_as_uint(w ? 1.f / (float)w : 1.f));
-      }
-      s_meta[threadIdx.x * kDupPer + k] = meta;
+      rect[k] = i0 + k < n ? a.sp_rect[sp[k]] : make_uint2(0u, 0u);
+      view[k] = i0 + k < n ? a.sp_view[sp[k]] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kDupPer; ++k) {
+      const uint32_t x0 = rect[k].x & 0xffffu, y0 = rect[k].x >> 16;
+      const uint32_t w = (rect[k].y & 0xffffu) - x0, h = (rect[k].y >> 16) - y0;
+      cnt[k] = w * h;
       run += cnt[k];
+      if (i0 + k < n) {
+        const ViewInfo& vi = vs.v[view[k]];
+        const uint32_t first = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
+        a.dup_meta[i0 + k] = make_uint4(sp[k], first, (uint32_t)vi.gx | (w << 16),
+                                        __float_as_uint(w ? 1.f / (float)w : 1.f));
+      }
     }
     uint32_t total;
     uint32_t ex = block_excl_scan(run, s_tmp, &total);
-#pragma unroll
-    for (int k = 0; k < kDupPer; ++k) {
-      s_excl[threadIdx.x * kDupPer + k] = ex;
-      ex += cnt[k];
-    }
     if (threadIdx.x < 32) {
       const uint32_t prefix = warp_lookback(a.lookback, tile, tag, total, a.ctr);
       if (threadIdx.x == 0) {
-        s_excl[kDupSplats] = total;
         s_base = prefix;
-        if (tile == n_tiles - 1) a.ctr[kCtrDups] = prefix + total;
+        if (tile == n_tiles - 1) {
+          a.ctr[kCtrDups] = prefix + total;
+          a.dup_excl[n] = prefix + total;              // sentinel
+          if ((int64_t)prefix + total > a.cap_dups) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
+        }
       }
     }
     __syncthreads();
-    const uint32_t base = s_base;
-    // ---- expansion: 8 consecutive outputs per thread
-    for (uint32_t c0 = 0; c0 < total; c0 += kDupThreads * kDupItems) {
-      const uint32_t o0 = c0 + threadIdx.x * kDupItems;
-      if (o0 >= total) continue;
-      int lo = 0, hi = kDupSplats;          // last q with s_excl[q] <= o0
+    ex += s_base;
+#pragma unroll
+    for (int k = 0; k < kDupPer; ++k) {
+      if (i0 + k < n) a.dup_excl[i0 + k] = ex;
+      ex += cnt[k];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
+  __shared__ uint32_t s_excl[kExpChunk + 1];
+  __shared__ uint32_t s_key[kExpChunk];
+  __shared__ uint32_t s_val[kExpChunk];
+  __shared__ uint32_t s_chunk, s_q0, s_q1;
+  const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
+  const int64_t total = min((int64_t)a.ctr[kCtrDups], a.cap_dups);
+  const int64_t n_chunks = (total + kExpChunk - 1) / kExpChunk;
+  const uint32_t lane = lane_id();
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(a.ctr + kCtrTileBase + kStageExpand, 1u);
+    __syncthreads();
+    const int64_t chunk = s_chunk;
+    if (chunk >= n_chunks) break;
+    const uint32_t O0 = (uint32_t)(chunk * kExpChunk);
+    const uint32_t O1 = (uint32_t)min((int64_t)O0 + kExpChunk, total);   // exclusive
+    if (threadIdx.x < 32) {
+      // last q with excl[q] <= O0, and last q with excl[q] <= O1 - 1: 32-ary search
+      for (int which = 0; which < 2; ++which) {
+        const uint32_t target = which ? O1 - 1 : O0;
+        int64_t lo = 0, hi = n;          // excl[lo] <= target < excl[hi] (excl[n] = total)
+        while (hi - lo > 1) {
+          const int64_t step = (hi - lo + 31) / 32;
+          const int64_t probe = lo + (int64_t)(lane + 1) * step;
+          const bool le = probe < hi && a.dup_excl[probe] <= target;
+          const uint32_t m = __ballot_sync(0xffffffffu, le);
+          const int c = __popc(m);                      // probes that are <= target (a prefix)
+          const int64_t nlo = lo + (int64_t)c * step;
+          const int64_t nhi = min(hi, lo + (int64_t)(c + 1) * step);
+          lo = nlo;
+          hi = nhi;
+        }
+        if (lane == 0) (which ? s_q1 : s_q0) = (uint32_t)lo;
+      }
+    }
+    __syncthreads();
+    const int q0 = (int)s_q0, nq = (int)s_q1 - q0 + 1;
+    for (int i = threadIdx.x; i <= nq; i += kDupThreads) s_excl[i] = a.dup_excl[q0 + i];
+    __syncthreads();
+    // 16 consecutive outputs per thread
+    const uint32_t o0 = O0 + threadIdx.x * kExpItems;
+    if (o0 < O1) {
+      int lo = 0, hi = nq;            // last local q with s_excl[q] <= o0
       while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (s_excl[mid] <= o0) lo = mid; else hi = mid;
       }
       int q = lo;
       uint32_t q_end = s_excl[q + 1];
-      uint4 meta = s_meta[q];
-      const uint32_t o_end = min(o0 + kDupItems, total);
-      for (uint32_t o = o0; o < o_end; ++o) {
+      uint4 meta = a.dup_meta[q0 + q];
+      const uint32_t oe = min(o0 + kExpItems, O1);
+      for (uint32_t o = o0; o < oe; ++o) {
         while (o >= q_end) {
           ++q;
           q_end = s_excl[q + 1];
-          meta = s_meta[q];
+          meta = a.dup_meta[q0 + q];
         }
         const uint32_t rr = o - s_excl[q];
         const uint32_t w = meta.z >> 16, gx = meta.z & 0xffffu;
         uint32_t row = (uint32_t)(((float)rr + 0.5f) * __uint_as_float(meta.w));
-        row -= (row * w > rr) ? 1u : 0u;          // one correction step keeps it exact
-        row += ((row + 1u) * w <= rr) ? 1u : 0u;  // for any rectangle size
-        const uint32_t tile_id = meta.y + row * gx + (rr - row * w);
-        const int64_t pos = (int64_t)base + o;
-        if (pos < a.cap_dups) {
-          __stcs(a.dup_key + pos, tile_id);
-          __stcs(a.dup_val + pos, meta.x);
-        } else {
-          overflow = true;
-        }
+        row -= (row * w > rr) ? 1u : 0u;
+        row += ((row + 1u) * w <= rr) ? 1u : 0u;
+        s_key[o - O0] = meta.y + row * gx + (rr - row * w);
+        s_val[o - O0] = meta.x;
       }
     }
     __syncthreads();
+    for (uint32_t i = threadIdx.x; i < O1 - O0; i += kDupThreads) {
+      __stcs(a.dup_key + O0 + i, s_key[i]);
+      __stcs(a.dup_val + O0 + i, s_val[i]);
+    }
+    (void)lane;
   }
-  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
 }
 
 // Per-tile pair counts from the projection's difference array (+1 / -1 at
@@ -347,9 +398,10 @@ int per_sm_for(const void* fn, int threads) {
 cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   cudaError_t e;
   // occupancy is queried once (outside any graph capture: the first call)
-  static thread_local int sweep_per_sm = 0, dup_per_sm = 0;
+  static thread_local int sweep_per_sm = 0, dup_per_sm = 0, exp_per_sm = 0;
   if (!sweep_per_sm) sweep_per_sm = per_sm_for((const void*)k_onesweep, kSortThreads);
-  if (!dup_per_sm) dup_per_sm = per_sm_for((const void*)k_duplicate, kDupThreads);
+  if (!dup_per_sm) dup_per_sm = per_sm_for((const void*)k_dup_scan, kDupThreads);
+  if (!exp_per_sm) exp_per_sm = per_sm_for((const void*)k_dup_expand, kDupThreads);
   const int g_sweep = ws->num_sms * sweep_per_sm;
   // depth digits on the splats: 4 passes, result back in buffer 0
   for (int p = 0; p < 4; ++p) {
@@ -376,6 +428,13 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.sp_rect = ws->sp_rect;
   d.sp_view = ws->sp_view;
   d.dup_key = ws->dup_key[0];
+  d.dup_val = ws->dup_val[0];
+  d.dup_excl = ws->dup_excl;
+  d.dup_meta = reinterpret_cast<uint4*>(ws->dup_meta);
+  d.cap_splats = ws->cap.max_splats;
+  d.cap_dups = ws->cap.max_duplicates;
+  d.ctr = ws->ctr;
+  d.lookback = ws->lookback;
   {
     KernelTimer timer(ws, kKTileCounts, st);
     k_tile_counts<<<1, kCountThreads, 0, st>>>(ws->tile_diff, ws->views.total_tiles, ws->tile_passes,
@@ -383,17 +442,14 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
                                                ws->hist + kHistTile * kRadix);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  d.dup_val = ws->dup_val[0];
-  d.hist = ws->hist;
-  d.tile_passes = ws->tile_passes;
-  d.cap_splats = ws->cap.max_splats;
-  d.cap_dups = ws->cap.max_duplicates;
-  d.ctr = ws->ctr;
-  d.lookback = ws->lookback;
-  const int g_dup = ws->num_sms * dup_per_sm;
   {
     KernelTimer timer(ws, kKDuplicate, st);
-    k_duplicate<<<g_dup, kDupThreads, 0, st>>>(ws->views, d);
+    k_dup_scan<<<ws->num_sms * dup_per_sm, kDupThreads, 0, st>>>(ws->views, d);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    KernelTimer timer(ws, kKExpand, st);
+    k_dup_expand<<<ws->num_sms * exp_per_sm, kDupThreads, 0, st>>>(d);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // tile digits on the pairs

@@ -35,7 +35,8 @@ enum Stage : int {
   kStageDepth0 = 3,   // 3..6: depth radix passes
   kStageTile0 = 7,    // 7..10: tile radix passes
   kStageProjectBwd = 11,
-  kStageCount = 12
+  kStageExpand = 12,  // chunk counter of the duplication expansion
+  kStageCount = 13
 };
 
 // Bounded spin: after this many polls a wait gives up, latches
@@ -72,7 +73,7 @@ constexpr int kHistCount = 8;
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
   kKBegin = 0, kKCompact, kKCompose, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
-  kKTile0, kKTile1, kKTile2, kKTile3, kKTileCounts, kKBlendFwd, kKZeroGrads, kKBlendBwd,
+  kKTile0, kKTile1, kKTile2, kKTile3, kKTileCounts, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
   kKProjectBwd, kKPoseChain, kKCount
 };
 
@@ -108,6 +109,8 @@ struct s3r_workspace {
   float* pose_dM;           // [views*(inst+1)*12]
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   int32_t* tile_diff;       // [tiles+1] difference array of per-tile pair counts
+  uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
+  uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
   int64_t bytes;
   // host-side state of the current call sequence
   s3r::ViewSet views;
