@@ -162,11 +162,19 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "sort_depth_pass1": ("hbm", S * 16),
         "sort_depth_pass2": ("hbm", S * 16),
         "sort_depth_pass3": ("hbm", S * 16),
-        "duplicate": ("hbm", S * (4 + 8 + 1) + K * 8),
-        "tile_ranges": ("hbm", K * 4 + tiles * 8),
+        # duplication: the scan reads each sorted splat's id, rect and view and
+        # writes its offset and descriptor; the expansion writes the pairs
+        "duplicate": ("hbm", S * (4 + 8 + 1) + S * (4 + 16)),
+        "duplicate_expand": ("hbm", S * (4 + 16) + K * 8),
+        "tile_counts": ("hbm", tiles * (4 * 3 + 8)),
         "zero_splat_grads": ("hbm", S * 48),
         "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + 2 * (geo + kk)) + S * 48),
+        # FP32 instructions per (pixel, splat) pair the forward visits: forward
+        # ~22 (offset, quadratic form, ex2, alpha, tests, blend); backward ~55
+        # (the same evaluation, transmittance recovery, colour-behind update,
+        # nine adjoints)
         "blend_fwd": ("alu", counts["n_blend_pairs"] * 22),
+        "blend_bwd": ("alu", counts["n_blend_pairs"] * 55),
     }
     for p in range(tile_passes):
         m[f"sort_tile_pass{p}"] = ("hbm", K * 16)

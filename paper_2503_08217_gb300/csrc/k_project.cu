@@ -38,6 +38,7 @@ struct ProjArgs {
   uint32_t* frustum_mask;
   uint32_t* keep_mask;
   uint32_t* splat_start;
+  uint32_t* kept_list;
   float2* sp_xy;
   float4* sp_conic_o;
   float4* sp_rgb_d;
@@ -210,6 +211,14 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
       a.keep_mask[j] = kmask;
       a.splat_start[j] = s;
     }
+    // append the kept Gaussians to the backward's work list (one atomic per warp)
+    {
+      const uint32_t kb = __ballot_sync(0xffffffffu, kmask != 0u);
+      uint32_t kbase = 0;
+      if (lane == 0 && kb) kbase = atomicAdd(a.ctr + kCtrKept, (uint32_t)__popc(kb));
+      kbase = __shfl_sync(0xffffffffu, kbase, 0);
+      if (kmask) a.kept_list[kbase + __popc(kb & lt)] = (uint32_t)j;
+    }
 
     // ---- pass 2: kept views -> splats
     if (kmask) {
@@ -336,6 +345,7 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.frustum_mask = ws->frustum_mask;
   a.keep_mask = ws->keep_mask;
   a.splat_start = ws->splat_start;
+  a.kept_list = ws->kept_list;
   a.sp_xy = ws->sp_xy;
   a.sp_conic_o = ws->sp_conic_o;
   a.sp_rgb_d = ws->sp_rgb_d;

@@ -30,6 +30,7 @@ struct BwdArgs {
   const float* pose_t;
   const uint32_t* selected;
   const uint32_t* keep_mask;
+  const uint32_t* kept_list;
   const uint32_t* splat_start;
   const float4* sp_grad;   // [S][3] float4
   int64_t cap_splats;
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   __syncthreads();
 
-  const uint32_t n_sel = a.ctr[kCtrSelected];
+  // only Gaussians kept in at least one view have adjoints
+  const uint32_t n_sel = a.ctr[kCtrKept];
   const int64_t n_tiles = ((int64_t)n_sel + kThreads - 1) / kThreads;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageProjectBwd, 1u);
@@ -127,8 +129,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     const int64_t tile = s_tile;
     __syncthreads();
     if (tile >= n_tiles) break;
-    const int64_t j = tile * kThreads + threadIdx.x;
-    if (j >= (int64_t)n_sel) continue;
+    const int64_t jt = tile * kThreads + threadIdx.x;
+    if (jt >= (int64_t)n_sel) continue;
+    const uint32_t j = a.kept_list[jt];
     const uint32_t kmask = a.keep_mask[j];
     if (!kmask) continue;
     const uint32_t gid = a.selected[j];
@@ -455,6 +458,7 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.pose_t = poses ? poses->trans : nullptr;
   a.selected = ws->selected;
   a.keep_mask = ws->keep_mask;
+  a.kept_list = ws->kept_list;
   a.splat_start = ws->splat_start;
   a.sp_grad = reinterpret_cast<const float4*>(ws->sp_grad);
   a.cap_splats = ws->cap.max_splats;

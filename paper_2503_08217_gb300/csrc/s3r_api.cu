@@ -70,7 +70,7 @@ void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   void* ptrs[] = {ws->ctr, ws->hist, ws->lookback, ws->selected, ws->frustum_mask,
-                  ws->keep_mask, ws->splat_start, ws->sp_xy, ws->sp_conic_o, ws->sp_rgb_d,
+                  ws->keep_mask, ws->splat_start, ws->kept_list, ws->sp_xy, ws->sp_conic_o, ws->sp_rgb_d,
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
@@ -173,6 +173,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->frustum_mask, N);
   S3R_ALLOC(ws->keep_mask, N);
   S3R_ALLOC(ws->splat_start, N);
+  S3R_ALLOC(ws->kept_list, N);
   S3R_ALLOC(ws->sp_xy, S);
   S3R_ALLOC(ws->sp_conic_o, S);
   S3R_ALLOC(ws->sp_rgb_d, S);

@@ -20,6 +20,7 @@ enum Ctr : int {
   kCtrStatus = 3,     // latched error bits
   kCtrEpoch = 4,      // bumped once per s3r_project; tags look-back words
   kCtrFrustum = 5,    // selected Gaussians inside >= 1 frustum
+  kCtrKept = 6,       // selected Gaussians kept in >= 1 view (length of kept_list)
   kCtrTileBase = 8,   // 16 dynamic tile-acquisition counters, one per stage
   kCtrPairs = 24,     // 64-bit: (pixel, splat) pairs evaluated by the forward blend
   kCtrCount = 32
@@ -93,6 +94,7 @@ struct s3r_workspace {
   uint32_t* frustum_mask;   // [N]
   uint32_t* keep_mask;      // [N]
   uint32_t* splat_start;    // [N]
+  uint32_t* kept_list;      // [N] compacted indices of Gaussians kept in >= 1 view (any order)
   float2* sp_xy;            // [S]
   float4* sp_conic_o;       // [S]
   float4* sp_rgb_d;         // [S]
