@@ -40,7 +40,21 @@ struct BlendArgs {
   uint32_t* n_contrib;
   float* sp_grad;         // backward only, [S*12]
   unsigned long long* pairs;  // forward only: evaluated (pixel, splat) pairs
+  uint32_t* contrib;          // [4][contrib_words]: pair blended into >= 1 pixel of the warp block
+  int64_t contrib_words;
 };
+
+// Set the bits of `bits` (positions gp .. gp+31 of the sorted pairs) in a
+// bit array; the window may straddle two words (shared with a neighbour tile).
+__device__ __forceinline__ void or_bits(uint32_t* arr, uint32_t gp, uint32_t bits) {
+  const uint32_t w = gp >> 5, sh = gp & 31u;
+  atomicOr(arr + w, bits << sh);
+  if (sh) atomicOr(arr + w + 1, bits >> (32u - sh));
+}
+__device__ __forceinline__ uint32_t get_bits(const uint32_t* arr, uint32_t gp) {
+  const uint32_t w = gp >> 5, sh = gp & 31u;
+  return __funnelshift_r(arr[w], arr[w + 1], sh);
+}
 
 __device__ __forceinline__ int view_of_tile(const ViewSet& vs, int tile) {
   int v = 0;
@@ -172,12 +186,14 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
       if (__all_sync(0xffffffffu, done0 && done1)) break;
       // which of the next 32 splats can reach this warp's 8x8 block
       uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane < m && !box_misses(s_box[c0 + lane], P));
+      uint32_t blended = 0;     // splats of this chunk blended into some pixel of the block
       while (todo) {
       const int j = c0 + __ffs(todo) - 1;
       todo &= todo - 1;
       const float4 sa = s_a[j], sb = s_b[j];
       const float cb = s_c[j];
       const int pos = b0 + j + 1;
+      bool any_blend = false;
       {
         const SplatEval e = eval_splat(sa, sb, P.fx, P.fy0);
         const bool ok = !done0 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
@@ -192,6 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         last0 = blend ? pos : last0;
         end0 = stop ? pos : end0;
         done0 = done0 || stop;
+        any_blend = blend;
       }
       {
         const SplatEval e = eval_splat(sa, sb, P.fx, P.fy1);
@@ -207,8 +224,12 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         last1 = blend ? pos : last1;
         end1 = stop ? pos : end1;
         done1 = done1 || stop;
+        any_blend = any_blend || blend;
       }
+      if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
       }
+      if (lane == 0 && blended)
+        or_bits(a.contrib + (threadIdx.x >> 5) * a.contrib_words, range.x + b0 + c0, blended);
     }
   }
   // work accounting: (pixel, splat) pairs visited, one 64-bit atomic per warp
@@ -341,7 +362,6 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
                                                         BlendArgs a) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
-  __shared__ float4 s_box[kBatch];
   __shared__ float s_c[kBatch];
   __shared__ uint32_t s_id[kBatch];
   __shared__ float s_g[kBatch][9];
@@ -376,16 +396,18 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
       const float2 xy = a.sp_xy[s];
       const float4 co = a.sp_conic_o[s];
       stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
-      s_box[i] = alpha_box(xy, co);
     }
     for (int i = threadIdx.x; i < kBatch * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
     // this warp's splats end at its own last contributor; walk them back to
-    // front, 32 at a time, visiting only those whose footprint box meets the
-    // warp's 8x8 block
+    // front, 32 at a time, visiting only the splats the forward blended into
+    // at least one pixel of the warp's 8x8 block (recorded bits)
+    const uint32_t* wbits = a.contrib + (threadIdx.x >> 5) * a.contrib_words;
     for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
       const int c0 = max(0, c1 - 31);
-      uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane <= c1 && !box_misses(s_box[c0 + lane], P));
+      uint32_t todo = get_bits(wbits, range.x + lo + c0);
+      const int span = c1 - c0 + 1;
+      if (span < 32) todo &= (1u << span) - 1u;
       while (todo) {
       const int bit = 31 - __clz(todo);
       todo &= ~(1u << bit);
@@ -397,7 +419,6 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
       const SplatEval e1 = eval_splat(sa, sb, P.fx, P.fy1);
       const bool act0 = (pos < q0.last) && !(e0.p > 0.f) && !(e0.alpha < kAlphaMin);
       const bool act1 = (pos < q1.last) && !(e1.p > 0.f) && !(e1.alpha < kAlphaMin);
-      if (!__any_sync(0xffffffffu, act0 || act1)) continue;  // warp-uniform
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bwd_pixel(q0, e0, sa, sb, cb, act0, g);
       bwd_pixel(q1, e1, sa, sb, cb, act1, g);
@@ -446,6 +467,8 @@ static BlendArgs make_args(s3r_workspace* ws) {
   a.n_contrib = ws->n_contrib;
   a.sp_grad = ws->sp_grad;
   a.pairs = reinterpret_cast<unsigned long long*>(ws->ctr + kCtrPairs);
+  a.contrib = ws->contrib;
+  a.contrib_words = ws->contrib_words;
   a.bg = nullptr;
   a.dL = nullptr;
   a.out = nullptr;
@@ -458,6 +481,8 @@ cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cu
   a.out = out;
   if (ws->views.total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.pairs, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ws->contrib, 0, sizeof(uint32_t) * 4 * (size_t)ws->contrib_words, st);
   if (e != cudaSuccess) return e;
   KernelTimer timer(ws, kKBlendFwd, st);
   k_blend_fwd<<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);

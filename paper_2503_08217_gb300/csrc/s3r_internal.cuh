@@ -113,6 +113,8 @@ struct s3r_workspace {
   int32_t* tile_diff;       // [tiles+1] difference array of per-tile pair counts
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
+  uint32_t* contrib;        // [4][K/32 + 2] bit per (warp block, sorted pair): blended in the forward
+  int64_t contrib_words;    // words per warp block
   int64_t bytes;
   // host-side state of the current call sequence
   s3r::ViewSet views;
