@@ -73,6 +73,7 @@ def lib():
         L.orc_render_backward_pixels.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp,
                                                  vp, vp, vp, vp, vp, vp]
         L.orc_num_threads.restype = i32
+        L.orc_adam_step.argtypes = [i64, vp, vp, vp, vp, f64, f64, f64, f64, i32]
         L.orc_set_margins.argtypes = [f64, f64, f64]
         _lib = L
     return _lib
@@ -358,3 +359,17 @@ def step_backward(scene, step: int, fwd: dict, dL_dimgs, lod_r: float, cams=None
     grads["M"] = gms
     grads["pixel_flags"] = flags
     return grads
+
+
+def adam_step(param, grad, exp_avg, exp_avg_sq, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in float64 (Kingma and Ba, Algorithm 1; PyTorch's form
+    without weight decay). Returns new (param, exp_avg, exp_avg_sq) arrays."""
+    p = np.array(param, dtype=np.float64, copy=True).reshape(-1)
+    g = np.ascontiguousarray(np.asarray(grad, dtype=np.float64).reshape(-1))
+    m = np.array(exp_avg, dtype=np.float64, copy=True).reshape(-1)
+    v = np.array(exp_avg_sq, dtype=np.float64, copy=True).reshape(-1)
+    assert p.shape == g.shape == m.shape == v.shape
+    lib().orc_adam_step(p.size, _P(p), _P(g), _P(m), _P(v), float(lr), float(beta1), float(beta2),
+                        float(eps), int(step))
+    shape = np.shape(param)
+    return p.reshape(shape), m.reshape(shape), v.reshape(shape)

@@ -1047,6 +1047,24 @@ void orc_sh_basis(const double* dir, double* Y, double* dY) {
       for (int r = 0; r < 3; ++r) dY[3 * k + r] = dYl[k][r];
 }
 
+// One Adam step (Kingma and Ba, "Adam: A Method for Stochastic
+// Optimization", Algorithm 1), in the form PyTorch's Adam uses without weight
+// decay: the first and second moment estimates are updated, bias-corrected by
+// 1 - beta^step, and the parameter moves by lr * mhat / (sqrt(vhat) + eps).
+// The paper reuses its baseline's optimiser and states none of this.
+void orc_adam_step(int64_t n, double* p, const double* g, double* m, double* v, double lr,
+                   double beta1, double beta2, double eps, int step) {
+  const double bc1 = 1.0 - std::pow(beta1, step);
+  const double bc2 = 1.0 - std::pow(beta2, step);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = beta1 * m[i] + (1.0 - beta1) * g[i];
+    v[i] = beta2 * v[i] + (1.0 - beta2) * g[i] * g[i];
+    const double mhat = m[i] / bc1;
+    const double vhat = v[i] / bc2;
+    p[i] -= lr * mhat / (std::sqrt(vhat) + eps);
+  }
+}
+
 void orc_set_margins(double alpha_tol, double T_tol, double power_tol) {
   g_tol_alpha = alpha_tol; g_tol_T = T_tol; g_tol_power = power_tol;
 }

@@ -431,3 +431,50 @@ def test_pixel_subset_render_equals_full_render(tiny):
     part = oracle.render_backward_pixels(sp, px, py, dL[:, py, px].T)
     for k in ("uv", "conic", "opacity", "rgb"):
         np.testing.assert_allclose(part[k], full[k], rtol=1e-12, atol=1e-12 * np.abs(full[k]).max())
+
+
+def test_adam_first_step_closed_form():
+    # from zero moments the bias corrections cancel: m_hat = g, v_hat = g^2,
+    # so the step is lr * g / (|g| + eps) (Kingma and Ba, Algorithm 1)
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal(257) * np.exp(rng.uniform(-6, 3, 257))
+    g[:3] = [0.0, 1e-12, -1e-12]
+    p0 = rng.standard_normal(257)
+    lr, b1, b2, eps = 0.01, 0.9, 0.999, 1e-8
+    p, m, v = oracle.adam_step(p0, g, np.zeros(257), np.zeros(257), lr, 1, b1, b2, eps)
+    np.testing.assert_allclose(m, (1 - b1) * g, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(v, (1 - b2) * g * g, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(p, p0 - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    assert p[0] == p0[0]
+
+
+def test_adam_without_momentum_is_normalised_gradient_every_step():
+    # beta1 = beta2 = 0: m = g and v = g^2 at every step, bias corrections are 1
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(64)
+    m = rng.standard_normal(64)
+    v = rng.uniform(0, 1, 64)
+    for step in range(1, 4):
+        g = rng.standard_normal(64)
+        p_new, m, v = oracle.adam_step(p, g, m, v, 0.1, step, 0.0, 0.0, 1e-3)
+        np.testing.assert_allclose(p_new, p - 0.1 * g / (np.abs(g) + 1e-3), rtol=0, atol=1e-15)
+        np.testing.assert_array_equal(m, g)
+        p = p_new
+
+
+def test_adam_matches_torch_optim_adam_float64():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    p0 = rng.standard_normal(1000)
+    tp = torch.nn.Parameter(torch.tensor(p0, dtype=torch.float64))
+    opt = torch.optim.Adam([tp], lr=3e-3, betas=(0.8, 0.95), eps=1e-6)
+    p, m, v = p0.copy(), np.zeros(1000), np.zeros(1000)
+    for step in range(1, 8):
+        g = rng.standard_normal(1000) * (0.1 if step % 2 else 10.0)
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        p, m, v = oracle.adam_step(p, g, m, v, 3e-3, step, 0.8, 0.95, 1e-6)
+    st = opt.state[tp]
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(m, st["exp_avg"].numpy(), rtol=1e-13, atol=0)
+    np.testing.assert_allclose(v, st["exp_avg_sq"].numpy(), rtol=1e-13, atol=0)
