@@ -156,8 +156,13 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
     geo = 12 + 12 + 16 + 4
     m = {
         "temporal_compact": ("hbm", 8 * n + 4 * nsel),
-        "project": ("hbm", nsel * (4 + geo + 12) + 8 * nfr + n_kept_gaussians * (4 + kk)
-                    + S * (8 + 16 + 16 + 8 + 1 + 4)),
+        # masks: ids, geometry, two masks out, the life record where in frustum,
+        # the (index, id) work list; scan: masks in, offsets out; splats: the
+        # work list, mask, offset, geometry and SH in, 53-byte records out
+        "project": ("hbm", nsel * (4 + geo + 8) + 8 * nfr + n_kept_gaussians * 8),
+        "splat_scan": ("hbm", nsel * 8),
+        "project_splats": ("hbm", n_kept_gaussians * (8 + 4 + 4 + geo + kk)
+                           + S * (8 + 16 + 16 + 8 + 1 + 4)),
         "sort_depth_pass0": ("hbm", S * (4 + 8)),
         "sort_depth_pass1": ("hbm", S * 16),
         "sort_depth_pass2": ("hbm", S * 16),
@@ -165,8 +170,9 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         # duplication: the scan reads each sorted splat's id, rect and view and
         # writes its offset and descriptor; the expansion writes the pairs
         "duplicate": ("hbm", S * (4 + 8 + 1) + S * (4 + 16)),
-        "duplicate_expand": ("hbm", S * (4 + 16) + K * 8),
-        "tile_counts": ("hbm", tiles * (4 * 3 + 8)),
+        "duplicate_expand": ("hbm", S * (4 + 16) + K * 8),   # + tile-digit histograms (on chip)
+        # boundary detection: the sorted pair keys in, [start, end) per tile out
+        "tile_ranges": ("hbm", K * 4 + tiles * 8),
         "zero_splat_grads": ("hbm", S * 48),
         "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + 2 * (geo + kk)) + S * 48),
         # FP32 instructions per (pixel, splat) pair the forward visits: forward

@@ -38,7 +38,7 @@ struct ProjArgs {
   uint32_t* frustum_mask;
   uint32_t* keep_mask;
   uint32_t* splat_start;
-  uint32_t* kept_list;
+  uint2* kept_list;
   float2* sp_xy;
   float4* sp_conic_o;
   float4* sp_rgb_d;
@@ -50,7 +50,6 @@ struct ProjArgs {
   unsigned long long* lookback;
   int64_t cap_splats;
   const InstMat* mats;      // [n_views][n_inst+1], from k_compose
-  int32_t* tile_diff;       // per-tile pair counts as a difference array
 };
 
 // W_v * P_k for every view v and segment k (k = 0: identity pose), and the
@@ -101,64 +100,45 @@ __global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __re
   }
 }
 
-template <int DEG>
-__global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ ViewSet vs, ProjArgs a) {
+// Pass 1: every selected Gaussian against every camera. Writes the frustum
+// and keep masks, applies Eq. 5 to the point life (on the frustum mask, before
+// LOD) and appends Gaussians kept in at least one view to the work list.
+__global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant__ ViewSet vs,
+                                                           ProjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // composed matrices are read through L1: a CTA's Gaussians are contiguous,
-  // so they touch the matrices of very few instances
   const InstMat* __restrict__ mats = a.mats;
   const int nk = a.n_inst + 1;
   uint32_t* s_off = reinterpret_cast<uint32_t*>(smem_raw);   // [n_inst+2]
-  __shared__ uint32_t s_hist[4][kRadix];
-  __shared__ uint32_t s_warp[kWarps];
-  __shared__ uint32_t s_tile, s_base, s_frustum;
-  constexpr int K = sh_count(DEG);
-
+  __shared__ uint32_t s_frustum;
+  __shared__ uint32_t s_wcount[kWarps];
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
-  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
   if (threadIdx.x == 0) s_frustum = 0;
   __syncthreads();
-
   const uint32_t n_sel = a.ctr[kCtrSelected];
-  const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageProject);
-  const int64_t n_tiles = ((int64_t)n_sel + kThreads - 1) / kThreads;
-  const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
   const uint32_t lt = lanemask_lt();
-  bool overflow = false;
-
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageProject, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= n_tiles) break;
-    const int64_t j = tile * kThreads + threadIdx.x;
+  uint32_t nfr_local = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int warp = threadIdx.x >> 5;
+  // whole blocks stay in the loop (block-wide append below)
+  const int64_t span = ((int64_t)n_sel + kThreads - 1) / kThreads * kThreads;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < span; j += stride) {
     const bool active = j < (int64_t)n_sel;
-
-    // ---- load the Gaussian (geometry only)
-    uint32_t gid = 0;
-    int k = 0;
-    float mu[3] = {0.f, 0.f, 0.f}, RS[9];
+    uint32_t fmask = 0, kmask = 0, gid = 0;
     if (active) {
       gid = a.selected[j];
-      k = segment_of(s_off, a.n_inst, gid);
-      mu[0] = a.means[3 * (size_t)gid];
-      mu[1] = a.means[3 * (size_t)gid + 1];
-      mu[2] = a.means[3 * (size_t)gid + 2];
+      const int k = segment_of(s_off, a.n_inst, gid);
+      const float mu[3] = {a.means[3 * (size_t)gid], a.means[3 * (size_t)gid + 1],
+                           a.means[3 * (size_t)gid + 2]};
       const float s0 = __expf(a.log_scales[3 * (size_t)gid]);
       const float s1 = __expf(a.log_scales[3 * (size_t)gid + 1]);
       const float s2 = __expf(a.log_scales[3 * (size_t)gid + 2]);
-      float R[9];
+      float R[9], RS[9];
       quat_to_rot(a.quats[gid], R);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         RS[3 * r] = R[3 * r] * s0; RS[3 * r + 1] = R[3 * r + 1] * s1; RS[3 * r + 2] = R[3 * r + 2] * s2;
       }
-    }
-
-    // ---- pass 1: frustum and keep masks
-    uint32_t fmask = 0, kmask = 0;
-    if (active) {
       for (int v = 0; v < vs.n_views; ++v) {
         const Proj2D p = project_view(mats[v * nk + k], mu, RS, vs.v[v]);
         if (p.infrustum) {
@@ -166,96 +146,228 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
           if (p.sigma >= a.lod) kmask |= 1u << v;
         }
       }
+      a.frustum_mask[j] = fmask;
+      a.keep_mask[j] = kmask;
+      // Eq. 5: point-life update on M_t (before LOD)
+      if (fmask && a.life) {
+        const float2 l = a.life[gid];
+        const float2 nl = make_float2(fminf(l.x, a.t), fmaxf(l.y, a.t));
+        if (nl.x != l.x || nl.y != l.y) a.life[gid] = nl;
+      }
     }
-    const uint32_t nkept = __popc(kmask);
-
-    // ---- Eq. 5: point-life update on M_t (before LOD)
-    if (fmask && a.life) {
-      const float2 l = a.life[gid];
-      const float2 nl = make_float2(fminf(l.x, a.t), fmaxf(l.y, a.t));
-      if (nl.x != l.x || nl.y != l.y) a.life[gid] = nl;
+    nfr_local += fmask ? 1u : 0u;
+    // append the kept Gaussians to the work list: one atomic per block
+    // iteration (a per-warp atomic on one counter serialises in L2)
+    const uint32_t kb = __ballot_sync(0xffffffffu, kmask != 0u);
+    if (lane == 0) s_wcount[warp] = (uint32_t)__popc(kb);
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t c = lane < kWarps ? s_wcount[lane] : 0u;
+      uint32_t incl = c;
+#pragma unroll
+      for (int o = 1; o < kWarps; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, kWarps - 1);
+      uint32_t base = 0;
+      if (lane == 0 && total) base = atomicAdd(a.ctr + kCtrKept, total);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (lane < kWarps) s_wcount[lane] = base + incl - c;
     }
+    __syncthreads();
+    if (kmask) a.kept_list[s_wcount[warp] + __popc(kb & lt)] = make_uint2((uint32_t)j, gid);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nfr_local += __shfl_xor_sync(0xffffffffu, nfr_local, o);
+  if (lane == 0 && nfr_local) atomicAdd(&s_frustum, nfr_local);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_frustum) atomicAdd(a.ctr + kCtrFrustum, s_frustum);
+}
 
-    // ---- block scan of kept-view counts, look-back for the splat base
-    uint32_t incl = nkept;
+// First splat of every selected Gaussian: an exclusive scan of the kept-view
+// counts popc(keep_mask) in 4096-Gaussian tiles (block scan + warp look-back).
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restrict__ keep_mask,
+                                                         uint32_t* __restrict__ splat_start,
+                                                         uint32_t* ctr,
+                                                         unsigned long long* lookback) {
+  __shared__ uint32_t s_tile, s_base;
+  __shared__ uint32_t s_warp[kWarps];
+  const uint32_t n_sel = ctr[kCtrSelected];
+  const int64_t n_tiles = ((int64_t)n_sel + kScanTile - 1) / kScanTile;
+  const uint32_t tag = stage_tag(ctr[kCtrEpoch], kStageProject);
+  const int warp = threadIdx.x >> 5;
+  const uint32_t lane = lane_id();
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= n_tiles) break;
+    const int64_t j0 = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t c[kScanItems], run = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      c[i] = (j0 + i < (int64_t)n_sel) ? (uint32_t)__popc(keep_mask[j0 + i]) : 0u;
+      run += c[i];
+    }
+    uint32_t incl = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= (uint32_t)o) incl += y;
     }
-    const uint32_t nfr = __popc(__ballot_sync(0xffffffffu, fmask != 0));
     if (lane == 31) s_warp[warp] = incl;
-    if (lane == 0 && nfr) atomicAdd(&s_frustum, nfr);
     __syncthreads();
     if (warp == 0) {
-      const uint32_t c = lane < kWarps ? s_warp[lane] : 0u;
-      uint32_t wincl = c;
+      const uint32_t wc = lane < kWarps ? s_warp[lane] : 0u;
+      uint32_t wi = wc;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, wincl, o);
-        if (lane >= (uint32_t)o) wincl += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= (uint32_t)o) wi += y;
       }
-      const uint32_t total = __shfl_sync(0xffffffffu, wincl, 31);
-      const uint32_t prefix = warp_lookback(a.lookback, tile, tag, total, a.ctr);
-      if (lane < kWarps) s_warp[lane] = wincl - c;
+      const uint32_t total = __shfl_sync(0xffffffffu, wi, 31);
+      const uint32_t prefix = warp_lookback(lookback, tile, tag, total, ctr);
+      if (lane < kWarps) s_warp[lane] = wi - wc;
       if (lane == 0) {
         s_base = prefix;
-        if (tile == n_tiles - 1) a.ctr[kCtrSplats] = prefix + total;
+        if (tile == n_tiles - 1) ctr[kCtrSplats] = prefix + total;
       }
     }
     __syncthreads();
-    uint32_t s = s_base + s_warp[warp] + incl - nkept;
-
-    if (active) {
-      a.frustum_mask[j] = fmask;
-      a.keep_mask[j] = kmask;
-      a.splat_start[j] = s;
+    uint32_t off = s_base + s_warp[warp] + incl - run;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      if (j0 + i < (int64_t)n_sel) splat_start[j0 + i] = off;
+      off += c[i];
     }
-    // append the kept Gaussians to the backward's work list (one atomic per warp)
-    {
-      const uint32_t kb = __ballot_sync(0xffffffffu, kmask != 0u);
-      uint32_t kbase = 0;
-      if (lane == 0 && kb) kbase = atomicAdd(a.ctr + kCtrKept, (uint32_t)__popc(kb));
-      kbase = __shfl_sync(0xffffffffu, kbase, 0);
-      if (kmask) a.kept_list[kbase + __popc(kb & lt)] = (uint32_t)j;
-    }
+    __syncthreads();
+  }
+}
 
-    // ---- pass 2: kept views -> splats
-    if (kmask) {
+// Pass 2: the kept (Gaussian, view) pairs become splats: projection of the
+// kept views, SH colour, the splat record and its depth-key digit histograms.
+// A warp takes 32 work-list entries; their SH rows are staged through shared
+// memory with coalesced loads (a lane per 16 B of the warp's rows) instead of
+// 32 scattered rows per load instruction.
+
+template <int DEG>
+struct ShStage {
+  static constexpr int K = sh_count(DEG);
+  static constexpr bool kVec = (K * 3) % 4 == 0;
+  static constexpr int kRow = kVec ? K * 3 / 4 : K * 3;     // float4s or floats per Gaussian
+  static constexpr int kPitch = kVec ? kRow + 1 : kRow + 1;  // padded (bank spread)
+  static constexpr int kWords = 32 * kPitch * (kVec ? 4 : 1);
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_constant__ ViewSet vs,
+                                                             ProjArgs a) {
+  using St = ShStage<DEG>;
+  constexpr int K = St::K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const InstMat* __restrict__ mats = a.mats;
+  const int nk = a.n_inst + 1;
+  float* s_sh = reinterpret_cast<float*>(smem_raw);                        // [warps][kWords]
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_sh + kWarps * St::kWords);  // [n_inst+2]
+  __shared__ uint32_t s_hist[4][kRadix];
+  // per-lane view indices differ: camera records are read from shared memory
+  __shared__ ViewInfo s_views[S3R_MAX_VIEWS];
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(vs.v);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
+    const int words = vs.n_views * (int)(sizeof(ViewInfo) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const uint32_t lane = lane_id();
+  float* my_sh = s_sh + warp * St::kWords;
+  const uint32_t n_kept = a.ctr[kCtrKept];
+  bool overflow = false;
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < (int64_t)n_kept;
+       base += (int64_t)gridDim.x * kThreads) {
+    const int64_t t = base + lane;
+    const int n_here = (int)min((int64_t)32, (int64_t)n_kept - base);
+    const bool valid = lane < (uint32_t)n_here;
+    const uint2 e = valid ? a.kept_list[t] : make_uint2(0u, 0u);
+    const uint32_t j = e.x, gid = e.y;
+    // coalesced SH stage: element q of row g goes to my_sh[g * pitch + q]
+    if constexpr (St::kVec) {
+      const float4* src = a.sh;
+      float4* dst = reinterpret_cast<float4*>(my_sh);
+#pragma unroll
+      for (int it = 0; it < St::kRow; ++it) {
+        const int idx = it * 32 + (int)lane;
+        const int g = idx / St::kRow, q = idx - g * St::kRow;
+        const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+        if (g < n_here) dst[g * St::kPitch + q] = __ldg(src + (size_t)gg * St::kRow + q);
+      }
+    } else {
+      const float* src = a.sh_f;
+#pragma unroll
+      for (int it = 0; it < St::kRow; ++it) {
+        const int idx = it * 32 + (int)lane;
+        const int g = idx / St::kRow, q = idx - g * St::kRow;
+        const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+        if (g < n_here) my_sh[g * St::kPitch + q] = __ldg(src + (size_t)gg * St::kRow + q);
+      }
+    }
+    __syncwarp();
+    if (valid) {
+      const uint32_t kmask = a.keep_mask[j];
+      uint32_t s = a.splat_start[j];
+      const int k = segment_of(s_off, a.n_inst, gid);
+      const float mu[3] = {a.means[3 * (size_t)gid], a.means[3 * (size_t)gid + 1],
+                           a.means[3 * (size_t)gid + 2]};
+      const float s0 = __expf(a.log_scales[3 * (size_t)gid]);
+      const float s1 = __expf(a.log_scales[3 * (size_t)gid + 1]);
+      const float s2 = __expf(a.log_scales[3 * (size_t)gid + 2]);
+      const float4 qv = a.quats[gid];
       const float opac = 1.f / (1.f + __expf(-a.opac_logits[gid]));
-      const float4* sh4 = a.sh + (size_t)gid * (K * 3 / 4);   // K*3 % 4 == 0 for K = 4, 16
-      const float* sh1 = a.sh_f + (size_t)gid * K * 3;
+      float R[9], RS[9];
+      quat_to_rot(qv, R);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        RS[3 * r] = R[3 * r] * s0; RS[3 * r + 1] = R[3 * r + 1] * s1; RS[3 * r + 2] = R[3 * r + 2] * s2;
+      }
+      const float* row_sh = my_sh + lane * St::kPitch * (St::kVec ? 4 : 1);
       uint32_t m = kmask;
       while (m) {
         const int v = __ffs(m) - 1;
         m &= m - 1;
         const InstMat& M = mats[v * nk + k];
-        const Proj2D p = project_view(M, mu, RS, vs.v[v]);
+        const ViewInfo& vi = s_views[v];
+        const Proj2D p = project_view(M, mu, RS, vi);
         float rp[3];
         rel_pos(M, mu, rp);
-        float dx = rp[0], dy = rp[1], dz = rp[2];
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
+        const float inv = rsqrtf(rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2]);
         float Y[16];
-        sh_basis<DEG>(dx, dy, dz, Y);
+        sh_basis<DEG>(rp[0] * inv, rp[1] * inv, rp[2] * inv, Y);
         float rgb[3] = {0.5f, 0.5f, 0.5f};
-        if constexpr ((K * 3) % 4 == 0) {
-          // 128-bit loads: coefficient 4q+e of the [K][3] row
+        if constexpr (St::kVec) {
+          const float4* r4 = reinterpret_cast<const float4*>(row_sh);
 #pragma unroll
-          for (int qd = 0; qd < K * 3 / 4; ++qd) {
-            const float4 c4 = __ldg(sh4 + qd);
+          for (int qd = 0; qd < St::kRow; ++qd) {
+            const float4 c4 = r4[qd];
             const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int f = 4 * qd + e;
-              rgb[f % 3] = fmaf(cv[e], Y[f / 3], rgb[f % 3]);
+            for (int ee = 0; ee < 4; ++ee) {
+              const int f = 4 * qd + ee;
+              rgb[f % 3] = fmaf(cv[ee], Y[f / 3], rgb[f % 3]);
             }
           }
         } else {
 #pragma unroll
           for (int i = 0; i < K; ++i)
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(__ldg(sh1 + 3 * i + ch), Y[i], rgb[ch]);
+            for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaf(row_sh[3 * i + ch], Y[i], rgb[ch]);
         }
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
@@ -272,54 +384,61 @@ __global__ void __launch_bounds__(kThreads) k_project(const __grid_constant__ Vi
           atomicAdd(&s_hist[1][(key >> 8) & 0xffu], 1u);
           atomicAdd(&s_hist[2][(key >> 16) & 0xffu], 1u);
           atomicAdd(&s_hist[3][key >> 24], 1u);
-          // pairs per tile: +1 / -1 at the ends of each covered tile row
-          const int gx = vs.v[v].gx, w = p.x1 - p.x0;
-          int32_t* row = a.tile_diff + vs.v[v].tile_base + p.y0 * gx + p.x0;
-          for (int ty = p.y0; ty < p.y1; ++ty, row += gx) {
-            atomicAdd(row, 1);
-            atomicAdd(row + w, -1);
-          }
         } else {
           overflow = true;
         }
         ++s;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
-
-  // ---- flush the CTA's digit histograms and counters
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
     const uint32_t c = (&s_hist[0][0])[i];
     if (c) atomicAdd(a.hist + kHistDepth * kRadix + i, c);
   }
-  if (threadIdx.x == 0 && s_frustum) atomicAdd(a.ctr + kCtrFrustum, s_frustum);
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
+}
+
+template <typename F>
+int occupancy(F fn, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm;
 }
 
 template <int DEG>
 cudaError_t launch_deg(s3r_workspace* ws, const ProjArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(uint32_t) * (ws->n_inst + 2) + 16;
-  // attribute and occupancy are queried once per shared-memory size, so that a
-  // launch inside CUDA-graph capture issues nothing but the kernel
-  static thread_local size_t cached_smem = 0;
-  static thread_local int cached_per_sm = 0;
-  if (smem != cached_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_project<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_project<DEG>, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    cached_smem = smem;
-    cached_per_sm = per_sm;
+  const size_t smem_splats = sizeof(float) * kWarps * ShStage<DEG>::kWords + smem;
+  // occupancy is queried once (the first, eager call), so that a launch
+  // inside CUDA-graph capture issues nothing but the kernels
+  static thread_local int per_mask = 0, per_splats = 0, per_scan = 0;
+  if (!per_mask) per_mask = occupancy(k_project_mask, smem);
+  if (!per_splats) {
+    cudaFuncSetAttribute(k_project_splats<DEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(float) * kWarps * ShStage<DEG>::kWords + 16 * 1024));
+    per_splats = occupancy(k_project_splats<DEG>, smem_splats);
   }
-  const int per_sm = cached_per_sm;
-  const int grid = ws->num_sms * per_sm;
-  KernelTimer timer(ws, kKProject, st);
-  k_project<DEG><<<grid, kThreads, smem, st>>>(ws->views, a);
+  if (!per_scan) per_scan = occupancy(k_splat_scan, 0);
+  {
+    KernelTimer timer(ws, kKProject, st);
+    k_project_mask<<<ws->num_sms * per_mask, kThreads, smem, st>>>(ws->views, a);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  {
+    KernelTimer timer(ws, kKSplatScan, st);
+    k_splat_scan<<<ws->num_sms * per_scan, kThreads, 0, st>>>(a.keep_mask, a.splat_start, a.ctr,
+                                                              a.lookback);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    KernelTimer timer(ws, kKProjectSplats, st);
+    k_project_splats<DEG><<<ws->num_sms * per_splats, kThreads, smem_splats, st>>>(ws->views, a);
+  }
   return cudaGetLastError();
 }
 
@@ -357,11 +476,6 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.lookback = ws->lookback;
   a.cap_splats = ws->cap.max_splats;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
-  a.tile_diff = ws->tile_diff;
-  {
-    cudaError_t e0 = cudaMemsetAsync(ws->tile_diff, 0, sizeof(int32_t) * ((size_t)ws->views.total_tiles + 1), st);
-    if (e0 != cudaSuccess) return e0;
-  }
   {
     KernelTimer timer(ws, kKCompose, st);
     k_compose<<<ws->n_views, 128, 0, st>>>(ws->views, a.pose_q, a.pose_t, sc->n_inst,

@@ -30,7 +30,7 @@ struct BwdArgs {
   const float* pose_t;
   const uint32_t* selected;
   const uint32_t* keep_mask;
-  const uint32_t* kept_list;
+  const uint2* kept_list;
   const uint32_t* splat_start;
   const float4* sp_grad;   // [S][3] float4
   int64_t cap_splats;
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     if (tile >= n_tiles) break;
     const int64_t jt = tile * kThreads + threadIdx.x;
     if (jt >= (int64_t)n_sel) continue;
-    const uint32_t j = a.kept_list[jt];
+    const uint2 kept = a.kept_list[jt];
+    const uint32_t j = kept.x, gid = kept.y;
     const uint32_t kmask = a.keep_mask[j];
     if (!kmask) continue;
-    const uint32_t gid = a.selected[j];
     const int k = segment_of(s_off, a.n_inst, gid);
     uint32_t s = a.splat_start[j];
 

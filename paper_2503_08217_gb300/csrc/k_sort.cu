@@ -171,6 +171,8 @@ constexpr int kExpItems = 16;                         // outputs per thread per 
 constexpr int kExpChunk = kDupThreads * kExpItems;    // 4096 outputs per chunk
 
 struct DupArgs {
+  uint32_t* hist;        // tile-digit histograms of the radix passes that follow
+  int tile_passes;
   const uint32_t* sorted_splats;
   const uint2* sp_rect;
   const uint8_t* sp_view;
@@ -243,11 +245,42 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant_
   }
 }
 
+// Per-thread run-length counting of the radix digits of a key sequence: one
+// shared atomic per run of equal digits (consecutive outputs walk a tile
+// row, so the higher digits repeat for many outputs).
+struct DigitRuns {
+  uint32_t d[4], n[4];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) { d[p] = 0; n[p] = 0; }
+  }
+  __device__ __forceinline__ void add(uint32_t (*s_hist)[kRadix], uint32_t key, int passes) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (p >= passes) break;
+      const uint32_t dg = (key >> (8 * p)) & 0xffu;
+      if (dg != d[p]) {
+        if (n[p]) atomicAdd(&s_hist[p][d[p]], n[p]);
+        d[p] = dg;
+        n[p] = 0;
+      }
+      ++n[p];
+    }
+  }
+  __device__ __forceinline__ void flush(uint32_t (*s_hist)[kRadix], int passes) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+      if (p < passes && n[p]) atomicAdd(&s_hist[p][d[p]], n[p]);
+  }
+};
+
 __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
   __shared__ uint32_t s_excl[kExpChunk + 1];
   __shared__ uint32_t s_key[kExpChunk];
   __shared__ uint32_t s_val[kExpChunk];
   __shared__ uint32_t s_chunk, s_q0, s_q1;
+  __shared__ uint32_t s_hist[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += kDupThreads) (&s_hist[0][0])[i] = 0;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
   const int64_t total = min((int64_t)a.ctr[kCtrDups], a.cap_dups);
   const int64_t n_chunks = (total + kExpChunk - 1) / kExpChunk;
@@ -294,6 +327,8 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
       uint32_t q_end = s_excl[q + 1];
       uint4 meta = a.dup_meta[q0 + q];
       const uint32_t oe = min(o0 + kExpItems, O1);
+      DigitRuns runs;
+      runs.init();
       for (uint32_t o = o0; o < oe; ++o) {
         while (o >= q_end) {
           ++q;
@@ -305,9 +340,12 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
         uint32_t row = (uint32_t)(((float)rr + 0.5f) * __uint_as_float(meta.w));
         row -= (row * w > rr) ? 1u : 0u;
         row += ((row + 1u) * w <= rr) ? 1u : 0u;
-        s_key[o - O0] = meta.y + row * gx + (rr - row * w);
+        const uint32_t key = meta.y + row * gx + (rr - row * w);
+        s_key[o - O0] = key;
         s_val[o - O0] = meta.x;
+        runs.add(s_hist, key, a.tile_passes);
       }
+      runs.flush(s_hist, a.tile_passes);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < O1 - O0; i += kDupThreads) {
@@ -316,73 +354,41 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
     }
     (void)lane;
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.tile_passes * kRadix; i += kDupThreads) {
+    const uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(a.hist + i, c);
+  }
 }
 
-// Per-tile pair counts from the projection's difference array (+1 / -1 at
-// the two ends of every covered tile row), their exclusive scan (the [start,
-// end) range of every tile in the sorted pair array, clamped to capacity),
-// and the digit histograms of the tile-id radix passes. One CTA; three walks
-// over the tiles (sum of differences, sum of counts, output).
-constexpr int kCountThreads = 1024;
+// Tile ranges by boundary detection in the sorted pair keys: the first and
+// one-past-last position of every tile id present; tiles without pairs keep
+// the [0, 0) written by the memset before the sort. Each thread takes
+// kRangeItems consecutive keys plus the one after them.
+constexpr int kRangeThreads = 256;
+constexpr int kRangeItems = 8;
 
-__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t x, uint32_t* s_tmp /*[32]*/) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const int warp = threadIdx.x >> 5;
-  uint32_t incl = x;
+__global__ void __launch_bounds__(kRangeThreads) k_tile_ranges(const uint32_t* __restrict__ keys,
+                                                               const uint32_t* ctr, int64_t cap,
+                                                               uint2* __restrict__ ranges) {
+  const int64_t K = min((int64_t)ctr[kCtrDups], cap);
+  const int64_t per = (int64_t)kRangeThreads * kRangeItems;
+  for (int64_t base = (int64_t)blockIdx.x * per; base < K; base += (int64_t)gridDim.x * per) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kRangeItems;
+    if (i0 >= K) continue;
+    uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+    uint32_t cur = keys[i0];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= (uint32_t)o) incl += y;
-  }
-  if (lane == 31) s_tmp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const uint32_t w = s_tmp[lane];
-    uint32_t wi = w;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= (uint32_t)o) wi += y;
+    for (int k = 0; k < kRangeItems; ++k) {
+      const int64_t i = i0 + k;
+      if (i >= K) break;
+      const uint32_t next = i + 1 < K ? keys[i + 1] : 0xffffffffu;
+      if (cur != prev) ranges[cur].x = (uint32_t)i;
+      if (cur != next) ranges[cur].y = (uint32_t)(i + 1);
+      prev = cur;
+      cur = next;
     }
-    s_tmp[lane] = wi - w;
   }
-  __syncthreads();
-  const uint32_t r = s_tmp[warp] + incl - x;
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kCountThreads) k_tile_counts(const int32_t* __restrict__ diff,
-                                                               int tiles, int passes, int64_t cap,
-                                                               uint2* __restrict__ ranges,
-                                                               uint32_t* __restrict__ hist) {
-  __shared__ uint32_t s_hist[4][kRadix];
-  __shared__ uint32_t s_tmp[32];
-  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-  const int per = (tiles + kCountThreads - 1) / kCountThreads;
-  const int t0 = min(tiles, (int)threadIdx.x * per), t1 = min(tiles, t0 + per);
-  int32_t dsum = 0;
-  for (int t = t0; t < t1; ++t) dsum += diff[t];
-  const int32_t enter = (int32_t)block_excl_scan_1024((uint32_t)dsum, s_tmp);   // count entering t0
-  uint32_t csum = 0;
-  int32_t c = enter;
-  for (int t = t0; t < t1; ++t) {
-    c += diff[t];
-    csum += (uint32_t)c;
-  }
-  uint32_t start = block_excl_scan_1024(csum, s_tmp);
-  c = enter;
-  for (int t = t0; t < t1; ++t) {
-    c += diff[t];
-    const uint32_t cnt = (uint32_t)c;
-    const uint32_t b = (uint32_t)min((int64_t)start, cap), e = (uint32_t)min((int64_t)start + cnt, cap);
-    ranges[t] = cnt ? make_uint2(b, e) : make_uint2(0u, 0u);   // empty tiles: [0, 0)
-    start += cnt;
-    if (cnt)
-      for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][((uint32_t)t >> (8 * p)) & 0xffu], cnt);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) hist[i] = (&s_hist[0][0])[i];
 }
 
 int per_sm_for(const void* fn, int threads) {
@@ -435,13 +441,8 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.cap_dups = ws->cap.max_duplicates;
   d.ctr = ws->ctr;
   d.lookback = ws->lookback;
-  {
-    KernelTimer timer(ws, kKTileCounts, st);
-    k_tile_counts<<<1, kCountThreads, 0, st>>>(ws->tile_diff, ws->views.total_tiles, ws->tile_passes,
-                                               ws->cap.max_duplicates, ws->ranges,
-                                               ws->hist + kHistTile * kRadix);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  d.hist = ws->hist + kHistTile * kRadix;
+  d.tile_passes = ws->tile_passes;
   {
     KernelTimer timer(ws, kKDuplicate, st);
     k_dup_scan<<<ws->num_sms * dup_per_sm, kDupThreads, 0, st>>>(ws->views, d);
@@ -471,7 +472,18 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   ws->dup_final = ws->tile_passes & 1;
-  return cudaSuccess;
+  // ranges of the tiles present in the sorted pairs; the rest stay [0, 0)
+  if ((e = cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->views.total_tiles, st)) !=
+      cudaSuccess)
+    return e;
+  {
+    static thread_local int range_per_sm = 0;
+    if (!range_per_sm) range_per_sm = per_sm_for((const void*)k_tile_ranges, kRangeThreads);
+    KernelTimer timer(ws, kKTileRanges, st);
+    k_tile_ranges<<<ws->num_sms * range_per_sm, kRangeThreads, 0, st>>>(
+        ws->dup_key[ws->dup_final], ws->ctr, ws->cap.max_duplicates, ws->ranges);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace s3r

@@ -61,9 +61,9 @@ cudaError_t alloc(s3r_workspace* ws, T** p, int64_t count) {
 }
 
 const char* const kKernelNames[kKCount] = {
-    "begin", "temporal_compact", "compose", "project", "sort_depth_pass0", "sort_depth_pass1",
+    "begin", "temporal_compact", "compose", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
-    "sort_tile_pass2", "sort_tile_pass3", "tile_counts", "duplicate_expand", "blend_fwd", "zero_splat_grads",
+    "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd", "zero_splat_grads",
     "blend_bwd", "project_bwd", "pose_chain"};
 
 void free_all(s3r_workspace* ws) {
@@ -74,7 +74,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->tile_diff, ws->dup_excl, ws->dup_meta, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -193,7 +193,6 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->sp_grad, 12 * S);
   S3R_ALLOC(ws->pose_dM, (int64_t)cap->max_views * nk * 12);
   S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
-  S3R_ALLOC(ws->tile_diff, cap->max_tiles + 1);
   S3R_ALLOC(ws->dup_excl, S + 1);
   S3R_ALLOC(ws->dup_meta, 4 * S);
   ws->contrib_words = K / 32 + 2;

@@ -73,8 +73,8 @@ constexpr int kHistCount = 8;
 
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
-  kKBegin = 0, kKCompact, kKCompose, kKProject, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
-  kKTile0, kKTile1, kKTile2, kKTile3, kKTileCounts, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
+  kKBegin = 0, kKCompact, kKCompose, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
+  kKTile0, kKTile1, kKTile2, kKTile3, kKTileRanges, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
   kKProjectBwd, kKPoseChain, kKCount
 };
 
@@ -94,7 +94,7 @@ struct s3r_workspace {
   uint32_t* frustum_mask;   // [N]
   uint32_t* keep_mask;      // [N]
   uint32_t* splat_start;    // [N]
-  uint32_t* kept_list;      // [N] compacted indices of Gaussians kept in >= 1 view (any order)
+  uint2* kept_list;         // [N] (compacted index, Gaussian id) of those kept in >= 1 view (any order)
   float2* sp_xy;            // [S]
   float4* sp_conic_o;       // [S]
   float4* sp_rgb_d;         // [S]
@@ -110,7 +110,6 @@ struct s3r_workspace {
   float* sp_grad;           // [S*12]
   float* pose_dM;           // [views*(inst+1)*12]
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
-  int32_t* tile_diff;       // [tiles+1] difference array of per-tile pair counts
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
   uint32_t* contrib;        // [4][K/32 + 2] bit per (warp block, sorted pair): blended in the forward
