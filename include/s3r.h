@@ -218,6 +218,25 @@ s3r_status s3r_update_visibility(int64_t n, float t, const uint32_t* mask, float
 s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float* dL_dpred,
                        float* loss_out, void* stream);
 
+/* One Adam step over several parameter tensors in a single launch (the
+ * optimiser of the training configuration; the paper states none and uses
+ * the density control and optimiser of its baseline). For each element:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
+ * (PyTorch's Adam without weight decay). `tensors` is a HOST array of up to
+ * S3R_ADAM_MAX_TENSORS descriptors of device arrays (FP32, n elements each,
+ * 4-byte aligned); param, exp_avg and exp_avg_sq are updated in place. */
+#define S3R_ADAM_MAX_TENSORS 8
+typedef struct {
+  float* param;
+  const float* grad;
+  float* exp_avg;
+  float* exp_avg_sq;
+  int64_t n;
+} s3r_adam_tensor;
+s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void* stream);
+
 /* Per-kernel device timing (tracing). With timing enabled, every kernel the
  * workspace's calls launch is bracketed by a pair of CUDA events owned by the
  * workspace (recorded on the caller's stream, so this also works inside a

@@ -25,7 +25,8 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_sort", "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
-           "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static")
+           "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
+           "s3r_adam_step")
 
 
 class S3RError(RuntimeError):
@@ -65,6 +66,11 @@ class Capacity(ctypes.Structure):
                 ("max_pixels", ctypes.c_int64)]
 
 
+class AdamTensor(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("exp_avg", ctypes.c_void_p),
+                ("exp_avg_sq", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
 class Counts(ctypes.Structure):
     _fields_ = [("n_selected", ctypes.c_int64), ("n_splats", ctypes.c_int64),
                 ("n_duplicates", ctypes.c_int64), ("n_frustum", ctypes.c_int64),
@@ -98,6 +104,7 @@ def load(path: str = LIB_PATH):
     L.s3r_l1_loss.argtypes = [i64, vp, vp, vp, vp, vp]
     L.s3r_set_timing.argtypes = [vp, i32]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
+    L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
     L.s3r_kernel_count.restype = i32
     L.s3r_kernel_name.argtypes = [i32]
     L.s3r_kernel_name.restype = ctypes.c_char_p
@@ -111,7 +118,7 @@ def load(path: str = LIB_PATH):
     for name in ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_project", "s3r_sort",
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
-                 "s3r_kernel_times", "s3r_select_visible_static"):
+                 "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -287,6 +294,21 @@ def select_visible_static(vis_window, t: float, out_idx, out_count, stream=None)
     n = int(vis_window.shape[0]) if vis_window is not None else 0
     _check(load().s3r_select_visible_static(n, float(t), _ptr(vis_window), _ptr(out_idx),
                                             _ptr(out_count), _stream(stream)))
+
+
+def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    """One fused Adam step over up to 8 (param, grad, m, v) tensor groups."""
+    if not (len(params) == len(grads) == len(exp_avgs) == len(exp_avg_sqs)):
+        raise ValueError("adam_step: one gradient and two moment tensors per parameter")
+    arr = (AdamTensor * max(1, len(params)))()
+    for i, (p, g, m, v) in enumerate(zip(params, grads, exp_avgs, exp_avg_sqs)):
+        for t in (p, g, m, v):
+            if t.dtype != torch.float32 or t.numel() != p.numel():
+                raise ValueError("adam_step: float32 tensors of equal size required")
+        arr[i] = AdamTensor(_ptr(p), _ptr(g), _ptr(m), _ptr(v), int(p.numel()))
+    _check(load().s3r_adam_step(arr, len(params), float(lr), float(beta1), float(beta2),
+                                float(eps), int(step), _stream(stream)))
 
 
 def update_visibility(n: int, t: float, mask, point_life, vis_window, mode: int, stream=None):

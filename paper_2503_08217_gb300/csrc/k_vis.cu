@@ -50,7 +50,84 @@ __global__ void k_l1(int64_t n, const float* __restrict__ pred, const float* __r
   }
 }
 
+// Fused Adam over up to 8 tensors laid end to end in one index space of work
+// units: four elements (one 128-bit access per array) where all four arrays of
+// a tensor are 16-byte aligned, else one element.
+struct AdamSet {
+  s3r_adam_tensor t[S3R_ADAM_MAX_TENSORS];
+  int64_t ustart[S3R_ADAM_MAX_TENSORS + 1];   // first work unit of each tensor
+  int vec[S3R_ADAM_MAX_TENSORS];
+  int count;
+  float lr, b1, b2, eps, inv_bc1, inv_sqrt_bc2;
+};
+
+__device__ __forceinline__ void adam1(const AdamSet& s, float& p, float g, float& m, float& v) {
+  m = fmaf(s.b1, m, (1.f - s.b1) * g);
+  v = fmaf(s.b2, v, (1.f - s.b2) * g * g);
+  p -= s.lr * (m * s.inv_bc1) / (sqrtf(v) * s.inv_sqrt_bc2 + s.eps);
+}
+
+__global__ void k_adam(const __grid_constant__ AdamSet s) {
+  const int64_t total = s.ustart[s.count];
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (u >= s.ustart[k + 1]) ++k;
+    const s3r_adam_tensor& t = s.t[k];
+    if (s.vec[k]) {
+      const int64_t e = 4 * (u - s.ustart[k]);
+      if (e + 4 <= t.n) {
+        float4 p = *reinterpret_cast<const float4*>(t.param + e);
+        const float4 g = *reinterpret_cast<const float4*>(t.grad + e);
+        float4 m = *reinterpret_cast<const float4*>(t.exp_avg + e);
+        float4 v = *reinterpret_cast<const float4*>(t.exp_avg_sq + e);
+        adam1(s, p.x, g.x, m.x, v.x);
+        adam1(s, p.y, g.y, m.y, v.y);
+        adam1(s, p.z, g.z, m.z, v.z);
+        adam1(s, p.w, g.w, m.w, v.w);
+        *reinterpret_cast<float4*>(t.param + e) = p;
+        *reinterpret_cast<float4*>(t.exp_avg + e) = m;
+        *reinterpret_cast<float4*>(t.exp_avg_sq + e) = v;
+      } else {
+        for (int64_t i = e; i < t.n; ++i) adam1(s, t.param[i], t.grad[i], t.exp_avg[i], t.exp_avg_sq[i]);
+      }
+    } else {
+      const int64_t i = u - s.ustart[k];
+      adam1(s, t.param[i], t.grad[i], t.exp_avg[i], t.exp_avg_sq[i]);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t st) {
+  AdamSet s;
+  s.count = count;
+  s.ustart[0] = 0;
+  for (int k = 0; k < count; ++k) {
+    s.t[k] = t[k];
+    const bool al = ((reinterpret_cast<uintptr_t>(t[k].param) | reinterpret_cast<uintptr_t>(t[k].grad) |
+                      reinterpret_cast<uintptr_t>(t[k].exp_avg) |
+                      reinterpret_cast<uintptr_t>(t[k].exp_avg_sq)) & 15u) == 0;
+    s.vec[k] = al ? 1 : 0;
+    s.ustart[k + 1] = s.ustart[k] + (al ? (t[k].n + 3) / 4 : t[k].n);
+  }
+  for (int k = count; k < S3R_ADAM_MAX_TENSORS; ++k) {
+    s.t[k] = s3r_adam_tensor{nullptr, nullptr, nullptr, nullptr, 0};
+    s.vec[k] = 0;
+    s.ustart[k + 1] = s.ustart[count];
+  }
+  s.lr = lr; s.b1 = b1; s.b2 = b2; s.eps = eps;
+  s.inv_bc1 = 1.f / bc1;
+  s.inv_sqrt_bc2 = 1.f / sqrtf(bc2);
+  const int64_t total = s.ustart[count];
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_adam<<<(unsigned)blocks, 256, 0, st>>>(s);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
                            float* loss, cudaStream_t st) {

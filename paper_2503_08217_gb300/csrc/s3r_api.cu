@@ -389,6 +389,27 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n) {
   return S3R_OK;
 }
 
+s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void* stream) {
+  if (!tensors || count < 0 || count > S3R_ADAM_MAX_TENSORS)
+    return fail(S3R_ERR_INVALID, "adam: 0 <= count <= %d tensors required", S3R_ADAM_MAX_TENSORS);
+  if (step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) ||
+      !std::isfinite(lr))
+    return fail(S3R_ERR_INVALID, "adam: step >= 1, betas in [0, 1), eps > 0 required");
+  for (int k = 0; k < count; ++k) {
+    const s3r_adam_tensor& t = tensors[k];
+    if (t.n < 0) return fail(S3R_ERR_INVALID, "adam: tensor %d has n < 0", k);
+    if (t.n > 0 && (!t.param || !t.grad || !t.exp_avg || !t.exp_avg_sq || !aligned(t.param, 4) ||
+                    !aligned(t.grad, 4) || !aligned(t.exp_avg, 4) || !aligned(t.exp_avg_sq, 4)))
+      return fail(S3R_ERR_INVALID, "adam: tensor %d needs four float arrays", k);
+  }
+  const double bc1 = 1.0 - std::pow((double)beta1, step), bc2 = 1.0 - std::pow((double)beta2, step);
+  cudaError_t e = launch_adam(tensors, count, lr, beta1, beta2, eps, (float)bc1, (float)bc2,
+                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adam");
+  return S3R_OK;
+}
+
 s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float* dL_dpred,
                        float* loss_out, void* stream) {
   if (n < 0) return fail(S3R_ERR_INVALID, "n < 0");

@@ -171,6 +171,8 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
                               cudaStream_t st);
 cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                                const s3r_grads* g, cudaStream_t st);
+cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t st);
 cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
                            float* loss, cudaStream_t st);
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,

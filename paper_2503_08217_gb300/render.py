@@ -173,3 +173,23 @@ def render(renderer: Renderer, scene: DeviceScene, cams, t: float, lod: float, b
     p = scene.params() if params is None else params
     return S3RRender.apply(renderer, scene, cams, t, lod, background, vis_window, point_life, *p,
                            inst_quat, inst_trans)
+
+
+class FusedAdam:
+    """Adam over up to 8 float32 CUDA tensors, one `s3r_adam_step` launch per
+    step; the moments live beside the parameters. `step(grads)` takes one
+    gradient tensor per parameter, in the same order."""
+
+    def __init__(self, params, lr: float, betas=(0.9, 0.999), eps: float = 1e-8):
+        self.params = list(params)
+        if len(self.params) > 8:
+            raise ValueError("FusedAdam takes at most 8 tensors per launch")
+        self.lr, self.betas, self.eps = float(lr), tuple(float(b) for b in betas), float(eps)
+        self.exp_avg = [torch.zeros_like(p) for p in self.params]
+        self.exp_avg_sq = [torch.zeros_like(p) for p in self.params]
+        self.t = 0
+
+    def step(self, grads, stream=None):
+        self.t += 1
+        binding.adam_step(self.params, list(grads), self.exp_avg, self.exp_avg_sq, self.lr, self.t,
+                          self.betas[0], self.betas[1], self.eps, stream)

@@ -45,3 +45,17 @@ def test_invalid_calls_fail_without_a_gpu():
     assert L.s3r_update_visibility(-1, 0.0, None, None, None, 0, None) == 1
     assert L.s3r_update_visibility(10, 0.0, None, None, None, 7, None) == 1
     assert b"mode" in L.s3r_last_error()
+
+
+def test_adam_argument_checks_fail_without_a_gpu():
+    """s3r_adam_step validates its descriptors before any launch."""
+    from paper_2503_08217_gb300 import binding
+    L = binding.load()
+    T = binding.AdamTensor
+    arr = (T * 9)()
+    assert L.s3r_adam_step(arr, 9, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1     # > 8 tensors
+    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1     # step 0
+    assert L.s3r_adam_step(arr, 1, 1e-3, 1.0, 0.999, 1e-8, 1, None) == 1     # beta1 = 1
+    arr[0] = T(None, None, None, None, 10)
+    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1     # NULL arrays
+    assert b"adam" in L.s3r_last_error()
