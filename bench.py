@@ -35,6 +35,27 @@ if ROOT not in sys.path:
 
 METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM roofline"
 
+# DRAM bytes (read + write) per launch of a kernel at the rig workload, from
+# one ncu capture (summarised under profiles/), valid only while the kernel's
+# source file is the one the counters were taken on (first 16 hex digits of
+# its SHA-256); otherwise the roofline line reports traffic null.
+NCU_TRAFFIC = {
+    "blend_bwd": {"bytes": 333186560, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
+                  "sha256_16": "10da9c2fcf3979d2", "profile": "profiles/blend_bwd_traffic_rig.md"},
+}
+
+
+def measured_traffic(kernel: str, workload: str):
+    t = NCU_TRAFFIC.get(kernel)
+    if t is None or workload != "rig":
+        return None
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
+            return None
+    return t["bytes"]
+
 # workload name -> (scene spec, overrides, LOD threshold, description)
 WORKLOADS = {
     "rig": ("rig", {}, 1.0, "batched surround rig on the large corridor: 8M static + 80 instances "
@@ -309,7 +330,7 @@ def run_ours(args, rank, world, local):
         table[name] = row
     dom = max(kmean, key=kmean.get)
     roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+            "traffic": measured_traffic(dom, args.workload)}
     if dom in models:
         bound, amount = models[dom]
         if bound == "hbm":
