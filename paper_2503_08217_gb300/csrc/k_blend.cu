@@ -300,43 +300,43 @@ __device__ __forceinline__ void red_v4(float* p, float x, float y, float z, floa
                : "memory");
 }
 
-// Per-pixel state of the reverse walk.
+// Per-pixel state of the reverse walk: the recovered transmittance in front
+// of the current splat, and the colour already composited behind it, dotted
+// with dL/dC and in absolute terms,
+//   Bd = T_final (bg . d) + sum over blended splats k behind of (c_k . d) alpha_k T_k,
+// so that dL/dalpha_i = T_i (c_i . d) - Bd / (1 - alpha_i) (Eq. 2 differentiated).
 struct BwdPixel {
-  float T, T_final, bg_dot, d0, d1, d2;
-  float acc0, acc1, acc2, last_alpha, lc0, lc1, lc2;
+  float T, Bd, d0, d1, d2;
   int last;
 };
 
 // One splat's contribution to the adjoints at one pixel (reverse order),
-// accumulated into g[0..8]; updates the pixel's recovered transmittance and
-// the colour behind it only where the splat was blended in the forward.
+// accumulated into g[0..8] in scaled form (the constant factors ln 2, -1/2 and
+// -1 of the conic and position terms are applied once per splat when the
+// block's sums are flushed); updates the pixel's transmittance and Bd only
+// where the splat was blended in the forward.
 __device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sa,
-                                          const float4 sb, float cb, bool act, float g[9]) {
+                                          float A2x2, float C2x2, const float4 sb, float cb,
+                                          bool act, float g[9]) {
   const float inv = rcp_approx(1.f - e.alpha);
   q.T = act ? q.T * inv : q.T;
-  const float w = e.alpha * q.T;
-  const float la = q.last_alpha;
-  q.acc0 = act ? fmaf(la, q.lc0, (1.f - la) * q.acc0) : q.acc0;
-  q.acc1 = act ? fmaf(la, q.lc1, (1.f - la) * q.acc1) : q.acc1;
-  q.acc2 = act ? fmaf(la, q.lc2, (1.f - la) * q.acc2) : q.acc2;
-  q.lc0 = act ? sb.z : q.lc0;
-  q.lc1 = act ? sb.w : q.lc1;
-  q.lc2 = act ? cb : q.lc2;
-  q.last_alpha = act ? e.alpha : q.last_alpha;
-  float dalpha = ((sb.z - q.acc0) * q.d0 + (sb.w - q.acc1) * q.d1 + (cb - q.acc2) * q.d2) * q.T;
-  dalpha = fmaf(-q.T_final * inv, q.bg_dot, dalpha);
+  const float cd = fmaf(sb.z, q.d0, fmaf(sb.w, q.d1, cb * q.d2));
+  const float dalpha = fmaf(q.T, cd, -q.Bd * inv);
+  const float w = act ? e.alpha * q.T : 0.f;
+  q.Bd = fmaf(cd, w, q.Bd);
   const bool live = act && !(e.raw > kAlphaMax);         // alpha = 0.99 is constant
-  const float dpow = live ? sb.y * e.G * dalpha : 0.f;    // dL/d(power), natural units
-  const float dpl = dpow * kLn2;
-  g[0] += dpl * fmaf(2.f * sa.z, e.dx, sa.w * e.dy);     // d/du
-  g[1] += dpl * fmaf(sa.w, e.dx, 2.f * sb.x * e.dy);     // d/dv
-  g[2] -= 0.5f * dpow * e.dx * e.dx;                     // d/dA
-  g[3] -= dpow * e.dx * e.dy;                            // d/dB
-  g[4] -= 0.5f * dpow * e.dy * e.dy;                     // d/dC
-  g[5] += live ? e.G * dalpha : 0.f;                     // d/dopacity
-  g[6] += act ? w * q.d0 : 0.f;                          // d/drgb
-  g[7] += act ? w * q.d1 : 0.f;
-  g[8] += act ? w * q.d2 : 0.f;
+  const float gd = (live ? e.G : 0.f) * dalpha;           // dL/dopacity
+  const float dpow = sb.y * gd;                           // dL/d(power), natural units
+  const float t = dpow * e.dx, u = dpow * e.dy;
+  g[0] = fmaf(A2x2, t, fmaf(sa.w, u, g[0]));              // x ln 2     -> d/du
+  g[1] = fmaf(sa.w, t, fmaf(C2x2, u, g[1]));              // x ln 2     -> d/dv
+  g[2] = fmaf(t, e.dx, g[2]);                             // x -1/2     -> d/dA
+  g[3] = fmaf(t, e.dy, g[3]);                             // x -1       -> d/dB
+  g[4] = fmaf(u, e.dy, g[4]);                             // x -1/2     -> d/dC
+  g[5] += gd;
+  g[6] = fmaf(w, q.d0, g[6]);                             // d/drgb
+  g[7] = fmaf(w, q.d1, g[7]);
+  g[8] = fmaf(w, q.d2, g[8]);
 }
 
 __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const ViewInfo& vi,
@@ -352,13 +352,10 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
     q.T = a.final_T[vi.pix_base + pix];
     q.last = (int)a.n_contrib[vi.pix_base + pix];
   }
-  q.T_final = q.T;
-  q.bg_dot = a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2;
-  q.acc0 = q.acc1 = q.acc2 = 0.f;
-  q.last_alpha = q.lc0 = q.lc1 = q.lc2 = 0.f;
+  q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
-__global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ ViewSet vs,
+__global__ void __launch_bounds__(kThreads, 8) k_blend_bwd(const __grid_constant__ ViewSet vs,
                                                         BlendArgs a) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
@@ -408,20 +405,23 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
       uint32_t todo = get_bits(wbits, range.x + lo + c0);
       const int span = c1 - c0 + 1;
       if (span < 32) todo &= (1u << span) - 1u;
+      // as a ballot result the mask is warp-uniform to the compiler as well
+      todo = __ballot_sync(0xffffffffu, (todo >> lane) & 1u);
       while (todo) {
       const int bit = 31 - __clz(todo);
       todo &= ~(1u << bit);
       const int j = c0 + bit;
       const float4 sa = s_a[j], sb = s_b[j];
       const float cb = s_c[j];
+      const float A2x2 = 2.f * sa.z, C2x2 = 2.f * sb.x;
       const int pos = lo + j;
       const SplatEval e0 = eval_splat(sa, sb, P.fx, P.fy0);
       const SplatEval e1 = eval_splat(sa, sb, P.fx, P.fy1);
       const bool act0 = (pos < q0.last) && !(e0.p > 0.f) && !(e0.alpha < kAlphaMin);
       const bool act1 = (pos < q1.last) && !(e1.p > 0.f) && !(e1.alpha < kAlphaMin);
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bwd_pixel(q0, e0, sa, sb, cb, act0, g);
-      bwd_pixel(q1, e1, sa, sb, cb, act1, g);
+      bwd_pixel(q0, e0, sa, A2x2, C2x2, sb, cb, act0, g);
+      bwd_pixel(q1, e1, sa, A2x2, C2x2, sb, cb, act1, g);
       const float tot = warp_sum8_transposed(g, lane);
       float g8 = g[8];
 #pragma unroll
@@ -438,8 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(const __grid_constant__ 
       for (int r = 0; r < 9; ++r) any |= sg[r] != 0.f;
       if (any) {
         float* dst = a.sp_grad + 12 * (size_t)s_id[i];
-        red_v4(dst, sg[0], sg[1], sg[2], sg[3]);
-        red_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
+        red_v4(dst, kLn2 * sg[0], kLn2 * sg[1], -0.5f * sg[2], -sg[3]);
+        red_v4(dst + 4, -0.5f * sg[4], sg[5], sg[6], sg[7]);
         atomicAdd(dst + 8, sg[8]);
       }
     }
