@@ -256,15 +256,6 @@ __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restr
 // 32 scattered rows per load instruction.
 
 template <int DEG>
-struct ShStage {
-  static constexpr int K = sh_count(DEG);
-  static constexpr bool kVec = (K * 3) % 4 == 0;
-  static constexpr int kRow = kVec ? K * 3 / 4 : K * 3;     // float4s or floats per Gaussian
-  static constexpr int kPitch = kVec ? kRow + 1 : kRow + 1;  // padded (bank spread)
-  static constexpr int kWords = 32 * kPitch * (kVec ? 4 : 1);
-};
-
-template <int DEG>
 __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_constant__ ViewSet vs,
                                                              ProjArgs a) {
   using St = ShStage<DEG>;
@@ -298,27 +289,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
     const bool valid = lane < (uint32_t)n_here;
     const uint2 e = valid ? a.kept_list[t] : make_uint2(0u, 0u);
     const uint32_t j = e.x, gid = e.y;
-    // coalesced SH stage: element q of row g goes to my_sh[g * pitch + q]
-    if constexpr (St::kVec) {
-      const float4* src = a.sh;
-      float4* dst = reinterpret_cast<float4*>(my_sh);
-#pragma unroll
-      for (int it = 0; it < St::kRow; ++it) {
-        const int idx = it * 32 + (int)lane;
-        const int g = idx / St::kRow, q = idx - g * St::kRow;
-        const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
-        if (g < n_here) dst[g * St::kPitch + q] = __ldg(src + (size_t)gg * St::kRow + q);
-      }
-    } else {
-      const float* src = a.sh_f;
-#pragma unroll
-      for (int it = 0; it < St::kRow; ++it) {
-        const int idx = it * 32 + (int)lane;
-        const int g = idx / St::kRow, q = idx - g * St::kRow;
-        const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
-        if (g < n_here) my_sh[g * St::kPitch + q] = __ldg(src + (size_t)gg * St::kRow + q);
-      }
-    }
+    stage_sh_rows<DEG>(my_sh, a.sh_f, gid, n_here, lane);
     __syncwarp();
     if (valid) {
       const uint32_t kmask = a.keep_mask[j];
@@ -337,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
       for (int r = 0; r < 3; ++r) {
         RS[3 * r] = R[3 * r] * s0; RS[3 * r + 1] = R[3 * r + 1] * s1; RS[3 * r + 2] = R[3 * r + 2] * s2;
       }
-      const float* row_sh = my_sh + lane * St::kPitch * (St::kVec ? 4 : 1);
+      const float* row_sh = my_sh + lane * St::kFloatPitch;
       uint32_t m = kmask;
       while (m) {
         const int v = __ffs(m) - 1;

@@ -3,10 +3,13 @@
 // 2D adjoints written by the blend backward to the Gaussian parameters and to
 // every instance pose.
 //
-// One thread per selected Gaussian loops over its kept views (its splats are
-// contiguous), recomputes the forward intermediates of each view, and
-// accumulates the parameter adjoints in registers; the owning thread then adds
-// them to the caller's buffers (no atomics: a Gaussian has one thread).
+// One thread per kept Gaussian (a warp takes 32 consecutive entries of the
+// forward's work list) loops over its kept views (its splats are contiguous),
+// recomputes the forward intermediates of each view, and accumulates the
+// parameter adjoints in registers; the owning thread then adds them to the
+// caller's buffers (no atomics: a Gaussian has one thread). The SH rows are
+// read, and their adjoints added, through shared memory with coalesced
+// accesses of the whole warp.
 // Adjoints of the composed 3x4 matrices are summed per (view, instance) in
 // shared memory and flushed once per CTA; a tiny kernel then maps them to the
 // pose: dP = V_rot^T dW, and through R(q) to (dq, dt).
@@ -16,6 +19,7 @@ namespace s3r {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
 
 struct BwdArgs {
   const float* means;
@@ -106,35 +110,48 @@ __device__ __forceinline__ float4 quat_backward(float4 q, const float dR[9]) {
 template <int DEG>
 __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_constant__ ViewSet vs,
                                                           BwdArgs a) {
+  using St = ShStage<DEG>;
+  constexpr int K = St::K;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nk = a.n_inst + 1;
   // the composed matrices are read through L1 (a CTA touches few instances);
-  // shared memory holds only the per-(view, instance) matrix adjoints
+  // shared memory holds each warp's SH rows, the per-(view, instance) matrix
+  // adjoints and the camera records (per-lane view indices differ)
   const InstMat* __restrict__ mats = a.mats;
-  float* s_dM = reinterpret_cast<float*>(smem_raw);                      // [views][nk][12]
+  float* s_sh = reinterpret_cast<float*>(smem_raw);                        // [warps][kWords]
+  float* s_dM = s_sh + kWarps * St::kWords;                                // [views][nk][12]
   uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dM + vs.n_views * nk * 12);
-  __shared__ uint32_t s_tile;
-  constexpr int K = sh_count(DEG);
-
+  __shared__ ViewInfo s_views[S3R_MAX_VIEWS];
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(vs.v);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
+    const int words = vs.n_views * (int)(sizeof(ViewInfo) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
   for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) s_dM[i] = 0.f;
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31u;
+  float* my_sh = s_sh + warp * St::kWords;
+  float* row_sh = my_sh + lane * St::kFloatPitch;
 
-  // only Gaussians kept in at least one view have adjoints
-  const uint32_t n_sel = a.ctr[kCtrKept];
-  const int64_t n_tiles = ((int64_t)n_sel + kThreads - 1) / kThreads;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageProjectBwd, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    __syncthreads();
-    if (tile >= n_tiles) break;
-    const int64_t jt = tile * kThreads + threadIdx.x;
-    if (jt >= (int64_t)n_sel) continue;
-    const uint2 kept = a.kept_list[jt];
+  // only Gaussians kept in at least one view have adjoints; a warp takes 32
+  // consecutive work-list entries
+  const uint32_t n_kept = a.ctr[kCtrKept];
+  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < (int64_t)n_kept;
+       base += (int64_t)gridDim.x * kThreads) {
+    const int n_here = (int)min((int64_t)32, (int64_t)n_kept - base);
+    const bool valid = lane < (uint32_t)n_here;
+    const uint2 kept = valid ? a.kept_list[base + lane] : make_uint2(0u, 0u);
     const uint32_t j = kept.x, gid = kept.y;
-    const uint32_t kmask = a.keep_mask[j];
-    if (!kmask) continue;
+    stage_sh_rows<DEG>(my_sh, a.sh_f, gid, n_here, lane);
+    __syncwarp();
+    const uint32_t kmask = valid ? a.keep_mask[j] : 0u;
+    float g_sh[K * 3];
+#pragma unroll
+    for (int i = 0; i < K * 3; ++i) g_sh[i] = 0.f;
+    if (kmask) {
     const int k = segment_of(s_off, a.n_inst, gid);
     uint32_t s = a.splat_start[j];
 
@@ -151,26 +168,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 #pragma unroll
       for (int c = 0; c < 3; ++c) RS[3 * r + c] = R[3 * r + c] * sc[c];
     const float opac = 1.f / (1.f + __expf(-a.opac_logits[gid]));
-    float sh[K * 3];
-    if constexpr ((K * 3) % 4 == 0) {
-      const float4* src = a.sh + (size_t)gid * (K * 3 / 4);
-#pragma unroll
-      for (int i = 0; i < K * 3 / 4; ++i) {
-        const float4 v4 = __ldg(src + i);
-        sh[4 * i] = v4.x; sh[4 * i + 1] = v4.y; sh[4 * i + 2] = v4.z; sh[4 * i + 3] = v4.w;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < K * 3; ++i) sh[i] = __ldg(a.sh_f + (size_t)gid * K * 3 + i);
-    }
+    const volatile float* sh = row_sh;   // re-read per use: keeps 48 values out of registers
 
     float g_mu[3] = {0.f, 0.f, 0.f}, g_RS[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) g_RS[i] = 0.f;
     float g_ol = 0.f;
-    float g_sh[K * 3];
-#pragma unroll
-    for (int i = 0; i < K * 3; ++i) g_sh[i] = 0.f;
 
     uint32_t m = kmask;
     while (m) {
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gO = gb.y;
       const float grgb[3] = {gb.z, gb.w, gc.x};
       const InstMat& M = mats[v * nk + k];
-      const ViewInfo& vi = vs.v[v];
+      const ViewInfo& vi = s_views[v];
       const float* A = M.m;   // rows at 0, 4, 8; translation at 3, 7, 11
 
       // ---- forward recompute (the same arithmetic as project_view)
@@ -361,21 +364,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       *p = o;
     }
     if (a.g.opacity_logits) a.g.opacity_logits[gid] += g_ol;
-    if (a.g.sh) {
-      if constexpr ((K * 3) % 4 == 0) {
-        float4* p = reinterpret_cast<float4*>(a.g.sh) + (size_t)gid * (K * 3 / 4);
+    }
+    // SH adjoints: each lane writes its row over its (consumed) SH row, then
+    // the warp adds the rows to the caller's buffer with coalesced accesses
+    __syncwarp();
+    if (kmask) {
 #pragma unroll
-        for (int i = 0; i < K * 3 / 4; ++i) {
-          float4 o = p[i];
-          o.x += g_sh[4 * i]; o.y += g_sh[4 * i + 1]; o.z += g_sh[4 * i + 2]; o.w += g_sh[4 * i + 3];
-          p[i] = o;
+      for (int i = 0; i < K * 3; ++i) row_sh[i] = g_sh[i];
+    }
+    __syncwarp();
+    if (a.g.sh) {
+      const uint32_t live = __ballot_sync(0xffffffffu, kmask != 0u);
+      if constexpr (St::kVec) {
+        float4* dst = reinterpret_cast<float4*>(a.g.sh);
+        const float4* src = reinterpret_cast<const float4*>(my_sh);
+#pragma unroll
+        for (int it = 0; it < St::kRow; ++it) {
+          const int idx = it * 32 + (int)lane;
+          const int g = idx / St::kRow, qd = idx - g * St::kRow;
+          const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+          if ((live >> g) & 1u) {
+            float4 o = dst[(size_t)gg * St::kRow + qd];
+            const float4 d = src[g * St::kPitch + qd];
+            o.x += d.x; o.y += d.y; o.z += d.z; o.w += d.w;
+            dst[(size_t)gg * St::kRow + qd] = o;
+          }
         }
       } else {
-        float* p = a.g.sh + (size_t)gid * K * 3;
 #pragma unroll
-        for (int i = 0; i < K * 3; ++i) p[i] += g_sh[i];
+        for (int it = 0; it < St::kRow; ++it) {
+          const int idx = it * 32 + (int)lane;
+          const int g = idx / St::kRow, qd = idx - g * St::kRow;
+          const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+          if ((live >> g) & 1u) a.g.sh[(size_t)gg * St::kRow + qd] += my_sh[g * St::kPitch + qd];
+        }
       }
     }
+    __syncwarp();
   }
   __syncthreads();
   for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) {
@@ -420,8 +445,8 @@ __global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __
 template <int DEG>
 cudaError_t launch_deg(s3r_workspace* ws, const BwdArgs& a, cudaStream_t st) {
   const int nk = ws->n_inst + 1;
-  const size_t smem = (size_t)ws->n_views * nk * 12 * sizeof(float) +
-                      sizeof(uint32_t) * (nk + 1) + 16;
+  const size_t smem = sizeof(float) * kWarps * ShStage<DEG>::kWords +
+                      (size_t)ws->n_views * nk * 12 * sizeof(float) + sizeof(uint32_t) * (nk + 1) + 16;
   static thread_local size_t cached_smem = 0;
   static thread_local int cached_per_sm = 0;
   if (smem != cached_smem) {
@@ -469,11 +494,6 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   const int nk = ws->n_inst + 1;
   cudaError_t e = cudaMemsetAsync(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)ws->n_views * nk, st);
   if (e != cudaSuccess) return e;
-  // the tile counter of this stage is reset per call (several backward calls
-  // may follow one forward)
-  if ((e = cudaMemsetAsync(ws->ctr + kCtrTileBase + kStageProjectBwd, 0, sizeof(uint32_t), st)) !=
-      cudaSuccess)
-    return e;
   switch (sc->sh_degree) {
     case 0: e = launch_deg<0>(ws, a, st); break;
     case 1: e = launch_deg<1>(ws, a, st); break;

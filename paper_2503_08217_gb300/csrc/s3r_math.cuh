@@ -170,4 +170,45 @@ __device__ __forceinline__ void sh_basis(float dx, float dy, float dz, float Y[1
 
 __host__ __device__ constexpr int sh_count(int deg) { return (deg + 1) * (deg + 1); }
 
+// Shared-memory staging of the SH rows of a warp's 32 Gaussians: K*3 floats
+// per Gaussian, moved as float4s when K*3 is a multiple of 4 (degrees 1, 3),
+// each row padded by one element so that lanes reading their own rows spread
+// over the banks. kWords = floats per warp.
+template <int DEG>
+struct ShStage {
+  static constexpr int K = sh_count(DEG);
+  static constexpr bool kVec = (K * 3) % 4 == 0;
+  static constexpr int kRow = kVec ? K * 3 / 4 : K * 3;   // float4s or floats per Gaussian
+  static constexpr int kPitch = kRow + 1;
+  static constexpr int kFloatPitch = kPitch * (kVec ? 4 : 1);
+  static constexpr int kWords = 32 * kFloatPitch;
+};
+
+// Coalesced copy of the SH rows of the warp's Gaussians gid (lane g holds the
+// id of row g; rows g >= n_here are skipped) into `stage`.
+template <int DEG>
+__device__ __forceinline__ void stage_sh_rows(float* stage, const float* __restrict__ sh,
+                                              uint32_t gid, int n_here, uint32_t lane) {
+  using St = ShStage<DEG>;
+  if constexpr (St::kVec) {
+    const float4* src = reinterpret_cast<const float4*>(sh);
+    float4* dst = reinterpret_cast<float4*>(stage);
+#pragma unroll
+    for (int it = 0; it < St::kRow; ++it) {
+      const int idx = it * 32 + (int)lane;
+      const int g = idx / St::kRow, q = idx - g * St::kRow;
+      const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+      if (g < n_here) dst[g * St::kPitch + q] = __ldg(src + (size_t)gg * St::kRow + q);
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < St::kRow; ++it) {
+      const int idx = it * 32 + (int)lane;
+      const int g = idx / St::kRow, q = idx - g * St::kRow;
+      const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
+      if (g < n_here) stage[g * St::kPitch + q] = __ldg(sh + (size_t)gg * St::kRow + q);
+    }
+  }
+}
+
 }  // namespace s3r
