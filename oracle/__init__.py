@@ -57,7 +57,7 @@ def lib():
         L.orc_vis_finalize.argtypes = [i64, vp, vp]
         L.orc_vis_reset.argtypes = [i64, vp, vp]
         proj = [i64, vp, vp, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp, f64, vp]
-        L.orc_project.argtypes = proj
+        L.orc_project.argtypes = proj[:-1] + [i32, vp]
         L.orc_project_conventional.argtypes = proj
         L.orc_render.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.orc_render_tiled.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -66,7 +66,10 @@ def lib():
         L.orc_render_backward.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                           vp, vp, vp, vp, vp, vp]
         L.orc_project_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, vp, i32, vp, vp, vp,
-                                           f64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+                                           f64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        u32 = ctypes.c_uint32
+        L.orc_set_lod.argtypes = [i32, f64, f64, f64, f64, f64, u32, u32, u32]
+        L.orc_philox.argtypes = [vp, vp, vp]
         L.orc_sh_basis.argtypes = [vp, vp, vp]
         L.orc_render_pixels.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32,
                                         vp, vp, vp, vp, vp, vp]
@@ -149,16 +152,21 @@ def _widen(scene):
 
 
 def project(scene, sel: np.ndarray, step: int, cam, lod_r: float, *, conventional=False,
-            inst_quat=None, inst_trans=None) -> dict:
-    """Project the selected Gaussians into one camera at timestep `step`."""
+            inst_quat=None, inst_trans=None, view: int = 0) -> dict:
+    """Project the selected Gaussians into one camera at timestep `step`;
+    `view` is the camera's index in its call (a counter word of the
+    stochastic LOD's draws)."""
     means, ls, qs, ol, sh, off = _scene_arrays(scene)
     iq = np.ascontiguousarray(scene.inst_quat[step] if inst_quat is None else inst_quat, np.float64)
     it = np.ascontiguousarray(scene.inst_trans[step] if inst_trans is None else inst_trans, np.float64)
     sel = np.ascontiguousarray(sel, np.int64)
     rec = np.zeros((sel.shape[0], REC), np.float64)
-    fn = lib().orc_project_conventional if conventional else lib().orc_project
-    fn(sel.shape[0], _P(sel), _P(means), _P(ls), _P(qs), _P(ol), _P(sh), scene.sh_degree,
-       _P(off), scene.n_inst, _P(iq), _P(it), _P(cam_array(cam)), float(lod_r), _P(rec))
+    args = [sel.shape[0], _P(sel), _P(means), _P(ls), _P(qs), _P(ol), _P(sh), scene.sh_degree,
+            _P(off), scene.n_inst, _P(iq), _P(it), _P(cam_array(cam)), float(lod_r)]
+    if conventional:
+        lib().orc_project_conventional(*args, _P(rec))
+    else:
+        lib().orc_project(*args, int(view), _P(rec))
     return unpack_records(rec)
 
 
@@ -286,7 +294,7 @@ def zero_grads(scene) -> dict:
 
 
 def project_backward(scene, sel, step, cam, lod_r, sg: dict, grads: dict, *, inst_quat=None,
-                     inst_trans=None) -> np.ndarray:
+                     inst_trans=None, view: int = 0) -> np.ndarray:
     """Chain splat gradients (indexed like `sel`, zero where not kept) into
     `grads` (accumulated). Returns this view's composed-matrix gradient
     dL/dM [n_inst+1, 3, 4] (row 0 = static)."""
@@ -299,11 +307,31 @@ def project_backward(scene, sel, step, cam, lod_r, sg: dict, grads: dict, *, ins
     L = lib()
     L.orc_project_backward(sel.shape[0], _P(sel), _P(means), _P(ls), _P(qs), _P(ol), _P(sh),
                            scene.sh_degree, _P(off), scene.n_inst, _P(iq), _P(it),
-                           _P(cam_array(cam)), float(lod_r), *[_P(a) for a in args],
+                           _P(cam_array(cam)), float(lod_r), int(view), *[_P(a) for a in args],
                            _P(grads["means"]), _P(grads["log_scales"]), _P(grads["quats"]),
                            _P(grads["opacity_logits"]), _P(grads["sh"]), _P(gm),
                            _P(grads["inst_quat"]), _P(grads["inst_trans"]))
     return gm.reshape(scene.n_inst + 1, 3, 4)
+
+
+def set_lod(mode: int = 0, p_max: float = 0.0, dist: float = 1.0, offset=(0.0, 0.0, 0.0),
+            seed: int = 0, epoch: int = 0) -> None:
+    """Select the LOD of the projection: mode 0 = deterministic threshold
+    cull, 1 = Eq. 7 (depth-dependent Bernoulli drop and noisy offset of the
+    Gaussians below r), drawn by Philox4x32-10 with counter (Gaussian id,
+    view, epoch, block) and key (seed low, seed high 32 bits)."""
+    lib().orc_set_lod(int(mode), float(p_max), float(dist), float(offset[0]), float(offset[1]),
+                      float(offset[2]), int(seed) & 0xffffffff, (int(seed) >> 32) & 0xffffffff,
+                      int(epoch) & 0xffffffff)
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one 4-word counter under a 2-word key."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox(_P(c), _P(k), _P(out))
+    return out
 
 
 def sh_basis(direction) -> tuple:
@@ -324,8 +352,8 @@ def step_forward(scene, step: int, vis: np.ndarray, life: np.ndarray | None, lod
     sel = select(vis, t)
     views = []
     mt = np.zeros(sel.shape[0], bool)
-    for cam in cams:
-        rec = project(scene, sel, step, cam, lod_r)
+    for vi, cam in enumerate(cams):
+        rec = project(scene, sel, step, cam, lod_r, view=vi)
         mt |= rec["infrustum"]
         sp = select_splats(rec)
         out = render(cam.width, cam.height, sp, bg, tiled=tiled)
@@ -355,7 +383,7 @@ def step_backward(scene, step: int, fwd: dict, dL_dimgs, lod_r: float, cams=None
                 "opacity": np.zeros(kept.shape[0]), "rgb": np.zeros((kept.shape[0], 3))}
         for k in full:
             full[k][kept] = g[k]
-        gms.append(project_backward(scene, fwd["sel"], step, cam, lod_r, full, grads))
+        gms.append(project_backward(scene, fwd["sel"], step, cam, lod_r, full, grads, view=vi))
     grads["M"] = gms
     grads["pixel_flags"] = flags
     return grads

@@ -15,7 +15,10 @@
 //   3. the visible mask M_t from the view frustum, and the point-life update
 //      of Eq. 5 (done on M_t, before LOD);
 //   4. adaptive-LOD threshold cull (Sec. 3.3, "Adaptive LOD", deterministic
-//      reading: cull iff the projected 2D scale is below r);
+//      reading: cull iff the projected 2D scale is below r), or, when enabled,
+//      the stochastic form of Eq. 7 on the Gaussians below r (depth-dependent
+//      Bernoulli drop, noisy offset of the survivors), drawn from a
+//      Philox4x32-10 counter-based generator;
 //   5. SH colour and front-to-back alpha blending, Eq. 2;
 //   6. Eq. 6 (visibility from point life) and the reset to "always visible";
 //   7. the exact gradient of the rendered image w.r.t. every parameter and the
@@ -165,6 +168,42 @@ void sh_basis(const double d[3], double Y[16], double dY[16][3]) {
   set(15, -c3a * (3 * xx - 3 * yy), c3a * 6 * x * y, 0);
 }
 
+// ------------------------------------------------------- counter-based RNG
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel Random Numbers: As
+// Easy as 1, 2, 3", SC 2011): ten rounds of two 32x32->64 multiplications by
+// fixed odd multipliers, the high halves XORed with the other two counter
+// words and the round key; the key is bumped by two Weyl constants between
+// rounds.
+void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+  const uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += kW0;
+      k1 += kW1;
+    }
+    const uint64_t p0 = (uint64_t)kM0 * c0, p1 = (uint64_t)kM1 * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Stochastic LOD of Eq. 7 (off unless set by orc_set_lod).
+struct LodParams {
+  int mode = 0;                 // 0: deterministic threshold cull, 1: Eq. 7 on the small ones
+  float p_max = 0.f, dist = 1.f;
+  double offset[3] = {0, 0, 0}; // [dx, dy, dz] of Eq. 7
+  uint32_t key[2] = {0, 0};     // generator key (the seed)
+  uint32_t epoch = 0;           // third counter word: which call
+};
+LodParams g_lod;
+
 // ---------------------------------------------------------------- projection
 // Everything the forward computes for one Gaussian in one view.
 struct Proj {
@@ -172,7 +211,8 @@ struct Proj {
   int kept;        // infrustum and sigma_lod >= r
   int near_boundary;  // bits set when a decision lies within a tiny margin of its
                       // threshold: 1 near plane, 2 left, 4 right, 8 top, 16 bottom
-                      // rect edge, 32 radius ceil, 64 LOD threshold
+                      // rect edge, 32 radius ceil, 64 LOD threshold, 128 Eq. 7 draw
+  int offset;      // Eq. 7: projected at the noisy position (2D values below are there)
   double p[3];     // camera-space position
   double u, v;
   double conic[3]; // (A, B, C): power = -0.5 (A dx^2 + C dy^2) - B dx dy
@@ -346,6 +386,70 @@ void project_one(const Cam& cam, const double A[3][3], const double b[3], const 
   const double ls[3] = {log_scale[0], log_scale[1], log_scale[2]};
   const double q[4] = {quat[0], quat[1], quat[2], quat[3]};
   project_core(cam, A, b, mu, ls, q, opac_logit, sh, sh_deg, lod_r, nullptr, o);
+}
+
+// Eq. 7 for one (Gaussian, view) that is in the frustum with a 2D scale below
+// r. Reading of the garbled parts: p rises linearly from 0.01 at depth 0 to
+// p_max at depth D and stays there; "Bernoulli(p) <= 0" keeps the Gaussian
+// iff the draw is 0 (probability 1 - p); "normalize(d)" is min(1, d / D); the
+// standard normal is drawn per axis. The draw is decided in FP32, as the GPU
+// does: drop iff (a0 >> 8) < p * 2^24 with p evaluated in FP32 from the FP32
+// depth. Normals by Box-Muller on (0, 1] x [0, 1) uniforms of 24 bits.
+// Returns true if kept and writes the noisy mean.
+bool lod_draw(int64_t gid, int view, double z, const double mu[3], double mu_out[3],
+              int* near_bits) {
+  const uint32_t ctr0[4] = {(uint32_t)gid, (uint32_t)view, g_lod.epoch, 0u};
+  const uint32_t ctr1[4] = {(uint32_t)gid, (uint32_t)view, g_lod.epoch, 1u};
+  uint32_t a[4], b[4];
+  philox4x32_10(ctr0, g_lod.key, a);
+  const float zf = (float)z;
+  const float D = g_lod.dist;
+  const float p = g_lod.p_max + (g_lod.p_max - 0.01f) * std::min(0.f, (zf - D) / D);
+  const float thr = p * 16777216.f;
+  const float u0 = (float)(a[0] >> 8);
+  if (std::fabs((double)u0 - (double)thr) <= 2.0) *near_bits |= 128;
+  if (u0 < thr) return false;
+  philox4x32_10(ctr1, g_lod.key, b);
+  const double two24 = 16777216.0;
+  const double u1 = ((a[1] >> 8) + 1.0) / two24, u2 = (a[2] >> 8) / two24;
+  const double u3 = ((a[3] >> 8) + 1.0) / two24, u4 = (b[0] >> 8) / two24;
+  const double r1 = std::sqrt(-2.0 * std::log(u1)), r2 = std::sqrt(-2.0 * std::log(u3));
+  const double n[3] = {r1 * std::cos(2 * kPi * u2), r1 * std::sin(2 * kPi * u2),
+                       r2 * std::cos(2 * kPi * u4)};
+  const double s = std::min(1.0, z / (double)D);
+  for (int i = 0; i < 3; ++i) mu_out[i] = mu[i] + g_lod.offset[i] * n[i] * s;
+  return true;
+}
+
+// The projection of one (Gaussian, view) as the path renders it: Eq. 1 at the
+// mean; under the stochastic LOD a small Gaussian is dropped or re-projected
+// at its noisy mean (then kept even if that leaves the frustum: it is a splat
+// with no tiles). mu_used receives the mean the 2D values belong to.
+void project_lod(const Cam& cam, const double A[3][3], const double b[3], int64_t gid, int view,
+                 const double* mean, const double* log_scale, const double* quat,
+                 double opac_logit, const double* sh, int sh_deg, double lod_r, Proj& o,
+                 double mu_used[3]) {
+  project_one(cam, A, b, mean, log_scale, quat, opac_logit, sh, sh_deg, lod_r, o);
+  for (int i = 0; i < 3; ++i) mu_used[i] = mean[i];
+  if (g_lod.mode != 1 || !o.infrustum || o.kept) return;
+  int bits = o.near_boundary;
+  double mu2[3];
+  if (!lod_draw(gid, view, o.p[2], mean, mu2, &bits)) {
+    o.near_boundary = bits;
+    return;
+  }
+  Proj o2;
+  project_one(cam, A, b, mu2, log_scale, quat, opac_logit, sh, sh_deg, 0.0, o2);
+  if (!o2.infrustum) {
+    for (int i = 0; i < 4; ++i) o2.rect[i] = 0;
+  }
+  o2.near_boundary |= bits;
+  o2.infrustum = 1;   // M_t is the frustum test at the mean
+  o2.kept = 1;
+  o2.offset = 1;
+  o2.sigma_lod = o.sigma_lod;
+  o = o2;
+  for (int i = 0; i < 3; ++i) mu_used[i] = mu2[i];
 }
 
 // Gradient of one projected Gaussian: from the 2D quantities back to the
@@ -629,7 +733,7 @@ int orc_rec_width(void) { return 24; }
 void orc_project(int64_t n_sel, const int64_t* sel, const double* means, const double* log_scales,
                  const double* quats, const double* opac_logits, const double* sh, int sh_deg,
                  const int64_t* inst_off, int n_inst, const double* inst_q, const double* inst_t,
-                 const double* cam_raw, double lod_r, double* rec) {
+                 const double* cam_raw, double lod_r, int view, double* rec) {
   const Cam cam = load_cam(cam_raw);
   std::vector<double> As((n_inst + 1) * 9), bs((n_inst + 1) * 3);
   for (int k = 0; k <= n_inst; ++k) {
@@ -648,8 +752,9 @@ void orc_project(int64_t n_sel, const int64_t* sel, const double* means, const d
     for (int i = 0; i < 9; ++i) A[i / 3][i % 3] = As[9 * k + i];
     for (int i = 0; i < 3; ++i) b[i] = bs[3 * k + i];
     Proj o;
-    project_one(cam, A, b, means + 3 * g, log_scales + 3 * g, quats + 4 * g, opac_logits[g],
-                sh + (size_t)K * 3 * g, sh_deg, lod_r, o);
+    double mu_used[3];
+    project_lod(cam, A, b, g, view, means + 3 * g, log_scales + 3 * g, quats + 4 * g,
+                opac_logits[g], sh + (size_t)K * 3 * g, sh_deg, lod_r, o, mu_used);
     double* r = rec + 24 * j;
     r[0] = o.infrustum; r[1] = o.kept; r[2] = o.near_boundary;
     r[3] = o.p[0]; r[4] = o.p[1]; r[5] = o.p[2];
@@ -975,7 +1080,7 @@ void orc_project_backward(int64_t n_sel, const int64_t* sel, const double* means
                           const double* log_scales, const double* quats, const double* opac_logits,
                           const double* sh, int sh_deg, const int64_t* inst_off, int n_inst,
                           const double* inst_q, const double* inst_t, const double* cam_raw,
-                          double lod_r, const double* g_uv, const double* g_conic,
+                          double lod_r, int view, const double* g_uv, const double* g_conic,
                           const double* g_opac, const double* g_rgb, double* g_means,
                           double* g_log_scales, double* g_quats, double* g_opac_logits,
                           double* g_sh, double* g_M, double* g_inst_q, double* g_inst_t) {
@@ -998,11 +1103,16 @@ void orc_project_backward(int64_t n_sel, const int64_t* sel, const double* means
     for (int i = 0; i < 9; ++i) A[i / 3][i % 3] = As[9 * k + i];
     for (int i = 0; i < 3; ++i) b[i] = bs[3 * k + i];
     Proj o;
-    project_one(cam, A, b, means + 3 * g, log_scales + 3 * g, quats + 4 * g, opac_logits[g],
-                sh + (size_t)K * 3 * g, sh_deg, lod_r, o);
+    double mu_used[3];
+    project_lod(cam, A, b, g, view, means + 3 * g, log_scales + 3 * g, quats + 4 * g,
+                opac_logits[g], sh + (size_t)K * 3 * g, sh_deg, lod_r, o, mu_used);
     if (!o.kept) continue;
+    // a splat re-projected outside the frustum has no tiles and no adjoint
+    if (o.offset && (o.rect[2] - o.rect[0]) * (o.rect[3] - o.rect[1]) <= 0) continue;
+    // the noisy offset is a drawn constant: the adjoint of the noisy mean is
+    // that of the mean (no derivative through its depth-dependent scale)
     ProjGrad pg;
-    project_one_backward(cam, o, means + 3 * g, sh + (size_t)K * 3 * g, sh_deg, g_uv + 2 * j,
+    project_one_backward(cam, o, mu_used, sh + (size_t)K * 3 * g, sh_deg, g_uv + 2 * j,
                          g_conic + 3 * j, g_opac[j], g_rgb + 3 * j, pg);
     for (int i = 0; i < 3; ++i) g_means[3 * g + i] += pg.mean[i];
     for (int i = 0; i < 3; ++i) g_log_scales[3 * g + i] += pg.log_scale[i];
@@ -1063,6 +1173,24 @@ void orc_adam_step(int64_t n, double* p, const double* g, double* m, double* v, 
     const double vhat = v[i] / bc2;
     p[i] -= lr * mhat / (std::sqrt(vhat) + eps);
   }
+}
+
+// Stochastic LOD of Eq. 7: mode 0 = deterministic threshold cull, 1 = Eq. 7
+// on the Gaussians below r. key = the generator seed, epoch = the counter
+// word that distinguishes calls.
+void orc_set_lod(int mode, double p_max, double dist, double ox, double oy, double oz,
+                 uint32_t key0, uint32_t key1, uint32_t epoch) {
+  g_lod.mode = mode;
+  g_lod.p_max = (float)p_max;
+  g_lod.dist = (float)dist;
+  g_lod.offset[0] = ox; g_lod.offset[1] = oy; g_lod.offset[2] = oz;
+  g_lod.key[0] = key0; g_lod.key[1] = key1;
+  g_lod.epoch = epoch;
+}
+
+// Philox4x32-10 of one counter under one key (for pinning the generator).
+void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
 }
 
 void orc_set_margins(double alpha_tol, double T_tol, double power_tol) {
