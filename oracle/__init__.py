@@ -36,7 +36,10 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C++ compiler (no GPU involved)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", _LIB_PATH, _SRC]
+        # no contraction of a*b+c into FMA: the arithmetic is the written one on
+        # every host (the Eq. 7 draw threshold is compared in FP32)
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-o", _LIB_PATH, _SRC]
         subprocess.run(cmd, check=True)
     return _LIB_PATH
 

@@ -407,7 +407,7 @@ bool lod_draw(int64_t gid, int view, double z, const double mu[3], double mu_out
   const float p = g_lod.p_max + (g_lod.p_max - 0.01f) * std::min(0.f, (zf - D) / D);
   const float thr = p * 16777216.f;
   const float u0 = (float)(a[0] >> 8);
-  if (std::fabs((double)u0 - (double)thr) <= 2.0) *near_bits |= 128;
+  if (std::fabs((double)u0 - (double)thr) <= 8.0) *near_bits |= 128;
   if (u0 < thr) return false;
   philox4x32_10(ctr1, g_lod.key, b);
   const double two24 = 16777216.0;
