@@ -22,7 +22,8 @@ namespace s3r {
 namespace {
 
 constexpr int kThreads = kTilePixels / 2;   // 128: two pixels per thread
-constexpr int kBatch = 256;                   // splats staged per batch
+constexpr int kBatch = 256;                   // splats staged per batch (forward)
+constexpr int kBatchBwd = 128;                // splats staged per batch (backward)
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
@@ -355,13 +356,15 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
   q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
-__global__ void __launch_bounds__(kThreads, 8) k_blend_bwd(const __grid_constant__ ViewSet vs,
+// 16 CTAs (64 warps) per SM: the walk is latency-bound (shuffle, MUFU and
+// shared-memory results), so occupancy beats the few spilled registers
+__global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constant__ ViewSet vs,
                                                         BlendArgs a) {
-  __shared__ float4 s_a[kBatch];
-  __shared__ float4 s_b[kBatch];
-  __shared__ float s_c[kBatch];
-  __shared__ uint32_t s_id[kBatch];
-  __shared__ float s_g[kBatch][9];
+  __shared__ float4 s_a[kBatchBwd];
+  __shared__ float4 s_b[kBatchBwd];
+  __shared__ float s_c[kBatchBwd];
+  __shared__ uint32_t s_id[kBatchBwd];
+  __shared__ float s_g[kBatchBwd][9];
   __shared__ int s_max;
   const int tile = blockIdx.x;
   const int v = view_of_tile(vs, tile);
@@ -383,8 +386,8 @@ __global__ void __launch_bounds__(kThreads, 8) k_blend_bwd(const __grid_constant
   __syncthreads();
   const int n = s_max;
 
-  for (int hi = n; hi > 0; hi -= kBatch) {
-    const int lo = max(0, hi - kBatch);
+  for (int hi = n; hi > 0; hi -= kBatchBwd) {
+    const int lo = max(0, hi - kBatchBwd);
     const int m = hi - lo;
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += kThreads) {
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_blend_bwd(const __grid_constant
       const float4 co = a.sp_conic_o[s];
       stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
     }
-    for (int i = threadIdx.x; i < kBatch * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < kBatchBwd * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
     // this warp's splats end at its own last contributor; walk them back to
     // front, 32 at a time, visiting only the splats the forward blended into
