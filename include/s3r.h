@@ -131,6 +131,7 @@ typedef struct {
   int64_t n_frustum;       /* selected Gaussians inside at least one frustum */
   int64_t n_blend_pairs;   /* (pixel, splat) pairs the last forward blend evaluated */
   uint32_t device_status;  /* latched bits: 1 capacity, 2 timeout */
+  uint32_t epoch;          /* call counter of the last s3r_project (stochastic-LOD draws) */
 } s3r_counts;
 
 typedef struct s3r_workspace s3r_workspace;
@@ -236,6 +237,34 @@ typedef struct {
 } s3r_adam_tensor;
 s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
                          float beta2, float eps, int32_t step, void* stream);
+
+/* Level of detail (Sec. 3.3 "Adaptive LOD", Eq. 7). In the default
+ * S3R_LOD_THRESHOLD mode every in-frustum Gaussian whose projected 2D scale
+ * (square root of the largest eigenvalue of the undilated 2D covariance, in
+ * pixels) is below the lod_threshold r of s3r_project is culled. In
+ * S3R_LOD_STOCHASTIC mode those Gaussians are instead dropped with the
+ * depth-dependent probability of Eq. 7,
+ *   p = p_max + (p_max - 0.01) * min(0, (d - distance) / distance),
+ * d the camera-space depth, and the survivors are rendered at a noisy mean
+ *   mu + offset * min(1, d / distance) * (n0, n1, n2),  n ~ N(0, 1) per axis,
+ * in the Gaussian's own frame (the noise is a constant for the gradient).
+ * Draws are Philox4x32-10 of the counter (Gaussian id, view index in the
+ * call, call epoch, block 0/1) under the key (seed low, seed high); the
+ * epoch increments with every s3r_project of the workspace (and with every
+ * replay of a captured sequence) and is reported by s3r_query_counts. The
+ * setting applies to the following s3r_project and s3r_render_bwd calls of
+ * the workspace; params NULL restores the threshold mode. Requires
+ * 0 <= p_max <= 1 and distance > 0. */
+#define S3R_LOD_THRESHOLD 0
+#define S3R_LOD_STOCHASTIC 1
+typedef struct {
+  int32_t mode;
+  float p_max;
+  float distance;
+  float offset[3];
+  uint64_t seed;
+} s3r_lod_params;
+s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params);
 
 /* Per-kernel device timing (tracing). With timing enabled, every kernel the
  * workspace's calls launch is bracketed by a pair of CUDA events owned by the

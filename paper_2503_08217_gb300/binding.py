@@ -26,7 +26,10 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
-           "s3r_adam_step")
+           "s3r_adam_step", "s3r_set_lod")
+
+LOD_THRESHOLD = 0
+LOD_STOCHASTIC = 1
 
 
 class S3RError(RuntimeError):
@@ -74,7 +77,13 @@ class AdamTensor(ctypes.Structure):
 class Counts(ctypes.Structure):
     _fields_ = [("n_selected", ctypes.c_int64), ("n_splats", ctypes.c_int64),
                 ("n_duplicates", ctypes.c_int64), ("n_frustum", ctypes.c_int64),
-                ("n_blend_pairs", ctypes.c_int64), ("device_status", ctypes.c_uint32)]
+                ("n_blend_pairs", ctypes.c_int64), ("device_status", ctypes.c_uint32),
+                ("epoch", ctypes.c_uint32)]
+
+
+class LodParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("p_max", ctypes.c_float), ("distance", ctypes.c_float),
+                ("offset", ctypes.c_float * 3), ("seed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -103,6 +112,7 @@ def load(path: str = LIB_PATH):
     L.s3r_query_counts.argtypes = [vp, vp, P(Counts)]
     L.s3r_l1_loss.argtypes = [i64, vp, vp, vp, vp, vp]
     L.s3r_set_timing.argtypes = [vp, i32]
+    L.s3r_set_lod.argtypes = [vp, P(LodParams)]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
     L.s3r_kernel_count.restype = i32
@@ -118,7 +128,7 @@ def load(path: str = LIB_PATH):
     for name in ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_project", "s3r_sort",
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
-                 "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step"):
+                 "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -240,7 +250,18 @@ class Workspace:
         _check(load().s3r_query_counts(self._h, _stream(stream), ctypes.byref(c)))
         return {"n_selected": c.n_selected, "n_splats": c.n_splats,
                 "n_duplicates": c.n_duplicates, "n_frustum": c.n_frustum,
-                "n_blend_pairs": c.n_blend_pairs, "device_status": c.device_status}
+                "n_blend_pairs": c.n_blend_pairs, "device_status": c.device_status,
+                "epoch": c.epoch}
+
+    def set_lod(self, mode: int = LOD_THRESHOLD, p_max: float = 0.0, distance: float = 1.0,
+                offset=(0.0, 0.0, 0.0), seed: int = 0):
+        """LOD of the following projections (Eq. 7 when mode is LOD_STOCHASTIC)."""
+        if mode == LOD_THRESHOLD:
+            _check(load().s3r_set_lod(self._h, None))
+            return
+        prm = LodParams(int(mode), float(p_max), float(distance), (ctypes.c_float * 3)(*offset),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF)
+        _check(load().s3r_set_lod(self._h, ctypes.byref(prm)))
 
     def set_timing(self, enable: bool):
         _check(load().s3r_set_timing(self._h, 1 if enable else 0))

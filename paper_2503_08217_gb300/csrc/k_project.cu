@@ -33,6 +33,7 @@ struct ProjArgs {
   float t;
   float2* life;
   float lod;
+  LodArgs L;               // Eq. 7 on the Gaussians below lod (mode S3R_LOD_STOCHASTIC)
   // workspace
   const uint32_t* selected;
   uint32_t* frustum_mask;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant
   if (threadIdx.x == 0) s_frustum = 0;
   __syncthreads();
   const uint32_t n_sel = a.ctr[kCtrSelected];
+  const uint32_t epoch = a.ctr[kCtrEpoch];
   const uint32_t lane = lane_id();
   const uint32_t lt = lanemask_lt();
   uint32_t nfr_local = 0;
@@ -143,7 +145,9 @@ __global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant
         const Proj2D p = project_view(mats[v * nk + k], mu, RS, vs.v[v]);
         if (p.infrustum) {
           fmask |= 1u << v;
-          if (p.sigma >= a.lod) kmask |= 1u << v;
+          if (p.sigma >= a.lod ||
+              (a.L.mode == S3R_LOD_STOCHASTIC && lod_keep(a.L, gid, (uint32_t)v, epoch, p.z)))
+            kmask |= 1u << v;
         }
       }
       a.frustum_mask[j] = fmask;
@@ -281,6 +285,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
   const uint32_t lane = lane_id();
   float* my_sh = s_sh + warp * St::kWords;
   const uint32_t n_kept = a.ctr[kCtrKept];
+  const uint32_t epoch = a.ctr[kCtrEpoch];
   bool overflow = false;
   for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < (int64_t)n_kept;
        base += (int64_t)gridDim.x * kThreads) {
@@ -315,9 +320,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
         m &= m - 1;
         const InstMat& M = mats[v * nk + k];
         const ViewInfo& vi = s_views[v];
-        const Proj2D p = project_view(M, mu, RS, vi);
+        Proj2D p = project_view(M, mu, RS, vi);
+        // Eq. 7: a kept view below the LOD scale survived the drop draw and is
+        // rendered at its noisy mean (no tiles if that leaves the frustum)
+        float mv[3] = {mu[0], mu[1], mu[2]};
+        const bool moved = a.L.mode == S3R_LOD_STOCHASTIC && p.sigma < a.lod;
+        if (moved) {
+          lod_noisy_mean(a.L, gid, (uint32_t)v, epoch, p.z, mu, mv);
+          p = project_view(M, mv, RS, vi);
+          if (!p.infrustum) p.x0 = p.y0 = p.x1 = p.y1 = 0;
+        }
         float rp[3];
-        rel_pos(M, mu, rp);
+        rel_pos(M, mv, rp);
         const float inv = rsqrtf(rp[0] * rp[0] + rp[1] * rp[1] + rp[2] * rp[2]);
         float Y[16];
         sh_basis<DEG>(rp[0] * inv, rp[1] * inv, rp[2] * inv, Y);
@@ -348,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
           a.sp_rgb_d[s] = make_float4(rgb[0], rgb[1], rgb[2], p.z);
           a.sp_rect[s] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16),
                                     (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
-          a.sp_view[s] = (uint8_t)v;
+          a.sp_view[s] = (uint8_t)v | (moved ? kSplatMoved : (uint8_t)0);
           const uint32_t key = __float_as_uint(p.z);
           a.depth_key[s] = key;
           atomicAdd(&s_hist[0][key & 0xffu], 1u);
@@ -431,6 +445,12 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.t = t;
   a.life = reinterpret_cast<float2*>(life);
   a.lod = lod;
+  a.L.mode = ws->lod.mode;
+  a.L.p_max = ws->lod.p_max;
+  a.L.dist = ws->lod.distance;
+  for (int i = 0; i < 3; ++i) a.L.off[i] = ws->lod.offset[i];
+  a.L.key0 = (uint32_t)ws->lod.seed;
+  a.L.key1 = (uint32_t)(ws->lod.seed >> 32);
   a.selected = ws->selected;
   a.frustum_mask = ws->frustum_mask;
   a.keep_mask = ws->keep_mask;

@@ -37,6 +37,8 @@ struct BwdArgs {
   const uint2* kept_list;
   const uint32_t* splat_start;
   const float4* sp_grad;   // [S][3] float4
+  const uint8_t* sp_view;  // view | kSplatMoved
+  LodArgs L;
   int64_t cap_splats;
   uint32_t* ctr;
   float* pose_dM;          // [n_views][n_inst+1][12]
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
   // only Gaussians kept in at least one view have adjoints; a warp takes 32
   // consecutive work-list entries
   const uint32_t n_kept = a.ctr[kCtrKept];
+  const uint32_t epoch = a.ctr[kCtrEpoch];
   for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < (int64_t)n_kept;
        base += (int64_t)gridDim.x * kThreads) {
     const int n_here = (int)min((int64_t)32, (int64_t)n_kept - base);
@@ -182,15 +185,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       const int64_t si = s++;
       if (si >= a.cap_splats) break;
       const float4 ga = a.sp_grad[3 * si], gb = a.sp_grad[3 * si + 1], gc = a.sp_grad[3 * si + 2];
+      // a splat without adjoints (none of its pairs blended) adds nothing;
+      // skipping it also skips splats moved out of the frustum by Eq. 7
+      if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
+          gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
+        continue;
       const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gO = gb.y;
       const float grgb[3] = {gb.z, gb.w, gc.x};
       const InstMat& M = mats[v * nk + k];
       const ViewInfo& vi = s_views[v];
       const float* A = M.m;   // rows at 0, 4, 8; translation at 3, 7, 11
 
+      // ---- Eq. 7: a splat rendered at its noisy mean is differentiated there
+      // (the drawn offset is a constant)
+      float mv[3] = {mu[0], mu[1], mu[2]};
+      if (a.sp_view[si] & kSplatMoved) {
+        float rp0[3], x0, y0, z0;
+        rel_pos(M, mu, rp0);
+        cam_pos(M, rp0, x0, y0, z0);
+        lod_noisy_mean(a.L, gid, (uint32_t)v, epoch, z0, mu, mv);
+      }
+
       // ---- forward recompute (the same arithmetic as project_view)
       float rp[3], x, y, z;
-      rel_pos(M, mu, rp);
+      rel_pos(M, mv, rp);
       cam_pos(M, rp, x, y, z);
       float B[9];
 #pragma unroll
@@ -324,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       for (int c = 0; c < 3; ++c) g_mu[c] += A[c] * dp[0] + A[4 + c] * dp[1] + A[8 + c] * dp[2];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        dA[3 * r] += dp[r] * mu[0]; dA[3 * r + 1] += dp[r] * mu[1]; dA[3 * r + 2] += dp[r] * mu[2];
+        dA[3 * r] += dp[r] * mv[0]; dA[3 * r + 1] += dp[r] * mv[1]; dA[3 * r + 2] += dp[r] * mv[2];
         db[r] += dp[r];
       }
       if (k > 0) {
@@ -486,6 +504,13 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.kept_list = ws->kept_list;
   a.splat_start = ws->splat_start;
   a.sp_grad = reinterpret_cast<const float4*>(ws->sp_grad);
+  a.sp_view = ws->sp_view;
+  a.L.mode = ws->lod.mode;
+  a.L.p_max = ws->lod.p_max;
+  a.L.dist = ws->lod.distance;
+  for (int i = 0; i < 3; ++i) a.L.off[i] = ws->lod.offset[i];
+  a.L.key0 = (uint32_t)ws->lod.seed;
+  a.L.key1 = (uint32_t)(ws->lod.seed >> 32);
   a.cap_splats = ws->cap.max_splats;
   a.ctr = ws->ctr;
   a.pose_dM = ws->pose_dM;

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant_
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
       rect[k] = i0 + k < n ? a.sp_rect[sp[k]] : make_uint2(0u, 0u);
-      view[k] = i0 + k < n ? a.sp_view[sp[k]] : 0;
+      view[k] = i0 + k < n ? (a.sp_view[sp[k]] & 0x7f) : 0;   // bit 7: Eq. 7 moved
     }
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {

@@ -145,6 +145,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   DeviceGuard g(device);
   if (!g.ok) return fail(S3R_ERR_CUDA, "cannot select device %d", device);
   s3r_workspace* ws = new s3r_workspace();
+  ws->lod = s3r_lod_params{S3R_LOD_THRESHOLD, 0.f, 1.f, {0.f, 0.f, 0.f}, 0u};
   memset(ws, 0, sizeof(*ws));
   ws->device = device;
   ws->cap = *cap;
@@ -389,6 +390,23 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n) {
   return S3R_OK;
 }
 
+s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params) {
+  if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
+  if (!params) {
+    ws->lod = s3r_lod_params{S3R_LOD_THRESHOLD, 0.f, 1.f, {0.f, 0.f, 0.f}, 0u};
+    return S3R_OK;
+  }
+  if (params->mode != S3R_LOD_THRESHOLD && params->mode != S3R_LOD_STOCHASTIC)
+    return fail(S3R_ERR_INVALID, "lod mode %d unknown", params->mode);
+  if (params->mode == S3R_LOD_STOCHASTIC &&
+      (!(params->p_max >= 0.f && params->p_max <= 1.f) || !(params->distance > 0.f) ||
+       !std::isfinite(params->distance) || !std::isfinite(params->offset[0]) ||
+       !std::isfinite(params->offset[1]) || !std::isfinite(params->offset[2])))
+    return fail(S3R_ERR_INVALID, "stochastic LOD needs 0 <= p_max <= 1, distance > 0, finite offsets");
+  ws->lod = *params;
+  return S3R_OK;
+}
+
 s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
                          float beta2, float eps, int32_t step, void* stream) {
   if (!tensors || count < 0 || count > S3R_ADAM_MAX_TENSORS)
@@ -435,6 +453,7 @@ s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out) {
   out->n_duplicates = h[kCtrDups];
   out->n_frustum = h[kCtrFrustum];
   out->n_blend_pairs = (int64_t)((uint64_t)h[kCtrPairs] | ((uint64_t)h[kCtrPairs + 1] << 32));
+  out->epoch = h[kCtrEpoch];
   out->device_status = h[kCtrStatus];
   if (h[kCtrStatus] && (e = cudaMemset(ws->ctr + kCtrStatus, 0, sizeof(uint32_t))) != cudaSuccess)
     return cuda_fail(e, "cudaMemset status");

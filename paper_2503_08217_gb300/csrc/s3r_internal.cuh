@@ -125,6 +125,7 @@ struct s3r_workspace {
   int depth_final;          // which buffer holds the depth-sorted splats
   int dup_final;            // which buffer holds the tile-sorted pairs
   int tile_passes;
+  s3r_lod_params lod;       // mode S3R_LOD_THRESHOLD unless s3r_set_lod said otherwise
   // per-kernel timing hook
   int timing;
   cudaEvent_t ev[2 * s3r::kKCount];

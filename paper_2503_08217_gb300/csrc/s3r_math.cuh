@@ -86,6 +86,8 @@ __device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[
                                                const float RS[9], const ViewInfo& vi) {
   Proj2D o;
   o.infrustum = false;
+  o.u = o.v = o.ca = o.cb = o.cc = o.sigma = o.radius = 0.f;
+  o.x0 = o.y0 = o.x1 = o.y1 = 0;
   float d[3];
   rel_pos(M, mu, d);
   cam_pos(M, d, o.x, o.y, o.z);
@@ -169,6 +171,66 @@ __device__ __forceinline__ void sh_basis(float dx, float dy, float dz, float Y[1
 }
 
 __host__ __device__ constexpr int sh_count(int deg) { return (deg + 1) * (deg + 1); }
+
+// ---- stochastic LOD (Eq. 7) ---------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of two
+// 32x32 -> 64-bit products by fixed odd multipliers, high halves XORed with
+// the other counter words and the round key, key bumped by two Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+struct LodArgs {
+  int mode;            // S3R_LOD_THRESHOLD / S3R_LOD_STOCHASTIC
+  float p_max, dist;
+  float off[3];
+  uint32_t key0, key1;
+};
+
+// Eq. 7 drop decision for a small in-frustum (Gaussian, view) at depth z:
+// drop iff the top 24 bits of the first draw are below p * 2^24, p evaluated
+// with rounded single-precision operations (no contraction) so that it is the
+// same number on any IEEE host.
+__device__ __forceinline__ bool lod_keep(const LodArgs& L, uint32_t gid, uint32_t view,
+                                         uint32_t epoch, float z) {
+  const uint4 a = philox4x32_10(make_uint4(gid, view, epoch, 0u), L.key0, L.key1);
+  const float t = fminf(0.f, __fdiv_rn(__fsub_rn(z, L.dist), L.dist));
+  const float p = __fadd_rn(L.p_max, __fmul_rn(__fsub_rn(L.p_max, 0.01f), t));
+  return !((float)(a.x >> 8) < __fmul_rn(p, 16777216.f));
+}
+
+// Noisy mean of a surviving small Gaussian: offset * min(1, z / D) * n with
+// n per-axis standard normals by Box-Muller on 24-bit uniforms in (0, 1] and
+// [0, 1) from the remaining words of the two blocks.
+__device__ __forceinline__ void lod_noisy_mean(const LodArgs& L, uint32_t gid, uint32_t view,
+                                               uint32_t epoch, float z, const float mu[3],
+                                               float out[3]) {
+  const uint4 a = philox4x32_10(make_uint4(gid, view, epoch, 0u), L.key0, L.key1);
+  const uint4 b = philox4x32_10(make_uint4(gid, view, epoch, 1u), L.key0, L.key1);
+  const float k24 = 1.f / 16777216.f;
+  const float u1 = (float)((a.y >> 8) + 1u) * k24, u2 = (float)(a.z >> 8) * k24;
+  const float u3 = (float)((a.w >> 8) + 1u) * k24, u4 = (float)(b.x >> 8) * k24;
+  const float r1 = sqrtf(-2.f * logf(u1)), r2 = sqrtf(-2.f * logf(u3));
+  float s1, c1, s2, c2;
+  sincospif(2.f * u2, &s1, &c1);
+  sincospif(2.f * u4, &s2, &c2);
+  const float sc = fminf(1.f, z / L.dist);
+  out[0] = fmaf(L.off[0] * sc, r1 * c1, mu[0]);
+  out[1] = fmaf(L.off[1] * sc, r1 * s1, mu[1]);
+  out[2] = fmaf(L.off[2] * sc, r2 * c2, mu[2]);
+}
+
+constexpr uint8_t kSplatMoved = 0x80;   // splat view byte: rendered at its noisy mean
 
 // Shared-memory staging of the SH rows of a warp's 32 Gaussians: K*3 floats
 // per Gaussian, moved as float4s when K*3 is a multiple of 4 (degrees 1, 3),

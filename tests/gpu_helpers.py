@@ -43,7 +43,9 @@ def gpu_step(scene, step, cams, vis, life=None, lod=0.0, bg=(0.0, 0.0, 0.0), dL=
     rect = ws.debug("splat_rect", torch.int32, 2 * sp).cpu().numpy().view(np.uint32).reshape(-1, 2)
     res["rect"] = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16],
                            1).astype(np.int32)
-    res["view"] = ws.debug("splat_view", torch.uint8, sp).cpu().numpy().astype(np.int32)
+    vb = ws.debug("splat_view", torch.uint8, sp).cpu().numpy().astype(np.int32)
+    res["view"] = vb & 0x7F
+    res["moved"] = (vb >> 7).astype(bool)          # Eq. 7: rendered at its noisy mean
     nd = min(n_dup, r.ws.capacity.max_duplicates)
     res["sorted_splats"] = ws.debug("sorted_splats", torch.int32, nd).cpu().numpy().view(np.uint32)
     res["sorted_tiles"] = ws.debug("sorted_tiles", torch.int32, nd).cpu().numpy().view(np.uint32)

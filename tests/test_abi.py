@@ -59,3 +59,10 @@ def test_adam_argument_checks_fail_without_a_gpu():
     arr[0] = T(None, None, None, None, 10)
     assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1     # NULL arrays
     assert b"adam" in L.s3r_last_error()
+
+
+def test_set_lod_rejects_a_null_workspace_without_a_gpu():
+    from paper_2503_08217_gb300 import binding
+    L = binding.load()
+    prm = binding.LodParams(binding.LOD_STOCHASTIC, 0.5, 10.0, (0.1, 0.1, 0.1), 7)
+    assert L.s3r_set_lod(None, prm) == 1

@@ -77,6 +77,11 @@ def _compare_splats(res, f, scene, cams):
             i = idx[int(gids[s])]
             if rec["near"][i] or not rec["kept"][i]:
                 continue
+            rect = rec["rect"][i]
+            if (rect[2] - rect[0]) * (rect[3] - rect[1]) <= 0:
+                # an Eq. 7 splat moved out of the frustum: no tiles, nothing else rendered
+                np.testing.assert_array_equal(res["rect"][s], [0, 0, 0, 0])
+                continue
             u, vv = rec["uv"][i]
             assert abs(res["xy"][s, 0] - u) <= 1e-5 * abs(u) + 2e-4
             assert abs(res["xy"][s, 1] - vv) <= 1e-5 * abs(vv) + 2e-4
@@ -308,6 +313,57 @@ def test_multiview_rig_sh3_lod(built):
     res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3), dL=dL)
     _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
                                          "inst_quat", "inst_trans"))
+
+
+def test_stochastic_lod_eq7_rig(built):
+    """Eq. 7 on the three-camera rig crop: the GPU's Philox draws equal the
+    oracle's (drop masks exactly, noisy means through the splat records), and
+    images and gradients match at the noisy positions. The draws of a call
+    use the workspace epoch, which increments with every projection."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    sc = _rig_crop()
+    vis, _ = gpu_helpers.sweep_visibility(sc, lod=1.0)
+    step = 6
+    cams = sc.cams[step]
+    bg = (0.2, 0.1, 0.3)
+    prm = dict(p_max=0.5, distance=25.0, offset=(0.08, 0.05, 0.12), seed=0x1234_5678_9ABC)
+    r = gpu_helpers.Renderer(sc.n, sc.n_inst, cams)
+    r.ws.set_lod(binding.LOD_STOCHASTIC, **prm)
+    try:
+        res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=bg, renderer=r)
+        e1 = res["counts"]["epoch"]
+        oracle.set_lod(1, prm["p_max"], prm["distance"], prm["offset"], prm["seed"], e1)
+        f = _oracle_views(sc, step, cams, vis, 1.0, bg=bg)
+        small_kept = sum(int((v["rec"]["kept"] & (v["rec"]["sigma_lod"] < 1.0)).sum()) for v in f["views"])
+        small_drop = sum(int((v["rec"]["infrustum"] & ~v["rec"]["kept"]).sum()) for v in f["views"])
+        assert small_kept > 300 and small_drop > 300, (small_kept, small_drop)
+        assert res["moved"].sum() > 300
+        _compare_selection_and_masks(res, f, len(cams))
+        assert _compare_splats(res, f, sc, cams) > 500
+        _stage_isolated_sort(res, cams)
+        _stage_isolated_blend(res, cams, bg=bg)
+        _compare_images(res, f, cams)
+        # the backward run projects again: epoch e1 + 1
+        oracle.set_lod(1, prm["p_max"], prm["distance"], prm["offset"], prm["seed"], e1 + 1)
+        f = _oracle_views(sc, step, cams, vis, 1.0, bg=bg)
+        rng = np.random.default_rng(12)
+        dL = []
+        for v, cam in enumerate(cams):
+            d = rng.standard_normal((3, cam.height, cam.width))
+            view = f["views"][v]
+            d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+            dL.append(d)
+        g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=bg)
+        for v in range(len(cams)):
+            dL[v][:, g_orc["pixel_flags"][v]] = 0.0
+        g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=bg)
+        res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=bg, dL=dL, renderer=r)
+        assert res["counts"]["epoch"] == e1 + 1
+        _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                             "inst_quat", "inst_trans"))
+    finally:
+        oracle.set_lod(0)
 
 
 def test_empty_selection_renders_background(built, tiny):
