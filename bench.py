@@ -80,6 +80,17 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-adam", action="store_true", help="skip the optimiser-step timing")
+    p.add_argument("--lod-mode", default="threshold", choices=("threshold", "stochastic"),
+                   help="LOD of the projection: the threshold cull, or Eq. 7 on the Gaussians below r")
+    p.add_argument("--lod-r", type=float, default=None, help="LOD scale r in px (default: the workload's)")
+    p.add_argument("--lod-pmax", type=float, default=0.5)
+    p.add_argument("--lod-dist", type=float, default=100.0)
+    p.add_argument("--lod-offset", type=float, default=0.1)
+    p.add_argument("--lod-seed", type=int, default=2025)
+    p.add_argument("--sweep", default=None, choices=("scale",),
+                   help="scale: per-view fwd+bwd time of the large corridor stretched at constant "
+                        "density, with the temporal record and with every Gaussian visible")
+    p.add_argument("--sweep-scales", default="0.5,1,2,4")
     return p.parse_args()
 
 
@@ -219,6 +230,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     dev_name = f"cuda:{local}"
     scene, lod, desc = make_workload(args.workload, args.seed)
+    if args.lod_r is not None:
+        lod = float(args.lod_r)
     k = step_index(scene, rank)
     cams = scene.cams[k]
     n_views = len(cams)
@@ -228,6 +241,12 @@ def run_ours(args, rank, world, local):
     n = scene.n
     max_splats = max(4096, int(n * min(n_views, 3)))
     r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
+    lod_cfg = {"mode": args.lod_mode, "r_px": lod}
+    if args.lod_mode == "stochastic":
+        r.ws.set_lod(binding.LOD_STOCHASTIC, p_max=args.lod_pmax, distance=args.lod_dist,
+                     offset=(args.lod_offset,) * 3, seed=args.lod_seed)
+        lod_cfg.update(p_max=args.lod_pmax, distance_m=args.lod_dist, offset_m=args.lod_offset,
+                       seed=args.lod_seed)
 
     # --- first-epoch sweep: Eq. 5 over all timesteps, then Eq. 6
     vis = torch.empty((n, 2), device=dev_name)
@@ -347,6 +366,9 @@ def run_ours(args, rank, world, local):
     if not args.no_plain:
         r1 = Renderer(n, scene.n_inst, [max(cams, key=lambda c: c.width * c.height)],
                       max_splats=max(4096, n), max_duplicates=min(2**31 - 1, 6 * max(4096, n)))
+        if args.lod_mode == "stochastic":
+            r1.ws.set_lod(binding.LOD_STOCHASTIC, p_max=args.lod_pmax, distance=args.lod_dist,
+                          offset=(args.lod_offset,) * 3, seed=args.lod_seed)
         offs = np.cumsum([0] + [3 * c.width * c.height for c in cams])
 
         def plain_sweep():
@@ -451,7 +473,7 @@ def run_ours(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {desc}", "gaussians": n, "instances": scene.n_inst,
                        "cameras": n_views, "pixels_per_view_batch": P, "timestep": k,
-                       "sh_degree": scene.sh_degree, "lod_px": lod,
+                       "sh_degree": scene.sh_degree, "lod_px": lod, "lod": lod_cfg,
                        "l2": "flushed (512 MiB write) between timed steps, outside the timed events",
                        "graph": "whole step captured as one CUDA graph",
                        "parallelism": f"replicas x{world}, one timestep per rank, no collective"},
@@ -535,9 +557,101 @@ def run_reference(args, rank, world, local):
     }), flush=True)
 
 
+def run_scale_sweep(args):
+    """Per-view forward + backward time as the scene grows (the corridor of
+    the 'large' workload stretched at constant density: Gaussians, instances,
+    length and timesteps scale together; one 1920x1280 camera at the middle
+    timestep, LOD 1 px). 'temporal' selects with the visibility windows after a
+    first-epoch sweep (Eq. 5, then Eq. 6); 'all_visible' gives every Gaussian
+    the window [-1, 1], so every one is compacted and projected."""
+    import torch
+    from paper_2503_08217_gb300 import binding, build, scenegen
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer, pixel_count
+    build.build()
+    binding.load()
+    torch.cuda.set_device(0)
+    rows = []
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    for f in [float(x) for x in args.sweep_scales.split(",")]:
+        scene = scenegen.generate("large", seed=args.seed, length_scale=f)
+        lod = 1.0
+        k = scene.n_steps // 2
+        cams = scene.cams[k]
+        P = pixel_count(cams)
+        n = scene.n
+        dev = DeviceScene.from_host(scene)
+        cs = dev.c_scene()
+        max_splats = max(4096, n)
+        r = Renderer(n, scene.n_inst, cams, max_splats=max_splats,
+                     max_duplicates=min(2**31 - 1, 6 * max_splats))
+        vis = torch.empty((n, 2), device="cuda")
+        life = torch.empty((n, 2), device="cuda")
+        binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
+        all_vis = vis.clone()
+        for kk in range(scene.n_steps):
+            iq = torch.from_numpy(scene.inst_quat[kk]).cuda()
+            it = torch.from_numpy(scene.inst_trans[kk]).cuda()
+            r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
+                         life, lod)
+        binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+        torch.cuda.synchronize()
+        r.counts()
+        iq = torch.from_numpy(scene.inst_quat[k]).cuda()
+        it = torch.from_numpy(scene.inst_trans[k]).cuda()
+        t = float(scene.times[k])
+        target = torch.rand(3 * P, device="cuda")
+        out = torch.empty(3 * P, device="cuda")
+        dL = torch.empty(3 * P, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        bg = torch.zeros(3, device="cuda")
+        grads = {"means": torch.zeros_like(dev.means), "log_scales": torch.zeros_like(dev.log_scales),
+                 "quats": torch.zeros_like(dev.quats), "opacity_logits": torch.zeros_like(dev.opacity_logits),
+                 "sh": torch.zeros_like(dev.sh), "inst_quat": torch.zeros_like(iq),
+                 "inst_trans": torch.zeros_like(it)}
+        row = {"length_scale": f, "gaussians": n, "instances": scene.n_inst, "timesteps": scene.n_steps,
+               "corridor_m": round(float(scene.means[:, 2].max() - scene.means[:, 2].min()), 1)}
+        for mode, v in (("temporal", vis), ("all_visible", all_vis)):
+            def step():
+                for g in grads.values():
+                    g.zero_()
+                loss.zero_()
+                r.forward(dev, iq, it, cams, t, v, None, lod, bg, out=out, c_scene=cs)
+                binding.l1_loss(out, target, dL, loss)
+                r.backward(dev, iq, it, bg, dL, grads, c_scene=cs)
+            step()
+            torch.cuda.synchronize()
+            c = r.counts()
+            graph = r.capture(step)
+            for _ in range(args.warmup):
+                graph.replay()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.fill_(float(i))
+                ev[i][0].record()
+                graph.replay()
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            r.sync_status()
+            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            row[mode] = {"ms_per_view": round(ms / len(cams), 3), "selected": int(c["n_selected"]),
+                         "splats": int(c["n_splats"])}
+            del graph
+        rows.append(row)
+        del r, dev, grads, vis, life, all_vis, out, dL, target
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "scale", "metric": "fwd+bwd ms per view vs scene scale",
+                      "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.sweep == "scale":
+        if rank == 0:
+            run_scale_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world, local)
         return

@@ -208,14 +208,24 @@ def _static_means(rng, spec: CorridorSpec, n: int) -> np.ndarray:
 
 def generate(name: str, seed: int = 0, *, n_static: int | None = None,
              n_inst: int | None = None, n_steps: int | None = None,
-             rig=None, sh_degree: int | None = None) -> Scene:
+             rig=None, sh_degree: int | None = None, length_scale: float | None = None) -> Scene:
     """Draw the named corridor scene from a PCG64 stream seeded with `seed`.
 
     The keyword overrides shrink a scene (fewer Gaussians, instances or
     timesteps, a smaller camera) while keeping its distributions; tests use
-    them for crops the oracle finishes in seconds.
+    them for crops the oracle finishes in seconds. `length_scale` stretches the
+    corridor at constant density: its length, static Gaussians, instances and
+    timesteps all scale by that factor (a scene-scale sweep).
     """
     spec = SPECS[name]
+    if length_scale is not None:
+        f = float(length_scale)
+        z0, z1 = spec.z_range
+        spec = dataclasses.replace(spec, z_range=(z0, z0 + (z1 - z0) * f),
+                                   n_static=max(1, int(round(spec.n_static * f))),
+                                   n_inst=max(1, int(round(spec.n_inst * f))),
+                                   n_steps=max(2, int(round(spec.n_steps * f))),
+                                   inst_fixed=None)
     if n_static is not None or n_inst is not None or n_steps is not None or rig is not None \
             or sh_degree is not None:
         spec = dataclasses.replace(
