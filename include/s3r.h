@@ -129,9 +129,14 @@ typedef struct {
   int64_t n_splats;        /* kept (Gaussian, view) pairs */
   int64_t n_duplicates;    /* (tile, splat) pairs */
   int64_t n_frustum;       /* selected Gaussians inside at least one frustum */
-  int64_t n_blend_pairs;   /* (pixel, splat) pairs the last forward blend evaluated */
+  int64_t n_blend_pairs;   /* counting mode: (pixel, splat) pairs of the tile lists the last
+                              counted forward walked (each pixel up to its stop) */
   uint32_t device_status;  /* latched bits: 1 capacity, 2 timeout */
   uint32_t epoch;          /* call counter of the last s3r_project (stochastic-LOD draws) */
+  int64_t n_eval_fwd;      /* counting mode: pairs the last counted forward evaluated (its
+                              warp's footprint test passed and the pixel had not stopped) */
+  int64_t n_eval_bwd;      /* counting mode: pairs the last counted backward evaluated (in its
+                              warp's recorded contributors, up to the pixel's last one) */
 } s3r_counts;
 
 typedef struct s3r_workspace s3r_workspace;
@@ -265,6 +270,13 @@ typedef struct {
   uint64_t seed;
 } s3r_lod_params;
 s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params);
+
+/* Work accounting: with counting enabled the blend kernels also count the
+ * (pixel, splat) pairs they walk and evaluate (reported by s3r_query_counts;
+ * the counts persist until the next counted call). Counting runs a separate
+ * instantiation of each blend kernel with a few more instructions per pair,
+ * so it is off by default and off while timing. */
+s3r_status s3r_set_counting(s3r_workspace* ws, int32_t enable);
 
 /* Per-kernel device timing (tracing). With timing enabled, every kernel the
  * workspace's calls launch is bracketed by a pair of CUDA events owned by the

@@ -26,7 +26,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
-           "s3r_adam_step", "s3r_set_lod")
+           "s3r_adam_step", "s3r_set_lod", "s3r_set_counting")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -78,7 +78,8 @@ class Counts(ctypes.Structure):
     _fields_ = [("n_selected", ctypes.c_int64), ("n_splats", ctypes.c_int64),
                 ("n_duplicates", ctypes.c_int64), ("n_frustum", ctypes.c_int64),
                 ("n_blend_pairs", ctypes.c_int64), ("device_status", ctypes.c_uint32),
-                ("epoch", ctypes.c_uint32)]
+                ("epoch", ctypes.c_uint32), ("n_eval_fwd", ctypes.c_int64),
+                ("n_eval_bwd", ctypes.c_int64)]
 
 
 class LodParams(ctypes.Structure):
@@ -113,6 +114,7 @@ def load(path: str = LIB_PATH):
     L.s3r_l1_loss.argtypes = [i64, vp, vp, vp, vp, vp]
     L.s3r_set_timing.argtypes = [vp, i32]
     L.s3r_set_lod.argtypes = [vp, P(LodParams)]
+    L.s3r_set_counting.argtypes = [vp, i32]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
     L.s3r_kernel_count.restype = i32
@@ -128,7 +130,8 @@ def load(path: str = LIB_PATH):
     for name in ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_project", "s3r_sort",
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
-                 "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod"):
+                 "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
+                 "s3r_set_counting"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -251,7 +254,7 @@ class Workspace:
         return {"n_selected": c.n_selected, "n_splats": c.n_splats,
                 "n_duplicates": c.n_duplicates, "n_frustum": c.n_frustum,
                 "n_blend_pairs": c.n_blend_pairs, "device_status": c.device_status,
-                "epoch": c.epoch}
+                "epoch": c.epoch, "n_eval_fwd": c.n_eval_fwd, "n_eval_bwd": c.n_eval_bwd}
 
     def set_lod(self, mode: int = LOD_THRESHOLD, p_max: float = 0.0, distance: float = 1.0,
                 offset=(0.0, 0.0, 0.0), seed: int = 0):
@@ -262,6 +265,10 @@ class Workspace:
         prm = LodParams(int(mode), float(p_max), float(distance), (ctypes.c_float * 3)(*offset),
                         int(seed) & 0xFFFFFFFFFFFFFFFF)
         _check(load().s3r_set_lod(self._h, ctypes.byref(prm)))
+
+    def set_counting(self, enable: bool):
+        """Count the blend kernels' walked and evaluated pairs (see counts())."""
+        _check(load().s3r_set_counting(self._h, 1 if enable else 0))
 
     def set_timing(self, enable: bool):
         _check(load().s3r_set_timing(self._h, 1 if enable else 0))

@@ -40,7 +40,9 @@ struct BlendArgs {
   float* final_T;
   uint32_t* n_contrib;
   float* sp_grad;         // backward only, [S*12]
-  unsigned long long* pairs;  // forward only: evaluated (pixel, splat) pairs
+  unsigned long long* pairs;     // counting mode: list pairs the forward walked
+  unsigned long long* eval_fwd;  // counting mode: pairs the forward evaluated
+  unsigned long long* eval_bwd;  // counting mode: pairs the backward evaluated
   uint32_t* contrib;          // [4][contrib_words]: pair blended into >= 1 pixel of the warp block
   int64_t contrib_words;
 };
@@ -151,6 +153,9 @@ __device__ __forceinline__ bool box_misses(const float4 b, const TilePixels& t) 
   return b.x > t.bx1 || b.y < t.bx0 || b.z > t.by1 || b.w < t.by0;
 }
 
+// kCount: also count the (pixel, splat) pairs walked (list positions up to
+// each pixel's stop) and evaluated (footprint test passed, pixel not stopped).
+template <bool kCount>
 __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
                                                         BlendArgs a) {
   __shared__ float4 s_a[kBatch];
@@ -168,7 +173,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
 
   float T0 = 1.f, T1 = 1.f;
   float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-  int last0 = 0, last1 = 0, end0 = n, end1 = n;   // end: positions visited
+  int last0 = 0, last1 = 0, end0 = n, end1 = n;   // end: positions walked
+  uint32_t n_eval = 0;
   bool done0 = !P.in0, done1 = !P.in1;
   if (done0) end0 = 0;
   if (done1) end1 = 0;
@@ -195,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
       const float cb = s_c[j];
       const int pos = b0 + j + 1;
       bool any_blend = false;
+      if constexpr (kCount) n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
       {
         const SplatEval e = eval_splat(sa, sb, P.fx, P.fy0);
         const bool ok = !done0 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         C02 = fmaf(cb, w, C02);
         T0 = blend ? nT : T0;
         last0 = blend ? pos : last0;
-        end0 = stop ? pos : end0;
+        if constexpr (kCount) end0 = stop ? pos : end0;
         done0 = done0 || stop;
         any_blend = blend;
       }
@@ -223,7 +230,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         C12 = fmaf(cb, w, C12);
         T1 = blend ? nT : T1;
         last1 = blend ? pos : last1;
-        end1 = stop ? pos : end1;
+        if constexpr (kCount) end1 = stop ? pos : end1;
         done1 = done1 || stop;
         any_blend = any_blend || blend;
       }
@@ -233,11 +240,18 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
         or_bits(a.contrib + (threadIdx.x >> 5) * a.contrib_words, range.x + b0 + c0, blended);
     }
   }
-  // work accounting: (pixel, splat) pairs visited, one 64-bit atomic per warp
-  unsigned long long visited = (unsigned long long)end0 + (unsigned long long)end1;
+  if constexpr (kCount) {
+    // work accounting, one 64-bit atomic per warp and counter
+    unsigned long long walked = (unsigned long long)end0 + (unsigned long long)end1;
+    unsigned long long evald = n_eval;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) visited += __shfl_xor_sync(0xffffffffu, visited, o);
-  if (lane == 0 && visited) atomicAdd(a.pairs, visited);
+    for (int o = 16; o > 0; o >>= 1) {
+      walked += __shfl_xor_sync(0xffffffffu, walked, o);
+      evald += __shfl_xor_sync(0xffffffffu, evald, o);
+    }
+    if (lane == 0 && walked) atomicAdd(a.pairs, walked);
+    if (lane == 0 && evald) atomicAdd(a.eval_fwd, evald);
+  }
   const int64_t plane = (int64_t)vi.width * vi.height;
   if (P.in0) {
     const int64_t pix = (int64_t)P.py0 * vi.width + P.px;
@@ -358,6 +372,7 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
 
 // 16 CTAs (64 warps) per SM: the walk is latency-bound (shuffle, MUFU and
 // shared-memory results), so occupancy beats the few spilled registers
+template <bool kCount>
 __global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constant__ ViewSet vs,
                                                         BlendArgs a) {
   __shared__ float4 s_a[kBatchBwd];
@@ -385,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constan
   if (lane == 0 && wlast) atomicMax(&s_max, wlast);
   __syncthreads();
   const int n = s_max;
+  uint32_t n_eval = 0;   // counting mode: pairs inside their pixel's walk
 
   for (int hi = n; hi > 0; hi -= kBatchBwd) {
     const int lo = max(0, hi - kBatchBwd);
@@ -420,6 +436,7 @@ __global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constan
       const int pos = lo + j;
       const SplatEval e0 = eval_splat(sa, sb, P.fx, P.fy0);
       const SplatEval e1 = eval_splat(sa, sb, P.fx, P.fy1);
+      if constexpr (kCount) n_eval += (pos < q0.last ? 1u : 0u) + (pos < q1.last ? 1u : 0u);
       const bool act0 = (pos < q0.last) && !(e0.p > 0.f) && !(e0.alpha < kAlphaMin);
       const bool act1 = (pos < q1.last) && !(e1.p > 0.f) && !(e1.alpha < kAlphaMin);
       float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -447,6 +464,12 @@ __global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constan
       }
     }
   }
+  if constexpr (kCount) {
+    unsigned long long evald = n_eval;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) evald += __shfl_xor_sync(0xffffffffu, evald, o);
+    if (lane == 0 && evald) atomicAdd(a.eval_bwd, evald);
+  }
 }
 
 // Zero the per-splat adjoints of the splats written by the last projection.
@@ -470,6 +493,8 @@ static BlendArgs make_args(s3r_workspace* ws) {
   a.n_contrib = ws->n_contrib;
   a.sp_grad = ws->sp_grad;
   a.pairs = reinterpret_cast<unsigned long long*>(ws->ctr + kCtrPairs);
+  a.eval_fwd = reinterpret_cast<unsigned long long*>(ws->ctr + kCtrEvalFwd);
+  a.eval_bwd = reinterpret_cast<unsigned long long*>(ws->ctr + kCtrEvalBwd);
   a.contrib = ws->contrib;
   a.contrib_words = ws->contrib_words;
   a.bg = nullptr;
@@ -483,12 +508,18 @@ cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cu
   a.bg = bg;
   a.out = out;
   if (ws->views.total_tiles == 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(a.pairs, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (ws->counting) {
+    // pairs walked and evaluated (two adjacent 64-bit counters)
+    if ((e = cudaMemsetAsync(a.pairs, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(ws->contrib, 0, sizeof(uint32_t) * 4 * (size_t)ws->contrib_words, st);
   if (e != cudaSuccess) return e;
   KernelTimer timer(ws, kKBlendFwd, st);
-  k_blend_fwd<<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+  if (ws->counting)
+    k_blend_fwd<true><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+  else
+    k_blend_fwd<false><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
   return cudaGetLastError();
 }
 
@@ -505,8 +536,13 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ws->views.total_tiles == 0) return cudaSuccess;
+  if (ws->counting && (e = cudaMemsetAsync(a.eval_bwd, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+    return e;
   KernelTimer timer(ws, kKBlendBwd, st);
-  k_blend_bwd<<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+  if (ws->counting)
+    k_blend_bwd<true><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+  else
+    k_blend_bwd<false><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
   return cudaGetLastError();
 }
 

@@ -24,8 +24,10 @@ constexpr int kTileSpan = kWarps * kWarpSpan;         // 4096 Gaussians per tile
 __global__ void k_begin(uint32_t* ctr, uint32_t* hist) {
   // one block: zero the per-call counters and histograms, bump the epoch
   for (int i = threadIdx.x; i < kHistCount * kRadix; i += blockDim.x) hist[i] = 0;
+  // the status word, the epoch and the blend pair counts (which describe the
+  // last counted render) survive
   if (threadIdx.x < kCtrCount && threadIdx.x != kCtrStatus && threadIdx.x != kCtrEpoch &&
-      threadIdx.x != kCtrPairs && threadIdx.x != kCtrPairs + 1)
+      (threadIdx.x < kCtrPairs || threadIdx.x > kCtrEvalBwd + 1))
     ctr[threadIdx.x] = 0;
   if (threadIdx.x == 0) ctr[kCtrEpoch] = ctr[kCtrEpoch] + 1;
 }

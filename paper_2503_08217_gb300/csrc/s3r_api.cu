@@ -390,6 +390,12 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n) {
   return S3R_OK;
 }
 
+s3r_status s3r_set_counting(s3r_workspace* ws, int32_t enable) {
+  if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
+  ws->counting = enable ? 1 : 0;
+  return S3R_OK;
+}
+
 s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params) {
   if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
   if (!params) {
@@ -454,6 +460,8 @@ s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out) {
   out->n_frustum = h[kCtrFrustum];
   out->n_blend_pairs = (int64_t)((uint64_t)h[kCtrPairs] | ((uint64_t)h[kCtrPairs + 1] << 32));
   out->epoch = h[kCtrEpoch];
+  out->n_eval_fwd = (int64_t)((uint64_t)h[kCtrEvalFwd] | ((uint64_t)h[kCtrEvalFwd + 1] << 32));
+  out->n_eval_bwd = (int64_t)((uint64_t)h[kCtrEvalBwd] | ((uint64_t)h[kCtrEvalBwd + 1] << 32));
   out->device_status = h[kCtrStatus];
   if (h[kCtrStatus] && (e = cudaMemset(ws->ctr + kCtrStatus, 0, sizeof(uint32_t))) != cudaSuccess)
     return cuda_fail(e, "cudaMemset status");

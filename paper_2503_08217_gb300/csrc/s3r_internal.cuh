@@ -22,7 +22,9 @@ enum Ctr : int {
   kCtrFrustum = 5,    // selected Gaussians inside >= 1 frustum
   kCtrKept = 6,       // selected Gaussians kept in >= 1 view (length of kept_list)
   kCtrTileBase = 8,   // 16 dynamic tile-acquisition counters, one per stage
-  kCtrPairs = 24,     // 64-bit: (pixel, splat) pairs evaluated by the forward blend
+  kCtrPairs = 24,     // 64-bit: (pixel, splat) list pairs the forward walked (counting mode)
+  kCtrEvalFwd = 26,   // 64-bit: (pixel, splat) pairs the forward evaluated (counting mode)
+  kCtrEvalBwd = 28,   // 64-bit: (pixel, splat) pairs the backward evaluated (counting mode)
   kCtrCount = 32
 };
 constexpr uint32_t kStatusCapacity = 1u;
@@ -126,6 +128,7 @@ struct s3r_workspace {
   int dup_final;            // which buffer holds the tile-sorted pairs
   int tile_passes;
   s3r_lod_params lod;       // mode S3R_LOD_THRESHOLD unless s3r_set_lod said otherwise
+  int counting;             // blend kernels count their pairs (s3r_set_counting)
   // per-kernel timing hook
   int timing;
   cudaEvent_t ev[2 * s3r::kKCount];

@@ -504,3 +504,31 @@ def test_cuda_graph_replay_matches_eager(built, tiny, tiny_vis):
     torch.testing.assert_close(out, ref_out, rtol=0, atol=0)
     for k in ref_g:
         torch.testing.assert_close(grads[k], ref_g[k], rtol=1e-4, atol=1e-5)
+
+
+def test_counting_mode_changes_no_result(built, tiny, tiny_vis):
+    """The counting instantiations of the blend kernels give the same image
+    and gradients as the timed ones, and their counts are consistent:
+    evaluated <= walked pairs in the forward, the backward evaluates at most
+    the positions below each pixel's last contributor."""
+    import gpu_helpers
+    vis, _ = tiny_vis
+    step = 6
+    cams = tiny.cams[step]
+    rng = np.random.default_rng(21)
+    dL = [rng.standard_normal((3, c.height, c.width)) for c in cams]
+    r = gpu_helpers.Renderer(tiny.n, tiny.n_inst, cams)
+    off = gpu_helpers.gpu_step(tiny, step, cams, vis, dL=dL, renderer=r)
+    r.ws.set_counting(True)
+    on = gpu_helpers.gpu_step(tiny, step, cams, vis, dL=dL, renderer=r)
+    c = r.counts()          # after the backward (the step's own copy is taken after the forward)
+    r.ws.set_counting(False)
+    for a, b in zip(off["images"], on["images"]):
+        np.testing.assert_array_equal(a, b)
+    for k in off["grads"]:
+        np.testing.assert_allclose(on["grads"][k], off["grads"][k], rtol=1e-4,
+                                   atol=1e-5 * max(1e-30, np.abs(off["grads"][k]).max()))
+    contrib = int(on["n_contrib"].astype(np.int64).sum())
+    assert 0 < c["n_eval_bwd"] <= contrib <= c["n_blend_pairs"]
+    assert 0 < c["n_eval_fwd"] <= c["n_blend_pairs"]
+    assert c["n_eval_bwd"] <= c["n_eval_fwd"]
