@@ -96,7 +96,10 @@ __global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __re
       m.c[r] = (float)cr;
       m.c_lo[r] = (float)(cr - (double)m.c[r]);
     }
-    m.pad[0] = m.pad[1] = 0.f;
+    double f2 = 0.0;
+    for (int i = 0; i < 9; ++i) f2 += A[i] * A[i];
+    m.a_frob2 = (float)(f2 * (1.0 + 1e-6));
+    m.pad = 0.f;
     out[v * nk + k] = m;
   }
 }
@@ -112,6 +115,14 @@ __global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant
   uint32_t* s_off = reinterpret_cast<uint32_t*>(smem_raw);   // [n_inst+2]
   __shared__ uint32_t s_frustum;
   __shared__ uint32_t s_wcount[kWarps];
+  // per-lane view indices differ: camera records are read from shared memory
+  __shared__ ViewInfo s_views[S3R_MAX_VIEWS];
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(vs.v);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
+    const int words = vs.n_views * (int)(sizeof(ViewInfo) / 4);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   if (threadIdx.x == 0) s_frustum = 0;
   __syncthreads();
@@ -141,8 +152,16 @@ __global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant
       for (int r = 0; r < 3; ++r) {
         RS[3 * r] = R[3 * r] * s0; RS[3 * r + 1] = R[3 * r + 1] * s1; RS[3 * r + 2] = R[3 * r + 2] * s2;
       }
-      for (int v = 0; v < vs.n_views; ++v) {
-        const Proj2D p = project_view(mats[v * nk + k], mu, RS, vs.v[v]);
+      // cheap conservative test for every view, the full projection only for
+      // the candidates (each lane walks its own; the loop runs max-over-lanes times)
+      const float smax = fmaxf(s0, fmaxf(s1, s2));
+      uint32_t cand = 0;
+      for (int v = 0; v < vs.n_views; ++v)
+        if (may_touch_view(mats[v * nk + k], mu, smax * smax, s_views[v])) cand |= 1u << v;
+      while (cand) {
+        const int v = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const Proj2D p = project_view(mats[v * nk + k], mu, RS, s_views[v]);
         if (p.infrustum) {
           fmask |= 1u << v;
           if (p.sigma >= a.lod ||

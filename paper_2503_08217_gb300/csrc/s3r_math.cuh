@@ -18,7 +18,8 @@ struct __align__(16) InstMat {
   float m[12];
   float c[3];     // c_hi
   float c_lo[3];
-  float pad[2];
+  float a_frob2;  // squared Frobenius norm of A (bounds the splat radius, see may_touch_view)
+  float pad;
 };
 
 constexpr float kDilation = 0.3f;
@@ -137,6 +138,27 @@ __device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[
   o.y1 = (int)fminf((float)vi.gy, fmaxf(0.f, floorf((o.v + o.radius + (kTile - 1)) * inv_tile)));
   o.infrustum = (o.x1 > o.x0) && (o.y1 > o.y0);
   return o;
+}
+
+// Conservative frustum pre-test: false only if project_view would find the
+// tile rectangle empty (or the mean behind the near plane). The radius of
+// project_view is ceil(3 sqrt(lam)) with lam <= trace of the dilated 2D
+// covariance + sqrt(0.1) <= |J|_F^2 |A|_F^2 s_max^2 + 0.92 (|JB|_F <= |J|_F
+// |B|_2, |A RS|_2 <= |A|_F s_max), and |J|_F^2 <= (fx^2 (1 + limx^2) +
+// fy^2 (1 + limy^2)) / z^2 under the field-of-view clamp. The bound gets 1 %
+// and 2 px of slack for the FP32 rounding of both computations.
+__device__ __forceinline__ bool may_touch_view(const InstMat& M, const float mu[3], float smax2,
+                                               const ViewInfo& vi) {
+  float d[3], x, y, z;
+  rel_pos(M, mu, d);
+  cam_pos(M, d, x, y, z);
+  if (!(z > vi.near_z)) return false;
+  const float iz = 1.f / z;
+  const float u = fmaf(vi.fx, x * iz, vi.cx), v = fmaf(vi.fy, y * iz, vi.cy);
+  const float jc = vi.fx * vi.fx * fmaf(vi.limx, vi.limx, 1.f) + vi.fy * vi.fy * fmaf(vi.limy, vi.limy, 1.f);
+  const float rb = fmaf(3.03f, sqrtf(fmaf(jc * M.a_frob2 * smax2, iz * iz, 0.93f)), 3.f);
+  return !(u + rb < 0.f || u - rb > (float)(vi.gx * kTile) || v + rb < 0.f ||
+           v - rb > (float)(vi.gy * kTile));
 }
 
 // Real SH basis (orthonormal, Condon-Shortley sign) at a unit direction d,
