@@ -8,7 +8,8 @@
 // K); the splats are then expanded into (tile, splat) pairs in depth order,
 // and the one or two tile-digit passes finish the sort. Every pass is a
 // single-pass "onesweep" kernel: persistent CTAs take 3840-key tiles from an
-// atomic counter, rank digits with warp match.any, get each digit's global
+// atomic counter, rank digits with nine warp ballots per key (faster here than
+// match.any, which queues on the address-divergence unit), get each digit's global
 // offset from a precomputed histogram plus a decoupled look-back over tiles,
 // reorder the tile in shared memory and write it out coalesced.
 #include "s3r_internal.cuh"
@@ -58,7 +59,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_tmp 
   return wbase + incl - x;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
   __shared__ uint32_t s_keys[kSortTileKeys];
   __shared__ uint32_t s_vals[kSortTileKeys];
   __shared__ uint32_t s_cnt[kWarps][kRadix];   // per-warp digit counts -> exclusive offsets
@@ -101,7 +102,16 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(PassArgs a) {
       const int64_t idx = base + r * 32 + lane;
       const bool valid = idx < n;
       const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
-      const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : kRadix);
+      // peers with the same digit: the AND over the digit's nine bits (the
+      // ninth marks invalid slots) of the ballot or its complement
+      const uint32_t dv = valid ? d : kRadix;
+      uint32_t peers = 0xffffffffu;
+#pragma unroll
+      for (int b = 0; b < 9; ++b) {
+        const bool bit = (dv >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+      }
       uint32_t before = 0;
       if (valid) before = s_cnt[warp][d];
       rank[r] = before + __popc(peers & lt);
