@@ -419,10 +419,32 @@ def run_ours(args, rank, world, local):
             graph.replay()
             loss_host.copy_(loss, non_blocking=True)
         torch.cuda.synchronize()
+        # the next step's target image is copied host -> device on a second
+        # stream while the current step computes (double-buffered), then moved
+        # into the graph's input with a device copy; every step's H2D copy and
+        # its loss read-back lie between the two timing events
+        cs_ = torch.cuda.Stream()
+        staging = [torch.empty_like(target) for _ in range(2)]
+        ready = [torch.cuda.Event() for _ in range(2)]
+        consumed = [torch.cuda.Event() for _ in range(2)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
+        cs_.wait_event(e0)
+        with torch.cuda.stream(cs_):
+            staging[0].copy_(tgt_host, non_blocking=True)
+            ready[0].record(cs_)
         for i in range(args.steps):
-            target.copy_(tgt_host, non_blocking=True)
+            b = i & 1
+            if i + 1 < args.steps:
+                nb = (i + 1) & 1
+                with torch.cuda.stream(cs_):
+                    if i >= 1:
+                        cs_.wait_event(consumed[nb])
+                    staging[nb].copy_(tgt_host, non_blocking=True)
+                    ready[nb].record(cs_)
+            st.wait_event(ready[b])
+            target.copy_(staging[b], non_blocking=True)
+            consumed[b].record(st)
             iq.copy_(iq_host, non_blocking=True)
             it.copy_(it_host, non_blocking=True)
             graph.replay()
@@ -436,7 +458,9 @@ def run_ours(args, rank, world, local):
             ems = float(tt.item())
         bi = tgt_host.numel() * 4 + iq_host.numel() * 4 + it_host.numel() * 4
         e2e = {"value": round(world * n_views / (ems / 1e3), 3), "unit": "views/s",
-               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": 4, "ms_per_step": round(ems, 3)}
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": 4, "ms_per_step": round(ems, 3),
+               "how": "pinned host target image and poses copied every step, the image double-buffered "
+                      "on a copy stream so that it overlaps the previous step; loss read back every step"}
 
     # --- the optimiser step of training: fused Adam over every parameter array
     adam = None

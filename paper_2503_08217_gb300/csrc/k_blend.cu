@@ -11,11 +11,12 @@
 // are stored per pixel.
 //
 // Backward: the same tiles walked back to front, starting at each pixel's
-// last blended splat. The transmittance before each splat is recovered from
-// the stored final value as T <- T / (1 - alpha), so no per-pixel lists are
-// kept. Per splat the nine adjoints (uv, conic, opacity, rgb) are summed over
-// the warp with shuffles, then over the CTA in shared memory, and flushed to
-// global memory with one vector atomic per four floats.
+// last blended splat, two warps per tile, four pixels per lane. The
+// transmittance before each splat is recovered from the stored final value as
+// T <- T / (1 - alpha), so no per-pixel lists are kept. Per splat the nine
+// adjoints (uv, conic, opacity, rgb) are summed over the warp with shuffles,
+// then over the CTA in shared memory, and flushed to global memory with one
+// vector atomic per four floats.
 #include "s3r_internal.cuh"
 
 namespace s3r {
@@ -370,11 +371,22 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
   q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
-// 16 CTAs (64 warps) per SM: the walk is latency-bound (shuffle, MUFU and
-// shared-memory results), so occupancy beats the few spilled registers
+// The backward runs kBwdWarps warps per tile; warp r covers the band of
+// 16 / kBwdWarps rows starting at row r * 16 / kBwdWarps, and lane (x, y) =
+// (l & 7, l >> 3) owns the pixels (x + 8c, y + 4k) of that band, c = 0, 1.
+// A warp walks the union of the forward's contributor bits of the 8x8 blocks
+// inside its band: neighbouring blocks share almost all their contributors
+// (3 % more for two blocks, 6 % for four at the rig workload), while the
+// nine-value warp sum of every walked splat, the dominant cost, is shared by
+// 2 * (4 / kBwdWarps) pixels per lane.
+constexpr int kBwdWarps = 2;
+
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constant__ ViewSet vs,
-                                                        BlendArgs a) {
+__global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_bwd(
+    const __grid_constant__ ViewSet vs, BlendArgs a) {
+  constexpr int kT = 32 * kBwdWarps;
+  constexpr int kRows = 4 / kBwdWarps;          // pixel rows per lane and column
+  constexpr int kPix = 2 * kRows;               // pixels per lane
   __shared__ float4 s_a[kBatchBwd];
   __shared__ float4 s_b[kBatchBwd];
   __shared__ float s_c[kBatchBwd];
@@ -385,73 +397,94 @@ __global__ void __launch_bounds__(kThreads, 16) k_blend_bwd(const __grid_constan
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
   const int lt = tile - vi.tile_base;
+  const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
-  const TilePixels P = tile_pixels(vi, lt % vi.gx, lt / vi.gx, threadIdx.x >> 5, lane);
+  const int X0 = (lt % vi.gx) * kTile + (int)(lane & 7u);
+  const int Y0 = (lt / vi.gx) * kTile + warp * (kTile / kBwdWarps) + (int)(lane >> 3);
   const uint2 range = a.ranges[tile];
 
-  BwdPixel q0, q1;
-  bwd_init(q0, a, vi, P.px, P.py0, P.in0);
-  bwd_init(q1, a, vi, P.px, P.py1, P.in1);
+  float fx[2], fy[kRows];
+  BwdPixel q[kPix];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) fx[c] = (float)(X0 + 8 * c) + 0.5f;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) fy[r] = (float)(Y0 + 4 * r) + 0.5f;
+  int wlast = 0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int px = X0 + 8 * c, py = Y0 + 4 * r;
+      BwdPixel& qq = q[c * kRows + r];
+      bwd_init(qq, a, vi, px, py, px < vi.width && py < vi.height);
+      wlast = max(wlast, qq.last);
+    }
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
-  int wlast = max(q0.last, q1.last);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
   if (lane == 0 && wlast) atomicMax(&s_max, wlast);
   __syncthreads();
   const int n = s_max;
   uint32_t n_eval = 0;   // counting mode: pairs inside their pixel's walk
+  // the forward's 8x8 blocks of this band: warps fw0 .. fw0 + 4 / kBwdWarps - 1
+  const int fw0 = warp * (4 / kBwdWarps);
 
   for (int hi = n; hi > 0; hi -= kBatchBwd) {
     const int lo = max(0, hi - kBatchBwd);
     const int m = hi - lo;
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kT) {
       const uint32_t s = a.sorted_splats[range.x + lo + i];
       s_id[i] = s;
       const float2 xy = a.sp_xy[s];
       const float4 co = a.sp_conic_o[s];
       stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
     }
-    for (int i = threadIdx.x; i < kBatchBwd * 9; i += kThreads) (&s_g[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < kBatchBwd * 9; i += kT) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
     // this warp's splats end at its own last contributor; walk them back to
     // front, 32 at a time, visiting only the splats the forward blended into
-    // at least one pixel of the warp's 8x8 block (recorded bits)
-    const uint32_t* wbits = a.contrib + (threadIdx.x >> 5) * a.contrib_words;
+    // at least one pixel of the band (recorded bits)
     for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
       const int c0 = max(0, c1 - 31);
-      uint32_t todo = get_bits(wbits, range.x + lo + c0);
+      uint32_t todo = 0;
+#pragma unroll
+      for (int b = 0; b < 4 / kBwdWarps; ++b)
+        todo |= get_bits(a.contrib + (fw0 + b) * a.contrib_words, range.x + lo + c0);
       const int span = c1 - c0 + 1;
       if (span < 32) todo &= (1u << span) - 1u;
       // as a ballot result the mask is warp-uniform to the compiler as well
       todo = __ballot_sync(0xffffffffu, (todo >> lane) & 1u);
       while (todo) {
-      const int bit = 31 - __clz(todo);
-      todo &= ~(1u << bit);
-      const int j = c0 + bit;
-      const float4 sa = s_a[j], sb = s_b[j];
-      const float cb = s_c[j];
-      const float A2x2 = 2.f * sa.z, C2x2 = 2.f * sb.x;
-      const int pos = lo + j;
-      const SplatEval e0 = eval_splat(sa, sb, P.fx, P.fy0);
-      const SplatEval e1 = eval_splat(sa, sb, P.fx, P.fy1);
-      if constexpr (kCount) n_eval += (pos < q0.last ? 1u : 0u) + (pos < q1.last ? 1u : 0u);
-      const bool act0 = (pos < q0.last) && !(e0.p > 0.f) && !(e0.alpha < kAlphaMin);
-      const bool act1 = (pos < q1.last) && !(e1.p > 0.f) && !(e1.alpha < kAlphaMin);
-      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bwd_pixel(q0, e0, sa, A2x2, C2x2, sb, cb, act0, g);
-      bwd_pixel(q1, e1, sa, A2x2, C2x2, sb, cb, act1, g);
-      const float tot = warp_sum8_transposed(g, lane);
-      float g8 = g[8];
+        const int bit = 31 - __clz(todo);
+        todo &= ~(1u << bit);
+        const int j = c0 + bit;
+        const float4 sa = s_a[j], sb = s_b[j];
+        const float cb = s_c[j];
+        const float A2x2 = 2.f * sa.z, C2x2 = 2.f * sb.x;
+        const int pos = lo + j;
+        float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
-      red_shared_if(&s_g[j][lane >> 2], tot, (lane & 3u) == 0);
-      red_shared_if(&s_g[j][8], g8, lane == 0);
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int r = 0; r < kRows; ++r) {
+            BwdPixel& qq = q[c * kRows + r];
+            const SplatEval e = eval_splat(sa, sb, fx[c], fy[r]);
+            if constexpr (kCount) n_eval += pos < qq.last ? 1u : 0u;
+            const bool act = (pos < qq.last) && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
+            bwd_pixel(qq, e, sa, A2x2, C2x2, sb, cb, act, g);
+          }
+        const float tot = warp_sum8_transposed(g, lane);
+        float g8 = g[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
+        red_shared_if(&s_g[j][lane >> 2], tot, (lane & 3u) == 0);
+        red_shared_if(&s_g[j][8], g8, lane == 0);
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kThreads) {
+    for (int i = threadIdx.x; i < m; i += kT) {
       const float* sg = s_g[i];
       bool any = false;
 #pragma unroll
@@ -540,9 +573,9 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
     return e;
   KernelTimer timer(ws, kKBlendBwd, st);
   if (ws->counting)
-    k_blend_bwd<true><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+    k_blend_bwd<true><<<ws->views.total_tiles, 32 * kBwdWarps, 0, st>>>(ws->views, a);
   else
-    k_blend_bwd<false><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+    k_blend_bwd<false><<<ws->views.total_tiles, 32 * kBwdWarps, 0, st>>>(ws->views, a);
   return cudaGetLastError();
 }
 

@@ -510,7 +510,9 @@ def test_counting_mode_changes_no_result(built, tiny, tiny_vis):
     """The counting instantiations of the blend kernels give the same image
     and gradients as the timed ones, and their counts are consistent:
     evaluated <= walked pairs in the forward, the backward evaluates at most
-    the positions below each pixel's last contributor."""
+    the positions below each pixel's last contributor (it walks the union of
+    the forward's 8x8 contributor sets over its 16x8 band, so it may
+    evaluate pairs the forward's footprint test skipped)."""
     import gpu_helpers
     vis, _ = tiny_vis
     step = 6
@@ -531,4 +533,3 @@ def test_counting_mode_changes_no_result(built, tiny, tiny_vis):
     contrib = int(on["n_contrib"].astype(np.int64).sum())
     assert 0 < c["n_eval_bwd"] <= contrib <= c["n_blend_pairs"]
     assert 0 < c["n_eval_fwd"] <= c["n_blend_pairs"]
-    assert c["n_eval_bwd"] <= c["n_eval_fwd"]
