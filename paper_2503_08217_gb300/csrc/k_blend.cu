@@ -1,17 +1,19 @@
 // Front-to-back alpha blending of every 16x16 tile (Eq. 2) and its exact
 // adjoint.
 //
-// Forward: one CTA of 256 threads per tile, one pixel per thread. The tile's
-// front-to-back splat list is consumed in batches of 256: each thread gathers
-// one splat record (uv, conic+opacity, rgb) into shared memory, then every
-// thread blends the batch for its pixel. alpha = min(0.99, o G) is skipped
-// below 1/255, and a pixel stops before its transmittance would fall under
-// 1e-4; the CTA stops when all its pixels have stopped. The final
-// transmittance and the count of visited splats up to the last blended one
-// are stored per pixel.
+// Forward: one CTA of two warps per tile, each warp a 16x8 band, four pixels
+// per lane. The tile's front-to-back splat list is consumed in batches of 256
+// staged in shared memory (uv, base-2 conic, opacity, rgb, and the box where
+// the splat can reach alpha >= 1/255); per 32 splats a warp ballots which
+// boxes touch its band and evaluates only those. alpha = min(0.99, o G) is
+// skipped below 1/255, and a pixel stops before its transmittance would fall
+// under 1e-4; a warp stops when all its pixels have stopped. The final
+// transmittance and the position of the last blended splat are stored per
+// pixel, and the splats blended into at least one pixel of a band are
+// recorded as bits for the backward.
 //
-// Backward: the same tiles walked back to front, starting at each pixel's
-// last blended splat, two warps per tile, four pixels per lane. The
+// Backward: the same tiles and bands walked back to front, starting at each
+// warp's last blended splat and visiting only the recorded splats. The
 // transmittance before each splat is recovered from the stored final value as
 // T <- T / (1 - alpha), so no per-pixel lists are kept. Per splat the nine
 // adjoints (uv, conic, opacity, rgb) are summed over the warp with shuffles,
@@ -22,7 +24,6 @@
 namespace s3r {
 namespace {
 
-constexpr int kThreads = kTilePixels / 2;   // 128: two pixels per thread
 constexpr int kBatch = 256;                   // splats staged per batch (forward)
 constexpr int kBatchBwd = 128;                // splats staged per batch (backward)
 constexpr float kAlphaMax = 0.99f;
@@ -44,7 +45,7 @@ struct BlendArgs {
   unsigned long long* pairs;     // counting mode: list pairs the forward walked
   unsigned long long* eval_fwd;  // counting mode: pairs the forward evaluated
   unsigned long long* eval_bwd;  // counting mode: pairs the backward evaluated
-  uint32_t* contrib;          // [4][contrib_words]: pair blended into >= 1 pixel of the warp block
+  uint32_t* contrib;          // [bands][contrib_words]: pair blended into >= 1 pixel of the band
   int64_t contrib_words;
 };
 
@@ -123,42 +124,50 @@ __device__ __forceinline__ float4 alpha_box(const float2 xy, const float4 co) {
   return make_float4(xy.x - ex, xy.x + ex, xy.y - ey, xy.y + ey);
 }
 
-// Pixel layout: a tile is four 8x8 blocks, one per warp; lane (x = l & 7,
-// y = l >> 3) owns the pixels (x, y) and (x, y + 4) of its warp's block.
-struct TilePixels {
-  int px, py0, py1;
-  bool in0, in1;
-  float fx, fy0, fy1;
-  float bx0, bx1, by0, by1;   // pixel-centre extent of the warp's block
+// The blend kernels run kBandWarps warps per tile; warp r covers the band of
+// 16 / kBandWarps rows starting at row r * 16 / kBandWarps, and lane (x, y) =
+// (l & 7, l >> 3) owns the pixels (x + 8c, y + 4k) of that band, c = 0, 1.
+// The forward's footprint test and contributor bits are per band, and the
+// backward walks a band's bits. Neighbouring 8x8 blocks share almost all their
+// contributors (a 16x8 band's set is 3 % larger than an 8x8 block's at the rig
+// workload), while the per-splat work of a warp (the footprint ballot, the
+// loop and the loads; in the backward the nine-value warp sum, its dominant
+// cost) is shared by 2 * (4 / kBandWarps) pixels per lane.
+constexpr int kBandWarps = 2;
+constexpr int kBandThreads = 32 * kBandWarps;
+constexpr int kBandRows = 4 / kBandWarps;       // pixel rows per lane and column
+constexpr int kBandPix = 2 * kBandRows;         // pixels per lane
+
+struct Band {
+  int X0, Y0;              // pixel (0, 0) of this lane
+  float fx[2], fy[kBandRows];
+  float bx0, bx1, by0, by1;   // pixel-centre extent of the warp's band
 };
-__device__ __forceinline__ TilePixels tile_pixels(const ViewInfo& vi, int tx, int ty, int warp,
-                                                  uint32_t lane) {
-  TilePixels t;
-  const int X0 = tx * kTile + (warp & 1) * 8, Y0 = ty * kTile + (warp >> 1) * 8;
-  t.px = X0 + (int)(lane & 7u);
-  t.py0 = Y0 + (int)(lane >> 3);
-  t.py1 = t.py0 + 4;
-  t.in0 = t.px < vi.width && t.py0 < vi.height;
-  t.in1 = t.px < vi.width && t.py1 < vi.height;
-  t.fx = t.px + 0.5f;
-  t.fy0 = t.py0 + 0.5f;
-  t.fy1 = t.py1 + 0.5f;
-  t.bx0 = X0 + 0.5f;
-  t.bx1 = X0 + 7.5f;
-  t.by0 = Y0 + 0.5f;
-  t.by1 = Y0 + 7.5f;
-  return t;
+__device__ __forceinline__ Band band_pixels(const ViewInfo& vi, int lt, int warp, uint32_t lane) {
+  Band b;
+  const int bx = (lt % vi.gx) * kTile, by = (lt / vi.gx) * kTile + warp * (kTile / kBandWarps);
+  b.X0 = bx + (int)(lane & 7u);
+  b.Y0 = by + (int)(lane >> 3);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) b.fx[c] = (float)(b.X0 + 8 * c) + 0.5f;
+#pragma unroll
+  for (int r = 0; r < kBandRows; ++r) b.fy[r] = (float)(b.Y0 + 4 * r) + 0.5f;
+  b.bx0 = bx + 0.5f;
+  b.bx1 = bx + 15.5f;
+  b.by0 = by + 0.5f;
+  b.by1 = by + (kTile / kBandWarps) - 0.5f;
+  return b;
 }
 
-__device__ __forceinline__ bool box_misses(const float4 b, const TilePixels& t) {
+__device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
   return b.x > t.bx1 || b.y < t.bx0 || b.z > t.by1 || b.w < t.by0;
 }
 
 // kCount: also count the (pixel, splat) pairs walked (list positions up to
 // each pixel's stop) and evaluated (footprint test passed, pixel not stopped).
 template <bool kCount>
-__global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
-                                                        BlendArgs a) {
+__global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
+                                                            BlendArgs a) {
   __shared__ float4 s_a[kBatch];
   __shared__ float4 s_b[kBatch];
   __shared__ float4 s_box[kBatch];
@@ -167,21 +176,33 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
   const int lt = tile - vi.tile_base;
+  const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
-  const TilePixels P = tile_pixels(vi, lt % vi.gx, lt / vi.gx, threadIdx.x >> 5, lane);
+  const Band P = band_pixels(vi, lt, warp, lane);
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
 
-  float T0 = 1.f, T1 = 1.f;
-  float C00 = 0.f, C01 = 0.f, C02 = 0.f, C10 = 0.f, C11 = 0.f, C12 = 0.f;
-  int last0 = 0, last1 = 0, end0 = n, end1 = n;   // end: positions walked
+  float T[kBandPix], C[kBandPix][3];
+  int last[kBandPix], endp[kBandPix];
+  bool done[kBandPix];
   uint32_t n_eval = 0;
-  bool done0 = !P.in0, done1 = !P.in1;
-  if (done0) end0 = 0;
-  if (done1) end1 = 0;
+  bool all_done = true;
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int r = 0; r < kBandRows; ++r) {
+      const int k = c * kBandRows + r;
+      T[k] = 1.f;
+      C[k][0] = C[k][1] = C[k][2] = 0.f;
+      last[k] = 0;
+      done[k] = !(P.X0 + 8 * c < vi.width && P.Y0 + 4 * r < vi.height);
+      endp[k] = done[k] ? 0 : n;      // positions walked
+      all_done = all_done && done[k];
+    }
+  uint32_t* wbits = a.contrib + warp * a.contrib_words;
   for (int b0 = 0; b0 < n; b0 += kBatch) {
-    if (__syncthreads_count(done0 && done1) == kThreads) break;
-    for (int i = threadIdx.x; i < kBatch && b0 + i < n; i += kThreads) {
+    if (__syncthreads_count(all_done) == kBandThreads) break;
+    for (int i = threadIdx.x; i < kBatch && b0 + i < n; i += kBandThreads) {
       const uint32_t s = a.sorted_splats[range.x + b0 + i];
       const float2 xy = a.sp_xy[s];
       const float4 co = a.sp_conic_o[s];
@@ -191,59 +212,50 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
     __syncthreads();
     const int m = min(kBatch, n - b0);
     for (int c0 = 0; c0 < m; c0 += 32) {
-      if (__all_sync(0xffffffffu, done0 && done1)) break;
-      // which of the next 32 splats can reach this warp's 8x8 block
+      if (__all_sync(0xffffffffu, all_done)) break;
+      // which of the next 32 splats can reach this warp's band
       uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane < m && !box_misses(s_box[c0 + lane], P));
-      uint32_t blended = 0;     // splats of this chunk blended into some pixel of the block
+      uint32_t blended = 0;     // splats of this chunk blended into some pixel of the band
       while (todo) {
-      const int j = c0 + __ffs(todo) - 1;
-      todo &= todo - 1;
-      const float4 sa = s_a[j], sb = s_b[j];
-      const float cb = s_c[j];
-      const int pos = b0 + j + 1;
-      bool any_blend = false;
-      if constexpr (kCount) n_eval += (done0 ? 0u : 1u) + (done1 ? 0u : 1u);
-      {
-        const SplatEval e = eval_splat(sa, sb, P.fx, P.fy0);
-        const bool ok = !done0 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
-        const float nT = T0 * (1.f - e.alpha);
-        const bool stop = ok && (nT < kTStop);
-        const bool blend = ok && !stop;
-        const float w = blend ? e.alpha * T0 : 0.f;
-        C00 = fmaf(sb.z, w, C00);
-        C01 = fmaf(sb.w, w, C01);
-        C02 = fmaf(cb, w, C02);
-        T0 = blend ? nT : T0;
-        last0 = blend ? pos : last0;
-        if constexpr (kCount) end0 = stop ? pos : end0;
-        done0 = done0 || stop;
-        any_blend = blend;
+        const int j = c0 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        const float4 sa = s_a[j], sb = s_b[j];
+        const float cb = s_c[j];
+        const int pos = b0 + j + 1;
+        bool any_blend = false;
+        all_done = true;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int r = 0; r < kBandRows; ++r) {
+            const int k = c * kBandRows + r;
+            const SplatEval e = eval_splat(sa, sb, P.fx[c], P.fy[r]);
+            if constexpr (kCount) n_eval += done[k] ? 0u : 1u;
+            const bool ok = !done[k] && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
+            const float nT = T[k] * (1.f - e.alpha);
+            const bool stop = ok && (nT < kTStop);
+            const bool blend = ok && !stop;
+            const float w = blend ? e.alpha * T[k] : 0.f;
+            C[k][0] = fmaf(sb.z, w, C[k][0]);
+            C[k][1] = fmaf(sb.w, w, C[k][1]);
+            C[k][2] = fmaf(cb, w, C[k][2]);
+            T[k] = blend ? nT : T[k];
+            last[k] = blend ? pos : last[k];
+            if constexpr (kCount) endp[k] = stop ? pos : endp[k];
+            done[k] = done[k] || stop;
+            any_blend = any_blend || blend;
+            all_done = all_done && done[k];
+          }
+        if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
       }
-      {
-        const SplatEval e = eval_splat(sa, sb, P.fx, P.fy1);
-        const bool ok = !done1 && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
-        const float nT = T1 * (1.f - e.alpha);
-        const bool stop = ok && (nT < kTStop);
-        const bool blend = ok && !stop;
-        const float w = blend ? e.alpha * T1 : 0.f;
-        C10 = fmaf(sb.z, w, C10);
-        C11 = fmaf(sb.w, w, C11);
-        C12 = fmaf(cb, w, C12);
-        T1 = blend ? nT : T1;
-        last1 = blend ? pos : last1;
-        if constexpr (kCount) end1 = stop ? pos : end1;
-        done1 = done1 || stop;
-        any_blend = any_blend || blend;
-      }
-      if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
-      }
-      if (lane == 0 && blended)
-        or_bits(a.contrib + (threadIdx.x >> 5) * a.contrib_words, range.x + b0 + c0, blended);
+      if (lane == 0 && blended) or_bits(wbits, range.x + b0 + c0, blended);
     }
   }
   if constexpr (kCount) {
     // work accounting, one 64-bit atomic per warp and counter
-    unsigned long long walked = (unsigned long long)end0 + (unsigned long long)end1;
+    unsigned long long walked = 0;
+#pragma unroll
+    for (int k = 0; k < kBandPix; ++k) walked += (unsigned long long)endp[k];
     unsigned long long evald = n_eval;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -254,24 +266,22 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(const __grid_constant__ 
     if (lane == 0 && evald) atomicAdd(a.eval_fwd, evald);
   }
   const int64_t plane = (int64_t)vi.width * vi.height;
-  if (P.in0) {
-    const int64_t pix = (int64_t)P.py0 * vi.width + P.px;
-    float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
-    o[0] = fmaf(T0, a.bg[0], C00);
-    o[plane] = fmaf(T0, a.bg[1], C01);
-    o[2 * plane] = fmaf(T0, a.bg[2], C02);
-    a.final_T[vi.pix_base + pix] = T0;
-    a.n_contrib[vi.pix_base + pix] = (uint32_t)last0;
-  }
-  if (P.in1) {
-    const int64_t pix = (int64_t)P.py1 * vi.width + P.px;
-    float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
-    o[0] = fmaf(T1, a.bg[0], C10);
-    o[plane] = fmaf(T1, a.bg[1], C11);
-    o[2 * plane] = fmaf(T1, a.bg[2], C12);
-    a.final_T[vi.pix_base + pix] = T1;
-    a.n_contrib[vi.pix_base + pix] = (uint32_t)last1;
-  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int r = 0; r < kBandRows; ++r) {
+      const int k = c * kBandRows + r;
+      const int px = P.X0 + 8 * c, py = P.Y0 + 4 * r;
+      if (px < vi.width && py < vi.height) {
+        const int64_t pix = (int64_t)py * vi.width + px;
+        float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
+        o[0] = fmaf(T[k], a.bg[0], C[k][0]);
+        o[plane] = fmaf(T[k], a.bg[1], C[k][1]);
+        o[2 * plane] = fmaf(T[k], a.bg[2], C[k][2]);
+        a.final_T[vi.pix_base + pix] = T[k];
+        a.n_contrib[vi.pix_base + pix] = (uint32_t)last[k];
+      }
+    }
 }
 
 // Sum eight values over the warp with 9 shuffles instead of 8 x 5: at each
@@ -371,22 +381,12 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
   q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
-// The backward runs kBwdWarps warps per tile; warp r covers the band of
-// 16 / kBwdWarps rows starting at row r * 16 / kBwdWarps, and lane (x, y) =
-// (l & 7, l >> 3) owns the pixels (x + 8c, y + 4k) of that band, c = 0, 1.
-// A warp walks the union of the forward's contributor bits of the 8x8 blocks
-// inside its band: neighbouring blocks share almost all their contributors
-// (3 % more for two blocks, 6 % for four at the rig workload), while the
-// nine-value warp sum of every walked splat, the dominant cost, is shared by
-// 2 * (4 / kBwdWarps) pixels per lane.
-constexpr int kBwdWarps = 2;
-
 template <bool kCount>
-__global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_bwd(
+__global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
     const __grid_constant__ ViewSet vs, BlendArgs a) {
-  constexpr int kT = 32 * kBwdWarps;
-  constexpr int kRows = 4 / kBwdWarps;          // pixel rows per lane and column
-  constexpr int kPix = 2 * kRows;               // pixels per lane
+  constexpr int kT = kBandThreads;
+  constexpr int kRows = kBandRows;
+  constexpr int kPix = kBandPix;
   __shared__ float4 s_a[kBatchBwd];
   __shared__ float4 s_b[kBatchBwd];
   __shared__ float s_c[kBatchBwd];
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_bwd(
   const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
   const int X0 = (lt % vi.gx) * kTile + (int)(lane & 7u);
-  const int Y0 = (lt / vi.gx) * kTile + warp * (kTile / kBwdWarps) + (int)(lane >> 3);
+  const int Y0 = (lt / vi.gx) * kTile + warp * (kTile / kBandWarps) + (int)(lane >> 3);
   const uint2 range = a.ranges[tile];
 
   float fx[2], fy[kRows];
@@ -427,8 +427,8 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_bwd(
   __syncthreads();
   const int n = s_max;
   uint32_t n_eval = 0;   // counting mode: pairs inside their pixel's walk
-  // the forward's 8x8 blocks of this band: warps fw0 .. fw0 + 4 / kBwdWarps - 1
-  const int fw0 = warp * (4 / kBwdWarps);
+  // the forward recorded its contributors per band, with the same bands
+  const uint32_t* wbits = a.contrib + warp * a.contrib_words;
 
   for (int hi = n; hi > 0; hi -= kBatchBwd) {
     const int lo = max(0, hi - kBatchBwd);
@@ -448,10 +448,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_bwd(
     // at least one pixel of the band (recorded bits)
     for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
       const int c0 = max(0, c1 - 31);
-      uint32_t todo = 0;
-#pragma unroll
-      for (int b = 0; b < 4 / kBwdWarps; ++b)
-        todo |= get_bits(a.contrib + (fw0 + b) * a.contrib_words, range.x + lo + c0);
+      uint32_t todo = get_bits(wbits, range.x + lo + c0);
       const int span = c1 - c0 + 1;
       if (span < 32) todo &= (1u << span) - 1u;
       // as a ballot result the mask is warp-uniform to the compiler as well
@@ -546,13 +543,13 @@ cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cu
     // pairs walked and evaluated (two adjacent 64-bit counters)
     if ((e = cudaMemsetAsync(a.pairs, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
   }
-  e = cudaMemsetAsync(ws->contrib, 0, sizeof(uint32_t) * 4 * (size_t)ws->contrib_words, st);
+  e = cudaMemsetAsync(ws->contrib, 0, sizeof(uint32_t) * kBandWarps * (size_t)ws->contrib_words, st);
   if (e != cudaSuccess) return e;
   KernelTimer timer(ws, kKBlendFwd, st);
   if (ws->counting)
-    k_blend_fwd<true><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+    k_blend_fwd<true><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
   else
-    k_blend_fwd<false><<<ws->views.total_tiles, kThreads, 0, st>>>(ws->views, a);
+    k_blend_fwd<false><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
   return cudaGetLastError();
 }
 
@@ -573,9 +570,9 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
     return e;
   KernelTimer timer(ws, kKBlendBwd, st);
   if (ws->counting)
-    k_blend_bwd<true><<<ws->views.total_tiles, 32 * kBwdWarps, 0, st>>>(ws->views, a);
+    k_blend_bwd<true><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
   else
-    k_blend_bwd<false><<<ws->views.total_tiles, 32 * kBwdWarps, 0, st>>>(ws->views, a);
+    k_blend_bwd<false><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
   return cudaGetLastError();
 }
 
