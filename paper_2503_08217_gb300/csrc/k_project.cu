@@ -382,7 +382,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
           a.sp_rect[s] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16),
                                     (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
           a.sp_view[s] = (uint8_t)v | (moved ? kSplatMoved : (uint8_t)0);
-          const uint32_t key = __float_as_uint(p.z);
+          // a splat without tiles (an Eq. 7 splat moved out of the frustum)
+          // sorts after every real one (+inf), so that no expansion chunk
+          // meets it between splats that have pairs
+          const bool tiled = p.x1 > p.x0 && p.y1 > p.y0;
+          const uint32_t key = tiled ? __float_as_uint(p.z) : 0x7F800000u;
           a.depth_key[s] = key;
           atomicAdd(&s_hist[0][key & 0xffu], 1u);
           atomicAdd(&s_hist[1][(key >> 8) & 0xffu], 1u);

@@ -190,6 +190,7 @@ struct DupArgs {
   uint32_t* dup_val;
   uint32_t* dup_excl;    // [S+1] first output of each sorted splat
   uint4* dup_meta;       // [S] descriptors
+  uint32_t* dup_chunk;   // [chunks+1] splat holding each chunk's first output; last: final splat
   int64_t cap_splats, cap_dups;
   uint32_t* ctr;
   unsigned long long* lookback;
@@ -248,8 +249,20 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant_
     ex += s_base;
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
-      if (i0 + k < n) a.dup_excl[i0 + k] = ex;
+      if (i0 + k < n) {
+        a.dup_excl[i0 + k] = ex;
+        // every chunk boundary inside this splat's outputs [ex, ex + cnt)
+        // (below capacity) starts with this splat
+        const uint64_t e1 = min((uint64_t)ex + cnt[k], (uint64_t)a.cap_dups);
+        for (uint64_t c = ((uint64_t)ex + kExpChunk - 1) / kExpChunk; c * kExpChunk < e1; ++c)
+          a.dup_chunk[c] = (uint32_t)(i0 + k);
+      }
       ex += cnt[k];
+    }
+    if (tile == n_tiles - 1 && threadIdx.x == 0) {
+      // after the last chunk: the last splat (chunks end at an inclusive splat bound)
+      const uint64_t tot = min((uint64_t)s_base + total, (uint64_t)a.cap_dups);
+      a.dup_chunk[(tot + kExpChunk - 1) / kExpChunk] = (uint32_t)(n - 1);
     }
     __syncthreads();
   }
@@ -302,27 +315,16 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
     if (chunk >= n_chunks) break;
     const uint32_t O0 = (uint32_t)(chunk * kExpChunk);
     const uint32_t O1 = (uint32_t)min((int64_t)O0 + kExpChunk, total);   // exclusive
-    if (threadIdx.x < 32) {
-      // last q with excl[q] <= O0, and last q with excl[q] <= O1 - 1: 32-ary search
-      for (int which = 0; which < 2; ++which) {
-        const uint32_t target = which ? O1 - 1 : O0;
-        int64_t lo = 0, hi = n;          // excl[lo] <= target < excl[hi] (excl[n] = total)
-        while (hi - lo > 1) {
-          const int64_t step = (hi - lo + 31) / 32;
-          const int64_t probe = lo + (int64_t)(lane + 1) * step;
-          const bool le = probe < hi && a.dup_excl[probe] <= target;
-          const uint32_t m = __ballot_sync(0xffffffffu, le);
-          const int c = __popc(m);                      // probes that are <= target (a prefix)
-          const int64_t nlo = lo + (int64_t)c * step;
-          const int64_t nhi = min(hi, lo + (int64_t)(c + 1) * step);
-          lo = nlo;
-          hi = nhi;
-        }
-        if (lane == 0) (which ? s_q1 : s_q0) = (uint32_t)lo;
-      }
+    // the chunk's splats: from the one holding its first output to (at most)
+    // the one holding the next chunk's first output, from the scan's map
+    if (threadIdx.x == 0) {
+      s_q0 = a.dup_chunk[chunk];
+      s_q1 = a.dup_chunk[chunk + 1];
     }
     __syncthreads();
-    const int q0 = (int)s_q0, nq = (int)s_q1 - q0 + 1;
+    // at most one splat per output has outputs here, and splats without any
+    // sort after all of them, so kExpChunk bounds the count
+    const int q0 = (int)s_q0, nq = min((int)s_q1 - q0 + 1, kExpChunk);
     for (int i = threadIdx.x; i <= nq; i += kDupThreads) s_excl[i] = a.dup_excl[q0 + i];
     __syncthreads();
     // 16 consecutive outputs per thread
@@ -447,6 +449,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.dup_val = ws->dup_val[0];
   d.dup_excl = ws->dup_excl;
   d.dup_meta = reinterpret_cast<uint4*>(ws->dup_meta);
+  d.dup_chunk = ws->dup_chunk;
   d.cap_splats = ws->cap.max_splats;
   d.cap_dups = ws->cap.max_duplicates;
   d.ctr = ws->ctr;

@@ -74,7 +74,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->dup_chunk, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -196,6 +196,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
   S3R_ALLOC(ws->dup_excl, S + 1);
   S3R_ALLOC(ws->dup_meta, 4 * S);
+  S3R_ALLOC(ws->dup_chunk, K / 4096 + 2);
   ws->contrib_words = K / 32 + 2;
   S3R_ALLOC(ws->contrib, 4 * ws->contrib_words);
 #undef S3R_ALLOC

@@ -114,6 +114,7 @@ struct s3r_workspace {
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
+  uint32_t* dup_chunk;      // [K/4096 + 2] sorted splat holding the first pair of each 4096-pair chunk
   uint32_t* contrib;        // [4][K/32 + 2] bit per (warp block, sorted pair): blended in the forward
   int64_t contrib_words;    // words per warp block
   int64_t bytes;
