@@ -101,6 +101,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the slowest rank's time); the
+    identity on one rank. The reduction runs on `device` (the GPU under NCCL,
+    the CPU under gloo)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's
+    time (weak scaling, one timestep per rank)."""
+    return world * units_per_rank / (slowest_ms / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -321,17 +339,13 @@ def run_ours(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev_name)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev_name)
     r.ws.set_timing(False)
     r.sync_status()
     clock = clocks.summary()
     ms_per_step = total_ms / args.steps
-    views_s = world * n_views * args.steps / (total_ms / 1e3)
-    mpix_s = world * P * args.steps / (total_ms / 1e3) / 1e6
+    views_s = job_throughput(n_views * args.steps, world, total_ms)
+    mpix_s = job_throughput(P * args.steps, world, total_ms) / 1e6
 
     # --- kernel table and roofline of the dominant kernel
     keep = r.ws.debug("keep_mask", torch.int32, counts["n_selected"])
@@ -451,13 +465,9 @@ def run_ours(args, rank, world, local):
             loss_host.copy_(loss, non_blocking=True)
         e1.record(st)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            tt = torch.tensor([ems], device=dev_name)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            ems = float(tt.item())
+        ems = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev_name)
         bi = tgt_host.numel() * 4 + iq_host.numel() * 4 + it_host.numel() * 4
-        e2e = {"value": round(world * n_views / (ems / 1e3), 3), "unit": "views/s",
+        e2e = {"value": round(job_throughput(n_views, world, ems), 3), "unit": "views/s",
                "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": 4, "ms_per_step": round(ems, 3),
                "how": "pinned host target image and poses copied every step, the image double-buffered "
                       "on a copy stream so that it overlaps the previous step; loss read back every step"}
