@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--lod-dist", type=float, default=100.0)
     p.add_argument("--lod-offset", type=float, default=0.1)
     p.add_argument("--lod-seed", type=int, default=2025)
+    p.add_argument("--no-temporal", action="store_true",
+                   help="select every Gaussian (windows [-1, 1]) instead of the recorded windows")
     p.add_argument("--sweep", default=None, choices=("scale",),
                    help="scale: per-view fwd+bwd time of the large corridor stretched at constant "
                         "density, with the temporal record and with every Gaussian visible")
@@ -281,6 +283,8 @@ def run_ours(args, rank, world, local):
         r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
                      life, lod)
     binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    if args.no_temporal:
+        vis = all_vis
     torch.cuda.synchronize()
     sweep_s = time.time() - sweep_t0
     r.counts()  # clears any capacity flag raised while sweeping
@@ -514,6 +518,7 @@ def run_ours(args, rank, world, local):
             "config": {"workload": f"{args.workload}: {desc}", "gaussians": n, "instances": scene.n_inst,
                        "cameras": n_views, "pixels_per_view_batch": P, "timestep": k,
                        "sh_degree": scene.sh_degree, "lod_px": lod, "lod": lod_cfg,
+                       "temporal_selection": not args.no_temporal,
                        "l2": "flushed (512 MiB write) between timed steps, outside the timed events",
                        "graph": "whole step captured as one CUDA graph",
                        "parallelism": f"replicas x{world}, one timestep per rank, no collective"},

@@ -336,14 +336,16 @@ struct BwdPixel {
   int last;
 };
 
-// One splat's contribution to the adjoints at one pixel (reverse order),
-// accumulated into g[0..8] in scaled form (the constant factors ln 2, -1/2 and
-// -1 of the conic and position terms are applied once per splat when the
-// block's sums are flushed); updates the pixel's transmittance and Bd only
-// where the splat was blended in the forward.
-__device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sa,
-                                          float A2x2, float C2x2, const float4 sb, float cb,
-                                          bool act, float g[9]) {
+// One splat's contribution to the adjoints at one pixel (reverse order);
+// updates the pixel's transmittance and Bd only where the splat was blended in
+// the forward. The per-pixel part of the sums goes to g[4..8]; dL/d(power) of
+// the pixel is returned in dpow for the per-column sums of the caller (the
+// pixels of a column share dx). The sums are kept in moment form,
+//   g0 = sum dpow dx, g1 = sum dpow dy, g2 = sum dpow dx^2, g3 = sum dpow dx dy,
+//   g4 = sum dpow dy^2, g5 = sum dL/dopacity, g6..8 = sum w dL/dC,
+// and turned into the adjoints of (u, v, conic) once per splat at the flush.
+__device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sb,
+                                          float cb, bool act, float g[9], float& dpow) {
   const float inv = rcp_approx(1.f - e.alpha);
   q.T = act ? q.T * inv : q.T;
   const float cd = fmaf(sb.z, q.d0, fmaf(sb.w, q.d1, cb * q.d2));
@@ -352,13 +354,8 @@ __device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const
   q.Bd = fmaf(cd, w, q.Bd);
   const bool live = act && !(e.raw > kAlphaMax);         // alpha = 0.99 is constant
   const float gd = (live ? e.G : 0.f) * dalpha;           // dL/dopacity
-  const float dpow = sb.y * gd;                           // dL/d(power), natural units
-  const float t = dpow * e.dx, u = dpow * e.dy;
-  g[0] = fmaf(A2x2, t, fmaf(sa.w, u, g[0]));              // x ln 2     -> d/du
-  g[1] = fmaf(sa.w, t, fmaf(C2x2, u, g[1]));              // x ln 2     -> d/dv
-  g[2] = fmaf(t, e.dx, g[2]);                             // x -1/2     -> d/dA
-  g[3] = fmaf(t, e.dy, g[3]);                             // x -1       -> d/dB
-  g[4] = fmaf(u, e.dy, g[4]);                             // x -1/2     -> d/dC
+  dpow = sb.y * gd;                                       // dL/d(power), natural units
+  g[4] = fmaf(dpow * e.dy, e.dy, g[4]);
   g[5] += gd;
   g[6] = fmaf(w, q.d0, g[6]);                             // d/drgb
   g[7] = fmaf(w, q.d1, g[7]);
@@ -459,19 +456,30 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
         const int j = c0 + bit;
         const float4 sa = s_a[j], sb = s_b[j];
         const float cb = s_c[j];
-        const float A2x2 = 2.f * sa.z, C2x2 = 2.f * sb.x;
         const int pos = lo + j;
         float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < 2; ++c) {
+          float D = 0.f, E = 0.f;     // sum over the column of dpow and dpow * dy
+          float dx = 0.f;
 #pragma unroll
           for (int r = 0; r < kRows; ++r) {
             BwdPixel& qq = q[c * kRows + r];
             const SplatEval e = eval_splat(sa, sb, fx[c], fy[r]);
             if constexpr (kCount) n_eval += pos < qq.last ? 1u : 0u;
             const bool act = (pos < qq.last) && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
-            bwd_pixel(qq, e, sa, A2x2, C2x2, sb, cb, act, g);
+            float dpow;
+            bwd_pixel(qq, e, sb, cb, act, g, dpow);
+            D += dpow;
+            E = fmaf(dpow, e.dy, E);
+            dx = e.dx;
           }
+          const float t = dx * D;
+          g[0] += t;
+          g[1] += E;
+          g[2] = fmaf(t, dx, g[2]);
+          g[3] = fmaf(dx, E, g[3]);
+        }
         const float tot = warp_sum8_transposed(g, lane);
         float g8 = g[8];
 #pragma unroll
@@ -488,7 +496,12 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
       for (int r = 0; r < 9; ++r) any |= sg[r] != 0.f;
       if (any) {
         float* dst = a.sp_grad + 12 * (size_t)s_id[i];
-        red_v4(dst, kLn2 * sg[0], kLn2 * sg[1], -0.5f * sg[2], -sg[3]);
+        // moments -> adjoints: power*log2(e) = dx (A2 dx + B2 dy) + C2 dy^2 with
+        // dx = u - px, so d/du = ln 2 (2 A2 g0 + B2 g1), d/dv = ln 2 (B2 g0 + 2 C2 g1)
+        const float A2 = s_a[i].z, B2 = s_a[i].w, C2 = s_b[i].x;
+        const float gu = kLn2 * fmaf(2.f * A2, sg[0], B2 * sg[1]);
+        const float gv = kLn2 * fmaf(B2, sg[0], 2.f * C2 * sg[1]);
+        red_v4(dst, gu, gv, -0.5f * sg[2], -sg[3]);
         red_v4(dst + 4, -0.5f * sg[4], sg[5], sg[6], sg[7]);
         atomicAdd(dst + 8, sg[8]);
       }
