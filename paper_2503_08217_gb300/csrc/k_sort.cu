@@ -99,24 +99,22 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
     }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      const int64_t idx = base + r * 32 + lane;
-      const bool valid = idx < n;
+      // peers with the same digit: the AND over the digit's eight bits of the
+      // ballot or its complement. Slots past the end hold key 0xffffffff
+      // (digit 255) and are counted with it: they are the tile's last slots,
+      // so they only follow the valid keys of that digit and are never written
       const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
-      // peers with the same digit: the AND over the digit's nine bits (the
-      // ninth marks invalid slots) of the ballot or its complement
-      const uint32_t dv = valid ? d : kRadix;
       uint32_t peers = 0xffffffffu;
 #pragma unroll
-      for (int b = 0; b < 9; ++b) {
-        const bool bit = (dv >> b) & 1u;
+      for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
         peers &= bit ? bal : ~bal;
       }
-      uint32_t before = 0;
-      if (valid) before = s_cnt[warp][d];
+      const uint32_t before = s_cnt[warp][d];
       rank[r] = before + __popc(peers & lt);
       __syncwarp();
-      if (valid && (peers & lt) == 0) s_cnt[warp][d] = before + __popc(peers);
+      if ((peers & lt) == 0) s_cnt[warp][d] = before + __popc(peers);
       __syncwarp();
     }
     __syncthreads();
