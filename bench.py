@@ -229,13 +229,16 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "zero_splat_grads": ("hbm", S * 48),
         "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + 2 * (geo + kk)) + S * 48),
         # FP32 operations per evaluated (pixel, splat) pair, counted in the code
-        # (one MUFU op besides): forward 18 (offset, quadratic form, opacity
-        # scale, alpha clamp, two tests, transmittance update and stop test,
-        # weight, three colour FMAs); backward 44 (the evaluation, reciprocal
-        # recovery of T, colour-behind dot products, dalpha, nine adjoint
-        # accumulations, and the ~9 additions per pair of the over-pixel sums)
-        "blend_fwd": ("alu", counts["n_eval_fwd"] * 18),
-        "blend_bwd": ("alu", counts["n_eval_bwd"] * 44),
+        # (MUFU ops besides). Forward 17: offset (1, the column's dx shared),
+        # quadratic form (5), opacity scale and alpha clamp (2), three tests,
+        # transmittance update (2), weight (1), three colour FMAs. Backward 42:
+        # the same evaluation and two tests (10), 1 - alpha, T recovery, the
+        # colour-behind dot product (3), dL/dalpha (2), weight and Bd update
+        # (2), the clamp test, dL/dopacity and dL/dpower (2), the moment sums
+        # (4.5 per pixel, column terms shared by its two rows), dL/dopacity and
+        # colour sums (4), and the 9 additions per pair of the sums over pixels
+        "blend_fwd": ("alu", counts["n_eval_fwd"] * 17),
+        "blend_bwd": ("alu", counts["n_eval_bwd"] * 42),
     }
     for p in range(tile_passes):
         m[f"sort_tile_pass{p}"] = ("hbm", K * 16)

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           B[3 * r + c] = fmaf(A[4 * r], RS[c], fmaf(A[4 * r + 1], RS[3 + c], A[4 * r + 2] * RS[6 + c]));
-      const float iz = 1.f / z;
+      const float iz = rcp_fast(z);
       const float rx = x * iz, ry = y * iz;
       const bool clx = rx < -vi.limx || rx > vi.limx;
       const bool cly = ry < -vi.limy || ry > vi.limy;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       const float sb = fmaf(C0[0], C1[0], fmaf(C0[1], C1[1], C0[2] * C1[2]));
       const float scc = fmaf(C1[0], C1[0], fmaf(C1[1], C1[1], C1[2] * C1[2]));
       const float ad = sa + kDilation, cd = scc + kDilation;
-      const float idet = 1.f / (ad * cd - sb * sb);
+      const float idet = rcp_fast(ad * cd - sb * sb);
       const float qa = cd * idet, qb = -sb * idet, qc = ad * idet;
 
       float dA[9], db[3], dp[3] = {0.f, 0.f, 0.f};

@@ -267,6 +267,7 @@ s3r_status s3r_project(s3r_workspace* ws, const s3r_scene* scene, const s3r_pose
     vi.near_z = c.near_z > 0.f ? c.near_z : 0.2f;
     vi.limx = 1.3f * (0.5f * (float)c.width / c.fx);
     vi.limy = 1.3f * (0.5f * (float)c.height / c.fy);
+    vi.jc = c.fx * c.fx * (1.f + vi.limx * vi.limx) + c.fy * c.fy * (1.f + vi.limy * vi.limy);
     for (int i = 0; i < 12; ++i) vi.V[i] = c.world_to_cam[i];
     tiles += (int64_t)vi.gx * vi.gy;
     pixels += (int64_t)c.width * c.height;

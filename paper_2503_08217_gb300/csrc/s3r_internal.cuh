@@ -51,6 +51,7 @@ struct ViewInfo {
   int32_t width, height, gx, gy;
   int32_t tile_base, pix_base;
   float fx, fy, cx, cy, near_z, limx, limy;
+  float jc;                   // fx^2 (1 + limx^2) + fy^2 (1 + limy^2): bounds |J|_F^2 z^2
   float V[12];
 };
 

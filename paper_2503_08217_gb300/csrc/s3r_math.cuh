@@ -22,6 +22,22 @@ struct __align__(16) InstMat {
   float pad;
 };
 
+// Single-instruction approximations (hardware reciprocal and square root,
+// within a few ulp): the projection's decisions that they could move
+// (near plane, rectangle edges, radius ceiling, LOD threshold) are compared
+// with margins far wider than that, and the forward, the splat writer and the
+// backward all call these same functions.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 constexpr float kDilation = 0.3f;
 constexpr float kMinEig = 0.1f;
 
@@ -100,7 +116,7 @@ __device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       B[3 * r + c] = fmaf(M.m[4 * r], RS[c], fmaf(M.m[4 * r + 1], RS[3 + c], M.m[4 * r + 2] * RS[6 + c]));
-  const float iz = 1.f / o.z;
+  const float iz = rcp_fast(o.z);
   const float rx = o.x * iz, ry = o.y * iz;
   const float txr = fminf(vi.limx, fmaxf(-vi.limx, rx));
   const float tyr = fminf(vi.limy, fmaxf(-vi.limy, ry));
@@ -118,17 +134,17 @@ __device__ __forceinline__ Proj2D project_view(const InstMat& M, const float mu[
   const float c = fmaf(C1[0], C1[0], fmaf(C1[1], C1[1], C1[2] * C1[2]));
   const float mid0 = 0.5f * (a + c);
   const float det0 = a * c - b * b;
-  o.sigma = sqrtf(mid0 + sqrtf(fmaxf(0.f, mid0 * mid0 - det0)));
+  o.sigma = sqrt_fast(mid0 + sqrt_fast(fmaxf(0.f, mid0 * mid0 - det0)));
   const float ad = a + kDilation, cd = c + kDilation;
   const float det = ad * cd - b * b;
   if (!(det > 0.f)) return o;
-  const float idet = 1.f / det;
+  const float idet = rcp_fast(det);
   o.ca = cd * idet;
   o.cb = -b * idet;
   o.cc = ad * idet;
   const float mid = 0.5f * (ad + cd);
-  const float lam = mid + sqrtf(fmaxf(kMinEig, mid * mid - det));
-  o.radius = ceilf(3.f * sqrtf(lam));
+  const float lam = mid + sqrt_fast(fmaxf(kMinEig, mid * mid - det));
+  o.radius = ceilf(3.f * sqrt_fast(lam));
   o.u = fmaf(vi.fx, rx, vi.cx);
   o.v = fmaf(vi.fy, ry, vi.cy);
   const float inv_tile = 1.f / kTile;
@@ -153,10 +169,9 @@ __device__ __forceinline__ bool may_touch_view(const InstMat& M, const float mu[
   rel_pos(M, mu, d);
   cam_pos(M, d, x, y, z);
   if (!(z > vi.near_z)) return false;
-  const float iz = 1.f / z;
+  const float iz = rcp_fast(z);
   const float u = fmaf(vi.fx, x * iz, vi.cx), v = fmaf(vi.fy, y * iz, vi.cy);
-  const float jc = vi.fx * vi.fx * fmaf(vi.limx, vi.limx, 1.f) + vi.fy * vi.fy * fmaf(vi.limy, vi.limy, 1.f);
-  const float rb = fmaf(3.03f, sqrtf(fmaf(jc * M.a_frob2 * smax2, iz * iz, 0.93f)), 3.f);
+  const float rb = fmaf(3.03f, sqrt_fast(fmaf(vi.jc * M.a_frob2 * smax2, iz * iz, 0.93f)), 3.f);
   return !(u + rb < 0.f || u - rb > (float)(vi.gx * kTile) || v + rb < 0.f ||
            v - rb > (float)(vi.gy * kTile));
 }
