@@ -32,6 +32,7 @@ constexpr float kTStop = 1e-4f;
 
 struct BlendArgs {
   const uint2* ranges;
+  const uint32_t* tile_order;
   const uint32_t* sorted_splats;
   const float2* sp_xy;
   const float4* sp_conic_o;
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
   __shared__ float4 s_b[kBatch];
   __shared__ float4 s_box[kBatch];
   __shared__ float s_c[kBatch];
-  const int tile = blockIdx.x;
+  const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
   const int lt = tile - vi.tile_base;
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
   __shared__ uint32_t s_id[kBatchBwd];
   __shared__ float s_g[kBatchBwd][9];
   __shared__ int s_max;
-  const int tile = blockIdx.x;
+  const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
   const int lt = tile - vi.tile_base;
@@ -528,6 +529,7 @@ __global__ void k_zero_grads(float4* g, const uint32_t* ctr, int64_t cap) {
 static BlendArgs make_args(s3r_workspace* ws) {
   BlendArgs a;
   a.ranges = ws->ranges;
+  a.tile_order = ws->tile_order;
   a.sorted_splats = ws->dup_val[ws->dup_final];
   a.sp_xy = ws->sp_xy;
   a.sp_conic_o = ws->sp_conic_o;

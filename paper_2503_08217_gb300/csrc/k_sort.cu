@@ -401,6 +401,39 @@ __global__ void __launch_bounds__(kRangeThreads) k_tile_ranges(const uint32_t* _
   }
 }
 
+// Blend schedule: the tiles in descending order of their pair count (by
+// power-of-two bucket, any order inside a bucket), so that the longest lists
+// start first and do not trail the launch. One CTA.
+constexpr int kOrderThreads = 1024;
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __restrict__ ranges,
+                                                              int tiles,
+                                                              uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_cnt[33];
+  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y - r.x;
+    atomicAdd(&s_cnt[len ? __clz(len) : 32], 1u);   // bucket 0 = longest
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = 0; b < 33; ++b) {
+      const uint32_t c = s_cnt[b];
+      s_cnt[b] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y - r.x;
+    order[atomicAdd(&s_cnt[len ? __clz(len) : 32], 1u)] = (uint32_t)t;
+  }
+}
+
 int per_sm_for(const void* fn, int threads) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0) != cudaSuccess ||
@@ -493,6 +526,11 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     KernelTimer timer(ws, kKTileRanges, st);
     k_tile_ranges<<<ws->num_sms * range_per_sm, kRangeThreads, 0, st>>>(
         ws->dup_key[ws->dup_final], ws->ctr, ws->cap.max_duplicates, ws->ranges);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    KernelTimer timer(ws, kKTileOrder, st);
+    k_tile_order<<<1, kOrderThreads, 0, st>>>(ws->ranges, ws->views.total_tiles, ws->tile_order);
   }
   return cudaGetLastError();
 }

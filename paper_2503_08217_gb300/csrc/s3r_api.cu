@@ -64,7 +64,7 @@ const char* const kKernelNames[kKCount] = {
     "begin", "temporal_compact", "compose", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
     "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd", "zero_splat_grads",
-    "blend_bwd", "project_bwd", "pose_chain"};
+    "blend_bwd", "project_bwd", "pose_chain", "tile_order"};
 
 void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
@@ -74,7 +74,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->dup_chunk, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->dup_chunk, ws->tile_order, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -189,6 +189,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->dup_val[0], K);
   S3R_ALLOC(ws->dup_val[1], K);
   S3R_ALLOC(ws->ranges, cap->max_tiles);
+  S3R_ALLOC(ws->tile_order, cap->max_tiles);
   S3R_ALLOC(ws->final_T, cap->max_pixels);
   S3R_ALLOC(ws->n_contrib, cap->max_pixels);
   S3R_ALLOC(ws->sp_grad, 12 * S);

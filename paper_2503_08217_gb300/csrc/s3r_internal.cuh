@@ -78,7 +78,7 @@ constexpr int kHistCount = 8;
 enum KernelId : int {
   kKBegin = 0, kKCompact, kKCompose, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
   kKTile0, kKTile1, kKTile2, kKTile3, kKTileRanges, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
-  kKProjectBwd, kKPoseChain, kKCount
+  kKProjectBwd, kKPoseChain, kKTileOrder, kKCount
 };
 
 }  // namespace s3r
@@ -108,6 +108,7 @@ struct s3r_workspace {
   uint32_t* dup_key[2];     // [K]
   uint32_t* dup_val[2];     // [K]
   uint2* ranges;            // [tiles]
+  uint32_t* tile_order;     // [tiles] tiles by descending pair count (power-of-two buckets)
   float* final_T;           // [P]
   uint32_t* n_contrib;      // [P]
   float* sp_grad;           // [S*12]
