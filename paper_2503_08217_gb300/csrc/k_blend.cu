@@ -558,7 +558,7 @@ cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cu
     // pairs walked and evaluated (two adjacent 64-bit counters)
     if ((e = cudaMemsetAsync(a.pairs, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
   }
-  e = cudaMemsetAsync(ws->contrib, 0, sizeof(uint32_t) * kBandWarps * (size_t)ws->contrib_words, st);
+  e = launch_zero(ws->contrib, kBandWarps * ws->contrib_words, st);
   if (e != cudaSuccess) return e;
   KernelTimer timer(ws, kKBlendFwd, st);
   if (ws->counting)

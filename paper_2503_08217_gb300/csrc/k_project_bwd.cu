@@ -517,7 +517,7 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.g = *g;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
   const int nk = ws->n_inst + 1;
-  cudaError_t e = cudaMemsetAsync(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)ws->n_views * nk, st);
+  cudaError_t e = launch_zero(ws->pose_dM, 12 * (int64_t)ws->n_views * nk, st);
   if (e != cudaSuccess) return e;
   switch (sc->sh_degree) {
     case 0: e = launch_deg<0>(ws, a, st); break;

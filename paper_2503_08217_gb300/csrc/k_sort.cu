@@ -517,9 +517,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   }
   ws->dup_final = ws->tile_passes & 1;
   // ranges of the tiles present in the sorted pairs; the rest stay [0, 0)
-  if ((e = cudaMemsetAsync(ws->ranges, 0, sizeof(uint2) * (size_t)ws->views.total_tiles, st)) !=
-      cudaSuccess)
-    return e;
+  if ((e = launch_zero(ws->ranges, 2 * (int64_t)ws->views.total_tiles, st)) != cudaSuccess) return e;
   {
     static thread_local int range_per_sm = 0;
     if (!range_per_sm) range_per_sm = per_sm_for((const void*)k_tile_ranges, kRangeThreads);

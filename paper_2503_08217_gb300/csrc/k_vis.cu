@@ -129,6 +129,27 @@ cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1,
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void k_zero(uint4* p4, int64_t n4, uint32_t* tail, int tail_words) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p4[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (blockIdx.x == 0 && (int)threadIdx.x < tail_words) tail[threadIdx.x] = 0u;
+}
+}  // namespace
+
+cudaError_t launch_zero(void* p, int64_t words, cudaStream_t st) {
+  if (words <= 0) return cudaSuccess;
+  const int64_t n4 = words / 4;
+  int64_t blocks = (n4 + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_zero<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<uint4*>(p), n4,
+                                           reinterpret_cast<uint32_t*>(p) + 4 * n4,
+                                           (int)(words - 4 * n4));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
                            float* loss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

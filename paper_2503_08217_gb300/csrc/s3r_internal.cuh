@@ -180,6 +180,10 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
                                const s3r_grads* g, cudaStream_t st);
 cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, cudaStream_t st);
+// Zero `words` 32-bit words at a 16-byte aligned device address with a
+// kernel (no copy-engine memset: a captured step then overlaps host-to-device
+// copies on another stream).
+cudaError_t launch_zero(void* p, int64_t words, cudaStream_t st);
 cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
                            float* loss, cudaStream_t st);
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
