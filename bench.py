@@ -220,10 +220,14 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "sort_depth_pass1": ("hbm", S * 16),
         "sort_depth_pass2": ("hbm", S * 16),
         "sort_depth_pass3": ("hbm", S * 16),
-        # duplication: the scan reads each sorted splat's id, rect and view and
-        # writes its offset and descriptor; the expansion writes the pairs
-        "duplicate": ("hbm", S * (4 + 8 + 1) + S * (4 + 16)),
-        "duplicate_expand": ("hbm", S * (4 + 16) + K * 8),   # + tile-digit histograms (on chip)
+        # duplication: per splat, its (u, v), conic, rect and view in, its
+        # 32-byte tile record out (row-table entries beyond three rows not
+        # counted); the scan reads each sorted splat's id and record and
+        # writes its offset and the record in depth order; the expansion reads
+        # offsets and records and writes the pairs
+        "splat_tiles": ("hbm", S * (8 + 16 + 8 + 1) + S * 32),
+        "duplicate": ("hbm", S * (4 + 32) + S * (4 + 32)),
+        "duplicate_expand": ("hbm", S * (4 + 32) + K * 8),   # + tile-digit histograms (on chip)
         # boundary detection: the sorted pair keys in, [start, end) per tile out
         "tile_ranges": ("hbm", K * 4 + tiles * 8),
         "zero_splat_grads": ("hbm", S * 48),

@@ -66,7 +66,7 @@ class Capacity(ctypes.Structure):
     _fields_ = [("max_gaussians", ctypes.c_int64), ("max_splats", ctypes.c_int64),
                 ("max_duplicates", ctypes.c_int64), ("max_views", ctypes.c_int32),
                 ("max_instances", ctypes.c_int32), ("max_tiles", ctypes.c_int64),
-                ("max_pixels", ctypes.c_int64)]
+                ("max_pixels", ctypes.c_int64), ("max_rows", ctypes.c_int64)]
 
 
 class AdamTensor(ctypes.Structure):
@@ -191,11 +191,11 @@ class Workspace:
 
     def __init__(self, *, max_gaussians: int, max_splats: int, max_duplicates: int,
                  max_views: int, max_instances: int, max_tiles: int, max_pixels: int,
-                 device: int | None = None):
+                 max_rows: int = 0, device: int | None = None):
         L = load()
         self.device = torch.cuda.current_device() if device is None else int(device)
         cap = Capacity(max_gaussians, max_splats, max_duplicates, max_views, max_instances,
-                       max_tiles, max_pixels)
+                       max_tiles, max_pixels, max_rows)
         self.capacity = cap
         h = ctypes.c_void_p()
         _check(L.s3r_workspace_create(ctypes.byref(cap), self.device, ctypes.byref(h)))

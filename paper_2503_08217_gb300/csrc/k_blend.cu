@@ -4,8 +4,9 @@
 // Forward: one CTA of two warps per tile, each warp a 16x8 band, four pixels
 // per lane. The tile's front-to-back splat list is consumed in batches of 256
 // staged in shared memory (uv, base-2 conic, opacity, rgb, and the box where
-// the splat can reach alpha >= 1/255); per 32 splats a warp ballots which
-// boxes touch its band and evaluates only those. alpha = min(0.99, o G) is
+// the splat can reach alpha >= 1/255); per 32 splats a warp ballots which of
+// them can reach alpha >= 1/255 somewhere in its band (box, then the exact
+// ellipse-rectangle test) and evaluates only those. alpha = min(0.99, o G) is
 // skipped below 1/255, and a pixel stops before its transmittance would fall
 // under 1e-4; a warp stops when all its pixels have stopped. The final
 // transmittance and the position of the last blended splat are stored per
@@ -17,8 +18,8 @@
 // transmittance before each splat is recovered from the stored final value as
 // T <- T / (1 - alpha), so no per-pixel lists are kept. Per splat the nine
 // adjoints (uv, conic, opacity, rgb) are summed over the warp with shuffles,
-// then over the CTA in shared memory, and flushed to global memory with one
-// vector atomic per four floats.
+// then over the CTA in shared memory (one shared atomic per splat and warp),
+// and flushed to global memory with one vector atomic per four floats.
 #include "s3r_internal.cuh"
 
 namespace s3r {
@@ -114,12 +115,14 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 a, const float4 b, 
 // Bounding box of the region where a staged splat can reach alpha >= 1/255:
 // the ellipse d^T Q d <= 2 ln(255 o) (Q the conic), grown by a small relative
 // and absolute margin so that FP32 rounding of the exact test can never fall
-// outside it. Empty (xmin = +inf) when o < 1/255.
+// outside it. Empty (xmin = +inf) when o < 1/255; unbounded for a splat too
+// anisotropic for that guarantee (the per-pixel test then decides alone).
 __device__ __forceinline__ float4 alpha_box(const float2 xy, const float4 co) {
   const float o = co.w;
   if (!(o * 255.f > 1.f)) return make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
+  const float det = conic_det_lower(co.x, co.y, co.z);
+  if (det < 0.f) return make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
   const float L2 = 2.f * __logf(255.f * o);
-  const float det = co.x * co.z - co.y * co.y;
   const float ex = sqrtf(fmaxf(L2 * co.z / det, 0.f)) * 1.002f + 0.02f;
   const float ey = sqrtf(fmaxf(L2 * co.x / det, 0.f)) * 1.002f + 0.02f;
   return make_float4(xy.x - ex, xy.x + ex, xy.y - ey, xy.y + ey);
@@ -158,6 +161,38 @@ __device__ __forceinline__ Band band_pixels(const ViewInfo& vi, int lt, int warp
   b.by0 = by + 0.5f;
   b.by1 = by + (kTile / kBandWarps) - 0.5f;
   return b;
+}
+
+// Whether a staged splat can reach alpha >= 1/255 at some pixel centre of the
+// band. The base-2 exponent p = dx (A2 dx + B2 dy) + C2 dy^2 (dx = u - px,
+// dy = v - py) is concave, so its maximum over the band's pixel-centre
+// rectangle is 0 if the centre lies inside and otherwise lies on an edge, at
+// the clamped stationary point of that edge (dy = -B2 X / (2 C2) on the edge
+// dx = X, dx = -B2 Y / (2 A2) on dy = Y). The splat passes if that maximum
+// reaches log2(1 / (255 o)) less a margin far above FP32 rounding, so that no
+// splat the per-pixel test would keep is dropped. Most splats are small and
+// anisotropic, and their bounding box touches many bands that the ellipse
+// itself misses.
+__device__ __forceinline__ bool ellipse_reaches(const float4 a, const float4 b, const Band& t) {
+  // the staged conic is (A, B, C) scaled by -log2(e) (A2 = -A/2, B2 = -B, C2 = -C/2)
+  if (conic_det_lower(-a.z, -0.5f * a.w, -b.x) < 0.f) return true;
+  const float dx0 = a.x - t.bx1, dx1 = a.x - t.bx0;
+  const float dy0 = a.y - t.by1, dy1 = a.y - t.by0;
+  const bool inside = (dx0 <= 0.f) & (dx1 >= 0.f) & (dy0 <= 0.f) & (dy1 >= 0.f);
+  const float A2 = a.z, B2 = a.w, C2 = b.x;
+  const float kx = -0.5f * B2 * rcp_approx(C2), ky = -0.5f * B2 * rcp_approx(A2);
+  float best = -INFINITY;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const float X = s ? dx1 : dx0;
+    const float dy = fminf(fmaxf(kx * X, dy0), dy1);
+    best = fmaxf(best, fmaf(X, fmaf(A2, X, B2 * dy), C2 * dy * dy));
+    const float Y = s ? dy1 : dy0;
+    const float dx = fminf(fmaxf(ky * Y, dx0), dx1);
+    best = fmaxf(best, fmaf(dx, fmaf(A2, dx, B2 * Y), C2 * Y * Y));
+  }
+  const float thr = -__log2f(255.f * b.y);
+  return inside | (best >= thr - (0.05f + 1e-3f * fabsf(thr)));
 }
 
 __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
@@ -214,8 +249,10 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
     const int m = min(kBatch, n - b0);
     for (int c0 = 0; c0 < m; c0 += 32) {
       if (__all_sync(0xffffffffu, all_done)) break;
-      // which of the next 32 splats can reach this warp's band
-      uint32_t todo = __ballot_sync(0xffffffffu, c0 + (int)lane < m && !box_misses(s_box[c0 + lane], P));
+      // which of the next 32 splats can reach alpha >= 1/255 in this warp's band
+      const int jl = c0 + (int)lane;
+      const bool reach = !box_misses(s_box[jl], P) & ellipse_reaches(s_a[jl], s_b[jl], P);
+      uint32_t todo = __ballot_sync(0xffffffffu, (jl < m) & reach);
       uint32_t blended = 0;     // splats of this chunk blended into some pixel of the band
       while (todo) {
         const int j = c0 + __ffs(todo) - 1;
@@ -236,11 +273,13 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
             const float nT = T[k] * (1.f - e.alpha);
             const bool stop = ok && (nT < kTStop);
             const bool blend = ok && !stop;
-            const float w = blend ? e.alpha * T[k] : 0.f;
+            // one select: T (1 - 0) = T exactly where the splat is not blended
+            const float ab = blend ? e.alpha : 0.f;
+            const float w = ab * T[k];
             C[k][0] = fmaf(sb.z, w, C[k][0]);
             C[k][1] = fmaf(sb.w, w, C[k][1]);
             C[k][2] = fmaf(cb, w, C[k][2]);
-            T[k] = blend ? nT : T[k];
+            T[k] = T[k] * (1.f - ab);
             last[k] = blend ? pos : last[k];
             if constexpr (kCount) endp[k] = stop ? pos : endp[k];
             done[k] = done[k] || stop;
@@ -285,6 +324,18 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
     }
 }
 
+// a ? x : y as one selp. Written out because the compiler turned the
+// lane-dependent selects of the warp sum below into divergent branches around
+// the shuffles (57 branch instructions per splat in the backward), which made
+// the sum several times dearer than its 14 shuffles.
+__device__ __forceinline__ float select_f(bool a, float x, float y) {
+  float r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\tselp.f32 %0, %1, %2, p;\n\t}"
+      : "=f"(r)
+      : "f"(x), "f"(y), "r"((int)a));
+  return r;
+}
+
 // Sum eight values over the warp with 9 shuffles instead of 8 x 5: at each
 // butterfly level every lane keeps half of its remaining values and sends the
 // other half to its partner. On return, lane l holds the warp total of value
@@ -294,31 +345,27 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], uint32_t
   float k4[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float send = b4 ? v[j] : v[j + 4];
-    const float keep = b4 ? v[j + 4] : v[j];
+    const float send = select_f(b4, v[j], v[j + 4]);
+    const float keep = select_f(b4, v[j + 4], v[j]);
     k4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
   float k2[2];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const float send = b3 ? k4[j] : k4[j + 2];
-    const float keep = b3 ? k4[j + 2] : k4[j];
+    const float send = select_f(b3, k4[j], k4[j + 2]);
+    const float keep = select_f(b3, k4[j + 2], k4[j]);
     k2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
-  const float send = b2 ? k2[0] : k2[1];
-  float k1 = (b2 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  const float send = select_f(b2, k2[0], k2[1]);
+  float k1 = select_f(b2, k2[1], k2[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
   k1 += __shfl_xor_sync(0xffffffffu, k1, 2);
   k1 += __shfl_xor_sync(0xffffffffu, k1, 1);
   return k1;
 }
 
-// red.shared.add.f32 executed only where `pred` holds, without a branch.
-__device__ __forceinline__ void red_shared_if(float* addr, float v, bool pred) {
+__device__ __forceinline__ void red_shared(float* addr, float v) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(addr);
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p red.shared.add.f32 [%0], %1;\n\t}" ::"r"(sa),
-      "f"(v), "r"((int)pred)
-      : "memory");
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(sa), "f"(v) : "memory");
 }
 
 __device__ __forceinline__ void red_v4(float* p, float x, float y, float z, float w) {
@@ -348,13 +395,13 @@ struct BwdPixel {
 __device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sb,
                                           float cb, bool act, float g[9], float& dpow) {
   const float inv = rcp_approx(1.f - e.alpha);
-  q.T = act ? q.T * inv : q.T;
+  q.T = select_f(act, q.T * inv, q.T);
   const float cd = fmaf(sb.z, q.d0, fmaf(sb.w, q.d1, cb * q.d2));
   const float dalpha = fmaf(q.T, cd, -q.Bd * inv);
-  const float w = act ? e.alpha * q.T : 0.f;
+  const float w = select_f(act, e.alpha * q.T, 0.f);
   q.Bd = fmaf(cd, w, q.Bd);
   const bool live = act && !(e.raw > kAlphaMax);         // alpha = 0.99 is constant
-  const float gd = (live ? e.G : 0.f) * dalpha;           // dL/dopacity
+  const float gd = select_f(live, e.G, 0.f) * dalpha;     // dL/dopacity
   dpow = sb.y * gd;                                       // dL/d(power), natural units
   g[4] = fmaf(dpow * e.dy, e.dy, g[4]);
   g[5] += gd;
@@ -390,6 +437,7 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
   __shared__ float s_c[kBatchBwd];
   __shared__ uint32_t s_id[kBatchBwd];
   __shared__ float s_g[kBatchBwd][9];
+  __shared__ float s_sink[kBandThreads];   // target of the lanes with no sum to add
   __shared__ int s_max;
   const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
   const int v = view_of_tile(vs, tile);
@@ -485,8 +533,12 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
         float g8 = g[8];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
-        red_shared_if(&s_g[j][lane >> 2], tot, (lane & 3u) == 0);
-        red_shared_if(&s_g[j][8], g8, lane == 0);
+        // one shared atomic per warp: lanes 4m add value m, lane 1 the ninth
+        // sum, the rest add to their own sink word. Predicated atomics compiled
+        // to divergent branches (two per splat).
+        const bool own = (lane & 3u) == 0;
+        float* dst = own ? &s_g[j][lane >> 2] : (lane == 1 ? &s_g[j][8] : &s_sink[threadIdx.x]);
+        red_shared(dst, select_f(own, tot, g8));
       }
     }
     __syncthreads();

@@ -160,23 +160,134 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
 // Expand depth-sorted splats into (view-tile id, splat) pairs, in two kernels
 // so that the work is balanced by OUTPUT count: the nearest splats come first
 // in depth order and may each cover hundreds of tiles.
-//  k_dup_scan:   per sorted splat, its tile count and a compact descriptor
-//                (splat id, first tile id, grid width | rect width << 16,
-//                1/width); a block scan + decoupled look-back over 1024-splat
-//                tiles gives every splat its first output position.
-//  k_dup_expand: persistent CTAs take fixed chunks of 4096 outputs; a warp
-//                finds the chunk's first splat by a 32-ary search of the
-//                offsets, each thread expands 16 consecutive outputs (binary
-//                search in shared memory, then an incremental cursor), the
-//                pairs are staged in shared memory and written coalesced. The
-//                tile id of output r of a splat of rectangle width w is
-//                first + (r / w) * gx + r % w, r / w from a float reciprocal
-//                with one integer correction step.
+//
+// A splat is listed in the tiles of its 3-sigma rectangle (the record's rect)
+// that its alpha >= 1/255 region reaches: the blend skips every pixel outside
+// that region, so the other tiles of the rectangle would only lengthen the
+// lists (they are 40-50 % of the rectangle's tiles on the rig workload). With
+// the conic q = A dx^2 + 2 B dx dy + C dy^2 the region is the ellipse q <= L,
+// L = 2 ln(255 o). A row of tiles is a strip of pixel-centre rows, and the
+// ellipse's extent in x within a strip is one interval: its left end
+//   x_l(dy) = (-B dy - sqrt(L A - det dy^2)) / A
+// is convex in dy with its minimum -sqrt(L C / det) (the ellipse's leftmost
+// point) at dy = s = B sqrt(L A / (det (det + B^2))); over a strip it is that
+// minimum if s lies in the strip, else the smaller value at the strip's ends.
+// The right end is the mirror image (-s, +sqrt(L C / det)). L is raised
+// (1.02 L + 0.1), det lowered by a bound on its rounding, the square roots and
+// the strip padded, so every interval only grows: a tile is dropped only when
+// none of its pixel centres can pass the blend's FP32 test. Splats too
+// anisotropic for that guarantee keep their whole rectangle. The square roots
+// and reciprocals are the hardware approximations (errors of about 1 ulp, far
+// inside the margins), deterministic like the rest of the arithmetic.
+//
+//  k_splat_tiles: per splat (by id, in any order), a 32-byte record: its
+//                tile count (one interval per row of its rectangle), the tile
+//                id of the rectangle's corner, grid and rectangle widths,
+//                rectangle height, and its rows: 4 bytes per row in a row
+//                table (offsets from a warp-aggregated bump counter), the
+//                first kInlineRows of them also in the record. A splat that no
+//                longer fits the table stores its region (32 bytes) instead,
+//                and the expansion recomputes its later rows from it with the
+//                same function. Outside the scan below, whose look-back chain
+//                would otherwise wait on the few splats with tens of rows.
+//  k_dup_scan:   per sorted splat, the count from its record and a copy of
+//                the record in depth order (the count replaced by the splat
+//                id), so that the expansion reads most splats' rows without a
+//                dependent load; a block scan + decoupled look-back over
+//                1024-splat tiles gives every splat its first output.
+//  k_dup_expand: persistent CTAs take fixed chunks of 4096 outputs; each
+//                thread expands 16 consecutive outputs (binary search of the
+//                chunk's splat offsets in shared memory, a walk over the
+//                splat's rows to the first one, then an incremental cursor
+//                over rows and splats); the pairs are staged in shared memory
+//                and written coalesced.
 constexpr int kDupThreads = 256;
 constexpr int kDupPer = 4;                            // splats per thread in the scan
 constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per scan tile
-constexpr int kExpItems = 16;                         // outputs per thread per chunk
-constexpr int kExpChunk = kDupThreads * kExpItems;    // 4096 outputs per chunk
+constexpr int kExpItems = 8;                          // outputs per thread per chunk
+constexpr int kExpChunk = kDupThreads * kExpItems;    // outputs per chunk
+static_assert(kExpChunk >= kDupChunkMin, "the chunk map is sized for chunks of kDupChunkMin");
+
+constexpr float kSpanPad = 0.05f;        // pixels, on the strips and the column bounds
+
+// The alpha >= 1/255 region of a splat in the frame of its rectangle's
+// top-left pixel corner. Stored as two float4: (u, v, B, 1/A), (L A, det, ye, xe).
+struct Region {
+  float u, v, B, inv_A;
+  float LA, det;        // det < 0: no usable bound, every tile of a row
+  float ye, xe;         // half-extents in y and x; ye < 0: reaches no pixel
+  float s;              // dy of the leftmost point (-s: the rightmost)
+};
+
+__device__ __forceinline__ void region_store(const Region& g, float4* dst) {
+  dst[0] = make_float4(g.u, g.v, g.B, g.inv_A);
+  dst[1] = make_float4(g.LA, g.det, g.ye, g.xe);
+}
+
+// The stationary point s from the stored fields, so that the scan and the
+// expansion derive it identically.
+__device__ __forceinline__ void region_finish(Region& g) {
+  g.s = (g.det > 0.f && g.ye > 0.f)
+            ? __fmul_rn(__fmul_rn(g.B, g.ye), approx_rcp(approx_sqrt(__fmaf_rn(g.B, g.B, g.det))))
+            : 0.f;
+}
+
+__device__ __forceinline__ Region region_load(const float4 a, const float4 b) {
+  Region g;
+  g.u = a.x; g.v = a.y; g.B = a.z; g.inv_A = a.w;
+  g.LA = b.x; g.det = b.y; g.ye = b.z; g.xe = b.w;
+  region_finish(g);
+  return g;
+}
+
+__device__ __forceinline__ Region region_of(const float2 xy, const float4 co, uint32_t x0,
+                                            uint32_t y0) {
+  const float A = co.x, B = co.y, C = co.z, o = co.w;
+  Region g;
+  g.u = __fsub_rn(xy.x, 16.f * (float)x0);
+  g.v = __fsub_rn(xy.y, 16.f * (float)y0);
+  g.B = B;
+  g.inv_A = A > 0.f ? approx_rcp(A) : 0.f;
+  g.det = conic_det_lower(A, B, C);
+  const float L = __fmaf_rn(2.04f, __logf(__fmul_rn(255.f, o)), 0.1f);   // 1.02 * 2 ln(255 o) + 0.1
+  g.LA = __fmul_rn(L, A);
+  g.ye = g.xe = 0.f;
+  if (g.det > 0.f) {
+    if (L > 0.f) {
+      g.ye = __fmaf_rn(approx_sqrt(__fmul_rn(g.LA, approx_rcp(g.det))), 1.00001f, kSpanPad);
+      g.xe = __fmaf_rn(approx_sqrt(__fmul_rn(__fmul_rn(L, C), approx_rcp(g.det))), 1.00001f, kSpanPad);
+    } else {
+      g.ye = -1.f;
+    }
+  }
+  region_finish(g);
+  return g;
+}
+
+// Columns [first, second) (relative to the rectangle, clamped to [0, w)) of
+// the tiles in row r of the rectangle that the region reaches.
+__device__ __forceinline__ uint2 row_span(const Region& g, uint32_t r, uint32_t w) {
+  if (!(g.det > 0.f)) return make_uint2(0u, w);
+  const float top = 16.f * (float)r;
+  const float lo = fmaxf(__fsub_rn(__fadd_rn(top, 0.5f - kSpanPad), g.v), -g.ye);
+  const float hi = fminf(__fsub_rn(__fadd_rn(top, 15.5f + kSpanPad), g.v), g.ye);
+  if (!(lo <= hi)) return make_uint2(0u, 0u);
+  const float pad = __fmul_rn(4e-6f, g.LA);
+  const float rl = approx_sqrt(__fadd_rn(fmaxf(__fmaf_rn(__fmul_rn(-g.det, lo), lo, g.LA), 0.f), pad));
+  const float rh = approx_sqrt(__fadd_rn(fmaxf(__fmaf_rn(__fmul_rn(-g.det, hi), hi, g.LA), 0.f), pad));
+  const float bl = __fmul_rn(-g.B, lo), bh = __fmul_rn(-g.B, hi);
+  float xl = __fmul_rn(fminf(__fsub_rn(bl, rl), __fsub_rn(bh, rh)), g.inv_A);
+  float xr = __fmul_rn(fmaxf(__fadd_rn(bl, rl), __fadd_rn(bh, rh)), g.inv_A);
+  if (lo <= g.s && g.s <= hi) xl = fminf(xl, -g.xe);
+  if (lo <= -g.s && -g.s <= hi) xr = fmaxf(xr, g.xe);
+  // tile c holds the pixel centres 16 c + 0.5 .. 16 c + 15.5
+  const float ca = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(g.u, xl), 15.5f + kSpanPad), 0.0625f));
+  const float cb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(g.u, xr), 0.5f - kSpanPad), 0.0625f)) + 1.f;
+  const float fw = (float)w;
+  const float a = ca > 0.f ? fminf(ca, fw) : 0.f;           // NaN: 0
+  const float b = cb < fw ? fmaxf(cb, 0.f) : fw;            // NaN: w
+  return a < b ? make_uint2((uint32_t)a, (uint32_t)b) : make_uint2(0u, 0u);
+}
 
 struct DupArgs {
   uint32_t* hist;        // tile-digit histograms of the radix passes that follow
@@ -184,18 +295,84 @@ struct DupArgs {
   const uint32_t* sorted_splats;
   const uint2* sp_rect;
   const uint8_t* sp_view;
+  const uint4* sp_tiles;       // [S][2] records of k_splat_tiles, by splat id
+  const uint32_t* row_spans;   // per row of a rectangle: first | end << 16 (columns)
+  const float4* sp_region;     // [S][2] region, by splat id, where sp_rowoff is kNoRows
   uint32_t* dup_key;
   uint32_t* dup_val;
   uint32_t* dup_excl;    // [S+1] first output of each sorted splat
-  uint4* dup_meta;       // [S] descriptors
+  uint4* dup_meta;       // [S][2] records in depth order: (splat, corner tile, gx | w << 16, h),
+                         // (first row-table entry or kNoRows, rows 0..2)
   uint32_t* dup_chunk;   // [chunks+1] splat holding each chunk's first output; last: final splat
   int64_t cap_splats, cap_dups;
   uint32_t* ctr;
   unsigned long long* lookback;
 };
 
-__global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant__ ViewSet vs,
-                                                          DupArgs a) {
+constexpr int kTilesThreads = 256;
+constexpr uint32_t kNoRows = 0xffffffffu;
+constexpr int kInlineRows = 3;
+
+struct TilesArgs {
+  const float2* xy;
+  const float4* co;
+  const uint2* rect;
+  const uint8_t* view;
+  uint32_t* ctr;
+  int64_t cap;
+  uint4* rec;
+  uint32_t* row_spans;
+  int64_t rows_cap;
+  float4* region;
+};
+
+__global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_constant__ ViewSet vs,
+                                                              TilesArgs a) {
+  const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap);
+  const uint32_t lane = lane_id();
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool live = i < n;
+    const uint2 rc = live ? a.rect[i] : make_uint2(0u, 0u);
+    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16;
+    const uint32_t w = (rc.y & 0xffffu) - x0, h = (rc.y >> 16) - y0;
+    // table entries for every row of the rectangle, one atomic per warp
+    const uint32_t need = (live && w != 0) ? h : 0u;
+    uint32_t incl = need;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    unsigned long long wbase = 0;
+    if (lane == 31 && incl)
+      wbase = atomicAdd(reinterpret_cast<unsigned long long*>(a.ctr + kCtrRows),
+                        (unsigned long long)incl);
+    wbase = __shfl_sync(0xffffffffu, wbase, 31);
+    if (!live) continue;
+    const uint64_t off = wbase + incl - need;
+    const bool table = off + need <= (uint64_t)a.rows_cap;
+    const Region g = region_of(a.xy[i], a.co[i], x0, y0);
+    uint32_t cnt = 0;
+    uint32_t head[kInlineRows] = {0u, 0u, 0u};
+    if (w != 0)
+      for (uint32_t r = 0; r < h; ++r) {
+        const uint2 c = row_span(g, r, w);
+        const uint32_t e = c.x | (c.y << 16);
+        cnt += c.y - c.x;
+        if (r < kInlineRows) head[r] = e;
+        if (table) a.row_spans[off + r] = e;
+      }
+    const ViewInfo& vi = vs.v[a.view[i] & 0x7f];   // bit 7: Eq. 7 moved
+    const uint32_t corner = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
+    a.rec[2 * i] = make_uint4(cnt, corner, (uint32_t)vi.gx | (w << 16), h);
+    a.rec[2 * i + 1] = make_uint4(table ? (uint32_t)off : kNoRows, head[0], head[1], head[2]);
+    if (!table) region_store(g, a.region + 2 * i);
+  }
+}
+
+__global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile, s_base;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
@@ -210,24 +387,19 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(const __grid_constant_
     uint32_t sp[kDupPer], cnt[kDupPer], run = 0;
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) sp[k] = i0 + k < n ? a.sorted_splats[i0 + k] : 0u;
-    uint2 rect[kDupPer];
-    int view[kDupPer];
+    uint4 r0[kDupPer], r1[kDupPer];
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
-      rect[k] = i0 + k < n ? a.sp_rect[sp[k]] : make_uint2(0u, 0u);
-      view[k] = i0 + k < n ? (a.sp_view[sp[k]] & 0x7f) : 0;   // bit 7: Eq. 7 moved
+      r0[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k]] : make_uint4(0u, 0u, 0u, 0u);
+      r1[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k] + 1] : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
-      const uint32_t x0 = rect[k].x & 0xffffu, y0 = rect[k].x >> 16;
-      const uint32_t w = (rect[k].y & 0xffffu) - x0, h = (rect[k].y >> 16) - y0;
-      cnt[k] = w * h;
+      cnt[k] = r0[k].x;
       run += cnt[k];
       if (i0 + k < n) {
-        const ViewInfo& vi = vs.v[view[k]];
-        const uint32_t first = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
-        a.dup_meta[i0 + k] = make_uint4(sp[k], first, (uint32_t)vi.gx | (w << 16),
-                                        __float_as_uint(w ? 1.f / (float)w : 1.f));
+        a.dup_meta[2 * (i0 + k)] = make_uint4(sp[k], r0[k].y, r0[k].z, r0[k].w);
+        a.dup_meta[2 * (i0 + k) + 1] = r1[k];
       }
     }
     uint32_t total;
@@ -295,6 +467,64 @@ struct DigitRuns {
   }
 };
 
+// Position in the expansion of one splat: row r of its rectangle, column c in
+// the row's interval [.., ce). Rows past the rectangle (an inconsistent count,
+// which the shared row function rules out) stay on its last row, so every key
+// is a tile of the splat's view.
+struct Cursor {
+  const uint32_t* row_spans;
+  const float4* region;
+  uint32_t sp, corner, gx, w, h, off;
+  uint32_t head[kInlineRows];
+  uint32_t r, c, ce, row_tile;
+  __device__ __forceinline__ void load(const uint4* m, const DupArgs& a) {
+    row_spans = a.row_spans;
+    region = a.sp_region;
+    const uint4 d = m[0], e = m[1];
+    sp = d.x;
+    corner = d.y;
+    gx = d.z & 0xffffu;
+    w = d.z >> 16;
+    h = d.w;
+    off = e.x;
+    head[0] = e.y;
+    head[1] = e.z;
+    head[2] = e.w;
+  }
+  // rows past the inline ones: the row table, or (where it had no room) the
+  // stored region through the same function that counted them
+  __device__ __forceinline__ uint32_t far_row(uint32_t row) const {
+    if (off != kNoRows) return row_spans[off + row];
+    const Region g = region_load(region[2 * (size_t)sp], region[2 * (size_t)sp + 1]);
+    const uint2 s = row_span(g, row, w);
+    return s.x | (s.y << 16);
+  }
+  __device__ __forceinline__ void set_row(uint32_t rr) {
+    r = rr;
+    const uint32_t row = min(r, h - 1u);
+    static_assert(kInlineRows == 3, "the selects below take rows 0..2 from registers");
+    const uint32_t e = row == 0 ? head[0] : row == 1 ? head[1] : row == 2 ? head[2] : far_row(row);
+    c = e & 0xffffu;
+    ce = e >> 16;
+    row_tile = corner + row * gx;
+  }
+  // the k-th output of the splat (k < its count)
+  __device__ __forceinline__ void seek(uint32_t k) {
+    set_row(0);
+    while (r + 1 < h && k >= ce - c) {
+      k -= ce - c;
+      set_row(r + 1);
+    }
+    c += min(k, ce > c ? ce - c - 1 : 0u);
+  }
+  __device__ __forceinline__ void next() {
+    if (++c < ce) return;
+    do {
+      set_row(r + 1);
+    } while (c >= ce && r + 1 < h);
+  }
+};
+
 __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
   __shared__ uint32_t s_excl[kExpChunk + 1];
   __shared__ uint32_t s_key[kExpChunk];
@@ -334,26 +564,26 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
         if (s_excl[mid] <= o0) lo = mid; else hi = mid;
       }
       int q = lo;
-      uint32_t q_end = s_excl[q + 1];
-      uint4 meta = a.dup_meta[q0 + q];
       const uint32_t oe = min(o0 + kExpItems, O1);
+      // cursor: splat q, its row r with columns [c, ce), tile id of column 0 of row r
+      Cursor cur;
+      cur.load(a.dup_meta + 2 * (q0 + q), a);
+      cur.seek(o0 - s_excl[q]);
+      uint32_t q_end = s_excl[q + 1];
       DigitRuns runs;
       runs.init();
       for (uint32_t o = o0; o < oe; ++o) {
         while (o >= q_end) {
           ++q;
           q_end = s_excl[q + 1];
-          meta = a.dup_meta[q0 + q];
+          cur.load(a.dup_meta + 2 * (q0 + q), a);
+          cur.seek(0);
         }
-        const uint32_t rr = o - s_excl[q];
-        const uint32_t w = meta.z >> 16, gx = meta.z & 0xffffu;
-        uint32_t row = (uint32_t)(((float)rr + 0.5f) * __uint_as_float(meta.w));
-        row -= (row * w > rr) ? 1u : 0u;
-        row += ((row + 1u) * w <= rr) ? 1u : 0u;
-        const uint32_t key = meta.y + row * gx + (rr - row * w);
+        const uint32_t key = cur.row_tile + cur.c;
         s_key[o - O0] = key;
-        s_val[o - O0] = meta.x;
+        s_val[o - O0] = cur.sp;
         runs.add(s_hist, key, a.tile_passes);
+        cur.next();
       }
       runs.flush(s_hist, a.tile_passes);
     }
@@ -476,6 +706,9 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.sorted_splats = ws->depth_val[0];
   d.sp_rect = ws->sp_rect;
   d.sp_view = ws->sp_view;
+  d.sp_tiles = reinterpret_cast<const uint4*>(ws->sp_tiles);
+  d.row_spans = ws->row_spans;
+  d.sp_region = reinterpret_cast<const float4*>(ws->sp_region);
   d.dup_key = ws->dup_key[0];
   d.dup_val = ws->dup_val[0];
   d.dup_excl = ws->dup_excl;
@@ -488,8 +721,26 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.hist = ws->hist + kHistTile * kRadix;
   d.tile_passes = ws->tile_passes;
   {
+    static thread_local int tiles_per_sm = 0;
+    if (!tiles_per_sm) tiles_per_sm = per_sm_for((const void*)k_splat_tiles, kTilesThreads);
+    KernelTimer timer(ws, kKSplatTiles, st);
+    TilesArgs t;
+    t.xy = ws->sp_xy;
+    t.co = ws->sp_conic_o;
+    t.rect = ws->sp_rect;
+    t.view = ws->sp_view;
+    t.ctr = ws->ctr;
+    t.cap = ws->cap.max_splats;
+    t.rec = reinterpret_cast<uint4*>(ws->sp_tiles);
+    t.row_spans = ws->row_spans;
+    t.rows_cap = ws->rows_cap;
+    t.region = reinterpret_cast<float4*>(ws->sp_region);
+    k_splat_tiles<<<ws->num_sms * tiles_per_sm, kTilesThreads, 0, st>>>(ws->views, t);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
     KernelTimer timer(ws, kKDuplicate, st);
-    k_dup_scan<<<ws->num_sms * dup_per_sm, kDupThreads, 0, st>>>(ws->views, d);
+    k_dup_scan<<<ws->num_sms * dup_per_sm, kDupThreads, 0, st>>>(d);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {

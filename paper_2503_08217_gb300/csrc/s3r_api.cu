@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -64,7 +65,7 @@ const char* const kKernelNames[kKCount] = {
     "begin", "temporal_compact", "compose", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
     "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd", "zero_splat_grads",
-    "blend_bwd", "project_bwd", "pose_chain", "tile_order"};
+    "blend_bwd", "project_bwd", "pose_chain", "tile_order", "splat_tiles"};
 
 void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
@@ -74,7 +75,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->dup_chunk, ws->tile_order, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_order, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -136,7 +137,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   *out = nullptr;
   if (cap->max_gaussians < 1 || cap->max_splats < 1 || cap->max_duplicates < 1 ||
       cap->max_views < 1 || cap->max_views > S3R_MAX_VIEWS || cap->max_instances < 0 ||
-      cap->max_tiles < 1 || cap->max_pixels < 1)
+      cap->max_tiles < 1 || cap->max_pixels < 1 || cap->max_rows < 0)
     return fail(S3R_ERR_INVALID, "capacities must be positive and max_views <= %d", S3R_MAX_VIEWS);
   if (cap->max_gaussians > 0xffffffffLL || cap->max_splats > 0xffffffffLL ||
       cap->max_duplicates > 0x7fffffffLL || cap->max_tiles > 0x7fffffffLL ||
@@ -196,8 +197,13 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->pose_dM, (int64_t)cap->max_views * nk * 12);
   S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
   S3R_ALLOC(ws->dup_excl, S + 1);
-  S3R_ALLOC(ws->dup_meta, 4 * S);
-  S3R_ALLOC(ws->dup_chunk, K / 4096 + 2);
+  S3R_ALLOC(ws->dup_meta, 8 * S);
+  S3R_ALLOC(ws->sp_tiles, 8 * S);
+  S3R_ALLOC(ws->sp_region, 8 * S);
+  // about 2.5 rows per splat at 1 px LOD; past the table, rows are recomputed
+  ws->rows_cap = std::min<int64_t>(cap->max_rows > 0 ? cap->max_rows : 4 * S, 0xfffffff0LL);
+  S3R_ALLOC(ws->row_spans, ws->rows_cap);
+  S3R_ALLOC(ws->dup_chunk, K / kDupChunkMin + 2);
   ws->contrib_words = K / 32 + 2;
   S3R_ALLOC(ws->contrib, 4 * ws->contrib_words);
 #undef S3R_ALLOC

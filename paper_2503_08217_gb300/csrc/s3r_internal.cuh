@@ -25,6 +25,7 @@ enum Ctr : int {
   kCtrPairs = 24,     // 64-bit: (pixel, splat) list pairs the forward walked (counting mode)
   kCtrEvalFwd = 26,   // 64-bit: (pixel, splat) pairs the forward evaluated (counting mode)
   kCtrEvalBwd = 28,   // 64-bit: (pixel, splat) pairs the backward evaluated (counting mode)
+  kCtrRows = 30,      // 64-bit: row-table entries requested by the tile counts of the sort
   kCtrCount = 32
 };
 constexpr uint32_t kStatusCapacity = 1u;
@@ -73,12 +74,13 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kHistDepth = 0;
 constexpr int kHistTile = 4;
 constexpr int kHistCount = 8;
+constexpr int kDupChunkMin = 1024;   // smallest output chunk of the pair expansion
 
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
   kKBegin = 0, kKCompact, kKCompose, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
   kKTile0, kKTile1, kKTile2, kKTile3, kKTileRanges, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
-  kKProjectBwd, kKPoseChain, kKTileOrder, kKCount
+  kKProjectBwd, kKPoseChain, kKTileOrder, kKSplatTiles, kKCount
 };
 
 }  // namespace s3r
@@ -116,6 +118,10 @@ struct s3r_workspace {
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
+  uint32_t* sp_tiles;       // [S] x 8: tiles of its rectangle a splat's alpha region reaches, rows
+  float* sp_region;         // [S] x 8: that region, where the row table had no room
+  uint32_t* row_spans;      // [rows_cap] column interval of one rectangle row
+  int64_t rows_cap;
   uint32_t* dup_chunk;      // [K/4096 + 2] sorted splat holding the first pair of each 4096-pair chunk
   uint32_t* contrib;        // [4][K/32 + 2] bit per (warp block, sorted pair): blended in the forward
   int64_t contrib_words;    // words per warp block
@@ -308,6 +314,41 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
+}
+
+// Hardware approximations (about 1 ulp); deterministic, so two kernels that
+// evaluate the same expression with them get the same bits.
+__device__ __forceinline__ float approx_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float approx_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------- alpha-region bounds
+// The blend keeps a (pixel, splat) pair iff alpha = min(0.99, o G) >= 1/255
+// with G = exp(-q / 2), q = A dx^2 + 2 B dx dy + C dy^2 (the conic), i.e. iff q
+// <= 2 ln(255 o) up to the FP32 rounding of the per-pixel evaluation. Its
+// error grows with the conic's eigenvalue ratio (cancellation between the
+// terms along a thin splat): about 2^-24 L ratio in units of q. Below a ratio
+// of kMaxConicRatio that is under 0.02, far inside the margins of the cull
+// tests; above it the tests give up and keep everything.
+constexpr float kMaxConicRatio = 3e4f;
+
+// det(conic) lowered by a bound on the rounding of A C - B^2 (so that the
+// ellipse built from it contains the exact one); -1 where the splat is too
+// anisotropic for the cull tests, or the conic is not positive definite.
+__device__ __forceinline__ float conic_det_lower(float A, float B, float C) {
+  const float bb = __fmul_rn(B, B);
+  const float det = __fmaf_rn(A, C, -bb);
+  const float lo = __fsub_rn(__fmul_rn(det, 1.f - 0x1p-20f), __fmul_rn(bb, 0x1p-20f));
+  const float tr = __fadd_rn(A, C);
+  const bool ok = (A > 0.f) & (C > 0.f) & (lo > 0.f) & (__fmul_rn(tr, tr) <= __fmul_rn(kMaxConicRatio, lo));
+  return ok ? lo : -1.f;
 }
 #endif
 

@@ -68,14 +68,15 @@ class Renderer:
     """One workspace sized for a scene and a camera rig."""
 
     def __init__(self, n: int, n_inst: int, cams, *, max_splats: int | None = None,
-                 max_duplicates: int | None = None, device=None):
+                 max_duplicates: int | None = None, max_rows: int = 0, device=None):
         self.n_views_max = len(cams)
         splats = max_splats if max_splats is not None else max(1024, n * min(len(cams), 2))
         dups = max_duplicates if max_duplicates is not None else max(4096, 8 * splats)
         self.ws = binding.Workspace(max_gaussians=max(n, 1), max_splats=splats,
                                     max_duplicates=dups, max_views=len(cams),
                                     max_instances=max(n_inst, 0), max_tiles=tile_count(cams),
-                                    max_pixels=pixel_count(cams), device=device)
+                                    max_pixels=pixel_count(cams), max_rows=max_rows,
+                                    device=device)
         self.graph = None
 
     # ---------------------------------------------------------------- stages

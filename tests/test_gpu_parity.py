@@ -98,30 +98,74 @@ def _compare_splats(res, f, scene, cams):
     return checked
 
 
-def _stage_isolated_sort(res, cams):
-    """Feed the GPU's FP32 splats to the oracle's key construction + stable
-    sort + ranges; the GPU's sorted pairs and ranges must match exactly."""
+def _oracle_pairs(res, cams):
+    """The oracle's key construction + stable sort on the GPU's FP32 splats:
+    (splat, tile id) of every pair of the rectangles, in sorted order."""
     tile_base = 0
-    all_vals, all_tiles, all_ranges = [], [], []
+    all_vals, all_tiles = [], []
     for v, cam in enumerate(cams):
         mine = np.nonzero(res["view"] == v)[0]
         depth = res["rgb_d"][mine, 3].astype(np.float32)
-        keys, vals, ranges = oracle.tile_keys(cam.width, cam.height, depth, res["rect"][mine],
-                                              tile_base=tile_base)
+        keys, vals, _ = oracle.tile_keys(cam.width, cam.height, depth, res["rect"][mine],
+                                         tile_base=tile_base)
         all_vals.append(mine[vals])
         all_tiles.append((keys >> np.uint64(32)).astype(np.int64))
-        nz = ranges[:, 1] > ranges[:, 0]
-        ranges = ranges.copy()
-        off = sum(len(a) for a in all_vals[:-1])
-        ranges[nz] += off
-        all_ranges.append(ranges)
         tile_base += ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
-    vals = np.concatenate(all_vals)
-    tiles = np.concatenate(all_tiles)
-    ranges = np.concatenate(all_ranges)
-    np.testing.assert_array_equal(res["sorted_splats"].astype(np.int64), vals)
-    np.testing.assert_array_equal(res["sorted_tiles"].astype(np.int64), tiles)
+    return np.concatenate(all_vals), np.concatenate(all_tiles)
+
+
+def _assert_unreached(res, cams, splats, tiles):
+    """Every (splat, tile) pair given has alpha = o exp(-q/2) < 1/255 (FP64,
+    on the GPU's FP32 records) at every pixel centre of the tile inside the
+    image: no pixel's blend can take that splat."""
+    base = 0
+    off = np.arange(16) + 0.5
+    for cam in cams:
+        gx, gy = (cam.width + 15) // 16, (cam.height + 15) // 16
+        sel = np.nonzero((tiles >= base) & (tiles < base + gx * gy))[0]
+        for c0 in range(0, sel.size, 20000):
+            idx = sel[c0:c0 + 20000]
+            lt = tiles[idx] - base
+            s = splats[idx]
+            px = (lt % gx)[:, None] * 16 + off[None, :]
+            py = (lt // gx)[:, None] * 16 + off[None, :]
+            dx = px[:, None, :] - res["xy"][s, 0].astype(np.float64)[:, None, None]
+            dy = py[:, :, None] - res["xy"][s, 1].astype(np.float64)[:, None, None]
+            A, B, C = (res["conic_o"][s, k].astype(np.float64)[:, None, None] for k in range(3))
+            o = res["conic_o"][s, 3].astype(np.float64)[:, None, None]
+            alpha = o * np.exp(-0.5 * (A * dx * dx + 2.0 * B * dx * dy + C * dy * dy))
+            inside = (px[:, None, :] < cam.width) & (py[:, :, None] < cam.height)
+            worst = np.where(inside, alpha, 0.0).max(axis=(1, 2))
+            assert (worst < 1.0 / 255.0).all(), (int((worst >= 1.0 / 255.0).sum()), float(worst.max()))
+        base += gx * gy
+
+
+def _stage_isolated_sort(res, cams):
+    """The GPU's sorted pairs against the oracle's key construction + stable
+    sort of the GPU's FP32 splats. The GPU lists a splat only in the tiles of
+    its rectangle that its alpha >= 1/255 region reaches, so its pairs must be
+    the oracle's pairs, in the oracle's order, with some left out, and every
+    pair left out must be unreachable (no pixel centre of the tile at alpha >=
+    1/255). The ranges are those of the GPU's own list. Returns the number of
+    pairs left out."""
+    ov, ot = _oracle_pairs(res, cams)
+    gv = res["sorted_splats"].astype(np.int64)
+    gt = res["sorted_tiles"].astype(np.int64)
+    S = max(int(res["xy"].shape[0]), 1)
+    keep = np.isin(ot * S + ov, gt * S + gv)
+    assert int(keep.sum()) == gv.size            # no pair outside the rectangles, none twice
+    np.testing.assert_array_equal(gv, ov[keep])
+    np.testing.assert_array_equal(gt, ot[keep])
+    _assert_unreached(res, cams, ov[~keep], ot[~keep])
+    n_tiles = res["ranges"].shape[0]
+    ranges = np.zeros((n_tiles, 2), np.int64)
+    if gt.size:
+        first = np.r_[0, np.nonzero(np.diff(gt))[0] + 1]
+        last = np.r_[first[1:], gt.size]
+        ranges[gt[first], 0] = first
+        ranges[gt[first], 1] = last
     np.testing.assert_array_equal(res["ranges"].astype(np.int64), ranges)
+    return int((~keep).sum())
 
 
 def _compare_images(res, f, cams, bg=(0.0, 0.0, 0.0)):
@@ -140,6 +184,7 @@ def _compare_images(res, f, cams, bg=(0.0, 0.0, 0.0)):
 def _stage_isolated_blend(res, cams, bg=(0.0, 0.0, 0.0)):
     """Oracle blend (FP64) on the GPU's FP32 splat records."""
     P0 = 0
+    tile_base = 0
     for v, cam in enumerate(cams):
         mine = np.nonzero(res["view"] == v)[0]
         sp = {"uv": res["xy"][mine].astype(np.float64),
@@ -153,11 +198,22 @@ def _stage_isolated_blend(res, cams, bg=(0.0, 0.0, 0.0)):
         diff = np.abs(res["images"][v] - o["image"]).max(axis=0)
         assert diff[ok].max() <= 2e-5, (v, float(diff[ok].max()))
         P = cam.width * cam.height
-        nc = res["n_contrib"][P0:P0 + P].reshape(cam.height, cam.width)
-        np.testing.assert_array_equal(nc[ok], o["n_contrib"][ok])
+        nc = res["n_contrib"][P0:P0 + P].reshape(cam.height, cam.width).astype(np.int64)
+        # the last blended splat of each pixel, by identity: its position
+        # differs between the GPU's reach-culled lists and the rectangles'
+        gx = (cam.width + 15) // 16
+        yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+        lt = (yy // 16) * gx + xx // 16
+        _, vals, oranges = oracle.tile_keys(cam.width, cam.height, sp["depth32"], sp["rect"])
+        last_o = np.where(o["n_contrib"] > 0,
+                          mine[vals[np.maximum(oranges[lt, 0] + o["n_contrib"] - 1, 0)]], -1)
+        gr = res["ranges"][tile_base + lt, 0].astype(np.int64)
+        last_g = np.where(nc > 0, res["sorted_splats"].astype(np.int64)[np.maximum(gr + nc - 1, 0)], -1)
+        np.testing.assert_array_equal(last_g[ok], last_o[ok])
         T = res["final_T"][P0:P0 + P].reshape(cam.height, cam.width)
         np.testing.assert_allclose(T[ok], o["T"][ok], rtol=1e-4, atol=1e-6)
         P0 += P
+        tile_base += gx * ((cam.height + 15) // 16)
 
 
 def _compare_grads(g_gpu, g_orc, names):
@@ -175,6 +231,7 @@ def _compare_grads(g_gpu, g_orc, names):
 def test_tiny_forward_stages(built, tiny, tiny_vis):
     import gpu_helpers
     vis, _ = tiny_vis
+    dropped = 0
     for step in (0, 5, 9):
         cams = tiny.cams[step]
         res = gpu_helpers.gpu_step(tiny, step, cams, vis)
@@ -182,10 +239,11 @@ def test_tiny_forward_stages(built, tiny, tiny_vis):
         near = _compare_selection_and_masks(res, f, len(cams))
         assert near.sum() <= 0.005 * near.size
         assert _compare_splats(res, f, tiny, cams) > 1000
-        _stage_isolated_sort(res, cams)
+        dropped += _stage_isolated_sort(res, cams)
         _stage_isolated_blend(res, cams)
         worst, n_bad = _compare_images(res, f, cams)
         assert n_bad <= 0.15 * 320 * 192
+    assert dropped > 0          # the reach test did leave rectangle tiles out
 
 
 def test_tiny_gradients(built, tiny, tiny_vis):
@@ -418,6 +476,33 @@ def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
     with pytest.raises(binding.S3RError) as e:
         gpu_helpers.gpu_step(tiny, 3, tiny.cams[3], vis, max_splats=100, max_duplicates=50)
     assert e.value.status == 2   # S3R_ERR_CAPACITY
+
+
+def test_row_table_overflow_gives_the_same_pairs(built, tiny, tiny_vis):
+    """A splat whose rectangle rows do not fit the sort's row table is expanded
+    from its stored alpha region instead: with a table of 64 entries (most
+    splats overflow) the pairs, ranges and images equal those of a table with
+    room for every row."""
+    import gpu_helpers
+    vis, _ = tiny_vis
+    step = 5
+    cams = tiny.cams[step]
+    dL = [np.ones((3, c.height, c.width)) for c in cams]
+    outs = []
+    for max_rows in (0, 64):
+        r = gpu_helpers.Renderer(tiny.n, tiny.n_inst, cams, max_rows=max_rows)
+        res = gpu_helpers.gpu_step(tiny, step, cams, vis, dL=dL, renderer=r)
+        ident = gpu_helpers.splat_gids(res) * 128 + res["view"]
+        pairs = np.stack([res["sorted_tiles"].astype(np.int64),
+                          ident[res["sorted_splats"].astype(np.int64)]], 1)
+        outs.append((res, pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]))
+    (a, pa), (b, pb) = outs
+    assert a["counts"]["n_duplicates"] == b["counts"]["n_duplicates"] > 0
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(a["ranges"], b["ranges"])
+    for x, y in zip(a["images"], b["images"]):
+        np.testing.assert_allclose(x, y, atol=1e-6)
+    _stage_isolated_sort(b, cams)
 
 
 def test_invalid_arguments_are_rejected(built, tiny):
