@@ -123,9 +123,10 @@ typedef struct {
   int64_t max_tiles;       /* 16x16 tiles summed over the cameras of a call */
   int64_t max_pixels;      /* pixels summed over the cameras of a call */
   int64_t max_rows;        /* row-table entries of s3r_sort's tile counts (one per row of
-                              tiles of a splat's rectangle); 0: 4 x max_splats. A splat
-                              whose rows do not fit is expanded from its stored alpha
-                              region instead: the same pairs, computed again. */
+                              tiles of a splat's rectangle past its third); 0: 4 x
+                              max_splats. A splat whose rows do not fit is expanded from
+                              its stored alpha region instead: the same pairs, computed
+                              again. */
 } s3r_capacity;
 
 typedef struct {

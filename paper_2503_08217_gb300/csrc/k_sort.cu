@@ -183,9 +183,10 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
 //  k_splat_tiles: per splat (by id, in any order), a 32-byte record: its
 //                tile count (one interval per row of its rectangle), the tile
 //                id of the rectangle's corner, grid and rectangle widths,
-//                rectangle height, and its rows: 4 bytes per row in a row
-//                table (offsets from a warp-aggregated bump counter), the
-//                first kInlineRows of them also in the record. A splat that no
+//                rectangle height, and its rows: the first kInlineRows in the
+//                record, the others 4 bytes each in a row table (offsets from
+//                a warp-aggregated bump counter; the warp computes a tall
+//                splat's rows together, one per lane). A splat that no
 //                longer fits the table stores its region (32 bytes) instead,
 //                and the expansion recomputes its later rows from it with the
 //                same function. Outside the scan below, whose look-back chain
@@ -337,8 +338,8 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
     const uint2 rc = live ? a.rect[i] : make_uint2(0u, 0u);
     const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16;
     const uint32_t w = (rc.y & 0xffffu) - x0, h = (rc.y >> 16) - y0;
-    // table entries for every row of the rectangle, one atomic per warp
-    const uint32_t need = (live && w != 0) ? h : 0u;
+    // table entries for the rows past the inline ones, one atomic per warp
+    const uint32_t need = (live && w != 0 && h > kInlineRows) ? h - kInlineRows : 0u;
     uint32_t incl = need;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -350,20 +351,51 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
       wbase = atomicAdd(reinterpret_cast<unsigned long long*>(a.ctr + kCtrRows),
                         (unsigned long long)incl);
     wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    if (!live) continue;
     const uint64_t off = wbase + incl - need;
     const bool table = off + need <= (uint64_t)a.rows_cap;
-    const Region g = region_of(a.xy[i], a.co[i], x0, y0);
+    Region g = {};
+    if (live) g = region_of(a.xy[i], a.co[i], x0, y0);
+    // each lane: the inline rows of its own splat
     uint32_t cnt = 0;
     uint32_t head[kInlineRows] = {0u, 0u, 0u};
-    if (w != 0)
-      for (uint32_t r = 0; r < h; ++r) {
-        const uint2 c = row_span(g, r, w);
-        const uint32_t e = c.x | (c.y << 16);
-        cnt += c.y - c.x;
-        if (r < kInlineRows) head[r] = e;
-        if (table) a.row_spans[off + r] = e;
+    if (live && w != 0)
+#pragma unroll
+      for (uint32_t r = 0; r < (uint32_t)kInlineRows; ++r)
+        if (r < h) {
+          const uint2 c = row_span(g, r, w);
+          head[r] = c.x | (c.y << 16);
+          cnt += c.y - c.x;
+        }
+    // the warp: the further rows of its taller splats, one splat at a time,
+    // one row per lane (a per-lane loop would wait on the tallest splat)
+    uint32_t tall = __ballot_sync(0xffffffffu, need != 0u);
+    while (tall) {
+      const int b = __ffs(tall) - 1;
+      tall &= tall - 1;
+      Region gb;
+      gb.u = __shfl_sync(0xffffffffu, g.u, b);
+      gb.v = __shfl_sync(0xffffffffu, g.v, b);
+      gb.B = __shfl_sync(0xffffffffu, g.B, b);
+      gb.inv_A = __shfl_sync(0xffffffffu, g.inv_A, b);
+      gb.LA = __shfl_sync(0xffffffffu, g.LA, b);
+      gb.det = __shfl_sync(0xffffffffu, g.det, b);
+      gb.ye = __shfl_sync(0xffffffffu, g.ye, b);
+      gb.xe = __shfl_sync(0xffffffffu, g.xe, b);
+      gb.s = __shfl_sync(0xffffffffu, g.s, b);
+      const uint32_t wb = __shfl_sync(0xffffffffu, w, b), hb = __shfl_sync(0xffffffffu, h, b);
+      const uint64_t ob = __shfl_sync(0xffffffffu, (unsigned long long)off, b);
+      const bool tb = __shfl_sync(0xffffffffu, (int)table, b) != 0;
+      uint32_t part = 0;
+      for (uint32_t r = kInlineRows + lane; r < hb; r += 32) {
+        const uint2 c = row_span(gb, r, wb);
+        part += c.y - c.x;
+        if (tb) a.row_spans[ob + (r - kInlineRows)] = c.x | (c.y << 16);
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == (uint32_t)b) cnt += part;
+    }
+    if (!live) continue;
     const ViewInfo& vi = vs.v[a.view[i] & 0x7f];   // bit 7: Eq. 7 moved
     const uint32_t corner = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
     a.rec[2 * i] = make_uint4(cnt, corner, (uint32_t)vi.gx | (w << 16), h);
@@ -494,7 +526,7 @@ struct Cursor {
   // rows past the inline ones: the row table, or (where it had no room) the
   // stored region through the same function that counted them
   __device__ __forceinline__ uint32_t far_row(uint32_t row) const {
-    if (off != kNoRows) return row_spans[off + row];
+    if (off != kNoRows) return row_spans[off + row - kInlineRows];
     const Region g = region_load(region[2 * (size_t)sp], region[2 * (size_t)sp + 1]);
     const uint2 s = row_span(g, row, w);
     return s.x | (s.y << 16);

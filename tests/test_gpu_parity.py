@@ -480,16 +480,16 @@ def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
 
 def test_row_table_overflow_gives_the_same_pairs(built, tiny, tiny_vis):
     """A splat whose rectangle rows do not fit the sort's row table is expanded
-    from its stored alpha region instead: with a table of 64 entries (most
-    splats overflow) the pairs, ranges and images equal those of a table with
-    room for every row."""
+    from its stored alpha region instead: with a table of one entry (every
+    splat with more than four rows overflows) the pairs, ranges and images
+    equal those of a table with room for every row."""
     import gpu_helpers
     vis, _ = tiny_vis
     step = 5
     cams = tiny.cams[step]
     dL = [np.ones((3, c.height, c.width)) for c in cams]
     outs = []
-    for max_rows in (0, 64):
+    for max_rows in (0, 1):
         r = gpu_helpers.Renderer(tiny.n, tiny.n_inst, cams, max_rows=max_rows)
         res = gpu_helpers.gpu_step(tiny, step, cams, vis, dL=dL, renderer=r)
         ident = gpu_helpers.splat_gids(res) * 128 + res["view"]
@@ -587,8 +587,11 @@ def test_cuda_graph_replay_matches_eager(built, tiny, tiny_vis):
     g.replay()
     torch.cuda.synchronize()
     torch.testing.assert_close(out, ref_out, rtol=0, atol=0)
+    # the backward's float atomics sum in a run-dependent order: entries that
+    # cancel may move by rounding relative to the tensor's scale
     for k in ref_g:
-        torch.testing.assert_close(grads[k], ref_g[k], rtol=1e-4, atol=1e-5)
+        scale = max(float(ref_g[k].abs().max()), 1e-30)
+        torch.testing.assert_close(grads[k], ref_g[k], rtol=1e-4, atol=1e-5 * scale)
 
 
 def test_counting_mode_changes_no_result(built, tiny, tiny_vis):
