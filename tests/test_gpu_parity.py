@@ -469,6 +469,34 @@ def test_single_gaussian_and_ragged_sizes(built):
     np.testing.assert_allclose(res["images"][0], f["views"][0]["image"], atol=1e-5)
 
 
+def test_needle_splats_keep_their_rectangles(built, tiny, tiny_vis):
+    """Splats whose conic eigenvalue ratio exceeds 3e4 (where the FP32
+    per-pixel test's own rounding grows past the cull margins) keep every tile
+    of their 3-sigma rectangle; the other splats' left-out tiles stay
+    unreachable, and the sort stage holds as everywhere."""
+    import copy
+    import gpu_helpers
+    vis, _ = tiny_vis
+    scene = copy.deepcopy(tiny)
+    rng = np.random.default_rng(3)
+    needles = rng.choice(scene.n, 200, replace=False)
+    scene.log_scales[needles] = np.log(np.array([8.0, 1e-3, 1e-3], np.float32))
+    scene.opacity_logits[needles] = -1.0
+    step = 5
+    cams = scene.cams[step]
+    res = gpu_helpers.gpu_step(scene, step, cams, vis)
+    A, B, C = (res["conic_o"][:, k].astype(np.float64) for k in range(3))
+    ratio = (A + C) ** 2 / np.maximum(A * C - B * B, 1e-300)
+    thin = ratio > 3.3e4
+    assert thin.sum() >= 5
+    rect = res["rect"].astype(np.int64)
+    area = (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])
+    pairs = np.bincount(res["sorted_splats"].astype(np.int64), minlength=area.size)
+    np.testing.assert_array_equal(pairs[thin], area[thin])
+    assert (pairs[~thin] <= area[~thin]).all() and pairs[~thin].sum() < area[~thin].sum()
+    _stage_isolated_sort(res, cams)
+
+
 def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
     import gpu_helpers
     from paper_2503_08217_gb300 import binding
