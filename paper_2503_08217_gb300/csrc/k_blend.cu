@@ -83,6 +83,40 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// Two FP32 values in one 64-bit register for the packed .f32x2 instructions
+// (sm_100 and later): one instruction does the same IEEE operation on both
+// halves, so the pixel pairs of a lane cost half the issue slots of scalar
+// code with bit-identical results.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Shared-memory form of a splat for the blend: the conic is pre-scaled so that
 // the exponent is evaluated directly in base 2:
 //   a = (u, v, A2, B2), b = (C2, opacity, r, g), c = b-channel, with
@@ -201,13 +235,24 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 
 // kCount: also count the (pixel, splat) pairs walked (list positions up to
 // each pixel's stop) and evaluated (footprint test passed, pixel not stopped).
+//
+// A lane's two pixels of a column (rows y and y + 4) are evaluated as one
+// packed pair: the splat's values are staged in shared memory as duplicated
+// pairs (A2 A2 B2 B2 | C2 C2 o o | r r g g | b b v v | u u), so every operand
+// of the packed arithmetic comes straight from a 64-bit shared load. The
+// arithmetic is that of eval_splat and of the scalar blend, in the same
+// order, so the backward's recomputation takes the same decisions.
+constexpr int kBatchFwd = 128;                // splats staged per batch (forward)
 template <bool kCount>
 __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
                                                             BlendArgs a) {
-  __shared__ float4 s_a[kBatch];
-  __shared__ float4 s_b[kBatch];
-  __shared__ float4 s_box[kBatch];
-  __shared__ float s_c[kBatch];
+  static_assert(kBandRows == 2, "the packed forward pairs the two rows of a lane's column");
+  __shared__ float4 s_p0[kBatchFwd];   // A2 A2 B2 B2
+  __shared__ float4 s_p1[kBatchFwd];   // C2 C2 o o
+  __shared__ float4 s_p2[kBatchFwd];   // r r g g
+  __shared__ float4 s_p3[kBatchFwd];   // b b v v
+  __shared__ float2 s_u[kBatchFwd];    // u u
+  __shared__ float4 s_box[kBatchFwd];
   const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
   const int v = view_of_tile(vs, tile);
   const ViewInfo& vi = vs.v[v];
@@ -217,75 +262,119 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
   const Band P = band_pixels(vi, lt, warp, lane);
   const uint2 range = a.ranges[tile];
   const int n = (int)(range.y - range.x);
+  const f2 FY = pk(P.fy[0], P.fy[1]);
+  const f2 FX[2] = {pk(P.fx[0], P.fx[0]), pk(P.fx[1], P.fx[1])};
+  const f2 ONE = pk(1.f, 1.f);
 
-  float T[kBandPix], C[kBandPix][3];
+  // per column c: the pair (row 0, row 1); scalar per-pixel state k = 2c + r
+  f2 T2[2], C2[2][3];
   int last[kBandPix], endp[kBandPix];
   bool done[kBandPix];
   uint32_t n_eval = 0;
   bool all_done = true;
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < 2; ++c) {
+    T2[c] = ONE;
+    C2[c][0] = C2[c][1] = C2[c][2] = pk(0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kBandRows; ++r) {
       const int k = c * kBandRows + r;
-      T[k] = 1.f;
-      C[k][0] = C[k][1] = C[k][2] = 0.f;
       last[k] = 0;
       done[k] = !(P.X0 + 8 * c < vi.width && P.Y0 + 4 * r < vi.height);
       endp[k] = done[k] ? 0 : n;      // positions walked
       all_done = all_done && done[k];
     }
+  }
   uint32_t* wbits = a.contrib + warp * a.contrib_words;
-  for (int b0 = 0; b0 < n; b0 += kBatch) {
+  for (int b0 = 0; b0 < n; b0 += kBatchFwd) {
     if (__syncthreads_count(all_done) == kBandThreads) break;
-    for (int i = threadIdx.x; i < kBatch && b0 + i < n; i += kBandThreads) {
+    for (int i = threadIdx.x; i < kBatchFwd && b0 + i < n; i += kBandThreads) {
       const uint32_t s = a.sorted_splats[range.x + b0 + i];
       const float2 xy = a.sp_xy[s];
       const float4 co = a.sp_conic_o[s];
-      stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
+      const float4 rgb = a.sp_rgb_d[s];
+      float4 sa, sb;
+      float sc;
+      stage_splat(xy, co, rgb, sa, sb, sc);
+      s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
+      s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
+      s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
+      s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
+      s_u[i] = make_float2(sa.x, sa.x);
       s_box[i] = alpha_box(xy, co);
     }
     __syncthreads();
-    const int m = min(kBatch, n - b0);
+    const int m = min(kBatchFwd, n - b0);
     for (int c0 = 0; c0 < m; c0 += 32) {
       if (__all_sync(0xffffffffu, all_done)) break;
       // which of the next 32 splats can reach alpha >= 1/255 in this warp's band
       const int jl = c0 + (int)lane;
-      const bool reach = !box_misses(s_box[jl], P) & ellipse_reaches(s_a[jl], s_b[jl], P);
-      uint32_t todo = __ballot_sync(0xffffffffu, (jl < m) & reach);
+      bool reach = false;
+      if (jl < m) {
+        const float4 p0 = s_p0[jl], p1 = s_p1[jl], p3 = s_p3[jl];
+        const float4 ea = make_float4(s_u[jl].x, p3.z, p0.x, p0.z);
+        const float4 eb = make_float4(p1.x, p1.z, 0.f, 0.f);
+        reach = !box_misses(s_box[jl], P) && ellipse_reaches(ea, eb, P);
+      }
+      uint32_t todo = __ballot_sync(0xffffffffu, reach);
       uint32_t blended = 0;     // splats of this chunk blended into some pixel of the band
       while (todo) {
         const int j = c0 + __ffs(todo) - 1;
         todo &= todo - 1;
-        const float4 sa = s_a[j], sb = s_b[j];
-        const float cb = s_c[j];
+        const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
+        const float2 qu = s_u[j];
+        const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
+        const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
+        const f2 U2 = pk(qu.x, qu.y);
         const int pos = b0 + j + 1;
+        // the rows' dy and the dy terms of the exponent, shared by both columns
+        const f2 dy = sub2(V2, FY);
+        const f2 bdy = mul2(B2, dy);
+        const f2 cdy = mul2(mul2(C2c, dy), dy);
         bool any_blend = false;
-        all_done = true;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < 2; ++c) {
+          const f2 dx = sub2(U2, FX[c]);
+          const f2 pw = fma2(dx, fma2(A2, dx, bdy), cdy);
+          float p[2], G[2];
+          upk(pw, p[0], p[1]);
+          G[0] = ex2_approx(p[0]);
+          G[1] = ex2_approx(p[1]);
+          float raw[2];
+          upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
+          float al[2], ab[2];
+          bool blend[2];
 #pragma unroll
-          for (int r = 0; r < kBandRows; ++r) {
+          for (int r = 0; r < 2; ++r) {
             const int k = c * kBandRows + r;
-            const SplatEval e = eval_splat(sa, sb, P.fx[c], P.fy[r]);
+            al[r] = fminf(kAlphaMax, raw[r]);
             if constexpr (kCount) n_eval += done[k] ? 0u : 1u;
-            const bool ok = !done[k] && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
-            const float nT = T[k] * (1.f - e.alpha);
-            const bool stop = ok && (nT < kTStop);
-            const bool blend = ok && !stop;
+            blend[r] = !done[k] && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
+          }
+          float nT[2];
+          upk(mul2(T2[c], sub2(ONE, pk(al[0], al[1]))), nT[0], nT[1]);
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int k = c * kBandRows + r;
+            const bool stop = blend[r] && (nT[r] < kTStop);
+            blend[r] = blend[r] && !stop;
             // one select: T (1 - 0) = T exactly where the splat is not blended
-            const float ab = blend ? e.alpha : 0.f;
-            const float w = ab * T[k];
-            C[k][0] = fmaf(sb.z, w, C[k][0]);
-            C[k][1] = fmaf(sb.w, w, C[k][1]);
-            C[k][2] = fmaf(cb, w, C[k][2]);
-            T[k] = T[k] * (1.f - ab);
-            last[k] = blend ? pos : last[k];
+            ab[r] = blend[r] ? al[r] : 0.f;
+            last[k] = blend[r] ? pos : last[k];
             if constexpr (kCount) endp[k] = stop ? pos : endp[k];
             done[k] = done[k] || stop;
-            any_blend = any_blend || blend;
-            all_done = all_done && done[k];
+            any_blend = any_blend || blend[r];
           }
+          const f2 AB = pk(ab[0], ab[1]);
+          const f2 w = mul2(AB, T2[c]);
+          C2[c][0] = fma2(R2, w, C2[c][0]);
+          C2[c][1] = fma2(G2, w, C2[c][1]);
+          C2[c][2] = fma2(Bl2, w, C2[c][2]);
+          T2[c] = mul2(T2[c], sub2(ONE, AB));
+        }
+        all_done = true;
+#pragma unroll
+        for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
         if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
       }
       if (lane == 0 && blended) or_bits(wbits, range.x + b0 + c0, blended);
@@ -307,7 +396,12 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
   }
   const int64_t plane = (int64_t)vi.width * vi.height;
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < 2; ++c) {
+    float T[2], Cr[2], Cg[2], Cb[2];
+    upk(T2[c], T[0], T[1]);
+    upk(C2[c][0], Cr[0], Cr[1]);
+    upk(C2[c][1], Cg[0], Cg[1]);
+    upk(C2[c][2], Cb[0], Cb[1]);
 #pragma unroll
     for (int r = 0; r < kBandRows; ++r) {
       const int k = c * kBandRows + r;
@@ -315,13 +409,14 @@ __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constan
       if (px < vi.width && py < vi.height) {
         const int64_t pix = (int64_t)py * vi.width + px;
         float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
-        o[0] = fmaf(T[k], a.bg[0], C[k][0]);
-        o[plane] = fmaf(T[k], a.bg[1], C[k][1]);
-        o[2 * plane] = fmaf(T[k], a.bg[2], C[k][2]);
-        a.final_T[vi.pix_base + pix] = T[k];
+        o[0] = fmaf(T[r], a.bg[0], Cr[r]);
+        o[plane] = fmaf(T[r], a.bg[1], Cg[r]);
+        o[2 * plane] = fmaf(T[r], a.bg[2], Cb[r]);
+        a.final_T[vi.pix_base + pix] = T[r];
         a.n_contrib[vi.pix_base + pix] = (uint32_t)last[k];
       }
     }
+  }
 }
 
 // a ? x : y as one selp. Written out because the compiler turned the
