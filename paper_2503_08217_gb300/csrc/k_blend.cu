@@ -2,9 +2,10 @@
 // adjoint.
 //
 // Forward: one CTA of two warps per tile, each warp a 16x8 band, four pixels
-// per lane. The tile's front-to-back splat list is consumed in batches of 256
-// staged in shared memory (uv, base-2 conic, opacity, rgb, and the box where
-// the splat can reach alpha >= 1/255); per 32 splats a warp ballots which of
+// per lane, the two of a column evaluated as one packed f32x2 pair. The
+// tile's front-to-back splat list is consumed in batches of 128 staged in
+// shared memory (uv, base-2 conic, opacity, rgb as duplicated pairs, and the
+// box where the splat can reach alpha >= 1/255); per 32 splats a warp ballots which of
 // them can reach alpha >= 1/255 somewhere in its band (box, then the exact
 // ellipse-rectangle test) and evaluates only those. alpha = min(0.99, o G) is
 // skipped below 1/255, and a pixel stops before its transmittance would fall
@@ -16,7 +17,8 @@
 // Backward: the same tiles and bands walked back to front, starting at each
 // warp's last blended splat and visiting only the recorded splats. The
 // transmittance before each splat is recovered from the stored final value as
-// T <- T / (1 - alpha), so no per-pixel lists are kept. Per splat the nine
+// T <- T / (1 - alpha), so no per-pixel lists are kept; a lane's two pixels
+// of a column again form one packed pair. Per splat the nine
 // adjoints (uv, conic, opacity, rgb) are summed over the warp with shuffles,
 // then over the CTA in shared memory (one shared atomic per splat and warp),
 // and flushed to global memory with one vector atomic per four floats.
@@ -25,7 +27,6 @@
 namespace s3r {
 namespace {
 
-constexpr int kBatch = 256;                   // splats staged per batch (forward)
 constexpr int kBatchBwd = 128;                // splats staged per batch (backward)
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -129,22 +130,12 @@ __device__ __forceinline__ void stage_splat(const float2 xy, const float4 co, co
   c = rgb.z;
 }
 
-// Exponent (base 2) and alpha of a staged splat at pixel centre (fx, fy).
-// The forward and the backward call this same function, so both take the
-// same FP32 decisions.
-struct SplatEval {
-  float dx, dy, p, G, raw, alpha;
-};
-__device__ __forceinline__ SplatEval eval_splat(const float4 a, const float4 b, float fx, float fy) {
-  SplatEval e;
-  e.dx = a.x - fx;
-  e.dy = a.y - fy;
-  e.p = fmaf(e.dx, fmaf(a.z, e.dx, a.w * e.dy), b.x * e.dy * e.dy);
-  e.G = ex2_approx(e.p);
-  e.raw = b.y * e.G;
-  e.alpha = fminf(kAlphaMax, e.raw);
-  return e;
-}
+// Exponent (base 2) and alpha of a staged splat at pixel centre (fx, fy), as
+// both blend kernels evaluate them (in packed pairs, with these operations in
+// this order, so that both take the same FP32 decisions):
+//   dx = u - fx, dy = v - fy, p = fma(dx, fma(A2, dx, B2 dy), (C2 dy) dy),
+//   G = 2^p (ex2.approx), raw = o G, alpha = min(0.99, raw);
+// the pixel takes the splat iff p <= 0 and alpha >= 1/255.
 
 // Bounding box of the region where a staged splat can reach alpha >= 1/255:
 // the ellipse d^T Q d <= 2 ln(255 o) (Q the conic), grown by a small relative
@@ -240,7 +231,7 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 // packed pair: the splat's values are staged in shared memory as duplicated
 // pairs (A2 A2 B2 B2 | C2 C2 o o | r r g g | b b v v | u u), so every operand
 // of the packed arithmetic comes straight from a 64-bit shared load. The
-// arithmetic is that of eval_splat and of the scalar blend, in the same
+// arithmetic is the exponent and alpha of stage_splat's comment, in that
 // order, so the backward's recomputation takes the same decisions.
 constexpr int kBatchFwd = 128;                // splats staged per batch (forward)
 template <bool kCount>
@@ -479,31 +470,16 @@ struct BwdPixel {
   int last;
 };
 
-// One splat's contribution to the adjoints at one pixel (reverse order);
-// updates the pixel's transmittance and Bd only where the splat was blended in
-// the forward. The per-pixel part of the sums goes to g[4..8]; dL/d(power) of
-// the pixel is returned in dpow for the per-column sums of the caller (the
-// pixels of a column share dx). The sums are kept in moment form,
+// One splat's contribution to the adjoints at one pixel (reverse order), with
+// act = the forward blended it there: T <- T / (1 - alpha) where act;
+// cd = c . d; dL/dalpha = T cd - Bd / (1 - alpha); w = act ? alpha T : 0;
+// Bd += cd w; dL/dopacity = (act and raw <= 0.99 ? G : 0) dL/dalpha (alpha =
+// 0.99 is constant); dpow = o dL/dopacity is dL/d(power). The per-splat sums
+// are kept in moment form over the warp's pixels,
 //   g0 = sum dpow dx, g1 = sum dpow dy, g2 = sum dpow dx^2, g3 = sum dpow dx dy,
 //   g4 = sum dpow dy^2, g5 = sum dL/dopacity, g6..8 = sum w dL/dC,
+// (a column's pixels share dx, so g0..g3 take its sums of dpow and dpow dy)
 // and turned into the adjoints of (u, v, conic) once per splat at the flush.
-__device__ __forceinline__ void bwd_pixel(BwdPixel& q, const SplatEval& e, const float4 sb,
-                                          float cb, bool act, float g[9], float& dpow) {
-  const float inv = rcp_approx(1.f - e.alpha);
-  q.T = select_f(act, q.T * inv, q.T);
-  const float cd = fmaf(sb.z, q.d0, fmaf(sb.w, q.d1, cb * q.d2));
-  const float dalpha = fmaf(q.T, cd, -q.Bd * inv);
-  const float w = select_f(act, e.alpha * q.T, 0.f);
-  q.Bd = fmaf(cd, w, q.Bd);
-  const bool live = act && !(e.raw > kAlphaMax);         // alpha = 0.99 is constant
-  const float gd = select_f(live, e.G, 0.f) * dalpha;     // dL/dopacity
-  dpow = sb.y * gd;                                       // dL/d(power), natural units
-  g[4] = fmaf(dpow * e.dy, e.dy, g[4]);
-  g[5] += gd;
-  g[6] = fmaf(w, q.d0, g[6]);                             // d/drgb
-  g[7] = fmaf(w, q.d1, g[7]);
-  g[8] = fmaf(w, q.d2, g[8]);
-}
 
 __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const ViewInfo& vi,
                                          int px, int py, bool inside) {
@@ -521,15 +497,24 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
   q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
+// The reverse walk evaluates a lane's two pixels of a column (rows y and
+// y + 4) as one packed pair, like the forward: the splat is staged as
+// duplicated pairs, the per-pixel state (T, Bd, dL/dC) is held as pairs per
+// column, and the recomputation, the recovery of T and dL/dalpha are the
+// scalar expressions in the same order. Only the order in which a lane adds
+// up its four pixels' shares of the nine sums differs from a scalar walk.
 template <bool kCount>
 __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
     const __grid_constant__ ViewSet vs, BlendArgs a) {
+  static_assert(kBandRows == 2, "the packed backward pairs the two rows of a lane's column");
   constexpr int kT = kBandThreads;
   constexpr int kRows = kBandRows;
   constexpr int kPix = kBandPix;
-  __shared__ float4 s_a[kBatchBwd];
-  __shared__ float4 s_b[kBatchBwd];
-  __shared__ float s_c[kBatchBwd];
+  __shared__ float4 s_p0[kBatchBwd];   // A2 A2 B2 B2
+  __shared__ float4 s_p1[kBatchBwd];   // C2 C2 o o
+  __shared__ float4 s_p2[kBatchBwd];   // r r g g
+  __shared__ float4 s_p3[kBatchBwd];   // b b v v
+  __shared__ float2 s_u[kBatchBwd];    // u u
   __shared__ uint32_t s_id[kBatchBwd];
   __shared__ float s_g[kBatchBwd][9];
   __shared__ float s_sink[kBandThreads];   // target of the lanes with no sum to add
@@ -545,21 +530,33 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
   const uint2 range = a.ranges[tile];
 
   float fx[2], fy[kRows];
-  BwdPixel q[kPix];
 #pragma unroll
   for (int c = 0; c < 2; ++c) fx[c] = (float)(X0 + 8 * c) + 0.5f;
 #pragma unroll
   for (int r = 0; r < kRows; ++r) fy[r] = (float)(Y0 + 4 * r) + 0.5f;
+  const f2 FY = pk(fy[0], fy[1]);
+  const f2 FX[2] = {pk(fx[0], fx[0]), pk(fx[1], fx[1])};
+  const f2 ONE = pk(1.f, 1.f);
+  // per column c: (row 0, row 1) pairs of T, Bd and dL/dC; scalar last contributor
+  f2 T2[2], Bd2[2], Q0[2], Q1[2], Q2[2];
+  int last[kPix];
   int wlast = 0;
 #pragma unroll
-  for (int c = 0; c < 2; ++c)
+  for (int c = 0; c < 2; ++c) {
+    BwdPixel qq[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int px = X0 + 8 * c, py = Y0 + 4 * r;
-      BwdPixel& qq = q[c * kRows + r];
-      bwd_init(qq, a, vi, px, py, px < vi.width && py < vi.height);
-      wlast = max(wlast, qq.last);
+      bwd_init(qq[r], a, vi, px, py, px < vi.width && py < vi.height);
+      last[c * kRows + r] = qq[r].last;
+      wlast = max(wlast, qq[r].last);
     }
+    T2[c] = pk(qq[0].T, qq[1].T);
+    Bd2[c] = pk(qq[0].Bd, qq[1].Bd);
+    Q0[c] = pk(qq[0].d0, qq[1].d0);
+    Q1[c] = pk(qq[0].d1, qq[1].d1);
+    Q2[c] = pk(qq[0].d2, qq[1].d2);
+  }
   if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
 #pragma unroll
@@ -580,7 +577,14 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
       s_id[i] = s;
       const float2 xy = a.sp_xy[s];
       const float4 co = a.sp_conic_o[s];
-      stage_splat(xy, co, a.sp_rgb_d[s], s_a[i], s_b[i], s_c[i]);
+      float4 sa, sb;
+      float sc;
+      stage_splat(xy, co, a.sp_rgb_d[s], sa, sb, sc);
+      s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
+      s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
+      s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
+      s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
+      s_u[i] = make_float2(sa.x, sa.x);
     }
     for (int i = threadIdx.x; i < kBatchBwd * 9; i += kT) (&s_g[0][0])[i] = 0.f;
     __syncthreads();
@@ -598,42 +602,97 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
         const int bit = 31 - __clz(todo);
         todo &= ~(1u << bit);
         const int j = c0 + bit;
-        const float4 sa = s_a[j], sb = s_b[j];
-        const float cb = s_c[j];
+        const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
+        const float2 qu = s_u[j];
+        const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
+        const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
+        const f2 U2 = pk(qu.x, qu.y);
         const int pos = lo + j;
-        float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const f2 dy = sub2(V2, FY);
+        const f2 bdy = mul2(B2, dy);
+        const f2 cdy = mul2(mul2(C2c, dy), dy);
+        float dyv[2];
+        upk(dy, dyv[0], dyv[1]);
+        float g[4] = {0.f, 0.f, 0.f, 0.f};
+        f2 g4 = pk(0.f, 0.f), g5 = g4, g6 = g4, g7 = g4, g8 = g4;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          float D = 0.f, E = 0.f;     // sum over the column of dpow and dpow * dy
-          float dx = 0.f;
+          const f2 dx2 = sub2(U2, FX[c]);
+          const f2 pw = fma2(dx2, fma2(A2, dx2, bdy), cdy);
+          float p[2], G[2], raw[2], al[2], inv[2];
+          bool act[2], live[2];
+          upk(pw, p[0], p[1]);
+          G[0] = ex2_approx(p[0]);
+          G[1] = ex2_approx(p[1]);
+          upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
 #pragma unroll
-          for (int r = 0; r < kRows; ++r) {
-            BwdPixel& qq = q[c * kRows + r];
-            const SplatEval e = eval_splat(sa, sb, fx[c], fy[r]);
-            if constexpr (kCount) n_eval += pos < qq.last ? 1u : 0u;
-            const bool act = (pos < qq.last) && !(e.p > 0.f) && !(e.alpha < kAlphaMin);
-            float dpow;
-            bwd_pixel(qq, e, sb, cb, act, g, dpow);
-            D += dpow;
-            E = fmaf(dpow, e.dy, E);
-            dx = e.dx;
+          for (int r = 0; r < 2; ++r) {
+            const int k = c * kRows + r;
+            al[r] = fminf(kAlphaMax, raw[r]);
+            if constexpr (kCount) n_eval += pos < last[k] ? 1u : 0u;
+            act[r] = (pos < last[k]) && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
+            live[r] = act[r] && !(raw[r] > kAlphaMax);     // alpha = 0.99 is constant
           }
+          const f2 AL = pk(al[0], al[1]);
+          upk(sub2(ONE, AL), inv[0], inv[1]);
+          inv[0] = rcp_approx(inv[0]);
+          inv[1] = rcp_approx(inv[1]);
+          // T before this splat where it was blended; Bd the colour behind it
+          float Tn[2], Tc[2];
+          upk(mul2(T2[c], pk(inv[0], inv[1])), Tn[0], Tn[1]);
+          upk(T2[c], Tc[0], Tc[1]);
+          Tc[0] = select_f(act[0], Tn[0], Tc[0]);
+          Tc[1] = select_f(act[1], Tn[1], Tc[1]);
+          T2[c] = pk(Tc[0], Tc[1]);
+          const f2 cd = fma2(R2, Q0[c], fma2(G2, Q1[c], mul2(Bl2, Q2[c])));
+          const f2 dal = fma2(T2[c], cd, mul2(Bd2[c], pk(-inv[0], -inv[1])));   // dL/dalpha
+          float wv[2];
+          upk(mul2(AL, T2[c]), wv[0], wv[1]);
+          wv[0] = select_f(act[0], wv[0], 0.f);
+          wv[1] = select_f(act[1], wv[1], 0.f);
+          const f2 w = pk(wv[0], wv[1]);
+          Bd2[c] = fma2(cd, w, Bd2[c]);
+          const f2 gd = mul2(pk(select_f(live[0], G[0], 0.f), select_f(live[1], G[1], 0.f)), dal);
+          const f2 dpow = mul2(O2, gd);                       // dL/d(power), natural units
+          const f2 pdy = mul2(dpow, dy);
+          g4 = fma2(pdy, dy, g4);
+          g5 = add2(g5, gd);
+          g6 = fma2(w, Q0[c], g6);
+          g7 = fma2(w, Q1[c], g7);
+          g8 = fma2(w, Q2[c], g8);
+          // the column's sums of dpow and dpow * dy (dx is shared by its rows)
+          float dp[2], pd[2];
+          upk(dpow, dp[0], dp[1]);
+          upk(pdy, pd[0], pd[1]);
+          const float D = dp[0] + dp[1];
+          const float E = fmaf(dp[1], dyv[1], pd[0]);
+          float dx, dxh;
+          upk(dx2, dx, dxh);
           const float t = dx * D;
           g[0] += t;
           g[1] += E;
           g[2] = fmaf(t, dx, g[2]);
           g[3] = fmaf(dx, E, g[3]);
         }
-        const float tot = warp_sum8_transposed(g, lane);
-        float g8 = g[8];
+        float gs[9] = {g[0], g[1], g[2], g[3], 0.f, 0.f, 0.f, 0.f, 0.f};
+        {
+          float lo4, hi4;
+          upk(g4, lo4, hi4); gs[4] = lo4 + hi4;
+          upk(g5, lo4, hi4); gs[5] = lo4 + hi4;
+          upk(g6, lo4, hi4); gs[6] = lo4 + hi4;
+          upk(g7, lo4, hi4); gs[7] = lo4 + hi4;
+          upk(g8, lo4, hi4); gs[8] = lo4 + hi4;
+        }
+        const float tot = warp_sum8_transposed(gs, lane);
+        float g8s = gs[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g8 += __shfl_xor_sync(0xffffffffu, g8, o);
+        for (int o = 16; o > 0; o >>= 1) g8s += __shfl_xor_sync(0xffffffffu, g8s, o);
         // one shared atomic per warp: lanes 4m add value m, lane 1 the ninth
         // sum, the rest add to their own sink word. Predicated atomics compiled
         // to divergent branches (two per splat).
         const bool own = (lane & 3u) == 0;
         float* dst = own ? &s_g[j][lane >> 2] : (lane == 1 ? &s_g[j][8] : &s_sink[threadIdx.x]);
-        red_shared(dst, select_f(own, tot, g8));
+        red_shared(dst, select_f(own, tot, g8s));
       }
     }
     __syncthreads();
@@ -646,7 +705,7 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
         float* dst = a.sp_grad + 12 * (size_t)s_id[i];
         // moments -> adjoints: power*log2(e) = dx (A2 dx + B2 dy) + C2 dy^2 with
         // dx = u - px, so d/du = ln 2 (2 A2 g0 + B2 g1), d/dv = ln 2 (B2 g0 + 2 C2 g1)
-        const float A2 = s_a[i].z, B2 = s_a[i].w, C2 = s_b[i].x;
+        const float A2 = s_p0[i].x, B2 = s_p0[i].z, C2 = s_p1[i].x;
         const float gu = kLn2 * fmaf(2.f * A2, sg[0], B2 * sg[1]);
         const float gv = kLn2 * fmaf(B2, sg[0], 2.f * C2 * sg[1]);
         red_v4(dst, gu, gv, -0.5f * sg[2], -sg[3]);
