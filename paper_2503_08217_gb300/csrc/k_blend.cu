@@ -3,7 +3,7 @@
 //
 // Forward: one CTA of two warps per tile, each warp a 16x8 band, four pixels
 // per lane, the two of a column evaluated as one packed f32x2 pair. The
-// tile's front-to-back splat list is consumed in batches of 128 staged in
+// tile's front-to-back splat list is consumed in batches of 64 staged in
 // shared memory (uv, base-2 conic, opacity, rgb as duplicated pairs, and the
 // box where the splat can reach alpha >= 1/255); per 32 splats a warp ballots which of
 // them can reach alpha >= 1/255 somewhere in its band (box, then the exact
@@ -27,7 +27,7 @@
 namespace s3r {
 namespace {
 
-constexpr int kBatchBwd = 128;                // splats staged per batch (backward)
+constexpr int kBatchBwd = 64;                // splats staged per batch (backward)
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
@@ -233,7 +233,7 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 // of the packed arithmetic comes straight from a 64-bit shared load. The
 // arithmetic is the exponent and alpha of stage_splat's comment, in that
 // order, so the backward's recomputation takes the same decisions.
-constexpr int kBatchFwd = 128;                // splats staged per batch (forward)
+constexpr int kBatchFwd = 64;                // splats staged per batch (forward)
 template <bool kCount>
 __global__ void __launch_bounds__(kBandThreads) k_blend_fwd(const __grid_constant__ ViewSet vs,
                                                             BlendArgs a) {
