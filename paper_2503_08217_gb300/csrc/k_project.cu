@@ -107,7 +107,9 @@ __global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __re
 // Pass 1: every selected Gaussian against every camera. Writes the frustum
 // and keep masks, applies Eq. 5 to the point life (on the frustum mask, before
 // LOD) and appends Gaussians kept in at least one view to the work list.
-__global__ void __launch_bounds__(kThreads) k_project_mask(const __grid_constant__ ViewSet vs,
+// six blocks per SM (40 registers, a small spill) measured 4 % faster than
+// the compiler's 64 registers
+__global__ void __launch_bounds__(kThreads, 6) k_project_mask(const __grid_constant__ ViewSet vs,
                                                            ProjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const InstMat* __restrict__ mats = a.mats;
