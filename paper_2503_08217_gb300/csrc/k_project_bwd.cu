@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     for (int i = 0; i < K * 3; ++i) g_sh[i] = 0.f;
     if (kmask) {
     const int k = segment_of(s_off, a.n_inst, gid);
-    uint32_t s = a.splat_start[j];
+    const uint32_t s0 = a.splat_start[j];
+    uint32_t s = s0;
 
     const float mu[3] = {a.means[3 * (size_t)gid], a.means[3 * (size_t)gid + 1],
                          a.means[3 * (size_t)gid + 2]};
@@ -178,20 +179,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     for (int i = 0; i < 9; ++i) g_RS[i] = 0.f;
     float g_ol = 0.f;
 
+    // Two passes over the kept views: the geometry (position, covariance and
+    // opacity adjoints), then the colour (SH and the view-direction term).
+    // The second pass recomputes the camera-relative position; the split
+    // keeps the 48 SH adjoints out of the registers of the first pass, whose
+    // chain is the longer one (fewer spills at the same occupancy).
     uint32_t m = kmask;
     while (m) {
       const int v = __ffs(m) - 1;
       m &= m - 1;
       const int64_t si = s++;
       if (si >= a.cap_splats) break;
-      const float4 ga = a.sp_grad[3 * si], gb = a.sp_grad[3 * si + 1], gc = a.sp_grad[3 * si + 2];
-      // a splat without adjoints (none of its pairs blended) adds nothing;
-      // skipping it also skips splats moved out of the frustum by Eq. 7
-      if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f &&
-          gb.z == 0.f && gb.w == 0.f && gc.x == 0.f)
+      const float4 ga = a.sp_grad[3 * si], gb = a.sp_grad[3 * si + 1];
+      // a splat without these adjoints (none of its pairs blended) adds
+      // nothing here; skipping it also skips splats moved out of the frustum
+      // by Eq. 7
+      if (ga.x == 0.f && ga.y == 0.f && ga.z == 0.f && ga.w == 0.f && gb.x == 0.f && gb.y == 0.f)
         continue;
       const float gu = ga.x, gv = ga.y, gA = ga.z, gB = ga.w, gC = gb.x, gO = gb.y;
-      const float grgb[3] = {gb.z, gb.w, gc.x};
       const InstMat& M = mats[v * nk + k];
       const ViewInfo& vi = s_views[v];
       const float* A = M.m;   // rows at 0, 4, 8; translation at 3, 7, 11
@@ -244,46 +249,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 
       // ---- opacity = sigmoid(logit)
       g_ol += gO * opac * (1.f - opac);
-
-      // ---- colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir from the camera centre
-      {
-        const float vx = rp[0], vy = rp[1], vz = rp[2];
-        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-        const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
-        float Y[16];
-        sh_basis<DEG>(dx, dy, dz, Y);
-        float graw[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          float acc = 0.5f;
-#pragma unroll
-          for (int i = 0; i < K; ++i) acc = fmaf(sh[3 * i + ch], Y[i], acc);
-          graw[ch] = acc < 0.f ? 0.f : grgb[ch];
-        }
-        float wk[16];
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-          g_sh[3 * i] += Y[i] * graw[0];
-          g_sh[3 * i + 1] += Y[i] * graw[1];
-          g_sh[3 * i + 2] += Y[i] * graw[2];
-          wk[i] = sh[3 * i] * graw[0] + sh[3 * i + 1] * graw[1] + sh[3 * i + 2] * graw[2];
-        }
-        if (DEG > 0) {
-          float gd[3];
-          sh_dir_grad<DEG>(dx, dy, dz, wk, gd);
-          const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
-          const float gv3[3] = {(gd[0] - dx * dd) * inv, (gd[1] - dy * dd) * inv,
-                                (gd[2] - dz * dd) * inv};
-          g_mu[0] += gv3[0]; g_mu[1] += gv3[1]; g_mu[2] += gv3[2];
-          // camera centre c = -A^{-1} b with gc = -gv3: dA = (A gv3) c^T, db = A gv3
-#pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const float t = A[4 * r] * gv3[0] + A[4 * r + 1] * gv3[1] + A[4 * r + 2] * gv3[2];
-            dA[3 * r] += t * M.c[0]; dA[3 * r + 1] += t * M.c[1]; dA[3 * r + 2] += t * M.c[2];
-            db[r] += t;
-          }
-        }
-      }
 
       // ---- conic = inverse of the dilated 2D covariance
       const float hb = 0.5f * gB;
@@ -367,10 +332,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     }
     const float4 g_q = quat_backward(q, dR);
 
-    if (a.g.means) {
-      float* p = a.g.means + 3 * (size_t)gid;
-      p[0] += g_mu[0]; p[1] += g_mu[1]; p[2] += g_mu[2];
-    }
     if (a.g.log_scales) {
       float* p = a.g.log_scales + 3 * (size_t)gid;
       p[0] += g_ls[0]; p[1] += g_ls[1]; p[2] += g_ls[2];
@@ -382,6 +343,88 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
       *p = o;
     }
     if (a.g.opacity_logits) a.g.opacity_logits[gid] += g_ol;
+
+    // ---- second pass: the colour of each kept view
+    m = kmask;
+    s = s0;
+    while (m) {
+      const int v = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t si = s++;
+      if (si >= a.cap_splats) break;
+      const float4 gb = a.sp_grad[3 * si + 1], gc = a.sp_grad[3 * si + 2];
+      if (gb.z == 0.f && gb.w == 0.f && gc.x == 0.f) continue;   // no colour adjoint
+      const float grgb[3] = {gb.z, gb.w, gc.x};
+      const InstMat& M = mats[v * nk + k];
+      const float* A = M.m;
+      float mv[3] = {mu[0], mu[1], mu[2]};
+      if (a.sp_view[si] & kSplatMoved) {
+        float rp0[3], x0, y0, z0;
+        rel_pos(M, mu, rp0);
+        cam_pos(M, rp0, x0, y0, z0);
+        lod_noisy_mean(a.L, gid, (uint32_t)v, epoch, z0, mu, mv);
+      }
+      float rp[3];
+      rel_pos(M, mv, rp);
+      float dA[9], db[3];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) dA[i] = 0.f;
+      db[0] = db[1] = db[2] = 0.f;
+      // ---- colour: rgb = max(0, sum_k sh_k Y_k(dir) + 0.5), dir from the camera centre
+      {
+        const float vx = rp[0], vy = rp[1], vz = rp[2];
+        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        const float dx = vx * inv, dy = vy * inv, dz = vz * inv;
+        float Y[16];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float graw[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float acc = 0.5f;
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc = fmaf(sh[3 * i + ch], Y[i], acc);
+          graw[ch] = acc < 0.f ? 0.f : grgb[ch];
+        }
+        float wk[16];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          g_sh[3 * i] += Y[i] * graw[0];
+          g_sh[3 * i + 1] += Y[i] * graw[1];
+          g_sh[3 * i + 2] += Y[i] * graw[2];
+          wk[i] = sh[3 * i] * graw[0] + sh[3 * i + 1] * graw[1] + sh[3 * i + 2] * graw[2];
+        }
+        if (DEG > 0) {
+          float gd[3];
+          sh_dir_grad<DEG>(dx, dy, dz, wk, gd);
+          const float dd = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+          const float gv3[3] = {(gd[0] - dx * dd) * inv, (gd[1] - dy * dd) * inv,
+                                (gd[2] - dz * dd) * inv};
+          g_mu[0] += gv3[0]; g_mu[1] += gv3[1]; g_mu[2] += gv3[2];
+          // camera centre c = -A^{-1} b with gc = -gv3: dA = (A gv3) c^T, db = A gv3
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float t = A[4 * r] * gv3[0] + A[4 * r + 1] * gv3[1] + A[4 * r + 2] * gv3[2];
+            dA[3 * r] += t * M.c[0]; dA[3 * r + 1] += t * M.c[1]; dA[3 * r + 2] += t * M.c[2];
+            db[r] += t;
+          }
+        }
+      }
+
+      if (DEG > 0 && k > 0) {
+        float* dst = s_dM + (v * nk + k) * 12;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          atomicAdd(dst + 4 * r, dA[3 * r]);
+          atomicAdd(dst + 4 * r + 1, dA[3 * r + 1]);
+          atomicAdd(dst + 4 * r + 2, dA[3 * r + 2]);
+          atomicAdd(dst + 4 * r + 3, db[r]);
+        }
+      }
+    }
+    if (a.g.means) {
+      float* p = a.g.means + 3 * (size_t)gid;
+      p[0] += g_mu[0]; p[1] += g_mu[1]; p[2] += g_mu[2];
+    }
     }
     // SH adjoints: each lane writes its row over its (consumed) SH row, then
     // the warp adds the rows to the caller's buffer with coalesced accesses
