@@ -234,6 +234,66 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 // arithmetic is the exponent and alpha of stage_splat's comment, in that
 // order, so the backward's recomputation takes the same decisions.
 constexpr int kBatchFwd = 64;                // splats staged per batch (forward)
+// One splat of the forward's walk over a warp's four pixels per lane (two
+// packed pairs). kClamp: the splat's opacity exceeds 0.99, so alpha = o G may
+// reach the 0.99 cap; for o <= 0.99 it cannot (G <= 1 where p <= 0), and the
+// clamp is left out (the backward takes the same branch per splat).
+template <bool kCount, bool kClamp>
+__device__ __forceinline__ void fwd_splat(const float4 q0, const float4 q1, const float4 q2,
+                                          const float4 q3, const float2 qu, const f2 FY,
+                                          const f2 (&FX)[2], const f2 ONE, int pos, f2 (&T2)[2],
+                                          f2 (&C2)[2][3], int (&last)[kBandPix],
+                                          int (&endp)[kBandPix], bool (&done)[kBandPix],
+                                          uint32_t& n_eval, bool& any_blend) {
+  const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
+  const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
+  const f2 U2 = pk(qu.x, qu.y);
+  // the rows' dy and the dy terms of the exponent, shared by both columns
+  const f2 dy = sub2(V2, FY);
+  const f2 bdy = mul2(B2, dy);
+  const f2 cdy = mul2(mul2(C2c, dy), dy);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const f2 dx = sub2(U2, FX[c]);
+    const f2 pw = fma2(dx, fma2(A2, dx, bdy), cdy);
+    float p[2], G[2];
+    upk(pw, p[0], p[1]);
+    G[0] = ex2_approx(p[0]);
+    G[1] = ex2_approx(p[1]);
+    float raw[2];
+    upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
+    float al[2], ab[2];
+    bool blend[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int k = c * kBandRows + r;
+      al[r] = kClamp ? fminf(kAlphaMax, raw[r]) : raw[r];
+      if constexpr (kCount) n_eval += done[k] ? 0u : 1u;
+      blend[r] = !done[k] && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
+    }
+    float nT[2];
+    upk(mul2(T2[c], sub2(ONE, pk(al[0], al[1]))), nT[0], nT[1]);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int k = c * kBandRows + r;
+      const bool stop = blend[r] && (nT[r] < kTStop);
+      blend[r] = blend[r] && !stop;
+      // one select: T (1 - 0) = T exactly where the splat is not blended
+      ab[r] = blend[r] ? al[r] : 0.f;
+      last[k] = blend[r] ? pos : last[k];
+      if constexpr (kCount) endp[k] = stop ? pos : endp[k];
+      done[k] = done[k] || stop;
+      any_blend = any_blend || blend[r];
+    }
+    const f2 AB = pk(ab[0], ab[1]);
+    const f2 w = mul2(AB, T2[c]);
+    C2[c][0] = fma2(R2, w, C2[c][0]);
+    C2[c][1] = fma2(G2, w, C2[c][1]);
+    C2[c][2] = fma2(Bl2, w, C2[c][2]);
+    T2[c] = mul2(T2[c], sub2(ONE, AB));
+  }
+}
+
 // 20 blocks per SM (48 registers, a small spill) measured fastest: 16 (64
 // registers) 6 % slower, 22 and 24 11 % slower.
 template <bool kCount>
@@ -316,55 +376,15 @@ __global__ void __launch_bounds__(kBandThreads, 20) k_blend_fwd(const __grid_con
         todo &= todo - 1;
         const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
         const float2 qu = s_u[j];
-        const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
-        const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
-        const f2 U2 = pk(qu.x, qu.y);
         const int pos = b0 + j + 1;
-        // the rows' dy and the dy terms of the exponent, shared by both columns
-        const f2 dy = sub2(V2, FY);
-        const f2 bdy = mul2(B2, dy);
-        const f2 cdy = mul2(mul2(C2c, dy), dy);
         bool any_blend = false;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const f2 dx = sub2(U2, FX[c]);
-          const f2 pw = fma2(dx, fma2(A2, dx, bdy), cdy);
-          float p[2], G[2];
-          upk(pw, p[0], p[1]);
-          G[0] = ex2_approx(p[0]);
-          G[1] = ex2_approx(p[1]);
-          float raw[2];
-          upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
-          float al[2], ab[2];
-          bool blend[2];
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int k = c * kBandRows + r;
-            al[r] = fminf(kAlphaMax, raw[r]);
-            if constexpr (kCount) n_eval += done[k] ? 0u : 1u;
-            blend[r] = !done[k] && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
-          }
-          float nT[2];
-          upk(mul2(T2[c], sub2(ONE, pk(al[0], al[1]))), nT[0], nT[1]);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int k = c * kBandRows + r;
-            const bool stop = blend[r] && (nT[r] < kTStop);
-            blend[r] = blend[r] && !stop;
-            // one select: T (1 - 0) = T exactly where the splat is not blended
-            ab[r] = blend[r] ? al[r] : 0.f;
-            last[k] = blend[r] ? pos : last[k];
-            if constexpr (kCount) endp[k] = stop ? pos : endp[k];
-            done[k] = done[k] || stop;
-            any_blend = any_blend || blend[r];
-          }
-          const f2 AB = pk(ab[0], ab[1]);
-          const f2 w = mul2(AB, T2[c]);
-          C2[c][0] = fma2(R2, w, C2[c][0]);
-          C2[c][1] = fma2(G2, w, C2[c][1]);
-          C2[c][2] = fma2(Bl2, w, C2[c][2]);
-          T2[c] = mul2(T2[c], sub2(ONE, AB));
-        }
+        // warp-uniform: every lane walks the same splat
+        if (q1.z > kAlphaMax)
+          fwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
+                                  n_eval, any_blend);
+        else
+          fwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
+                                   n_eval, any_blend);
         all_done = true;
 #pragma unroll
         for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
@@ -499,6 +519,90 @@ __device__ __forceinline__ void bwd_init(BwdPixel& q, const BlendArgs& a, const 
   q.Bd = q.T * (a.bg[0] * q.d0 + a.bg[1] * q.d1 + a.bg[2] * q.d2);
 }
 
+// One splat of the backward's walk (see above) over a lane's two packed
+// pixel pairs: updates T and Bd, returns the lane's shares of the nine sums
+// (g0..g3 scalar, g4..g8 as row pairs). kClamp as for fwd_splat, per splat.
+template <bool kCount, bool kClamp>
+__device__ __forceinline__ void bwd_splat(const float4 q0, const float4 q1, const float4 q2,
+                                          const float4 q3, const float2 qu, const f2 FY,
+                                          const f2 (&FX)[2], const f2 ONE, int pos,
+                                          const int (&last)[kBandPix], f2 (&T2)[2], f2 (&Bd2)[2],
+                                          const f2 (&Q0)[2], const f2 (&Q1)[2], const f2 (&Q2)[2],
+                                          uint32_t& n_eval, float (&g)[4], f2& g4, f2& g5, f2& g6,
+                                          f2& g7, f2& g8) {
+  constexpr int kRows = kBandRows;
+  const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
+  const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
+  const f2 U2 = pk(qu.x, qu.y);
+  const f2 dy = sub2(V2, FY);
+  const f2 bdy = mul2(B2, dy);
+  const f2 cdy = mul2(mul2(C2c, dy), dy);
+  float dyv[2];
+  upk(dy, dyv[0], dyv[1]);
+  g[0] = g[1] = g[2] = g[3] = 0.f;
+  g4 = g5 = g6 = g7 = g8 = pk(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const f2 dx2 = sub2(U2, FX[c]);
+    const f2 pw = fma2(dx2, fma2(A2, dx2, bdy), cdy);
+    float p[2], G[2], raw[2], al[2], inv[2];
+    bool act[2], live[2];
+    upk(pw, p[0], p[1]);
+    G[0] = ex2_approx(p[0]);
+    G[1] = ex2_approx(p[1]);
+    upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int k = c * kRows + r;
+      al[r] = kClamp ? fminf(kAlphaMax, raw[r]) : raw[r];
+      if constexpr (kCount) n_eval += pos < last[k] ? 1u : 0u;
+      act[r] = (pos < last[k]) && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
+      // alpha = 0.99 is constant in o; without the cap alpha = o G throughout
+      live[r] = kClamp ? act[r] && !(raw[r] > kAlphaMax) : act[r];
+    }
+    const f2 AL = pk(al[0], al[1]);
+    upk(sub2(ONE, AL), inv[0], inv[1]);
+    inv[0] = rcp_approx(inv[0]);
+    inv[1] = rcp_approx(inv[1]);
+    // T before this splat where it was blended; Bd the colour behind it
+    float Tn[2], Tc[2];
+    upk(mul2(T2[c], pk(inv[0], inv[1])), Tn[0], Tn[1]);
+    upk(T2[c], Tc[0], Tc[1]);
+    Tc[0] = select_f(act[0], Tn[0], Tc[0]);
+    Tc[1] = select_f(act[1], Tn[1], Tc[1]);
+    T2[c] = pk(Tc[0], Tc[1]);
+    const f2 cd = fma2(R2, Q0[c], fma2(G2, Q1[c], mul2(Bl2, Q2[c])));
+    const f2 dal = fma2(T2[c], cd, mul2(Bd2[c], pk(-inv[0], -inv[1])));   // dL/dalpha
+    float wv[2];
+    upk(mul2(AL, T2[c]), wv[0], wv[1]);
+    wv[0] = select_f(act[0], wv[0], 0.f);
+    wv[1] = select_f(act[1], wv[1], 0.f);
+    const f2 w = pk(wv[0], wv[1]);
+    Bd2[c] = fma2(cd, w, Bd2[c]);
+    const f2 gd = mul2(pk(select_f(live[0], G[0], 0.f), select_f(live[1], G[1], 0.f)), dal);
+    const f2 dpow = mul2(O2, gd);                       // dL/d(power), natural units
+    const f2 pdy = mul2(dpow, dy);
+    g4 = fma2(pdy, dy, g4);
+    g5 = add2(g5, gd);
+    g6 = fma2(w, Q0[c], g6);
+    g7 = fma2(w, Q1[c], g7);
+    g8 = fma2(w, Q2[c], g8);
+    // the column's sums of dpow and dpow * dy (dx is shared by its rows)
+    float dp[2], pd[2];
+    upk(dpow, dp[0], dp[1]);
+    upk(pdy, pd[0], pd[1]);
+    const float D = dp[0] + dp[1];
+    const float E = fmaf(dp[1], dyv[1], pd[0]);
+    float dx, dxh;
+    upk(dx2, dx, dxh);
+    const float t = dx * D;
+    g[0] += t;
+    g[1] += E;
+    g[2] = fmaf(t, dx, g[2]);
+    g[3] = fmaf(dx, E, g[3]);
+  }
+}
+
 // The reverse walk evaluates a lane's two pixels of a column (rows y and
 // y + 4) as one packed pair, like the forward: the splat is staged as
 // duplicated pairs, the per-pixel state (T, Bd, dL/dC) is held as pairs per
@@ -606,76 +710,16 @@ __global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
         const int j = c0 + bit;
         const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
         const float2 qu = s_u[j];
-        const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
-        const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
-        const f2 U2 = pk(qu.x, qu.y);
         const int pos = lo + j;
-        const f2 dy = sub2(V2, FY);
-        const f2 bdy = mul2(B2, dy);
-        const f2 cdy = mul2(mul2(C2c, dy), dy);
-        float dyv[2];
-        upk(dy, dyv[0], dyv[1]);
-        float g[4] = {0.f, 0.f, 0.f, 0.f};
-        f2 g4 = pk(0.f, 0.f), g5 = g4, g6 = g4, g7 = g4, g8 = g4;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const f2 dx2 = sub2(U2, FX[c]);
-          const f2 pw = fma2(dx2, fma2(A2, dx2, bdy), cdy);
-          float p[2], G[2], raw[2], al[2], inv[2];
-          bool act[2], live[2];
-          upk(pw, p[0], p[1]);
-          G[0] = ex2_approx(p[0]);
-          G[1] = ex2_approx(p[1]);
-          upk(mul2(O2, pk(G[0], G[1])), raw[0], raw[1]);
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int k = c * kRows + r;
-            al[r] = fminf(kAlphaMax, raw[r]);
-            if constexpr (kCount) n_eval += pos < last[k] ? 1u : 0u;
-            act[r] = (pos < last[k]) && !(p[r] > 0.f) && !(al[r] < kAlphaMin);
-            live[r] = act[r] && !(raw[r] > kAlphaMax);     // alpha = 0.99 is constant
-          }
-          const f2 AL = pk(al[0], al[1]);
-          upk(sub2(ONE, AL), inv[0], inv[1]);
-          inv[0] = rcp_approx(inv[0]);
-          inv[1] = rcp_approx(inv[1]);
-          // T before this splat where it was blended; Bd the colour behind it
-          float Tn[2], Tc[2];
-          upk(mul2(T2[c], pk(inv[0], inv[1])), Tn[0], Tn[1]);
-          upk(T2[c], Tc[0], Tc[1]);
-          Tc[0] = select_f(act[0], Tn[0], Tc[0]);
-          Tc[1] = select_f(act[1], Tn[1], Tc[1]);
-          T2[c] = pk(Tc[0], Tc[1]);
-          const f2 cd = fma2(R2, Q0[c], fma2(G2, Q1[c], mul2(Bl2, Q2[c])));
-          const f2 dal = fma2(T2[c], cd, mul2(Bd2[c], pk(-inv[0], -inv[1])));   // dL/dalpha
-          float wv[2];
-          upk(mul2(AL, T2[c]), wv[0], wv[1]);
-          wv[0] = select_f(act[0], wv[0], 0.f);
-          wv[1] = select_f(act[1], wv[1], 0.f);
-          const f2 w = pk(wv[0], wv[1]);
-          Bd2[c] = fma2(cd, w, Bd2[c]);
-          const f2 gd = mul2(pk(select_f(live[0], G[0], 0.f), select_f(live[1], G[1], 0.f)), dal);
-          const f2 dpow = mul2(O2, gd);                       // dL/d(power), natural units
-          const f2 pdy = mul2(dpow, dy);
-          g4 = fma2(pdy, dy, g4);
-          g5 = add2(g5, gd);
-          g6 = fma2(w, Q0[c], g6);
-          g7 = fma2(w, Q1[c], g7);
-          g8 = fma2(w, Q2[c], g8);
-          // the column's sums of dpow and dpow * dy (dx is shared by its rows)
-          float dp[2], pd[2];
-          upk(dpow, dp[0], dp[1]);
-          upk(pdy, pd[0], pd[1]);
-          const float D = dp[0] + dp[1];
-          const float E = fmaf(dp[1], dyv[1], pd[0]);
-          float dx, dxh;
-          upk(dx2, dx, dxh);
-          const float t = dx * D;
-          g[0] += t;
-          g[1] += E;
-          g[2] = fmaf(t, dx, g[2]);
-          g[3] = fmaf(dx, E, g[3]);
-        }
+        float g[4];
+        f2 g4, g5, g6, g7, g8;
+        // warp-uniform: every lane walks the same splat
+        if (q1.z > kAlphaMax)
+          bwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
+                                  n_eval, g, g4, g5, g6, g7, g8);
+        else
+          bwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
+                                   n_eval, g, g4, g5, g6, g7, g8);
         float gs[9] = {g[0], g[1], g[2], g[3], 0.f, 0.f, 0.f, 0.f, 0.f};
         {
           float lo4, hi4;
