@@ -40,8 +40,8 @@ METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM r
 # source file is the one the counters were taken on (first 16 hex digits of
 # its SHA-256); otherwise the roofline line reports traffic null.
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 307919616, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
-                  "sha256_16": "a7a1596253ccb214", "profile": "profiles/blend_bwd_traffic_rig.md"},
+    "blend_bwd": {"bytes": 307897856, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
+                  "sha256_16": "51d1bc1273a44730", "profile": "profiles/blend_bwd_traffic_rig.md"},
 }
 
 
