@@ -248,6 +248,21 @@ typedef struct {
 s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
                          float beta2, float eps, int32_t step, void* stream);
 
+/* The conventional pipeline of Fig. 1(a), the comparator that the
+ * instance-specific projection of Sec. 3.3 replaces: every Gaussian of a
+ * dynamic instance k is moved to the world frame by its pose at time t,
+ *   mu_w = R(q_k/|q_k|) mu + t_k,   q_w = (q_k/|q_k|) (x) (q/|q|)
+ * (Hamilton product, so R(q_w) = R(q_k) R(q)); static Gaussians are copied
+ * with their quaternion normalised. scene and poses as for s3r_project (only
+ * means, quats and inst_offsets are read); means_out [n,3] (4-B aligned) and
+ * quats_out [n,4] (16-B aligned) are caller-owned device arrays written on
+ * `stream`. A scene of them with no instances (inst_offsets {0, n}) renders
+ * the same geometry through s3r_project, with the SH of dynamic Gaussians
+ * evaluated on the world-frame view direction. S3R_ERR_INVALID on NULL or
+ * misaligned arrays, nothing launched. */
+s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* means_out,
+                        float* quats_out, void* stream);
+
 /* Level of detail (Sec. 3.3 "Adaptive LOD", Eq. 7). In the default
  * S3R_LOD_THRESHOLD mode every in-frustum Gaussian whose projected 2D scale
  * (square root of the largest eigenvalue of the undilated 2D covariance, in

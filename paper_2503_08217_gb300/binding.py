@@ -26,7 +26,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
-           "s3r_adam_step", "s3r_set_lod", "s3r_set_counting")
+           "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
     L.s3r_set_counting.argtypes = [vp, i32]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
+    L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp]
     L.s3r_kernel_count.restype = i32
     L.s3r_kernel_name.argtypes = [i32]
     L.s3r_kernel_name.restype = ctypes.c_char_p
@@ -322,6 +323,13 @@ def select_visible_static(vis_window, t: float, out_idx, out_count, stream=None)
     n = int(vis_window.shape[0]) if vis_window is not None else 0
     _check(load().s3r_select_visible_static(n, float(t), _ptr(vis_window), _ptr(out_idx),
                                             _ptr(out_count), _stream(stream)))
+
+
+def to_world(c_scene, poses, means_out, quats_out, stream=None):
+    """The conventional local-to-world transform (see s3r_to_world): writes
+    the world-frame means [n,3] and unit quaternions [n,4]."""
+    _check(load().s3r_to_world(ctypes.byref(c_scene), ctypes.byref(poses), _ptr(means_out),
+                               _ptr(quats_out), _stream(stream)))
 
 
 def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1: float = 0.9,

@@ -443,6 +443,32 @@ s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr
   return S3R_OK;
 }
 
+s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* means_out,
+                        float* quats_out, void* stream) {
+  if (!scene) return fail(S3R_ERR_INVALID, "NULL scene");
+  if (scene->n < 0 || scene->n > 0xffffffffLL) return fail(S3R_ERR_INVALID, "n outside [0, 2^32)");
+  if (scene->n_inst < 0) return fail(S3R_ERR_INVALID, "n_inst < 0");
+  if (!scene->inst_offsets || !aligned(scene->inst_offsets, 8))
+    return fail(S3R_ERR_INVALID, "inst_offsets must be an 8-byte aligned array");
+  if (scene->n == 0) return S3R_OK;
+  if (!scene->means || !scene->quats || !means_out || !quats_out)
+    return fail(S3R_ERR_INVALID, "means, quats and both outputs are required");
+  if (!aligned(scene->means, 4) || !aligned(means_out, 4) || !aligned(scene->quats, 16) ||
+      !aligned(quats_out, 16))
+    return fail(S3R_ERR_INVALID, "means 4-byte and quaternions 16-byte aligned required");
+  s3r_status st = check_poses(scene, poses);
+  if (st != S3R_OK) return st;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "to_world: device query");
+  const s3r_poses none = {nullptr, nullptr};
+  e = launch_to_world(scene, poses ? poses : &none, means_out, quats_out, sms > 0 ? sms : 1,
+                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "to_world");
+  return S3R_OK;
+}
+
 s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float* dL_dpred,
                        float* loss_out, void* stream) {
   if (n < 0) return fail(S3R_ERR_INVALID, "n < 0");

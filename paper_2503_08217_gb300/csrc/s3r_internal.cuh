@@ -179,6 +179,8 @@ cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float
 cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                            float t, float* life, float lod, cudaStream_t st);
 cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st);
+cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* means_out,
+                            float* quats_out, int num_sms, cudaStream_t st);
 cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cudaStream_t st);
 cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* dL,
                               cudaStream_t st);

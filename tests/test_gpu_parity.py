@@ -497,6 +497,62 @@ def test_needle_splats_keep_their_rectangles(built, tiny, tiny_vis):
     _stage_isolated_sort(res, cams)
 
 
+def test_conventional_world_transform_matches_oracle(built, tiny, tiny_vis):
+    """Fig. 1(a): s3r_to_world, then the projection and blend of the
+    transformed scene without instances, against the oracle's conventional
+    path (the transform in FP64, then the camera alone): every splat record of
+    a Gaussian away from a threshold, and the images (the tiny scene's colours
+    are SH0, so the view direction's frame does not matter)."""
+    import copy
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    from paper_2503_08217_gb300.render import DeviceScene
+    vis, _ = tiny_vis
+    step = 4
+    cams = tiny.cams[step]
+    dev = DeviceScene.from_host(tiny)
+    iq = torch.from_numpy(np.ascontiguousarray(tiny.inst_quat[step], np.float32)).cuda()
+    it = torch.from_numpy(np.ascontiguousarray(tiny.inst_trans[step], np.float32)).cuda()
+    mw = torch.empty_like(dev.means)
+    qw = torch.empty_like(dev.quats)
+    binding.to_world(dev.c_scene(), binding.make_poses(iq, it), mw, qw)
+    torch.cuda.synchronize()
+    world = copy.deepcopy(tiny)
+    world.means = mw.cpu().numpy()
+    world.quats = qw.cpu().numpy()
+    world.inst_offsets = np.array([0, tiny.n], np.int64)     # no instances
+    world.inst_quat = np.zeros((tiny.n_steps, 0, 4), np.float32)
+    world.inst_trans = np.zeros((tiny.n_steps, 0, 3), np.float32)
+    res = gpu_helpers.gpu_step(world, step, cams, vis)
+    sel = res["selected"]
+    gids = gpu_helpers.splat_gids(res)
+    j_of = np.searchsorted(sel, gids)
+    dynamic = gids >= tiny.inst_offsets[1]
+    checked = 0
+    for v, cam in enumerate(cams):
+        rec = oracle.project(tiny, sel, step, cam, 0.0, conventional=True)
+        mine = np.nonzero(res["view"] == v)[0]
+        j = j_of[mine]
+        ok = ~rec["near"][j]
+        assert ok.mean() > 0.99 and dynamic[mine].any()
+        s, jj = mine[ok], j[ok]
+        np.testing.assert_allclose(res["xy"][s], rec["uv"][jj], rtol=1e-5, atol=2e-4)
+        scale = np.abs(rec["conic"][jj]).max(axis=1, keepdims=True)
+        assert (np.abs(res["conic_o"][s, :3] - rec["conic"][jj]) <= 1e-3 * np.abs(rec["conic"][jj]) + 1e-5 * scale).all()
+        np.testing.assert_array_equal(res["rect"][s], rec["rect"][jj])
+        np.testing.assert_allclose(res["rgb_d"][s, :3], rec["rgb"][jj], atol=2e-5)
+        checked += s.size
+        # every kept Gaussian of the oracle has a splat here and vice versa
+        kept = np.nonzero(rec["kept"] & ~rec["near"])[0]
+        assert np.isin(kept, j).all()
+        o = oracle.render(cam.width, cam.height, oracle.select_splats(rec))
+        bad = gpu_helpers.bad_pixels(cam, rec, o["flag"])
+        diff = np.abs(res["images"][v] - o["image"]).max(axis=0)
+        assert diff[~bad].max() <= 1e-4, (v, float(diff[~bad].max()))
+        assert bad.mean() < 0.15
+    assert checked > 1000
+
+
 def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
     import gpu_helpers
     from paper_2503_08217_gb300 import binding
