@@ -89,6 +89,10 @@ def parse():
     p.add_argument("--lod-seed", type=int, default=2025)
     p.add_argument("--no-temporal", action="store_true",
                    help="select every Gaussian (windows [-1, 1]) instead of the recorded windows")
+    p.add_argument("--conventional", action="store_true",
+                   help="the conventional pipeline of Fig. 1(a): every step moves the dynamic "
+                        "Gaussians to the world frame (s3r_to_world) and renders the scene without "
+                        "instances, every Gaussian selected and no LOD")
     p.add_argument("--sweep", default=None, choices=("scale",),
                    help="scale: per-view fwd+bwd time of the large corridor stretched at constant "
                         "density, with the temporal record and with every Gaussian visible")
@@ -261,6 +265,9 @@ def run_ours(args, rank, world, local):
     scene, lod, desc = make_workload(args.workload, args.seed)
     if args.lod_r is not None:
         lod = float(args.lod_r)
+    if args.conventional:
+        lod = 0.0
+        args.no_temporal = True
     k = step_index(scene, rank)
     cams = scene.cams[k]
     n_views = len(cams)
@@ -310,11 +317,27 @@ def run_ours(args, rank, world, local):
              "sh": torch.zeros_like(dev.sh), "inst_quat": torch.zeros_like(iq),
              "inst_trans": torch.zeros_like(it)}
 
+    if args.conventional:
+        # Fig. 1(a): the world-frame copy of the scene, rendered without instances
+        mw = torch.empty_like(dev.means)
+        qw = torch.empty_like(dev.quats)
+        cs_w = binding.make_scene(mw, dev.log_scales, qw, dev.opacity_logits, dev.sh,
+                                  torch.tensor([0, n], dtype=torch.int64, device=dev_name),
+                                  dev.sh_degree)
+        no_q = torch.zeros((0, 4), device=dev_name)
+        no_t = torch.zeros((0, 3), device=dev_name)
+
     def make_step(tgt, iq_, it_):
         def step_fn():
             for g in grads.values():
                 g.zero_()
             loss.zero_()
+            if args.conventional:
+                binding.to_world(cs, binding.make_poses(iq_, it_), mw, qw)
+                r.forward(dev, no_q, no_t, cams, t, vis, life, lod, bg, out=out, c_scene=cs_w)
+                binding.l1_loss(out, tgt, dL, loss)
+                r.backward(dev, no_q, no_t, bg, dL, grads, c_scene=cs_w)
+                return
             r.forward(dev, iq_, it_, cams, t, vis, life, lod, bg, out=out, c_scene=cs)
             binding.l1_loss(out, tgt, dL, loss)
             r.backward(dev, iq_, it_, bg, dL, grads, c_scene=cs)
@@ -408,7 +431,10 @@ def run_ours(args, rank, world, local):
             roof.update(bound="alu", achieved=table[dom]["gops"], peak=round(alu_peak_gops, 1),
                         unit="Gop/s (FP32)", frac=table[dom]["frac"],
                         peak_source="152 SMs x 128 FP32 lanes x max SM clock")
-    launches_per_step = len(kmean) + 1      # + the L1 loss kernel
+    # the timed kernels, plus untimed ones of ours: the L1 loss, the three small
+    # zero fills (tile ranges, contributor bits, pose-adjoint sums) and, for the
+    # conventional pipeline, the world transform
+    launches_per_step = len(kmean) + 4 + (1 if args.conventional else 0)
 
     # --- plain per-view comparator: the same library, one camera per call, eager
     plain = None
@@ -560,6 +586,10 @@ def run_ours(args, rank, world, local):
                        "cameras": n_views, "pixels_per_view_batch": P, "timestep": k,
                        "sh_degree": scene.sh_degree, "lod_px": lod, "lod": lod_cfg,
                        "temporal_selection": not args.no_temporal,
+                       **({"pipeline": "conventional (Fig. 1(a)): dynamic Gaussians moved to the world "
+                                       "frame every step, rendered without instances; gradients "
+                                       "stop at the world-frame parameters (the transform's "
+                                       "backward is not run)"} if args.conventional else {}),
                        "l2": "flushed (512 MiB write) between timed steps, outside the timed events",
                        "graph": "whole step captured as one CUDA graph",
                        "parallelism": f"replicas x{world}, one timestep per rank, no collective"},
