@@ -4,10 +4,12 @@
 // every instance pose.
 //
 // One thread per kept Gaussian (a warp takes 32 consecutive entries of the
-// forward's work list) loops over its kept views (its splats are contiguous),
-// recomputes the forward intermediates of each view, and accumulates the
-// parameter adjoints in registers; the owning thread then adds them to the
-// caller's buffers (no atomics: a Gaussian has one thread). The SH rows are
+// forward's work list) walks its kept views (its splats are contiguous)
+// twice: first the geometry (recomputing the forward intermediates of each
+// view: position, covariance, opacity and pose adjoints), then the colour
+// (SH and the view-direction term), accumulating the parameter adjoints in
+// registers; the owning thread then adds them to the caller's buffers (no
+// atomics: a Gaussian has one thread). The SH rows are
 // read, and their adjoints added, through shared memory with coalesced
 // accesses of the whole warp.
 // Adjoints of the composed 3x4 matrices are summed per (view, instance) in

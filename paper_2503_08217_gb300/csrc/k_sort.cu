@@ -3,12 +3,13 @@
 //
 // The sorted order is the one of a stable LSD radix sort on the 64-bit key
 // (view-tile id << 32 | FP32 depth bits) over the duplicated pairs in
-// projection order. Duplicates of one splat share its depth, so the four
+// projection order (the pairs of the tiles a splat's alpha region reaches,
+// see the expansion below). Duplicates of one splat share its depth, so the four
 // depth-digit passes run on the splats BEFORE duplication (S keys instead of
 // K); the splats are then expanded into (tile, splat) pairs in depth order,
 // and the one or two tile-digit passes finish the sort. Every pass is a
 // single-pass "onesweep" kernel: persistent CTAs take 3840-key tiles from an
-// atomic counter, rank digits with nine warp ballots per key (faster here than
+// atomic counter, rank digits with eight warp ballots per key (faster here than
 // match.any, which queues on the address-divergence unit), get each digit's global
 // offset from a precomputed histogram plus a decoupled look-back over tiles,
 // reorder the tile in shared memory and write it out coalesced.
