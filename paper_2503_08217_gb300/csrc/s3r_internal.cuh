@@ -122,7 +122,7 @@ struct s3r_workspace {
   float* sp_region;         // [S] x 8: that region, where the row table had no room
   uint32_t* row_spans;      // [rows_cap] column interval of one rectangle row
   int64_t rows_cap;
-  uint32_t* dup_chunk;      // [K/4096 + 2] sorted splat holding the first pair of each 4096-pair chunk
+  uint32_t* dup_chunk;      // [K/kDupChunkMin + 2] sorted splat holding the first pair of each expansion chunk
   uint32_t* contrib;        // [4][K/32 + 2] bit per (warp block, sorted pair): blended in the forward
   int64_t contrib_words;    // words per warp block
   int64_t bytes;
