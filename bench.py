@@ -17,6 +17,8 @@ the public API with host buffers, and the SM clocks seen while timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rig|mid|large|tiny|small-rig]
   python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
+  python bench.py --conventional ...     # the Fig. 1(a) pipeline (world transform, no LOD)
+  python bench.py --sweep scale          # per-view time against scene size
 """
 from __future__ import annotations
 
