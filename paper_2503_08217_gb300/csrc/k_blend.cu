@@ -236,8 +236,10 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 constexpr int kBatchFwd = 64;                // splats staged per batch (forward)
 // One splat of the forward's walk over a warp's four pixels per lane (two
 // packed pairs). kClamp: the splat's opacity exceeds 0.99, so alpha = o G may
-// reach the 0.99 cap; for o <= 0.99 it cannot (G <= 1 where p <= 0), and the
-// clamp is left out (the backward takes the same branch per splat).
+// reach the 0.99 cap; for o <= 0.99 it cannot (G = 2^p <= 1 where p <= 0, up
+// to the last ulp of ex2.approx at p = 0), and the clamp is left out. The
+// backward takes the same branch per splat, and the FP64 o G of the exact
+// definition never reaches the cap for those splats either.
 template <bool kCount, bool kClamp>
 __device__ __forceinline__ void fwd_splat(const float4 q0, const float4 q1, const float4 q2,
                                           const float4 q3, const float2 qu, const f2 FY,
