@@ -39,23 +39,52 @@ METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM r
 
 # DRAM bytes (read + write) per launch of a kernel at the rig workload, from
 # one ncu capture (summarised under profiles/), valid only while the kernel's
-# source file is the one the counters were taken on (first 16 hex digits of
-# its SHA-256); otherwise the roofline line reports traffic null.
+# source code is the one the counters were taken on: the first 16 hex digits
+# of the SHA-256 of the file with its comments and blank lines removed (code
+# hash), so that a comment edit keeps the figure and any code edit drops it
+# (the roofline line then reports traffic null).
 NCU_TRAFFIC = {
     "blend_bwd": {"bytes": 307897856, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
-                  "sha256_16": "51d1bc1273a44730", "profile": "profiles/blend_bwd_traffic_rig.md"},
+                  "code_sha256_16": "8b008ae8b64cd83d", "profile": "profiles/blend_bwd_traffic_rig.md"},
 }
+
+
+def code_hash(path: str) -> str:
+    """SHA-256 (16 hex digits) of a C++/CUDA source without its // and /* */
+    comments, trailing blanks and blank lines."""
+    import hashlib
+    import re
+    text = open(path, encoding="utf-8").read()
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':                               # string literal: kept as is
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            while i < n and text[i] != "\n":
+                i += 1
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    body = "\n".join(ln for ln in lines if ln)
+    return hashlib.sha256(body.encode("utf-8")).hexdigest()[:16]
 
 
 def measured_traffic(kernel: str, workload: str):
     t = NCU_TRAFFIC.get(kernel)
     if t is None or workload != "rig":
         return None
-    import hashlib
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
-    with open(path, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest()[:16] != t["sha256_16"]:
-            return None
+    if code_hash(path) != t["code_sha256_16"]:
+        return None
     return t["bytes"]
 
 # workload name -> (scene spec, overrides, LOD threshold, description)
