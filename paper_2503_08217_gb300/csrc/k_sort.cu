@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
     if (!live) continue;
     const ViewInfo& vi = vs.v[a.view[i] & 0x7f];   // bit 7: Eq. 7 moved
     const uint32_t corner = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
-    a.rec[2 * i] = make_uint4(cnt, corner, (uint32_t)vi.gx | (w << 16), h);
+    // a rectangle without columns (an Eq. 7 splat moved out of the frustum)
+    // has no rows either for the expansion, which then reads no row table
+    a.rec[2 * i] = make_uint4(cnt, corner, (uint32_t)vi.gx | (w << 16), w != 0 ? h : 0u);
     a.rec[2 * i + 1] = make_uint4(table ? (uint32_t)off : kNoRows, head[0], head[1], head[2]);
     if (!table) region_store(g, a.region + 2 * i);
   }
