@@ -2,8 +2,10 @@
 
 Every computation runs in the CUDA library; this module turns torch tensors
 into device pointers, cameras into ``s3r_camera`` structs, and non-OK status
-codes into exceptions. It loads ``libs3r.so`` from the package directory and
-raises if it is missing: there is no fallback path.
+codes into exceptions. It loads ``libs3r.so`` from the package directory (or
+the variant build that the environment variable ``S3R_LIBRARY`` names, which
+is how the autotuner times alternative launch shapes) and raises if it is
+missing: there is no fallback path.
 """
 from __future__ import annotations
 
@@ -13,7 +15,8 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libs3r.so")
+DEFAULT_LIB_PATH = os.path.join(HERE, "libs3r.so")
+LIB_PATH = os.environ.get("S3R_LIBRARY") or DEFAULT_LIB_PATH
 
 S3R_MAX_VIEWS = 32
 VIS_RECORD, VIS_FINALIZE, VIS_RESET = 0, 1, 2

@@ -27,7 +27,23 @@
 namespace s3r {
 namespace {
 
-constexpr int kBatchBwd = 64;                // splats staged per batch (backward)
+// Launch shapes. Each is a build-time define, so that the autotuner
+// (autotune.py beside this package's build script) can build and time
+// alternatives; the values here are its choice at the surround-rig workload.
+#ifndef S3R_BLEND_FWD_BATCH
+#define S3R_BLEND_FWD_BATCH 64    // splats staged per batch (forward)
+#endif
+#ifndef S3R_BLEND_FWD_BLOCKS
+#define S3R_BLEND_FWD_BLOCKS 20   // resident forward blocks per SM (register budget)
+#endif
+#ifndef S3R_BLEND_BWD_BATCH
+#define S3R_BLEND_BWD_BATCH 64    // splats staged per batch (backward)
+#endif
+#ifndef S3R_BLEND_BWD_BLOCKS
+#define S3R_BLEND_BWD_BLOCKS 16   // resident backward blocks per SM (register budget)
+#endif
+
+constexpr int kBatchBwd = S3R_BLEND_BWD_BATCH;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
@@ -166,6 +182,12 @@ constexpr int kBandWarps = 2;
 constexpr int kBandThreads = 32 * kBandWarps;
 constexpr int kBandRows = 4 / kBandWarps;       // pixel rows per lane and column
 constexpr int kBandPix = 2 * kBandRows;         // pixels per lane
+static_assert(S3R_BLEND_FWD_BATCH % 32 == 0 && S3R_BLEND_FWD_BATCH <= 256 &&
+                  S3R_BLEND_BWD_BATCH % 32 == 0 && S3R_BLEND_BWD_BATCH <= 256,
+              "batches are whole 32-splat ballots and stay within static shared memory");
+static_assert(S3R_BLEND_FWD_BLOCKS >= 1 && S3R_BLEND_FWD_BLOCKS * kBandThreads <= 2048 &&
+                  S3R_BLEND_BWD_BLOCKS >= 1 && S3R_BLEND_BWD_BLOCKS * kBandThreads <= 2048,
+              "an SM holds at most 2048 threads");
 
 struct Band {
   int X0, Y0;              // pixel (0, 0) of this lane
@@ -233,7 +255,7 @@ __device__ __forceinline__ bool box_misses(const float4 b, const Band& t) {
 // of the packed arithmetic comes straight from a 64-bit shared load. The
 // arithmetic is the exponent and alpha of stage_splat's comment, in that
 // order, so the backward's recomputation takes the same decisions.
-constexpr int kBatchFwd = 64;                // splats staged per batch (forward)
+constexpr int kBatchFwd = S3R_BLEND_FWD_BATCH;
 // One splat of the forward's walk over a warp's four pixels per lane (two
 // packed pairs). kClamp: the splat's opacity exceeds 0.99, so alpha = o G may
 // reach the 0.99 cap; for o <= 0.99 it cannot (G = 2^p <= 1 where p <= 0, up
@@ -296,10 +318,10 @@ __device__ __forceinline__ void fwd_splat(const float4 q0, const float4 q1, cons
   }
 }
 
-// 20 blocks per SM (48 registers, a small spill) measured fastest: 16 (64
-// registers) 6 % slower, 22 and 24 11 % slower.
+// S3R_BLEND_FWD_BLOCKS: 20 blocks per SM (48 registers, a small spill)
+// measured fastest: 16 (64 registers) 6 % slower, 22 and 24 11 % slower.
 template <bool kCount>
-__global__ void __launch_bounds__(kBandThreads, 20) k_blend_fwd(const __grid_constant__ ViewSet vs,
+__global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fwd(const __grid_constant__ ViewSet vs,
                                                             BlendArgs a) {
   static_assert(kBandRows == 2, "the packed forward pairs the two rows of a lane's column");
   __shared__ float4 s_p0[kBatchFwd];   // A2 A2 B2 B2
@@ -612,7 +634,7 @@ __device__ __forceinline__ void bwd_splat(const float4 q0, const float4 q1, cons
 // scalar expressions in the same order. Only the order in which a lane adds
 // up its four pixels' shares of the nine sums differs from a scalar walk.
 template <bool kCount>
-__global__ void __launch_bounds__(kBandThreads, 32 / kBandWarps) k_blend_bwd(
+__global__ void __launch_bounds__(kBandThreads, S3R_BLEND_BWD_BLOCKS) k_blend_bwd(
     const __grid_constant__ ViewSet vs, BlendArgs a) {
   static_assert(kBandRows == 2, "the packed backward pairs the two rows of a lane's column");
   constexpr int kT = kBandThreads;

@@ -107,9 +107,14 @@ __global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __re
 // Pass 1: every selected Gaussian against every camera. Writes the frustum
 // and keep masks, applies Eq. 5 to the point life (on the frustum mask, before
 // LOD) and appends Gaussians kept in at least one view to the work list.
-// six blocks per SM (40 registers, a small spill) measured 4 % faster than
-// the compiler's 64 registers
-__global__ void __launch_bounds__(kThreads, 6) k_project_mask(const __grid_constant__ ViewSet vs,
+// S3R_PROJECT_MASK_BLOCKS: six blocks per SM (40 registers, a small spill)
+// measured 4 % faster than the compiler's 64 registers
+#ifndef S3R_PROJECT_MASK_BLOCKS
+#define S3R_PROJECT_MASK_BLOCKS 6   // build-time define the autotuner varies
+#endif
+static_assert(S3R_PROJECT_MASK_BLOCKS >= 1 && S3R_PROJECT_MASK_BLOCKS * kThreads <= 2048,
+              "an SM holds at most 2048 threads");
+__global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_mask(const __grid_constant__ ViewSet vs,
                                                            ProjArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const InstMat* __restrict__ mats = a.mats;

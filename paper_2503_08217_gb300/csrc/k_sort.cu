@@ -19,7 +19,7 @@ namespace s3r {
 namespace {
 
 constexpr int kWarps = kSortThreads / 32;
-constexpr int kWarpKeys = kSortItems * 32;   // 480 keys per warp per tile
+constexpr int kWarpKeys = kSortItems * 32;   // keys per warp per tile
 
 struct PassArgs {
   const uint32_t* keys_in;
@@ -60,7 +60,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_tmp 
   return wbase + incl - x;
 }
 
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
+__global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(PassArgs a) {
   __shared__ uint32_t s_keys[kSortTileKeys];
   __shared__ uint32_t s_vals[kSortTileKeys];
   __shared__ uint32_t s_cnt[kWarps][kRadix];   // per-warp digit counts -> exclusive offsets
@@ -197,18 +197,22 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(PassArgs a) {
 //                id), so that the expansion reads most splats' rows without a
 //                dependent load; a block scan + decoupled look-back over
 //                1024-splat tiles gives every splat its first output.
-//  k_dup_expand: persistent CTAs take fixed chunks of 4096 outputs; each
-//                thread expands 16 consecutive outputs (binary search of the
-//                chunk's splat offsets in shared memory, a walk over the
-//                splat's rows to the first one, then an incremental cursor
-//                over rows and splats); the pairs are staged in shared memory
-//                and written coalesced.
+//  k_dup_expand: persistent CTAs take fixed chunks of 256 * kExpItems outputs
+//                (2048 at 8); each thread expands kExpItems consecutive
+//                outputs (binary search of the chunk's splat offsets in
+//                shared memory, a walk over the splat's rows to the first
+//                one, then an incremental cursor over rows and splats); the
+//                pairs are staged in shared memory and written coalesced.
 constexpr int kDupThreads = 256;
 constexpr int kDupPer = 4;                            // splats per thread in the scan
 constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per scan tile
-constexpr int kExpItems = 8;                          // outputs per thread per chunk
+#ifndef S3R_DUP_EXPAND_ITEMS
+#define S3R_DUP_EXPAND_ITEMS 8   // build-time define the autotuner varies
+#endif
+constexpr int kExpItems = S3R_DUP_EXPAND_ITEMS;       // outputs per thread per chunk
 constexpr int kExpChunk = kDupThreads * kExpItems;    // outputs per chunk
 static_assert(kExpChunk >= kDupChunkMin, "the chunk map is sized for chunks of kDupChunkMin");
+static_assert(kExpItems <= 14, "above 14 outputs per thread the staged chunk exceeds 48 KB of shared memory");
 
 constexpr float kSpanPad = 0.05f;        // pixels, on the strips and the column bounds
 
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
     const int q0 = (int)s_q0, nq = min((int)s_q1 - q0 + 1, kExpChunk);
     for (int i = threadIdx.x; i <= nq; i += kDupThreads) s_excl[i] = a.dup_excl[q0 + i];
     __syncthreads();
-    // 16 consecutive outputs per thread
+    // kExpItems consecutive outputs per thread
     const uint32_t o0 = O0 + threadIdx.x * kExpItems;
     if (o0 < O1) {
       int lo = 0, hi = nq;            // last local q with s_excl[q] <= o0

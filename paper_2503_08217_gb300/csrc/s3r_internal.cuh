@@ -65,9 +65,22 @@ struct ViewSet {
 };
 
 // ---- radix sort geometry ----------------------------------------------------
+// S3R_SORT_ITEMS (keys per thread per tile) and S3R_SORT_BLOCKS (resident
+// onesweep blocks per SM) are build-time defines the autotuner varies; the
+// tile's keys and values take 8 * 256 * S3R_SORT_ITEMS bytes of shared memory.
+#ifndef S3R_SORT_ITEMS
+#define S3R_SORT_ITEMS 15
+#endif
+#ifndef S3R_SORT_BLOCKS
+#define S3R_SORT_BLOCKS 3
+#endif
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 15;                       // keys per thread per tile
-constexpr int kSortTileKeys = kSortThreads * kSortItems;  // 3840
+constexpr int kSortItems = S3R_SORT_ITEMS;
+constexpr int kSortTileKeys = kSortThreads * kSortItems;  // 3840 at 15
+static_assert(kSortItems >= 1 && kSortItems <= 18,
+              "above 18 keys per thread the onesweep tile exceeds 48 KB of static shared memory");
+static_assert(S3R_SORT_BLOCKS >= 1 && S3R_SORT_BLOCKS * kSortThreads <= 2048,
+              "an SM holds at most 2048 threads");
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 // digit histograms: 4 depth passes + up to 4 tile passes
