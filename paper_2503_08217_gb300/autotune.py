@@ -127,17 +127,23 @@ def coordinate_descent(start: dict, params, measure: Callable[[dict], float],
     (name, candidates) pairs searched, in order. Returns (best values, best
     time, trials) with trials = [(values, time or error string)]. A candidate
     is accepted only when faster than the incumbent by more than ``min_gain``
-    (relative). Stops starting new trials once ``deadline`` (time.time()) passes.
+    (relative). A configuration already timed is not timed again. Stops
+    starting new trials once ``deadline`` (time.time()) passes.
     """
     cur = dict(start)
     trials = []
+    seen = {}   # configuration -> time: each one is timed once
 
     def run(values):
+        key = tuple(sorted(values.items()))
+        if key in seen:
+            return seen[key]
         try:
             t = measure(values)
         except Exception as e:   # a variant that fails to build or run is skipped
             t = f"{type(e).__name__}: {str(e).splitlines()[0] if str(e) else ''}"
         trials.append((dict(values), t))
+        seen[key] = t
         if log:
             log(values, t)
         return t
@@ -222,9 +228,18 @@ def main(argv=None):
     def measure(values):
         return bench_step_ms(lib_for(values), a.workload, a.steps, a.warmup)
 
+    done = []   # (values, time) so far: the report is rewritten after every trial
+
     def log(values, t):
         diff = ", ".join(f"{k}={v}" for k, v in values.items() if v != start[k]) or "(start)"
         print(f"{diff}: {t if isinstance(t, str) else f'{t:.3f} ms'}", file=sys.stderr, flush=True)
+        done.append((dict(values), t))
+        if a.out and not isinstance(done[0][1], str):
+            ok = [(v, x) for v, x in done if not isinstance(x, str)]
+            bv, bt = min(ok, key=lambda vx: vx[1])
+            with open(a.out, "w") as f:
+                f.write(report(start, bv, bt, done, a.workload, a.steps, a.warmup)
+                        + "\n(partial: the search is still running)\n")
 
     deadline = time.time() + a.budget_s if a.budget_s else None
     best, best_ms, trials = coordinate_descent(start, search, measure, a.min_gain, a.passes,

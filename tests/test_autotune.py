@@ -58,6 +58,21 @@ def test_coordinate_descent_reaches_the_minimum_of_a_separable_cost():
     assert trials[0] == (start, 10.0 + 4 + 1)
 
 
+def test_coordinate_descent_times_each_configuration_once():
+    calls = []
+
+    def measure(v):
+        calls.append(dict(v))
+        return {1: 5.0, 2: 6.0, 3: 7.0}[v["A"]] + v["B"]
+
+    start = {"A": 2, "B": 0}
+    best, ms, trials = autotune.coordinate_descent(start, [("A", (3, 2, 1)), ("B", (0, 1))],
+                                                   measure, passes=3)
+    assert best == {"A": 1, "B": 0} and ms == 5.0
+    keys = [tuple(sorted(c.items())) for c in calls]
+    assert len(keys) == len(set(keys)) == len(trials)
+
+
 def test_coordinate_descent_keeps_the_incumbent_below_the_minimum_gain():
     start = {"A": 2}
     costs = {1: 100.0, 2: 100.5, 3: 101.0}
