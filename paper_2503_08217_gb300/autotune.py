@@ -98,9 +98,11 @@ def write_defaults(values: dict, csrc: str = libbuild.CSRC) -> list:
     return changed
 
 
-def bench_step_ms(lib: str | None, workload: str, steps: int, warmup: int,
-                  timeout_s: float = 600.0) -> float:
-    """Time one library with ``bench.py`` in a child process; returns ms per step."""
+def bench_record(lib: str | None, workload: str, steps: int, warmup: int,
+                 timeout_s: float = 600.0) -> dict:
+    """Time one library with ``bench.py`` in a child process; returns its JSON
+    line (``ms_per_step``, and ``clocks``: the SM clock and throttle reasons
+    sampled during the timed steps)."""
     env = dict(os.environ)
     if lib is None:
         env.pop("S3R_LIBRARY", None)
@@ -114,8 +116,17 @@ def bench_step_ms(lib: str | None, workload: str, steps: int, warmup: int,
         raise RuntimeError(f"bench failed ({r.returncode}):\n{r.stderr[-2000:]}")
     for line in reversed(r.stdout.strip().splitlines()):
         if line.startswith("{"):
-            return float(json.loads(line)["ms_per_step"])
+            return json.loads(line)
     raise RuntimeError("bench printed no JSON line")
+
+
+def clock_note(rec: dict) -> str:
+    """'<median SM MHz> / <max> MHz[, reasons]' from a bench line's clocks."""
+    c = rec.get("clocks") or {}
+    if not c.get("sm_mhz"):
+        return "not sampled"
+    reasons = ", ".join(c.get("reasons") or []) or "no reason"
+    return f"{c['sm_mhz']:.0f} / {c.get('sm_max_mhz') or 0:.0f} MHz, {reasons}"
 
 
 def coordinate_descent(start: dict, params, measure: Callable[[dict], float],
@@ -168,21 +179,29 @@ def coordinate_descent(start: dict, params, measure: Callable[[dict], float],
 
 
 def report(start: dict, best: dict, best_ms: float, trials, workload: str, steps: int,
-           warmup: int) -> str:
+           warmup: int, notes: dict | None = None, retimed: float | None = None) -> str:
+    """Markdown table of the trials; ``notes`` maps a configuration (sorted
+    items) to a clock note, ``retimed`` is a second timing of the chosen one."""
+    notes = notes or {}
     base = trials[0][1]
     lines = [f"# Launch-shape autotune, workload `{workload}` ({steps} timed steps after "
              f"{warmup} warm-up, one child process per trial)", "",
-             "| trial | changed from start | ms / step | vs start |", "|---|---|---|---|"]
+             "| trial | changed from start | ms / step | vs start | SM clock (median / max), reasons |",
+             "|---|---|---|---|---|"]
     for i, (vals, t) in enumerate(trials):
         diff = ", ".join(f"{k}={v}" for k, v in vals.items() if v != start[k]) or "(start)"
+        note = notes.get(tuple(sorted(vals.items())), "")
         if isinstance(t, str):
-            lines.append(f"| {i} | {diff} | failed: {t} | |")
+            lines.append(f"| {i} | {diff} | failed: {t} | | |")
         else:
-            lines.append(f"| {i} | {diff} | {t:.3f} | {t / base:.3f} |")
+            lines.append(f"| {i} | {diff} | {t:.3f} | {t / base:.3f} | {note} |")
     lines += ["", "| define | start | chosen |", "|---|---|---|"]
     for k in start:
         lines.append(f"| {k} | {start[k]} | {best[k]} |")
     lines += ["", f"best: {best_ms:.3f} ms / step (start {base:.3f})"]
+    if retimed is not None:
+        lines.append(f"chosen configuration timed again in a fresh process: {retimed:.3f} ms / step "
+                     f"({100 * (retimed / best_ms - 1):+.2f} %: the run-to-run spread)")
     return "\n".join(lines) + "\n"
 
 
@@ -201,6 +220,8 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="write the markdown report here")
     ap.add_argument("--write", action="store_true", help="write the winners into the sources")
     ap.add_argument("--dry-run", action="store_true", help="build every variant, time nothing")
+    ap.add_argument("--no-retime", action="store_true",
+                    help="skip the second timing of the chosen configuration")
     a = ap.parse_args(argv)
 
     start = source_defaults()
@@ -225,8 +246,12 @@ def main(argv=None):
                 print(n, v, lib_for({**start, n: v}))
         return 0
 
+    notes = {}
+
     def measure(values):
-        return bench_step_ms(lib_for(values), a.workload, a.steps, a.warmup)
+        rec = bench_record(lib_for(values), a.workload, a.steps, a.warmup)
+        notes[tuple(sorted(values.items()))] = clock_note(rec)
+        return float(rec["ms_per_step"])
 
     done = []   # (values, time) so far: the report is rewritten after every trial
 
@@ -238,13 +263,19 @@ def main(argv=None):
             ok = [(v, x) for v, x in done if not isinstance(x, str)]
             bv, bt = min(ok, key=lambda vx: vx[1])
             with open(a.out, "w") as f:
-                f.write(report(start, bv, bt, done, a.workload, a.steps, a.warmup)
+                f.write(report(start, bv, bt, done, a.workload, a.steps, a.warmup, notes)
                         + "\n(partial: the search is still running)\n")
 
     deadline = time.time() + a.budget_s if a.budget_s else None
     best, best_ms, trials = coordinate_descent(start, search, measure, a.min_gain, a.passes,
                                                deadline, log)
-    text = report(start, best, best_ms, trials, a.workload, a.steps, a.warmup)
+    retimed = None
+    if not a.no_retime:
+        try:
+            retimed = measure(best)
+        except Exception as e:
+            print(f"re-timing failed: {e}", file=sys.stderr)
+    text = report(start, best, best_ms, trials, a.workload, a.steps, a.warmup, notes, retimed)
     print(text)
     if a.out:
         with open(a.out, "w") as f:

@@ -179,3 +179,17 @@ def test_recorded_traffic_is_not_claimed_for_a_variant_library(monkeypatch):
     assert bench.measured_traffic("blend_bwd", "rig") is not None
     monkeypatch.setenv("S3R_LIBRARY", libbuild.variant_path({"S3R_BLEND_BWD_BATCH": 32}))
     assert bench.measured_traffic("blend_bwd", "rig") is None
+
+
+def test_report_carries_each_trials_clocks_and_the_second_timing():
+    start = {"A": 1}
+    trials = [(start, 5.0), ({"A": 2}, 5.5)]
+    notes = {(("A", 1),): autotune.clock_note({"clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070,
+                                                          "reasons": []}}),
+             (("A", 2),): autotune.clock_note({"clocks": {"sm_mhz": 1800.0, "sm_max_mhz": 2070,
+                                                          "reasons": ["sw_power_cap"]}})}
+    text = autotune.report(start, start, 5.0, trials, "rig", 20, 5, notes, retimed=5.05)
+    assert "| 0 | (start) | 5.000 | 1.000 | 2070 / 2070 MHz, no reason |" in text
+    assert "| 1 | A=2 | 5.500 | 1.100 | 1800 / 2070 MHz, sw_power_cap |" in text
+    assert "timed again in a fresh process: 5.050 ms / step (+1.00 %" in text
+    assert autotune.clock_note({"clocks": {"sm_mhz": None, "reasons": ["no samples"]}}) == "not sampled"
