@@ -3,7 +3,7 @@
 //
 // Forward: one CTA of two warps per tile, each warp a 16x8 band, four pixels
 // per lane, the two of a column evaluated as one packed f32x2 pair. The
-// tile's front-to-back splat list is consumed in batches of 64 staged in
+// tile's front-to-back splat list is consumed in batches (64 by default) staged in
 // shared memory (uv, base-2 conic, opacity, rgb as duplicated pairs, and the
 // box where the splat can reach alpha >= 1/255); per 32 splats a warp ballots which of
 // them can reach alpha >= 1/255 somewhere in its band (box, then the exact

@@ -8,11 +8,12 @@
 // depth-digit passes run on the splats BEFORE duplication (S keys instead of
 // K); the splats are then expanded into (tile, splat) pairs in depth order,
 // and the one or two tile-digit passes finish the sort. Every pass is a
-// single-pass "onesweep" kernel: persistent CTAs take 3840-key tiles from an
-// atomic counter, rank digits with eight warp ballots per key (faster here than
-// match.any, which queues on the address-divergence unit), get each digit's global
-// offset from a precomputed histogram plus a decoupled look-back over tiles,
-// reorder the tile in shared memory and write it out coalesced.
+// single-pass "onesweep" kernel: persistent CTAs take tiles of kSortTileKeys
+// keys (3840 by default) from an atomic counter, rank digits with eight warp
+// ballots per key (faster here than match.any, which queues on the
+// address-divergence unit), get each digit's global offset from a
+// precomputed histogram plus a decoupled look-back over tiles, reorder the
+// tile in shared memory and write it out coalesced.
 #include "s3r_internal.cuh"
 
 namespace s3r {
