@@ -298,6 +298,20 @@ s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params);
  * so it is off by default and off while timing. */
 s3r_status s3r_set_counting(s3r_workspace* ws, int32_t enable);
 
+/* Failure-detection test hook: every device-side wait of the library (the
+ * decoupled look-back of the scans and radix passes) is bounded, and on
+ * give-up latches a timeout into the workspace status instead of hanging.
+ * This call makes both look-back waits run out on purpose: one warp waits,
+ * as tile 1, on a tile-0 word that nothing publishes, giving up after
+ * `max_polls` polls (1 .. S3R_MAX_PROBE_POLLS; each poll sleeps ~20-30 ns, so
+ * at most a few tens of milliseconds). Asynchronous on `stream`; the next
+ * s3r_sync_status returns S3R_ERR_TIMEOUT and clears the status, and the
+ * workspace stays usable (the hook writes only four look-back words that no
+ * pass reads with a matching tag). Returns S3R_ERR_INVALID for a NULL
+ * workspace or `max_polls` out of range, launching nothing. */
+#define S3R_MAX_PROBE_POLLS (1 << 20)
+s3r_status s3r_check_wait_timeout(s3r_workspace* ws, int32_t max_polls, void* stream);
+
 /* Per-kernel device timing (tracing). With timing enabled, every kernel the
  * workspace's calls launch is bracketed by a pair of CUDA events owned by the
  * workspace (recorded on the caller's stream, so this also works inside a

@@ -29,7 +29,8 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_query_counts", "s3r_sync_status", "s3r_debug_buffer", "s3r_last_error",
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
-           "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world")
+           "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
+           "s3r_check_wait_timeout")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -121,6 +122,7 @@ def load(path: str = LIB_PATH):
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
     L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp]
+    L.s3r_check_wait_timeout.argtypes = [vp, i32, vp]
     L.s3r_kernel_count.restype = i32
     L.s3r_kernel_name.argtypes = [i32]
     L.s3r_kernel_name.restype = ctypes.c_char_p
@@ -135,7 +137,7 @@ def load(path: str = LIB_PATH):
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
                  "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
-                 "s3r_set_counting"):
+                 "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -287,6 +289,11 @@ class Workspace:
 
     def sync_status(self, stream=None):
         _check(load().s3r_sync_status(self._h, _stream(stream)))
+
+    def check_wait_timeout(self, max_polls: int = 1000, stream=None):
+        """Make the bounded look-back waits give up on purpose (failure-detection
+        test hook); the next sync_status() raises S3R_ERR_TIMEOUT."""
+        _check(load().s3r_check_wait_timeout(self._h, int(max_polls), _stream(stream)))
 
     def debug(self, name: str, dtype: torch.dtype, count: int) -> torch.Tensor:
         """Copy `count` elements of a workspace intermediate to a new tensor."""

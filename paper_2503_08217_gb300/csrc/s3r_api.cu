@@ -405,6 +405,17 @@ s3r_status s3r_set_counting(s3r_workspace* ws, int32_t enable) {
   return S3R_OK;
 }
 
+s3r_status s3r_check_wait_timeout(s3r_workspace* ws, int32_t max_polls, void* stream) {
+  if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
+  if (max_polls < 1 || max_polls > S3R_MAX_PROBE_POLLS)
+    return fail(S3R_ERR_INVALID, "max_polls %d outside [1, %d]", (int)max_polls,
+                S3R_MAX_PROBE_POLLS);
+  DeviceGuard g(ws->device);
+  const cudaError_t e = launch_wait_probe(ws, max_polls, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+  return S3R_OK;
+}
+
 s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params) {
   if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
   if (!params) {

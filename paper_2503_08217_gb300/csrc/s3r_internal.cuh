@@ -42,6 +42,10 @@ enum Stage : int {
   kStageExpand = 12,  // chunk counter of the duplication expansion
   kStageCount = 13
 };
+// Look-back tag stage of the bounded-wait test hook (k_probe.cu): no pass
+// uses it, so no word the hook writes can ever match a pass's tag.
+constexpr int kStageProbe = 15;
+static_assert(kStageCount <= kStageProbe && kStageProbe < 16, "stage tags carry 4 bits");
 
 // Bounded spin: after this many polls a wait gives up, latches
 // kStatusTimeout and carries on (results are then invalid, nothing hangs).
@@ -209,6 +213,7 @@ cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, fl
                            float* loss, cudaStream_t st);
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
                               int mode, cudaStream_t st);
+cudaError_t launch_wait_probe(s3r_workspace* ws, int max_polls, cudaStream_t st);
 // Record `msg` as the calling thread's last error and return `st`.
 s3r_status set_last_error(s3r_status st, const char* msg);
 
@@ -234,11 +239,11 @@ __device__ __forceinline__ uint32_t stage_tag(uint32_t epoch, int stage) {
 
 // Exclusive prefix for `tile` of one running sum (one digit). `words` points
 // at digit d's word of tile 0; consecutive tiles are `stride` words apart.
-// Publishes the inclusive value on exit. Bounded: on give-up latches
-// kStatusTimeout into ctr and returns the partial sum.
+// Publishes the inclusive value on exit. Bounded: after max_polls unanswered
+// polls it latches kStatusTimeout into ctr and returns the partial sum.
 __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, int64_t stride,
                                                      int64_t tile, uint32_t tag, uint32_t aggregate,
-                                                     uint32_t* ctr) {
+                                                     uint32_t* ctr, int max_polls = kSpinLimit) {
   unsigned long long* mine = words + tile * stride;
   if (tile == 0) {
     st_relaxed(mine, lb_word(tag, 2, aggregate));
@@ -253,7 +258,7 @@ __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, i
     uint32_t wtag = (uint32_t)(w >> 34);
     uint32_t flag = (uint32_t)(w >> 32) & 3u;
     if (wtag != tag || flag == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > max_polls) {
         atomicOr(ctr + kCtrStatus, kStatusTimeout);
         break;
       }
@@ -279,9 +284,11 @@ __device__ __forceinline__ uint32_t lane_id_() {
 // step reads 32 predecessors at once and stops at the nearest one that has
 // published its inclusive prefix, so a walk over w unfinished predecessors
 // takes ceil(w/32) dependent loads instead of w. Returns the exclusive
-// prefix in every lane; lane 0 publishes the inclusive value.
+// prefix in every lane; lane 0 publishes the inclusive value. Bounded like
+// lookback_prefix.
 __device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int64_t tile,
-                                                  uint32_t tag, uint32_t aggregate, uint32_t* ctr) {
+                                                  uint32_t tag, uint32_t aggregate, uint32_t* ctr,
+                                                  int max_polls = kSpinLimit) {
   const uint32_t lane = lane_id_();
   if (lane == 0) st_relaxed(words + tile, lb_word(tag, tile == 0 ? 2u : 1u, aggregate));
   if (tile == 0) return 0;
@@ -302,7 +309,7 @@ __device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int
     const int first = incl ? __ffs(incl) - 1 : 32;          // nearest inclusive
     const uint32_t need = first == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first));
     if (waiting & need) {
-      if (++spins > kSpinLimit) {
+      if (++spins > max_polls) {
         if (lane == 0) atomicOr(ctr + kCtrStatus, kStatusTimeout);
         break;
       }

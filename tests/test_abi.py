@@ -45,6 +45,8 @@ def test_invalid_calls_fail_without_a_gpu():
     assert L.s3r_update_visibility(-1, 0.0, None, None, None, 0, None) == 1
     assert L.s3r_update_visibility(10, 0.0, None, None, None, 7, None) == 1
     assert b"mode" in L.s3r_last_error()
+    assert L.s3r_check_wait_timeout(None, 100, None) == 1
+    assert b"workspace" in L.s3r_last_error()
 
 
 def test_adam_argument_checks_fail_without_a_gpu():

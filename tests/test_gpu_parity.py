@@ -562,6 +562,34 @@ def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
     assert e.value.status == 2   # S3R_ERR_CAPACITY
 
 
+def test_bounded_wait_gives_up_and_the_workspace_recovers(built, tiny, tiny_vis):
+    """Failure detection without a GPU fault: the look-back waits, made to wait
+    on a word that nothing publishes, give up after their poll limit; the host
+    reads S3R_ERR_TIMEOUT, the status clears, and the same workspace then
+    renders what it rendered before."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    vis, _ = tiny_vis
+    step = 3
+    cams = tiny.cams[step]
+    r = gpu_helpers.Renderer(tiny.n, tiny.n_inst, cams)
+    before = gpu_helpers.gpu_step(tiny, step, cams, vis, renderer=r)
+    for bad in (0, -1, (1 << 20) + 1):
+        with pytest.raises(binding.S3RError) as e:
+            r.ws.check_wait_timeout(bad)
+        assert e.value.status == 1   # S3R_ERR_INVALID, nothing launched
+    r.ws.sync_status()
+    r.ws.check_wait_timeout(1000)
+    with pytest.raises(binding.S3RError) as e:
+        r.ws.sync_status()
+    assert e.value.status == 4       # S3R_ERR_TIMEOUT
+    r.ws.sync_status()               # read once, then cleared
+    after = gpu_helpers.gpu_step(tiny, step, cams, vis, renderer=r)
+    assert after["counts"]["n_duplicates"] == before["counts"]["n_duplicates"] > 0
+    for x, y in zip(before["images"], after["images"]):
+        np.testing.assert_allclose(x, y, atol=1e-6)
+
+
 def test_row_table_overflow_gives_the_same_pairs(built, tiny, tiny_vis):
     """A splat whose rectangle rows do not fit the sort's row table is expanded
     from its stored alpha region instead: with a table of one entry (every
