@@ -355,6 +355,14 @@ s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out);
  * value (S3R_ERR_CAPACITY / S3R_ERR_TIMEOUT), clearing it. */
 s3r_status s3r_sync_status(s3r_workspace* ws, void* stream);
 
+/* Resume support: set the workspace's call counter (s3r_counts.epoch) so that
+ * the next s3r_project draws the stochastic-LOD numbers (Eq. 7) of call
+ * `epoch` + 1, as the run that saved the counter would have. Synchronises
+ * `stream`. The counter also tags the scans' look-back words, so once the
+ * workspace has run a projection it may only move forward, by less than 2^25
+ * (S3R_ERR_INVALID otherwise); a new workspace takes any value. */
+s3r_status s3r_set_epoch(s3r_workspace* ws, uint32_t epoch, void* stream);
+
 /* Read-only views of workspace intermediates, for tests and tools (device
  * pointers, valid until the next s3r_project on the workspace).
  *   name: "selected" u32[n_selected] ascending Gaussian ids;

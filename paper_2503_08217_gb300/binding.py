@@ -30,7 +30,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
            "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
-           "s3r_check_wait_timeout")
+           "s3r_check_wait_timeout", "s3r_set_epoch")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -123,6 +123,7 @@ def load(path: str = LIB_PATH):
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
     L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp]
     L.s3r_check_wait_timeout.argtypes = [vp, i32, vp]
+    L.s3r_set_epoch.argtypes = [vp, ctypes.c_uint32, vp]
     L.s3r_kernel_count.restype = i32
     L.s3r_kernel_name.argtypes = [i32]
     L.s3r_kernel_name.restype = ctypes.c_char_p
@@ -137,7 +138,8 @@ def load(path: str = LIB_PATH):
                  "s3r_render_fwd", "s3r_render_bwd", "s3r_update_visibility",
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
                  "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
-                 "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout"):
+                 "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout",
+                 "s3r_set_epoch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -289,6 +291,10 @@ class Workspace:
 
     def sync_status(self, stream=None):
         _check(load().s3r_sync_status(self._h, _stream(stream)))
+
+    def set_epoch(self, epoch: int, stream=None):
+        """Restore the call counter of a saved run (resume of the Eq. 7 draws)."""
+        _check(load().s3r_set_epoch(self._h, int(epoch) & 0xFFFFFFFF, _stream(stream)))
 
     def check_wait_timeout(self, max_polls: int = 1000, stream=None):
         """Make the bounded look-back waits give up on purpose (failure-detection

@@ -514,6 +514,27 @@ s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out) {
   return S3R_OK;
 }
 
+s3r_status s3r_set_epoch(s3r_workspace* ws, uint32_t epoch, void* stream) {
+  if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
+  DeviceGuard g(ws->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  uint32_t cur = 0;
+  if ((e = cudaMemcpy(&cur, ws->ctr + kCtrEpoch, sizeof(cur), cudaMemcpyDeviceToHost)) !=
+      cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy epoch");
+  // the counter tags look-back words: after the first call a tag in the array
+  // must never come back, so the counter only moves forward, by < 2^25
+  if (cur != 0 && (epoch < cur || epoch - cur >= (1u << 25)))
+    return fail(S3R_ERR_INVALID,
+                "after the first call the call counter only moves forward by less than 2^25 "
+                "(%u -> %u)", cur, epoch);
+  if ((e = cudaMemcpy(ws->ctr + kCtrEpoch, &epoch, sizeof(epoch), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return cuda_fail(e, "cudaMemcpy epoch");
+  return S3R_OK;
+}
+
 s3r_status s3r_sync_status(s3r_workspace* ws, void* stream) {
   s3r_counts c;
   s3r_status st = s3r_query_counts(ws, stream, &c);

@@ -46,6 +46,7 @@ def test_invalid_calls_fail_without_a_gpu():
     assert L.s3r_update_visibility(10, 0.0, None, None, None, 7, None) == 1
     assert b"mode" in L.s3r_last_error()
     assert L.s3r_check_wait_timeout(None, 100, None) == 1
+    assert L.s3r_set_epoch(None, 5, None) == 1
     assert b"workspace" in L.s3r_last_error()
 
 
