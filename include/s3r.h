@@ -26,7 +26,8 @@
  *     NULL = the legacy default stream). They perform no host synchronisation
  *     and allocate nothing, so a sequence of them can be captured into a CUDA
  *     graph. Only s3r_workspace_create/destroy allocate and free, and only
- *     s3r_query_counts / s3r_sync_status synchronise.
+ *     s3r_query_counts / s3r_sync_status and the resume call s3r_set_epoch
+ *     synchronise.
  *   - Data-dependent sizes (selected Gaussians, splats, duplicates) stay on
  *     the device; every kernel reads its own extent from there.
  *   - Device-side failures (a capacity overflow, an exhausted spin budget) are
