@@ -78,6 +78,17 @@ def code_hash(path: str) -> str:
     return hashlib.sha256(body.encode("utf-8")).hexdigest()[:16]
 
 
+def launch_shapes() -> dict:
+    """The build-time launch shapes of the library this run loads: the source
+    defaults (the autotuner's choice) for the default build, else the
+    variant's name."""
+    lib = os.environ.get("S3R_LIBRARY")
+    if lib:
+        return {"variant": os.path.basename(os.path.dirname(os.path.abspath(lib)))}
+    from paper_2503_08217_gb300 import autotune
+    return autotune.source_defaults()
+
+
 def measured_traffic(kernel: str, workload: str):
     t = NCU_TRAFFIC.get(kernel)
     if t is None or workload != "rig" or os.environ.get("S3R_LIBRARY"):
@@ -636,6 +647,7 @@ def run_ours(args, rank, world, local):
             "counts": {k2: int(v) for k2, v in counts.items()},
             "visibility_sweep_s": round(sweep_s, 3),
             "workspace_gb": round(r.ws.nbytes / 1e9, 3),
+            "launch_shapes": launch_shapes(),
         }
         print(json.dumps(line), flush=True)
 

@@ -35,3 +35,12 @@ def test_recorded_traffic_only_for_its_code_and_workload():
     assert bench.measured_traffic("blend_bwd", "rig") == (t["bytes"] if same else None)
     assert bench.measured_traffic("blend_bwd", "small-rig") is None
     assert bench.measured_traffic("blend_fwd", "rig") is None
+
+
+def test_the_bench_line_names_its_launch_shapes(monkeypatch):
+    import bench
+    from paper_2503_08217_gb300 import autotune, build
+    monkeypatch.delenv("S3R_LIBRARY", raising=False)
+    assert bench.launch_shapes() == autotune.source_defaults()
+    monkeypatch.setenv("S3R_LIBRARY", build.variant_path({"S3R_SORT_ITEMS": 11}))
+    assert bench.launch_shapes() == {"variant": "sort_items11"}
