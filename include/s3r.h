@@ -237,7 +237,13 @@ s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float*
  *   p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps)
  * (PyTorch's Adam without weight decay). `tensors` is a HOST array of up to
  * S3R_ADAM_MAX_TENSORS descriptors of device arrays (FP32, n elements each,
- * 4-byte aligned); param, exp_avg and exp_avg_sq are updated in place. */
+ * 4-byte aligned); param, exp_avg and exp_avg_sq are updated in place.
+ * `gate` (may be NULL) is a device uint32 read by the kernel: if it is not 0
+ * the step changes nothing. Passing s3r_device_status(ws) skips the update
+ * whenever a call of the workspace has latched a failure (dropped splats or
+ * pairs, a wait that gave up) since the status was last read, so that a
+ * truncated render never reaches the parameters, with no host
+ * synchronisation. */
 #define S3R_ADAM_MAX_TENSORS 8
 typedef struct {
   float* param;
@@ -247,7 +253,12 @@ typedef struct {
   int64_t n;
 } s3r_adam_tensor;
 s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
-                         float beta2, float eps, int32_t step, void* stream);
+                         float beta2, float eps, int32_t step, const uint32_t* gate, void* stream);
+
+/* Device address of the workspace's latched status word (0 while no failure
+ * is latched; bits 1 capacity, 2 timeout), for s3r_adam_step's gate. Valid
+ * for the workspace's lifetime; NULL for a NULL workspace. */
+const uint32_t* s3r_device_status(const s3r_workspace* ws);
 
 /* The conventional pipeline of Fig. 1(a), the comparator that the
  * instance-specific projection of Sec. 3.3 replaces: every Gaussian of a
@@ -336,14 +347,19 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n);
  *               larger n returns S3R_ERR_INVALID (nothing is launched).
  *   vis_window  [n,2] FP32 device array, 16-byte aligned.
  *   out_idx     [n] uint32 device array (caller-owned), receives the list.
- *   out_count   one uint32 in device memory, receives its length.
+ *   out_count   one uint32 in device memory, receives its length, or
+ *               S3R_STATIC_TIMEOUT if a bounded look-back wait of the call
+ *               gave up (out_idx is then not valid; the call itself cannot
+ *               return S3R_ERR_TIMEOUT, which is only known on the device).
  * The look-back scratch is a fixed array in the library's device image
  * (about 128 KB, held by every GPU that loads the library until the process
  * exits); every call shares it and clears the part it uses on entry, so
  * calls that overlap on the GPU (e.g. on two streams at once) race and must
  * be serialised by the caller. The first call on a device looks up the
- * array's device address (once per device); make that first call before any
- * stream capture. No allocation or free happens in any call. */
+ * array's device address and the device's SM count (once per device); make
+ * that first call before any stream capture. No allocation or free happens
+ * in any call. */
+#define S3R_STATIC_TIMEOUT 0xffffffffu
 #define S3R_STATIC_MAX_GAUSSIANS (1LL << 26)
 s3r_status s3r_select_visible_static(int64_t n, float t, const float* vis_window, uint32_t* out_idx,
                                      uint32_t* out_count, void* stream);
@@ -358,10 +374,10 @@ s3r_status s3r_sync_status(s3r_workspace* ws, void* stream);
 
 /* Resume support: set the workspace's call counter (s3r_counts.epoch) so that
  * the next s3r_project draws the stochastic-LOD numbers (Eq. 7) of call
- * `epoch` + 1, as the run that saved the counter would have. Synchronises
- * `stream`. The counter also tags the scans' look-back words, so once the
- * workspace has run a projection it may only move forward, by less than 2^25
- * (S3R_ERR_INVALID otherwise); a new workspace takes any value. */
+ * `epoch` + 1, as the run that saved the counter would have. The counter
+ * also tags the scans' look-back words, so the call clears those words (one
+ * memset of the workspace's look-back array) and any value is accepted.
+ * Synchronises `stream`. */
 s3r_status s3r_set_epoch(s3r_workspace* ws, uint32_t epoch, void* stream);
 
 /* Read-only views of workspace intermediates, for tests and tools (device

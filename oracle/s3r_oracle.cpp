@@ -829,27 +829,30 @@ void orc_render(int W, int H, int n, const double* u, const double* v, const dou
                 int32_t* out_ncontrib, int32_t* out_flag) {
   SplatView s{n, u, v, conic, opac, rgb, depth32, order, rect};
   const std::vector<int> all = depth_order(s);
-#pragma omp parallel for schedule(dynamic, 4)
-  for (int py = 0; py < H; ++py) {
+  const int gx = (W + kTile - 1) / kTile, gy = (H + kTile - 1) / kTile;
+  // every pixel of a tile has the same list (the Gaussians whose rectangle
+  // contains the tile, in global depth order): it is gathered once per tile
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int t = 0; t < gx * gy; ++t) {
+    const int tx = t % gx, ty = t / gx;
     PixelTrace tr;
     std::vector<int> list;
-    for (int px = 0; px < W; ++px) {
-      const int tx = px / kTile, ty = py / kTile;
-      list.clear();
-      for (int i : all)
-        if (covers(rect + 4 * i, tx, ty)) list.push_back(i);
-      blend_pixel(s, list, px + 0.5, py + 0.5, tr);
-      double C[3] = {0, 0, 0};
-      for (size_t c = 0; c < tr.contrib.size(); ++c) {
-        const int i = tr.list[tr.contrib[c]];
-        for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * tr.alpha[c] * tr.T[c];
+    for (int i : all)
+      if (covers(rect + 4 * i, tx, ty)) list.push_back(i);
+    for (int py = ty * kTile; py < std::min(H, (ty + 1) * kTile); ++py)
+      for (int px = tx * kTile; px < std::min(W, (tx + 1) * kTile); ++px) {
+        blend_pixel(s, list, px + 0.5, py + 0.5, tr);
+        double C[3] = {0, 0, 0};
+        for (size_t c = 0; c < tr.contrib.size(); ++c) {
+          const int i = tr.list[tr.contrib[c]];
+          for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * i + ch] * tr.alpha[c] * tr.T[c];
+        }
+        const size_t pix = (size_t)py * W + px;
+        for (int ch = 0; ch < 3; ++ch) out_rgb[(size_t)ch * W * H + pix] = C[ch] + tr.Tfinal * bg[ch];
+        out_T[pix] = tr.Tfinal;
+        out_ncontrib[pix] = tr.n_contrib;
+        out_flag[pix] = tr.flag;
       }
-      const size_t pix = (size_t)py * W + px;
-      for (int ch = 0; ch < 3; ++ch) out_rgb[(size_t)ch * W * H + pix] = C[ch] + tr.Tfinal * bg[ch];
-      out_T[pix] = tr.Tfinal;
-      out_ncontrib[pix] = tr.n_contrib;
-      out_flag[pix] = tr.flag;
-    }
   }
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
            "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
-           "s3r_check_wait_timeout", "s3r_set_epoch")
+           "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -120,7 +120,9 @@ def load(path: str = LIB_PATH):
     L.s3r_set_lod.argtypes = [vp, P(LodParams)]
     L.s3r_set_counting.argtypes = [vp, i32]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
-    L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp]
+    L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp, vp]
+    L.s3r_device_status.argtypes = [vp]
+    L.s3r_device_status.restype = vp
     L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp]
     L.s3r_check_wait_timeout.argtypes = [vp, i32, vp]
     L.s3r_set_epoch.argtypes = [vp, ctypes.c_uint32, vp]
@@ -292,6 +294,10 @@ class Workspace:
     def sync_status(self, stream=None):
         _check(load().s3r_sync_status(self._h, _stream(stream)))
 
+    def status_word(self) -> int:
+        """Device address of the latched status word (adam_step's gate)."""
+        return int(load().s3r_device_status(self._h) or 0)
+
     def set_epoch(self, epoch: int, stream=None):
         """Restore the call counter of a saved run (resume of the Eq. 7 draws)."""
         _check(load().s3r_set_epoch(self._h, int(epoch) & 0xFFFFFFFF, _stream(stream)))
@@ -349,8 +355,10 @@ def to_world(c_scene, poses, means_out, quats_out, stream=None):
 
 
 def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1: float = 0.9,
-              beta2: float = 0.999, eps: float = 1e-8, stream=None):
-    """One fused Adam step over up to 8 (param, grad, m, v) tensor groups."""
+              beta2: float = 0.999, eps: float = 1e-8, stream=None, gate: int | None = None):
+    """One fused Adam step over up to 8 (param, grad, m, v) tensor groups.
+    `gate`: device address of a uint32 (e.g. Workspace.status_word()); the
+    step changes nothing unless it reads 0 on the device."""
     if not (len(params) == len(grads) == len(exp_avgs) == len(exp_avg_sqs)):
         raise ValueError("adam_step: one gradient and two moment tensors per parameter")
     arr = (AdamTensor * max(1, len(params)))()
@@ -360,7 +368,8 @@ def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1:
                 raise ValueError("adam_step: float32 tensors of equal size required")
         arr[i] = AdamTensor(_ptr(p), _ptr(g), _ptr(m), _ptr(v), int(p.numel()))
     _check(load().s3r_adam_step(arr, len(params), float(lr), float(beta1), float(beta2),
-                                float(eps), int(step), _stream(stream)))
+                                float(eps), int(step), ctypes.c_void_p(gate) if gate else None,
+                                _stream(stream)))
 
 
 def update_visibility(n: int, t: float, mask, point_life, vis_window, mode: int, stream=None):

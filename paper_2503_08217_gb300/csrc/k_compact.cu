@@ -21,15 +21,23 @@ constexpr int kRounds = 8;                            // float4 loads per lane
 constexpr int kWarpSpan = kRounds * 32 * 2;           // Gaussians per warp
 constexpr int kTileSpan = kWarps * kWarpSpan;         // 4096 Gaussians per tile
 
-__global__ void k_begin(uint32_t* ctr, uint32_t* hist) {
+__global__ void k_begin(uint32_t* ctr, uint32_t* hist, unsigned long long* lookback,
+                        int64_t lookback_words) {
   // one block: zero the per-call counters and histograms, bump the epoch
   for (int i = threadIdx.x; i < kHistCount * kRadix; i += blockDim.x) hist[i] = 0;
+  const uint32_t epoch = ctr[kCtrEpoch] + 1;
+  __syncthreads();   // every thread has read the old epoch
   // the status word, the epoch and the blend pair counts (which describe the
   // last counted render) survive
   if (threadIdx.x < kCtrCount && threadIdx.x != kCtrStatus && threadIdx.x != kCtrEpoch &&
       (threadIdx.x < kCtrPairs || threadIdx.x > kCtrEvalBwd + 1))
     ctr[threadIdx.x] = 0;
-  if (threadIdx.x == 0) ctr[kCtrEpoch] = ctr[kCtrEpoch] + 1;
+  if (threadIdx.x == 0) ctr[kCtrEpoch] = epoch;
+  // look-back tags keep the epoch's low 26 bits: when they wrap, words of the
+  // call 2^26 calls ago would carry the current tags, so every word is
+  // cleared (once per 67,108,864 calls)
+  if ((epoch & ((1u << 26) - 1u)) == 0u)
+    for (int64_t i = threadIdx.x; i < lookback_words; i += blockDim.x) lookback[i] = 0ull;
 }
 
 __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ vis, int64_t n,
@@ -107,14 +115,14 @@ __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ 
 
 cudaError_t launch_begin(s3r_workspace* ws, cudaStream_t st) {
   KernelTimer timer(ws, kKBegin, st);
-  k_begin<<<1, 256, 0, st>>>(ws->ctr, ws->hist);
+  k_begin<<<1, 256, 0, st>>>(ws->ctr, ws->hist, ws->lookback, ws->lookback_words);
   return cudaGetLastError();
 }
 
 cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float t,
                            cudaStream_t st) {
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
-  int64_t grid = ws->num_sms * 8;
+  int64_t grid = (int64_t)ws->num_sms * 8;
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;
   KernelTimer timer(ws, kKCompact, st);
@@ -144,10 +152,12 @@ static __device__ __align__(256) StaticScratch g_static_scratch;
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 StaticScratch* g_static_ptr[kMaxDevices] = {};
+int g_static_sms[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (host code cannot use the symbol itself as a device pointer).
-s3r_status static_scratch(StaticScratch** out) {
+// Device address of the scratch array on the current device and the
+// device's SM count, looked up once per device (host code cannot use the
+// symbol itself as a device pointer).
+s3r_status static_scratch(StaticScratch** out, int* sms) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_last_error(S3R_ERR_CUDA, cudaGetErrorString(e));
@@ -161,10 +171,25 @@ s3r_status static_scratch(StaticScratch** out) {
       const std::string msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
       return set_last_error(S3R_ERR_CUDA, msg.c_str());
     }
+    int n_sms = 0;
+    e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess || n_sms < 1) {
+      const std::string msg = std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e);
+      return set_last_error(S3R_ERR_CUDA, msg.c_str());
+    }
+    g_static_sms[dev] = n_sms;
     g_static_ptr[dev] = static_cast<StaticScratch*>(p);
   }
   *out = g_static_ptr[dev];
+  *sms = g_static_sms[dev];
   return S3R_OK;
+}
+
+// The list length, or 0xffffffff where a look-back wait of the call gave up
+// (the list is then not valid): the status word is only in the scratch, so
+// the call reports it through its output.
+__global__ void k_static_finish(const uint32_t* ctr, uint32_t* out_count) {
+  *out_count = (ctr[kCtrStatus] & kStatusTimeout) ? 0xffffffffu : ctr[kCtrSelected];
 }
 
 }  // namespace
@@ -185,7 +210,8 @@ extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float*
                           "s3r_select_visible_static: vis_window (16-byte aligned) and out_idx are required");
   if (!(t == t)) return set_last_error(S3R_ERR_INVALID, "s3r_select_visible_static: t is NaN");
   StaticScratch* sc = nullptr;
-  s3r_status st = static_scratch(&sc);
+  int sms = 0;
+  s3r_status st = static_scratch(&sc, &sms);
   if (st != S3R_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
@@ -195,14 +221,16 @@ extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float*
   if (e == cudaSuccess && n_tiles > 0)
     e = cudaMemsetAsync(sc->lookback, 0, sizeof(unsigned long long) * (size_t)n_tiles, s);
   if (e == cudaSuccess) {
-    int64_t grid = 152 * 8;
+    int64_t grid = (int64_t)sms * 8;
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) grid = 1;
     k_compact<<<(unsigned)grid, kThreads, 0, s>>>(vis_window, n, t, out_idx, sc->ctr, sc->lookback);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(out_count, sc->ctr + kCtrSelected, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    k_static_finish<<<1, 1, 0, s>>>(sc->ctr, out_count);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return set_last_error(S3R_ERR_CUDA, cudaGetErrorString(e));
   return S3R_OK;
 }

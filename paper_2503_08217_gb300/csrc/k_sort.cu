@@ -412,6 +412,37 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
   }
 }
 
+// Exclusive saturating scan (sat_add) of one value per thread across a
+// 256-thread block; inputs <= kSat.
+__device__ __forceinline__ uint32_t block_excl_scan_sat(uint32_t x, uint32_t* s_tmp /*[8]*/,
+                                                        uint32_t* total) {
+  const uint32_t lane = lane_id();
+  const int warp = threadIdx.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (uint32_t)o) incl = sat_add(incl, y);
+  }
+  uint32_t excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = 0;
+  if (lane == 31) s_tmp[warp] = incl;
+  __syncthreads();
+  uint32_t wbase = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = s_tmp[w];
+    if (w < warp) wbase = sat_add(wbase, c);
+    tot = sat_add(tot, c);
+  }
+  __syncthreads();
+  *total = tot;
+  return sat_add(wbase, excl);
+}
+
+// Pair offsets saturate at kSat (above every capacity, which is < 2^31), so a
+// real pair count of 2^32 or more cannot wrap into a small one: it latches
+// the capacity status like any other overflow.
 __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
   __shared__ uint32_t s_tmp[8];
   __shared__ uint32_t s_tile, s_base;
@@ -435,28 +466,29 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
-      cnt[k] = r0[k].x;
-      run += cnt[k];
+      cnt[k] = min(r0[k].x, kSat);
+      run = sat_add(run, cnt[k]);
       if (i0 + k < n) {
         a.dup_meta[2 * (i0 + k)] = make_uint4(sp[k], r0[k].y, r0[k].z, r0[k].w);
         a.dup_meta[2 * (i0 + k) + 1] = r1[k];
       }
     }
     uint32_t total;
-    uint32_t ex = block_excl_scan(run, s_tmp, &total);
+    uint32_t ex = block_excl_scan_sat(run, s_tmp, &total);
     if (threadIdx.x < 32) {
-      const uint32_t prefix = warp_lookback(a.lookback, tile, tag, total, a.ctr);
+      const uint32_t prefix = warp_lookback<true>(a.lookback, tile, tag, total, a.ctr);
       if (threadIdx.x == 0) {
         s_base = prefix;
         if (tile == n_tiles - 1) {
-          a.ctr[kCtrDups] = prefix + total;
-          a.dup_excl[n] = prefix + total;              // sentinel
-          if ((int64_t)prefix + total > a.cap_dups) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
+          const uint32_t all = sat_add(prefix, total);
+          a.ctr[kCtrDups] = all;
+          a.dup_excl[n] = all;                          // sentinel
+          if ((int64_t)all > a.cap_dups) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
         }
       }
     }
     __syncthreads();
-    ex += s_base;
+    ex = sat_add(ex, s_base);
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
       if (i0 + k < n) {
@@ -467,11 +499,11 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
         for (uint64_t c = ((uint64_t)ex + kExpChunk - 1) / kExpChunk; c * kExpChunk < e1; ++c)
           a.dup_chunk[c] = (uint32_t)(i0 + k);
       }
-      ex += cnt[k];
+      ex = sat_add(ex, cnt[k]);
     }
     if (tile == n_tiles - 1 && threadIdx.x == 0) {
       // after the last chunk: the last splat (chunks end at an inclusive splat bound)
-      const uint64_t tot = min((uint64_t)s_base + total, (uint64_t)a.cap_dups);
+      const uint64_t tot = min((uint64_t)sat_add(s_base, total), (uint64_t)a.cap_dups);
       a.dup_chunk[(tot + kExpChunk - 1) / kExpChunk] = (uint32_t)(n - 1);
     }
     __syncthreads();

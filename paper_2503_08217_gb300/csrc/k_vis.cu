@@ -59,6 +59,7 @@ struct AdamSet {
   int vec[S3R_ADAM_MAX_TENSORS];
   int count;
   float lr, b1, b2, eps, inv_bc1, inv_sqrt_bc2;
+  const uint32_t* gate;   // optional device word: the step is skipped unless it reads 0
 };
 
 __device__ __forceinline__ void adam1(const AdamSet& s, float& p, float g, float& m, float& v) {
@@ -68,6 +69,7 @@ __device__ __forceinline__ void adam1(const AdamSet& s, float& p, float g, float
 }
 
 __global__ void k_adam(const __grid_constant__ AdamSet s) {
+  if (s.gate && *s.gate != 0u) return;   // an earlier call of the step failed: change nothing
   const int64_t total = s.ustart[s.count];
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < total;
        u += (int64_t)gridDim.x * blockDim.x) {
@@ -101,9 +103,10 @@ __global__ void k_adam(const __grid_constant__ AdamSet s) {
 }  // namespace
 
 cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
-                        float eps, float bc1, float bc2, cudaStream_t st) {
+                        float eps, float bc1, float bc2, const uint32_t* gate, cudaStream_t st) {
   AdamSet s;
   s.count = count;
+  s.gate = gate;
   s.ustart[0] = 0;
   for (int k = 0; k < count; ++k) {
     s.t[k] = t[k];
@@ -124,7 +127,7 @@ cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1,
   const int64_t total = s.ustart[count];
   if (total == 0) return cudaSuccess;
   int64_t blocks = (total + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
   k_adam<<<(unsigned)blocks, 256, 0, st>>>(s);
   return cudaGetLastError();
 }
@@ -142,7 +145,7 @@ cudaError_t launch_zero(void* p, int64_t words, cudaStream_t st) {
   if (words <= 0) return cudaSuccess;
   const int64_t n4 = words / 4;
   int64_t blocks = (n4 + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
   if (blocks < 1) blocks = 1;
   k_zero<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<uint4*>(p), n4,
                                            reinterpret_cast<uint32_t*>(p) + 4 * n4,
@@ -154,7 +157,7 @@ cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, fl
                            float* loss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
   k_l1<<<(unsigned)blocks, 256, 0, st>>>(n, pred, target, grad, loss);
   return cudaGetLastError();
 }
@@ -163,7 +166,7 @@ cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* l
                               int mode, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int64_t blocks = (n + 255) / 256;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > (int64_t)sm_count() * 64) blocks = (int64_t)sm_count() * 64;
   k_vis<<<(unsigned)blocks, 256, 0, st>>>(n, t, mask, reinterpret_cast<float2*>(life),
                                           reinterpret_cast<float2*>(vis), mode);
   return cudaGetLastError();

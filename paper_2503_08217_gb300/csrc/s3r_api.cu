@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -124,6 +125,18 @@ s3r_status set_last_error(s3r_status st, const char* msg) {
   g_last_error = msg;
   return st;
 }
+
+int sm_count() {
+  constexpr int kMaxDevices = 64;
+  static std::atomic<int> cache[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
 }  // namespace s3r
 
 extern "C" {
@@ -146,8 +159,8 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   DeviceGuard g(device);
   if (!g.ok) return fail(S3R_ERR_CUDA, "cannot select device %d", device);
   s3r_workspace* ws = new s3r_workspace();
-  ws->lod = s3r_lod_params{S3R_LOD_THRESHOLD, 0.f, 1.f, {0.f, 0.f, 0.f}, 0u};
   memset(ws, 0, sizeof(*ws));
+  ws->lod = s3r_lod_params{S3R_LOD_THRESHOLD, 0.f, 1.f, {0.f, 0.f, 0.f}, 0u};
   ws->device = device;
   ws->cap = *cap;
   cudaError_t e = cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -434,12 +447,14 @@ s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params) {
 }
 
 s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr, float beta1,
-                         float beta2, float eps, int32_t step, void* stream) {
+                         float beta2, float eps, int32_t step, const uint32_t* gate,
+                         void* stream) {
   if (!tensors || count < 0 || count > S3R_ADAM_MAX_TENSORS)
     return fail(S3R_ERR_INVALID, "adam: 0 <= count <= %d tensors required", S3R_ADAM_MAX_TENSORS);
   if (step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) ||
       !std::isfinite(lr))
     return fail(S3R_ERR_INVALID, "adam: step >= 1, betas in [0, 1), eps > 0 required");
+  if (gate && !aligned(gate, 4)) return fail(S3R_ERR_INVALID, "adam: gate must be a device uint32");
   for (int k = 0; k < count; ++k) {
     const s3r_adam_tensor& t = tensors[k];
     if (t.n < 0) return fail(S3R_ERR_INVALID, "adam: tensor %d has n < 0", k);
@@ -448,7 +463,7 @@ s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr
       return fail(S3R_ERR_INVALID, "adam: tensor %d needs four float arrays", k);
   }
   const double bc1 = 1.0 - std::pow((double)beta1, step), bc2 = 1.0 - std::pow((double)beta2, step);
-  cudaError_t e = launch_adam(tensors, count, lr, beta1, beta2, eps, (float)bc1, (float)bc2,
+  cudaError_t e = launch_adam(tensors, count, lr, beta1, beta2, eps, (float)bc1, (float)bc2, gate,
                               (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "adam");
   return S3R_OK;
@@ -469,13 +484,9 @@ s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* m
     return fail(S3R_ERR_INVALID, "means 4-byte and quaternions 16-byte aligned required");
   s3r_status st = check_poses(scene, poses);
   if (st != S3R_OK) return st;
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return cuda_fail(e, "to_world: device query");
   const s3r_poses none = {nullptr, nullptr};
-  e = launch_to_world(scene, poses ? poses : &none, means_out, quats_out, sms > 0 ? sms : 1,
-                      (cudaStream_t)stream);
+  cudaError_t e = launch_to_world(scene, poses ? poses : &none, means_out, quats_out, sm_count(),
+                                  (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "to_world");
   return S3R_OK;
 }
@@ -517,22 +528,20 @@ s3r_status s3r_query_counts(s3r_workspace* ws, void* stream, s3r_counts* out) {
 s3r_status s3r_set_epoch(s3r_workspace* ws, uint32_t epoch, void* stream) {
   if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
   DeviceGuard g(ws->device);
-  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  uint32_t cur = 0;
-  if ((e = cudaMemcpy(&cur, ws->ctr + kCtrEpoch, sizeof(cur), cudaMemcpyDeviceToHost)) !=
+  cudaStream_t s = (cudaStream_t)stream;
+  // the counter also tags the look-back words: a jump could bring back the
+  // tag of an earlier call, so every word is cleared with it
+  cudaError_t e = cudaMemsetAsync(ws->lookback, 0, sizeof(unsigned long long) * ws->lookback_words, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync look-back words");
+  if ((e = cudaMemcpyAsync(ws->ctr + kCtrEpoch, &epoch, sizeof(epoch), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
-    return cuda_fail(e, "cudaMemcpy epoch");
-  // the counter tags look-back words: after the first call a tag in the array
-  // must never come back, so the counter only moves forward, by < 2^25
-  if (cur != 0 && (epoch < cur || epoch - cur >= (1u << 25)))
-    return fail(S3R_ERR_INVALID,
-                "after the first call the call counter only moves forward by less than 2^25 "
-                "(%u -> %u)", cur, epoch);
-  if ((e = cudaMemcpy(ws->ctr + kCtrEpoch, &epoch, sizeof(epoch), cudaMemcpyHostToDevice)) !=
-      cudaSuccess)
-    return cuda_fail(e, "cudaMemcpy epoch");
+    return cuda_fail(e, "cudaMemcpyAsync epoch");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   return S3R_OK;
+}
+
+const uint32_t* s3r_device_status(const s3r_workspace* ws) {
+  return ws ? ws->ctr + kCtrStatus : nullptr;
 }
 
 s3r_status s3r_sync_status(s3r_workspace* ws, void* stream) {

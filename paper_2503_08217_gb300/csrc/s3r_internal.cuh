@@ -204,7 +204,9 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
 cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                                const s3r_grads* g, cudaStream_t st);
 cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
-                        float eps, float bc1, float bc2, cudaStream_t st);
+                        float eps, float bc1, float bc2, const uint32_t* gate, cudaStream_t st);
+// SM count of the current device (queried once per device, then cached).
+int sm_count();
 // Zero `words` 32-bit words at a 16-byte aligned device address with a
 // kernel (no copy-engine memset: a captured step then overlaps host-to-device
 // copies on another stream).
@@ -279,13 +281,24 @@ __device__ __forceinline__ uint32_t lane_id_() {
   return l;
 }
 
+// Saturating sum for running sums that may pass 2^32 (the pair offsets):
+// values at or above kSat mean "more than any capacity" and stay there. For
+// operands <= kSat the 64-bit sum cannot wrap, and min(a + b, kSat) is
+// associative, so any summation order gives min(exact sum, kSat).
+constexpr uint32_t kSat = 0x80000000u;
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
+  const unsigned long long s = (unsigned long long)a + b;
+  return s > kSat ? kSat : (uint32_t)s;
+}
+
 // Warp-cooperative form of lookback_prefix for one running sum over tiles at
 // stride 1: all 32 lanes of ONE warp call it with the same arguments. Each
 // step reads 32 predecessors at once and stops at the nearest one that has
 // published its inclusive prefix, so a walk over w unfinished predecessors
 // takes ceil(w/32) dependent loads instead of w. Returns the exclusive
 // prefix in every lane; lane 0 publishes the inclusive value. Bounded like
-// lookback_prefix.
+// lookback_prefix. kSaturate: every sum is sat_add (aggregates <= kSat).
+template <bool kSaturate = false>
 __device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int64_t tile,
                                                   uint32_t tag, uint32_t aggregate, uint32_t* ctr,
                                                   int max_polls = kSpinLimit) {
@@ -318,12 +331,16 @@ __device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int
     }
     uint32_t part = ((int)lane <= first) ? val : 0u;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    prefix += part;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, part, o);
+      part = kSaturate ? sat_add(part, y) : part + y;
+    }
+    prefix = kSaturate ? sat_add(prefix, part) : prefix + part;
     if (first < 32) break;
     base -= 32;
   }
-  if (lane == 0) st_relaxed(words + tile, lb_word(tag, 2u, prefix + aggregate));
+  if (lane == 0)
+    st_relaxed(words + tile, lb_word(tag, 2u, kSaturate ? sat_add(prefix, aggregate) : prefix + aggregate));
   return prefix;
 }
 

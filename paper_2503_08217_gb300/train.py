@@ -147,9 +147,19 @@ class Trainer:
         self.grads["inst_trans"] = torch.zeros((n_inst, 3), device=dev)
         self.loss = torch.zeros(1, device=dev)
 
-    def step(self, k: int, target: torch.Tensor):
+    def step(self, k: int, target: torch.Tensor, *, check: bool = True):
         """One optimisation step on timestep k; returns (loss [1], rendered
-        image, flat planar per view) as device tensors."""
+        image, flat planar per view) as device tensors.
+
+        Both Adam updates are gated on the device by the workspace's latched
+        status: if a call of this step (or an earlier unchecked one) dropped
+        splats or pairs for lack of capacity, or a bounded wait gave up, the
+        parameters and moments are left as they were. With `check` (the
+        default) the status is read after the step (one host
+        synchronisation): a failure raises binding.S3RError and the step is not
+        counted. With check=False no synchronisation happens; call check()
+        before relying on the step counters, which then count steps that the
+        device may have skipped."""
         s = self.state
         cams, t = self.cams[k], float(self.times[k])
         out = torch.empty(3 * pixel_count(cams), device=s.scene.means.device)
@@ -163,17 +173,30 @@ class Trainer:
         binding.l1_loss(out, target, dL, self.loss)
         self.renderer.backward(s.scene, iq, it, self.background, dL, self.grads)
         b1, b2 = self.betas
+        gate = self.renderer.ws.status_word()
+        counters = (s.adam_steps, s.pose_steps[k], s.step)
         s.adam_steps += 1
         binding.adam_step(s.scene.params(), [self.grads[n] for n in PARAM_NAMES], s.exp_avg,
-                          s.exp_avg_sq, self.lr, s.adam_steps, b1, b2, self.eps)
+                          s.exp_avg_sq, self.lr, s.adam_steps, b1, b2, self.eps, gate=gate)
         if iq.numel():
             s.pose_steps[k] += 1
             binding.adam_step([iq, it], [self.grads["inst_quat"], self.grads["inst_trans"]],
                               [s.pose_exp_avg[0][k], s.pose_exp_avg[1][k]],
                               [s.pose_exp_avg_sq[0][k], s.pose_exp_avg_sq[1][k]],
-                              self.pose_lr, s.pose_steps[k], b1, b2, self.eps)
+                              self.pose_lr, s.pose_steps[k], b1, b2, self.eps, gate=gate)
         s.step += 1
+        if check:
+            try:
+                self.check()
+            except binding.S3RError:
+                s.adam_steps, s.pose_steps[k], s.step = counters
+                raise
         return self.loss, out
+
+    def check(self) -> None:
+        """Synchronise and raise binding.S3RError if a call of the workspace
+        latched a failure since the last check (reading clears it)."""
+        self.renderer.sync_status()
 
     def save(self, path) -> None:
         """Checkpoint the state after the steps so far. Synchronises; raises

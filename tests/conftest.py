@@ -27,3 +27,14 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Print what the GPU parity comparisons left out (recorded by
+    gpu_helpers.report), so that a -q run's log shows how much was compared."""
+    gh = sys.modules.get("gpu_helpers")
+    lines = getattr(gh, "REPORT", None) if gh is not None else None
+    if lines:
+        terminalreporter.section("parity exclusions")
+        for line in lines:
+            terminalreporter.write_line(line)

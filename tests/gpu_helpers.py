@@ -13,6 +13,15 @@ from paper_2503_08217_gb300 import binding
 from paper_2503_08217_gb300.render import DeviceScene, Renderer, pixel_count, split_views
 
 
+# Lines for the "parity exclusions" section of the pytest summary: what each
+# comparison left out (near-threshold Gaussians, excluded pixels) and why.
+REPORT: list = []
+
+
+def report(test: str, **counts) -> None:
+    REPORT.append(test + ": " + ", ".join(f"{k} {v}" for k, v in counts.items()))
+
+
 def gpu_step(scene, step, cams, vis, life=None, lod=0.0, bg=(0.0, 0.0, 0.0), dL=None,
              renderer=None, max_splats=None, max_duplicates=None, dev=None):
     """Run project/sort/fwd (and bwd if dL is given) on cuda:0."""
@@ -108,43 +117,66 @@ def sweep_visibility(scene, cams_fn=None, lod=0.0):
     return oracle.vis_finalize(life), life
 
 
-def bad_pixels(cam, rec, flag):
-    """Pixels to leave out of an image comparison: the blend flagged them, or
-    they lie in a tile whose membership in a flagged Gaussian's list may flip
-    between FP32 and FP64: the tile column/row on either side of a flagged
-    rectangle edge, the whole ring for a flagged radius, the whole rectangle
-    (grown by one tile) for a near-plane or LOD flag."""
+def bad_pixels(cam, rec, flag, alpha_margin=1e-3):
+    """Pixels to leave out of an image comparison: the oracle's blend flagged
+    them (a decision within its margins of a threshold), or a near-threshold
+    decision of one Gaussian's projection may flip between FP32 and FP64 and
+    that Gaussian reaches the pixel. The decisions and the tiles they can
+    change: a rectangle edge (the tile column or row on either side of it), the
+    3-sigma radius (one tile on either side of every edge), the near plane,
+    the LOD threshold or an Eq. 7 draw (the whole rectangle grown by one tile).
+    Within those tiles only the pixels where the Gaussian's FP64 alpha = min(0.99,
+    o exp(-q/2)) reaches 1/255 (less a relative margin far above the FP32
+    rounding of alpha) are left out: at every other pixel the blend skips the
+    Gaussian, so whether it is in the tile's list does not matter. A Gaussian
+    whose record has no usable conic (behind the near plane in FP64) leaves
+    out every pixel of those tiles."""
     bad = flag.copy()
     H, W = cam.height, cam.width
     gx, gy = (W + 15) // 16, (H + 15) // 16
     bits = rec.get("near_bits", rec["near"].astype(np.int32) * 1)
     cand = np.nonzero((bits != 0) & (rec["infrustum"] | (rec["p"][:, 2] > 0)))[0]
-
-    def mark(xa, ya, xb, yb):
-        xa, ya = max(0, xa), max(0, ya)
-        xb, yb = min(gx, xb), min(gy, yb)
-        if xb > xa and yb > ya:
-            bad[ya * 16:yb * 16, xa * 16:xb * 16] = True
+    thr = (1.0 / 255.0) * (1.0 - alpha_margin)
 
     for i in cand:
         b = int(bits[i])
         x0, y0, x1, y1 = (int(q) for q in rec["rect"][i])
-        if (b & (1 | 64)) or x1 <= x0 or y1 <= y0:
+        u, v = (float(q) for q in rec["uv"][i])
+        A, B, C = (float(q) for q in rec["conic"][i])
+        o = float(rec["opacity"][i])
+        usable = (np.isfinite([u, v, A, B, C, o]).all() and A > 0 and C > 0 and A * C - B * B > 0
+                  and bool(rec["infrustum"][i] or rec["p"][i, 2] > 0))
+        boxes = []
+        if (b & (1 | 64 | 128)) or x1 <= x0 or y1 <= y0:
             if x1 <= x0 or y1 <= y0:   # a rect that may be empty on one side: around the centre
-                u, v = rec["uv"][i]
                 r = int(rec["radius"][i]) // 16 + 2
                 x0, x1 = int(u // 16) - r, int(u // 16) + r + 1
                 y0, y1 = int(v // 16) - r, int(v // 16) + r + 1
-            mark(x0 - 1, y0 - 1, x1 + 1, y1 + 1)
-            continue
-        if b & 32:
-            b |= 2 | 4 | 8 | 16
-        if b & 2:
-            mark(x0 - 1, y0 - 1, x0 + 1, y1 + 1)
-        if b & 4:
-            mark(x1 - 1, y0 - 1, x1 + 1, y1 + 1)
-        if b & 8:
-            mark(x0 - 1, y0 - 1, x1 + 1, y0 + 1)
-        if b & 16:
-            mark(x0 - 1, y1 - 1, x1 + 1, y1 + 1)
+            boxes.append((x0 - 1, y0 - 1, x1 + 1, y1 + 1))
+        else:
+            if b & 32:
+                b |= 2 | 4 | 8 | 16
+            if b & 2:
+                boxes.append((x0 - 1, y0 - 1, x0 + 1, y1 + 1))
+            if b & 4:
+                boxes.append((x1 - 1, y0 - 1, x1 + 1, y1 + 1))
+            if b & 8:
+                boxes.append((x0 - 1, y0 - 1, x1 + 1, y0 + 1))
+            if b & 16:
+                boxes.append((x0 - 1, y1 - 1, x1 + 1, y1 + 1))
+        for xa, ya, xb, yb in boxes:
+            xa, ya = max(0, xa), max(0, ya)
+            xb, yb = min(gx, xb), min(gy, yb)
+            if not (xb > xa and yb > ya):
+                continue
+            ys, ye = ya * 16, min(H, yb * 16)
+            xs, xe = xa * 16, min(W, xb * 16)
+            if not usable:
+                bad[ys:ye, xs:xe] = True
+                continue
+            dy = (np.arange(ys, ye) + 0.5 - v)[:, None]
+            dx = (np.arange(xs, xe) + 0.5 - u)[None, :]
+            q = A * dx * dx + 2.0 * B * dx * dy + C * dy * dy
+            alpha = np.minimum(0.99, o * np.exp(-0.5 * q))
+            bad[ys:ye, xs:xe] |= alpha >= thr
     return bad

@@ -48,6 +48,7 @@ def test_invalid_calls_fail_without_a_gpu():
     assert L.s3r_check_wait_timeout(None, 100, None) == 1
     assert L.s3r_set_epoch(None, 5, None) == 1
     assert b"workspace" in L.s3r_last_error()
+    assert L.s3r_device_status(None) is None
 
 
 def test_adam_argument_checks_fail_without_a_gpu():
@@ -56,11 +57,11 @@ def test_adam_argument_checks_fail_without_a_gpu():
     L = binding.load()
     T = binding.AdamTensor
     arr = (T * 9)()
-    assert L.s3r_adam_step(arr, 9, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1     # > 8 tensors
-    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1     # step 0
-    assert L.s3r_adam_step(arr, 1, 1e-3, 1.0, 0.999, 1e-8, 1, None) == 1     # beta1 = 1
+    assert L.s3r_adam_step(arr, 9, 1e-3, 0.9, 0.999, 1e-8, 1, None, None) == 1     # > 8 tensors
+    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 0, None, None) == 1     # step 0
+    assert L.s3r_adam_step(arr, 1, 1e-3, 1.0, 0.999, 1e-8, 1, None, None) == 1     # beta1 = 1
     arr[0] = T(None, None, None, None, 10)
-    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 1, None) == 1     # NULL arrays
+    assert L.s3r_adam_step(arr, 1, 1e-3, 0.9, 0.999, 1e-8, 1, None, None) == 1     # NULL arrays
     assert b"adam" in L.s3r_last_error()
 
 

@@ -1,16 +1,25 @@
 """Full-size parity on sampled outputs: the surround-rig workload the bench
-times (9.0M Gaussians, 7 cameras, 12.8 Mpix, SH3, LOD 1 px), in the bench's
-launch configuration (one batched call sequence over all cameras), against
+times (9.0M Gaussians, 7 cameras, 12.8 Mpix, SH3, LOD 1 px) at the bench's
+timestep and in its state and launch configuration (one batched call
+sequence over all cameras, after a first-epoch sweep has recorded the point
+lives, Eq. 5, and Eq. 6 has turned them into visibility windows), against
 the FP64 oracle computed one sample at a time:
 
-  * 3000 sampled Gaussians: frustum/keep masks exactly, splat records within
-    the FP32 tolerances, for every camera;
+  * the visibility record: the oracle's own sweep of 20,000 sampled
+    Gaussians over all 300 timesteps and 7 cameras, then Eq. 6, equals the
+    GPU's record at those Gaussians exactly (away from near-threshold
+    projection decisions);
+  * the selection of the bench's timestep from the GPU's record equals the
+    oracle's selection of the same record, every index;
+  * 3000 sampled selected Gaussians: frustum/keep masks exactly, splat
+    records within the FP32 tolerances, for every camera;
+  * the sort of all pairs over the 50,400 tiles (two tile-digit passes)
+    equals the oracle's stable sort of the GPU's FP32 splats with only
+    unreachable pairs left out (a sample of them checked), and the tile
+    ranges are those of the sorted list;
   * 24 sampled pixels per camera: Eq. 2 at those pixels (<= 1e-4);
   * the gradient of a loss supported on those pixels w.r.t. every parameter
     and pose (<= 1e-3 relative per tensor).
-
-The visibility record is the reset one (visible at all times), i.e. the first
-step of training, so that the oracle needs no sweep of its own.
 """
 from __future__ import annotations
 
@@ -24,52 +33,124 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+def _full_rig_pairs_isolated(res, cams, rng, n_unreached=200_000):
+    """The stage-isolated sort check of the parity tests at full size: the
+    GPU's pairs against the oracle's keys and stable sort of the GPU's FP32
+    splats (every pair), unreachability of a sample of the left-out pairs."""
+    from test_gpu_parity import _assert_unreached, _oracle_pairs
+    ov, ot = _oracle_pairs(res, cams)
+    gv = res["sorted_splats"].astype(np.int64)
+    gt = res["sorted_tiles"].astype(np.int64)
+    S = max(int(res["xy"].shape[0]), 1)
+    keep = np.isin(ot * S + ov, gt * S + gv)
+    assert int(keep.sum()) == gv.size
+    np.testing.assert_array_equal(gv, ov[keep])
+    np.testing.assert_array_equal(gt, ot[keep])
+    out = np.nonzero(~keep)[0]
+    pick = out if out.size <= n_unreached else rng.choice(out, n_unreached, replace=False)
+    _assert_unreached(res, cams, ov[pick], ot[pick])
+    ranges = np.zeros((res["ranges"].shape[0], 2), np.int64)
+    first = np.r_[0, np.nonzero(np.diff(gt))[0] + 1]
+    last = np.r_[first[1:], gt.size]
+    ranges[gt[first], 0] = first
+    ranges[gt[first], 1] = last
+    np.testing.assert_array_equal(res["ranges"].astype(np.int64), ranges)
+    return int(ov.size), int(out.size), int(pick.size)
+
+
 def test_rig_full_size_sampled():
     import gpu_helpers
-    from paper_2503_08217_gb300 import build
+    from paper_2503_08217_gb300 import binding, build
     from paper_2503_08217_gb300.render import DeviceScene, Renderer
     build.build()
+    binding.load()
     scene = scenegen.generate("rig", seed=0)
     k = scene.n_steps // 2
     cams = scene.cams[k]
     lod = 1.0
     n = scene.n
-    vis, _ = oracle.vis_reset(n)
     rng = np.random.default_rng(5)
 
+    # GPU, bench launch configuration and state: the first-epoch sweep with
+    # every Gaussian selectable, Eq. 5 into the point lives, then Eq. 6
+    max_splats = max(4096, int(n * min(len(cams), 3)))
+    r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
+    dev = DeviceScene.from_host(scene)
+    cs = dev.c_scene()
+    vis_t = torch.empty((n, 2), device="cuda")
+    life_t = torch.empty((n, 2), device="cuda")
+    binding.update_visibility(n, 0.0, None, life_t, vis_t, binding.VIS_RESET)
+    all_vis = vis_t.clone()
+    for kk in range(scene.n_steps):
+        iq = torch.from_numpy(scene.inst_quat[kk]).cuda()
+        it = torch.from_numpy(scene.inst_trans[kk]).cuda()
+        r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
+                     life_t, lod)
+    binding.update_visibility(n, 0.0, None, life_t, vis_t, binding.VIS_FINALIZE)
+    torch.cuda.synchronize()
+    r.counts()      # a capacity flag of the sweep's projections is not part of this check
+    vis = vis_t.cpu().numpy()
+    life = life_t.cpu().numpy()
+    del all_vis
+
+    # the oracle's own sweep of sampled Gaussians (M_t is per Gaussian: with
+    # every window open, a Gaussian's record depends on its own projections only)
+    samp = np.sort(rng.choice(n, 20_000, replace=False))
+    _, life_o = oracle.vis_reset(samp.size)
+    near_any = np.zeros(samp.size, bool)
+    for kk in range(scene.n_steps):
+        mt = np.zeros(samp.size, bool)
+        for cam in scene.cams[kk]:
+            rec = oracle.project(scene, samp, kk, cam, lod)
+            mt |= rec["infrustum"]
+            near_any |= rec["near"]
+        oracle.vis_record(life_o, mt, np.float32(scene.times[kk]))
+    vis_o = oracle.vis_finalize(life_o)
+    ok = ~near_any
+    np.testing.assert_array_equal(life[samp][ok], life_o[ok])
+    np.testing.assert_array_equal(vis[samp][ok], vis_o[ok])
+    assert near_any.sum() <= 3e-3 * samp.size
+    t = float(scene.times[k])
+    sel = oracle.select(vis, t)
+    assert 0 < sel.size < n                       # the record leaves Gaussians out
+
     # oracle projection of every camera (FP64), and the pixel samples
-    sel = oracle.select(vis, float(scene.times[k]))
     recs = [oracle.project(scene, sel, k, cam, lod) for cam in cams]
-    samples, dL, expect = [], [], []
+    samples, dL = [], []
+    cand = excl = flagged = 0
     for v, cam in enumerate(cams):
         bad = gpu_helpers.bad_pixels(cam, recs[v], np.zeros((cam.height, cam.width), bool))
         py = rng.integers(0, cam.height, 400)
         px = rng.integers(0, cam.width, 400)
         keep = ~bad[py, px]
+        cand += py.size
+        excl += int((~keep).sum())
         pix = np.unique(np.stack([py[keep], px[keep]], 1), axis=0)
         pix = pix[rng.permutation(pix.shape[0])][:48]
         o = oracle.render_pixels(oracle.select_splats(recs[v]), pix[:, 1], pix[:, 0])
+        flagged += int(o["flag"].sum())
         pix = pix[~o["flag"]][:24]          # no near-threshold blend decision
+        assert pix.shape[0] == 24
         samples.append((pix[:, 1], pix[:, 0]))
         d = np.zeros((3, cam.height, cam.width))
         d[:, pix[:, 0], pix[:, 1]] = rng.standard_normal((3, pix.shape[0]))
         dL.append(d)
 
-    # GPU, bench launch configuration
-    max_splats = max(4096, int(n * min(len(cams), 3)))
-    r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
-    dev = DeviceScene.from_host(scene)
-    res = gpu_helpers.gpu_step(scene, k, cams, vis, lod=lod, dL=dL, renderer=r, dev=dev)
+    res = gpu_helpers.gpu_step(scene, k, cams, vis, life=life, lod=lod, dL=dL, renderer=r, dev=dev)
     assert res["counts"]["n_splats"] > 1_000_000 and res["counts"]["n_duplicates"] > 10_000_000
     np.testing.assert_array_equal(res["selected"], sel)
+    # Eq. 5 at the bench's timestep leaves the finalised lives as they were
+    # (every Gaussian in a frustum now was in it when the record was taken)
+    np.testing.assert_array_equal(res["life"], life)
 
     # sampled Gaussians: masks and splat records
     gids = gpu_helpers.splat_gids(res)
     picks = rng.choice(sel.shape[0], 3000, replace=False)
-    checked = 0
+    checked = near_picks = 0
     for j in picks:
         near = any(recs[v]["near"][j] for v in range(len(cams)))
         if near:
+            near_picks += 1
             continue
         fm = sum(int(recs[v]["infrustum"][j]) << v for v in range(len(cams)))
         km = sum(int(recs[v]["kept"][j]) << v for v in range(len(cams)))
@@ -90,7 +171,11 @@ def test_rig_full_size_sampled():
             np.testing.assert_array_equal(res["rect"][s], rec["rect"][j])
             s += 1
             checked += 1
-    assert checked > 500
+    assert checked > 500 and near_picks <= 3e-3 * len(cams) * picks.size
+
+    # every pair of the 50,400 tiles, sorted with two tile-digit passes
+    assert res["ranges"].shape[0] == 50_400
+    n_rect, n_out, n_checked = _full_rig_pairs_isolated(res, cams, rng)
 
     # sampled pixels and the gradient of a loss on them
     grads = oracle.zero_grads(scene)
@@ -119,3 +204,10 @@ def test_rig_full_size_sampled():
         if np.abs(b).max() > 0:
             rel = np.linalg.norm(res["grads"][name] - b) / np.linalg.norm(b)
             assert rel <= 1e-3, (name, rel)
+    gpu_helpers.report("full rig", selected=f"{sel.size}/{n}",
+                       record_sample_near_threshold=f"{int(near_any.sum())}/{samp.size}",
+                       gaussian_sample_near_threshold=f"{near_picks}/{picks.size}",
+                       pixel_candidates_excluded=f"{excl}/{cand}",
+                       pixel_blend_flagged=f"{flagged}/{48 * len(cams)}",
+                       sorted_pairs=int(res["sorted_tiles"].size), rectangle_pairs=n_rect,
+                       left_out_checked_unreachable=f"{n_checked}/{n_out}")

@@ -168,16 +168,38 @@ def _stage_isolated_sort(res, cams):
     return int((~keep).sum())
 
 
-def _compare_images(res, f, cams, bg=(0.0, 0.0, 0.0)):
+# Bounds on what an image comparison may leave out, set above what the fixed
+# seeds give: on the tiny scene 3-5 near-threshold Gaussians of 12-14k
+# selected per view and 0.3-0.5 % of the pixels excluded (most of them pixels
+# whose own FP64 blend has a near-threshold decision); on the three-camera rig
+# crop 0-19 near-threshold Gaussians of 44k per view and 1.0 % of its pixels
+# (small images, dense near the cameras); on the 1920x1080 crop 102 of 80k
+# (the rectangle-edge margin is relative to the tile coordinate, so wide
+# images flag more) and 0.7 %.
+MAX_NEAR_FRACTION = 3e-3      # near-threshold Gaussians per selected Gaussian and view
+MAX_EXCLUDED_FRACTION = 0.02  # excluded pixels per pixel
+
+
+def _compare_images(res, f, cams, bg=(0.0, 0.0, 0.0), tag="images"):
+    """Every pixel outside the exclusions within 1e-4 of the oracle; the
+    exclusions (gpu_helpers.bad_pixels) counted, bounded and reported."""
     import gpu_helpers
-    worst, n_bad = 0.0, 0
+    worst, n_bad, n_flag, n_near, n_pix = 0.0, 0, 0, 0, 0
     for v, cam in enumerate(cams):
         view = f["views"][v]
         bad = gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])
         diff = np.abs(res["images"][v] - view["image"]).max(axis=0)
         worst = max(worst, float(diff[~bad].max()) if (~bad).any() else 0.0)
         n_bad += int(bad.sum())
+        n_flag += int(view["flag"].sum())
+        n_near += int(view["rec"]["near"].sum())
+        n_pix += cam.width * cam.height
         assert diff[~bad].max() <= 1e-4, (v, float(diff[~bad].max()))
+    n_sel = int(f["sel"].shape[0])
+    gpu_helpers.report(tag, pixels=n_pix, excluded=n_bad, blend_flagged=n_flag,
+                       near_threshold_gaussians=f"{n_near}/{n_sel}", max_abs_err=f"{worst:.2e}")
+    assert n_bad <= MAX_EXCLUDED_FRACTION * n_pix, (n_bad, n_pix)
+    assert n_near <= MAX_NEAR_FRACTION * max(n_sel, 1) * len(cams), (n_near, n_sel)
     return worst, n_bad
 
 
@@ -237,12 +259,11 @@ def test_tiny_forward_stages(built, tiny, tiny_vis):
         res = gpu_helpers.gpu_step(tiny, step, cams, vis)
         f = _oracle_views(tiny, step, cams, vis, 0.0)
         near = _compare_selection_and_masks(res, f, len(cams))
-        assert near.sum() <= 0.005 * near.size
+        assert near.sum() <= MAX_NEAR_FRACTION * near.size
         assert _compare_splats(res, f, tiny, cams) > 1000
         dropped += _stage_isolated_sort(res, cams)
         _stage_isolated_blend(res, cams)
-        worst, n_bad = _compare_images(res, f, cams)
-        assert n_bad <= 0.15 * 320 * 192
+        _compare_images(res, f, cams, tag=f"tiny step {step}")
     assert dropped > 0          # the reach test did leave rectangle tiles out
 
 
@@ -356,7 +377,7 @@ def test_multiview_rig_sh3_lod(built):
     assert _compare_splats(res, f, sc, cams) > 500
     _stage_isolated_sort(res, cams)
     _stage_isolated_blend(res, cams, bg=(0.2, 0.1, 0.3))
-    _compare_images(res, f, cams)
+    _compare_images(res, f, cams, tag="rig crop SH3 LOD 1 px")
     rng = np.random.default_rng(11)
     dL = []
     for v, cam in enumerate(cams):
@@ -371,6 +392,44 @@ def test_multiview_rig_sh3_lod(built):
     res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3), dL=dL)
     _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
                                          "inst_quat", "inst_trans"))
+
+
+def _wide_crop(seed=4):
+    """A 60k-Gaussian crop of the mid corridor (SH3, four instances in front of
+    the camera) seen by one 1920x1080 camera: 8,160 tiles, so view-tile ids
+    need 13 bits and the pair sort runs two 8-bit tile-digit passes."""
+    sc = scenegen.generate("mid", seed=seed, n_static=60_000, n_inst=4, n_steps=3)
+    sc.means[: sc.inst_offsets[1], 2] *= 0.2      # static strip within z in [0, 60]
+    sc.inst_trans[:, :, 2] = np.linspace(10.0, 40.0, 4)[None, :]
+    sc.inst_trans[:, :, 0] = np.array([-4.0, 3.0, -2.0, 5.0])[None, :]
+    cams = [[make_camera(1920, 1080, 960.0, (0.0, 0.0, -20.0 + 2.0 * k), 0.0)] for k in range(sc.n_steps)]
+    return scenegen.with_cameras(sc, cams)
+
+
+def test_two_tile_digit_passes_1080p(built):
+    """The radix sort's second tile-digit pass: one 1920x1080 camera, pairs
+    keyed by tile ids up to 8,159. Stage-isolated sort and ranges (the GPU's
+    pairs are the oracle's stable sort of the same FP32 splats, with only
+    unreachable pairs left out), blend on the GPU's records, and the image
+    against the end-to-end oracle."""
+    import gpu_helpers
+    sc = _wide_crop()
+    vis, _ = oracle.vis_reset(sc.n)
+    step = 1
+    cams = sc.cams[step]
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0)
+    f = _oracle_views(sc, step, cams, vis, 1.0)
+    near = _compare_selection_and_masks(res, f, len(cams))
+    assert near.sum() <= MAX_NEAR_FRACTION * near.size
+    assert _compare_splats(res, f, sc, cams) > 5000
+    tiles = res["sorted_tiles"].astype(np.int64)
+    assert res["ranges"].shape[0] == 120 * 68 and tiles.max() >= 4096
+    # both digits vary: tiles of one low byte in several high bytes and vice versa
+    assert np.unique(tiles >> 8).size > 20 and np.unique(tiles & 255).size == 256
+    dropped = _stage_isolated_sort(res, cams)
+    _stage_isolated_blend(res, cams)
+    _compare_images(res, f, cams, tag="1080p, two tile-digit passes")
+    gpu_helpers.report("1080p sort", pairs=int(tiles.size), rectangle_pairs_left_out=dropped)
 
 
 def test_stochastic_lod_eq7_rig(built):
@@ -401,7 +460,7 @@ def test_stochastic_lod_eq7_rig(built):
         assert _compare_splats(res, f, sc, cams) > 500
         _stage_isolated_sort(res, cams)
         _stage_isolated_blend(res, cams, bg=bg)
-        _compare_images(res, f, cams)
+        _compare_images(res, f, cams, tag="rig crop Eq. 7")
         # the backward run projects again: epoch e1 + 1
         oracle.set_lod(1, prm["p_max"], prm["distance"], prm["offset"], prm["seed"], e1 + 1)
         f = _oracle_views(sc, step, cams, vis, 1.0, bg=bg)
@@ -549,7 +608,12 @@ def test_conventional_world_transform_matches_oracle(built, tiny, tiny_vis):
         bad = gpu_helpers.bad_pixels(cam, rec, o["flag"])
         diff = np.abs(res["images"][v] - o["image"]).max(axis=0)
         assert diff[~bad].max() <= 1e-4, (v, float(diff[~bad].max()))
-        assert bad.mean() < 0.15
+        gpu_helpers.report(f"conventional view {v}", pixels=bad.size, excluded=int(bad.sum()),
+                           blend_flagged=int(o["flag"].sum()),
+                           near_threshold_gaussians=f"{int(rec['near'].sum())}/{sel.size}",
+                           max_abs_err=f"{float(diff[~bad].max()):.2e}")
+        assert bad.mean() <= MAX_EXCLUDED_FRACTION
+        assert rec["near"].sum() <= MAX_NEAR_FRACTION * sel.size
     assert checked > 1000
 
 

@@ -73,3 +73,28 @@ def test_resume_continues_the_run(tiny_and_record, tmp_path, lod):
         assert float((d > 1e-6).float().mean()) < 1e-2, name
     assert a.state.adam_steps == b.state.adam_steps == 4
     assert a.state.pose_steps == b.state.pose_steps
+
+
+def test_a_failed_step_changes_no_parameter(tiny_and_record):
+    """A step whose render overflowed the workspace (splats dropped) must not
+    reach the optimiser: both Adam updates are gated on the device by the
+    latched status, the step raises S3R_ERR_CAPACITY and is not counted, and
+    every parameter, moment and pose is unchanged. Without the per-step
+    check the device skips the updates all the same."""
+    from paper_2503_08217_gb300 import binding
+    tiny, (vis, life) = tiny_and_record
+    a = train.Trainer(_initial(tiny, vis, life, LODS["threshold"]), tiny.cams, tiny.times,
+                      max_splats=100, max_duplicates=50)
+    before = {k: v.clone() for k, v in a.state.tensors().items()}
+    target = torch.rand(3 * pixel_count(tiny.cams[3]), device="cuda")
+    with pytest.raises(binding.S3RError) as e:
+        a.step(3, target)
+    assert e.value.status == 2                                    # S3R_ERR_CAPACITY
+    assert (a.state.step, a.state.adam_steps, a.state.pose_steps[3]) == (0, 0, 0)
+    a.step(3, target, check=False)
+    a.step(4, target, check=False)
+    with pytest.raises(binding.S3RError):
+        a.check()
+    for k, v in a.state.tensors().items():
+        if k != "point_life":                                     # Eq. 5 records as it renders
+            assert torch.equal(v, before[k]), k

@@ -4,22 +4,25 @@ Some callers cannot allocate device memory at all: code inside a host
 framework whose caching allocator owns the whole device, or a real-time loop
 that may not call cudaMalloc after start-up. For them the library offers the
 temporal selection with its scratch in a fixed array of the library's device
-image. This test calls it through the C ABI twice in a row (the scratch keeps
-the previous call's contents, so the second call checks that it is cleared)
-and compares both results with the selection that s3r_project computes in a
-workspace. It is self-contained, so it passes alone in a fresh process and
-after the other tests (this file is collected last).
+image. This test calls it through the C ABI twice in a row, on two different
+visibility records and times over the same number of Gaussians (the scratch
+keeps the previous call's contents, and its look-back words would hold the
+first call's prefixes if the call did not clear them), and compares both
+results with the oracle's selection and with the selection that s3r_project
+computes in a workspace. It is self-contained, so it passes alone in a fresh
+process and after the other tests (this file is collected last).
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2503_08217_gb300 import scenegen
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_static_selection_matches_workspace_selection():
+def test_static_selection_matches_oracle_and_workspace():
     from paper_2503_08217_gb300 import binding, build
     from paper_2503_08217_gb300.render import DeviceScene, Renderer
     build.build()
@@ -28,34 +31,39 @@ def test_static_selection_matches_workspace_selection():
     scene = scenegen.generate("tiny", seed=3, n_static=100_001)
     n = scene.n
     rng = np.random.default_rng(8)
-    vis = np.sort(rng.uniform(-1.2, 1.2, (n, 2)).astype(np.float32), axis=1)
-    vis[rng.random(n) < 0.1] = (0.9, -0.9)            # some never-visible windows
-    step = 4
-    t = float(scene.times[step])
-    vis_t = torch.from_numpy(vis).cuda()
+    records = []
+    for lo, hi, never in ((-1.2, 1.2, 0.1), (-0.3, 0.9, 0.4)):
+        vis = np.sort(rng.uniform(lo, hi, (n, 2)).astype(np.float32), axis=1)
+        vis[rng.random(n) < never] = (0.9, -0.9)          # never-visible windows
+        records.append(vis)
+    steps = (4, 7)
 
-    # the existing path: s3r_project in a workspace
     dev = DeviceScene.from_host(scene)
-    cams = scene.cams[step]
-    r = Renderer(n, scene.n_inst, cams)
-    iq = torch.from_numpy(scene.inst_quat[step]).cuda()
-    it = torch.from_numpy(scene.inst_trans[step]).cuda()
-    r.ws.project(dev.c_scene(), binding.make_poses(iq, it), cams, t, vis_t, None, 0.0)
-    c = r.counts()
-    ref = r.ws.debug("selected", torch.int32, c["n_selected"]).cpu().numpy().view(np.uint32)
-    assert 0 < ref.size < n
-
-    # the allocation-free entry point, twice in a row
     out_idx = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     out_count = torch.zeros(1, dtype=torch.int32, device="cuda")
-    for _ in range(2):
+    for vis, step in zip(records, steps):
+        t = float(scene.times[step])
+        vis_t = torch.from_numpy(vis).cuda()
+        expect = oracle.select(vis, t)
+        assert 0 < expect.size < n
+        # the existing path: s3r_project in a workspace
+        cams = scene.cams[step]
+        r = Renderer(n, scene.n_inst, cams)
+        iq = torch.from_numpy(scene.inst_quat[step]).cuda()
+        it = torch.from_numpy(scene.inst_trans[step]).cuda()
+        r.ws.project(dev.c_scene(), binding.make_poses(iq, it), cams, t, vis_t, None, 0.0)
+        c = r.counts()
+        ref = r.ws.debug("selected", torch.int32, c["n_selected"]).cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(ref.astype(np.int64), expect)
+        # the allocation-free entry point
         out_idx.fill_(-1)
         out_count.fill_(-7)
         binding.select_visible_static(vis_t, t, out_idx, out_count)
         torch.cuda.synchronize()
-        m = int(out_count.item())
-        assert m == ref.size
-        np.testing.assert_array_equal(out_idx[:m].cpu().numpy().view(np.uint32), ref)
+        m = int(out_count.item()) & 0xFFFFFFFF
+        assert m != 0xFFFFFFFF                            # no look-back wait gave up
+        assert m == expect.size
+        np.testing.assert_array_equal(out_idx[:m].cpu().numpy().view(np.uint32).astype(np.int64), expect)
 
 
 def test_static_selection_rejects_too_many_gaussians():
