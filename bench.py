@@ -371,18 +371,17 @@ def run_ours(args, rank, world, local):
 
     def make_step(tgt, iq_, it_):
         def step_fn():
-            for g in grads.values():
-                g.zero_()
-            loss.zero_()
+            # the loss and every gradient element are written by the library
+            # (L1 loss and the overwrite mode of the backward): no zero fills
             if args.conventional:
                 binding.to_world(cs, binding.make_poses(iq_, it_), mw, qw)
                 r.forward(dev, no_q, no_t, cams, t, vis, life, lod, bg, out=out, c_scene=cs_w)
                 binding.l1_loss(out, tgt, dL, loss)
-                r.backward(dev, no_q, no_t, bg, dL, grads, c_scene=cs_w)
+                r.backward(dev, no_q, no_t, bg, dL, grads, c_scene=cs_w, overwrite=True)
                 return
             r.forward(dev, iq_, it_, cams, t, vis, life, lod, bg, out=out, c_scene=cs)
             binding.l1_loss(out, tgt, dL, loss)
-            r.backward(dev, iq_, it_, bg, dL, grads, c_scene=cs)
+            r.backward(dev, iq_, it_, bg, dL, grads, c_scene=cs, overwrite=True)
         return step_fn
 
     step = make_step(target, iq, it)
@@ -480,10 +479,10 @@ def run_ours(args, rank, world, local):
                         unit="Gop/s (FP32)", frac=table[dom]["frac"],
                         peak_source=f"{n_sms} SMs (queried) x 128 FP32 lanes x max SM clock "
                                     f"{sm_max:.0f} MHz")
-    # the timed kernels, plus untimed ones of ours: the L1 loss, the three small
-    # zero fills (tile ranges, contributor bits, pose-adjoint sums) and, for the
-    # conventional pipeline, the world transform
-    launches_per_step = len(kmean) + 4 + (1 if args.conventional else 0)
+    # the timed kernels, plus untimed ones of ours: the L1 loss and its zeroed
+    # output, the three small zero fills (tile ranges, contributor bits,
+    # pose-adjoint sums) and, for the conventional pipeline, the world transform
+    launches_per_step = len(kmean) + 5 + (1 if args.conventional else 0)
 
     # --- plain per-view comparator: the same library, one camera per call, eager
     plain = None
@@ -496,15 +495,13 @@ def run_ours(args, rank, world, local):
         offs = np.cumsum([0] + [3 * c.width * c.height for c in cams])
 
         def plain_sweep():
-            for g in grads.values():
-                g.zero_()
+            # the first view's backward writes the gradients, the others add
             for v, cam in enumerate(cams):
                 o = out[offs[v]:offs[v + 1]]
                 d = dL[offs[v]:offs[v + 1]]
-                loss.zero_()
                 r1.forward(dev, iq, it, [cam], t, vis, life, lod, bg, out=o, c_scene=cs)
                 binding.l1_loss(o, target[offs[v]:offs[v + 1]], d, loss)
-                r1.backward(dev, iq, it, bg, d, grads, c_scene=cs)
+                r1.backward(dev, iq, it, bg, d, grads, c_scene=cs, overwrite=v == 0)
 
         for _ in range(max(1, args.warmup)):
             plain_sweep()
@@ -785,12 +782,9 @@ def run_scale_sweep(args):
                "corridor_m": round(float(scene.means[:, 2].max() - scene.means[:, 2].min()), 1)}
         for mode, v in (("temporal", vis), ("all_visible", all_vis)):
             def step():
-                for g in grads.values():
-                    g.zero_()
-                loss.zero_()
                 r.forward(dev, iq, it, cams, t, v, None, lod, bg, out=out, c_scene=cs)
                 binding.l1_loss(out, target, dL, loss)
-                r.backward(dev, iq, it, bg, dL, grads, c_scene=cs)
+                r.backward(dev, iq, it, bg, dL, grads, c_scene=cs, overwrite=True)
             step()
             torch.cuda.synchronize()
             c = r.counts()

@@ -102,9 +102,13 @@ typedef struct {
   const float* trans;
 } s3r_poses;
 
-/* Gradient outputs, ACCUMULATED (+=) into caller-zeroed device buffers with
- * the layouts of s3r_scene / s3r_poses. Any pointer may be NULL to skip it
- * (its work is still done where other outputs need it). */
+/* Gradient outputs with the layouts of s3r_scene / s3r_poses, device
+ * buffers. By default ACCUMULATED (+=) into caller-zeroed buffers, so that
+ * calls over different cameras sum; in the overwrite mode of
+ * s3r_set_grad_mode every element of every non-NULL buffer is written
+ * instead (zeros for the Gaussians kept in no view), so the caller zeroes
+ * nothing. Any pointer may be NULL to skip it (its work is still done where
+ * other outputs need it). */
 typedef struct {
   float* means;           /* [n,3] */
   float* log_scales;      /* [n,3] */
@@ -224,7 +228,7 @@ s3r_status s3r_update_visibility(int64_t n, float t, const uint32_t* mask, float
 
 /* Photometric L1 loss of a rendered batch (the paper does not state its
  * loss; this is the plain mean absolute error a training step can use):
- *   loss = sum |pred - target| / n   (added to *loss_out, one FP32 scalar)
+ *   loss = sum |pred - target| / n   (written to *loss_out, one FP32 scalar)
  *   dL_dpred[i] = sign(pred[i] - target[i]) / n   (written)
  * pred, target, dL_dpred: [n] FP32 device arrays; loss_out: device FP32. */
 s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float* dL_dpred,
@@ -302,6 +306,19 @@ typedef struct {
   uint64_t seed;
 } s3r_lod_params;
 s3r_status s3r_set_lod(s3r_workspace* ws, const s3r_lod_params* params);
+
+/* Gradient output mode of the following s3r_render_bwd calls of the
+ * workspace. S3R_GRAD_ACCUMULATE (the default): the gradients are added to
+ * the caller's buffers. S3R_GRAD_OVERWRITE: the call writes every element of
+ * the n rows of each non-NULL Gaussian buffer and of the n_inst rows of the
+ * pose buffers: the gradient rows of the Gaussians kept in at least one view
+ * are written once, by the thread that computes them (no read of the old
+ * contents), and the other rows are set to zero by a coalesced pass over a
+ * per-Gaussian bitmap of the kept ones. The result equals accumulation into
+ * zeroed buffers. */
+#define S3R_GRAD_ACCUMULATE 0
+#define S3R_GRAD_OVERWRITE 1
+s3r_status s3r_set_grad_mode(s3r_workspace* ws, int32_t mode);
 
 /* Work accounting: with counting enabled the blend kernels also count the
  * (pixel, splat) pairs they walk and evaluate (reported by s3r_query_counts;

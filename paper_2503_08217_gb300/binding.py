@@ -30,10 +30,12 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
            "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
-           "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status")
+           "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status", "s3r_set_grad_mode")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
+GRAD_ACCUMULATE = 0
+GRAD_OVERWRITE = 1
 
 
 class S3RError(RuntimeError):
@@ -119,6 +121,7 @@ def load(path: str = LIB_PATH):
     L.s3r_set_timing.argtypes = [vp, i32]
     L.s3r_set_lod.argtypes = [vp, P(LodParams)]
     L.s3r_set_counting.argtypes = [vp, i32]
+    L.s3r_set_grad_mode.argtypes = [vp, i32]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp, vp]
     L.s3r_device_status.argtypes = [vp]
@@ -141,7 +144,7 @@ def load(path: str = LIB_PATH):
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
                  "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
                  "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout",
-                 "s3r_set_epoch"):
+                 "s3r_set_epoch", "s3r_set_grad_mode"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,6 +297,12 @@ class Workspace:
     def sync_status(self, stream=None):
         _check(load().s3r_sync_status(self._h, _stream(stream)))
 
+    def set_grad_mode(self, mode: int):
+        """GRAD_ACCUMULATE (default): render_bwd adds to the gradient buffers;
+        GRAD_OVERWRITE: it writes every element (zeros where no view kept the
+        Gaussian), so the buffers need no zeroing."""
+        _check(load().s3r_set_grad_mode(self._h, int(mode)))
+
     def status_word(self) -> int:
         """Device address of the latched status word (adam_step's gate)."""
         return int(load().s3r_device_status(self._h) or 0)
@@ -332,7 +341,7 @@ class _DeviceArray:
 
 
 def l1_loss(pred, target, dL_dpred, loss_out, stream=None):
-    """loss_out += mean|pred - target|; dL_dpred = sign(pred - target) / n."""
+    """loss_out = mean|pred - target|; dL_dpred = sign(pred - target) / n."""
     _check(load().s3r_l1_loss(int(pred.numel()), _ptr(pred), _ptr(target), _ptr(dL_dpred),
                               _ptr(loss_out), _stream(stream)))
 

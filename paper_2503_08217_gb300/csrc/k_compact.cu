@@ -40,10 +40,28 @@ __global__ void k_begin(uint32_t* ctr, uint32_t* hist, unsigned long long* lookb
     for (int64_t i = threadIdx.x; i < lookback_words; i += blockDim.x) lookback[i] = 0ull;
 }
 
+// Bits 2m (even) and 2m + 1 (odd) of a 32-bit word from bit m of the low
+// halves of `even` and `odd`: the ballots of a round cover its Gaussians
+// 2 lane and 2 lane + 1.
+__device__ __forceinline__ uint32_t interleave16(uint32_t even, uint32_t odd) {
+  auto spread = [](uint32_t x) {
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+  };
+  return spread(even) | (spread(odd) << 1);
+}
+
+// sel_bits (may be null): bit i of word i / 32 set iff Gaussian i is
+// selected; every word of every tile is written (zeros past n).
 __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ vis, int64_t n,
                                                       float t, uint32_t* __restrict__ sel,
                                                       uint32_t* ctr,
-                                                      unsigned long long* lookback) {
+                                                      unsigned long long* lookback,
+                                                      uint32_t* __restrict__ sel_bits) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_base;
@@ -75,6 +93,15 @@ __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ 
       b0[r] = __ballot_sync(0xffffffffu, f0);
       b1[r] = __ballot_sync(0xffffffffu, f1);
       count += __popc(b0[r]) + __popc(b1[r]);
+    }
+    if (sel_bits && lane < 2 * kRounds) {
+      // round r covers Gaussians g0 + 64 r .. + 63: two words, lanes 2r and 2r + 1
+      uint32_t e = 0, o = 0;
+#pragma unroll
+      for (int r = 0; r < kRounds; ++r)
+        if ((int)(lane >> 1) == r) { e = b0[r]; o = b1[r]; }
+      const uint32_t sh = (lane & 1u) * 16u;
+      sel_bits[(g0 >> 5) + lane] = interleave16(e >> sh, o >> sh);
     }
     if (lane == 0) s_warp[warp] = count;
     __syncthreads();
@@ -126,7 +153,8 @@ cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;
   KernelTimer timer(ws, kKCompact, st);
-  k_compact<<<(unsigned)grid, kThreads, 0, st>>>(vis, n, t, ws->selected, ws->ctr, ws->lookback);
+  k_compact<<<(unsigned)grid, kThreads, 0, st>>>(vis, n, t, ws->selected, ws->ctr, ws->lookback,
+                                                 ws->kept_bits);
   return cudaGetLastError();
 }
 
@@ -224,7 +252,8 @@ extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float*
     int64_t grid = (int64_t)sms * 8;
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) grid = 1;
-    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(vis_window, n, t, out_idx, sc->ctr, sc->lookback);
+    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(vis_window, n, t, out_idx, sc->ctr, sc->lookback,
+                                                   nullptr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

@@ -40,6 +40,7 @@ struct ProjArgs {
   uint32_t* keep_mask;
   uint32_t* splat_start;
   uint2* kept_list;
+  uint32_t* kept_bits;      // selection bitmap from the compaction; unkept bits cleared here
   float2* sp_xy;
   float4* sp_conic_o;
   float4* sp_rgb_d;
@@ -186,6 +187,24 @@ __global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_m
       }
     }
     nfr_local += fmask ? 1u : 0u;
+    // clear the bitmap bits of selected Gaussians kept in no view, one atomic
+    // per run of lanes in the same word (a warp's ids ascend, so the runs are
+    // contiguous; a segmented OR collects each run's bits at its first lane)
+    {
+      const bool drop = active && kmask == 0u;
+      if (__any_sync(0xffffffffu, drop)) {
+        const uint32_t word = active ? gid >> 5 : 0xffffffffu;
+        uint32_t bits = drop ? 1u << (gid & 31u) : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_down_sync(0xffffffffu, bits, o);
+          const uint32_t wy = __shfl_down_sync(0xffffffffu, word, o);
+          if (lane + (uint32_t)o < 32u && wy == word) bits |= y;
+        }
+        const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+        if (active && (lane == 0 || wprev != word) && bits) atomicAnd(a.kept_bits + word, ~bits);
+      }
+    }
     // append the kept Gaussians to the work list: one atomic per block
     // iteration (a per-warp atomic on one counter serialises in L2)
     const uint32_t kb = __ballot_sync(0xffffffffu, kmask != 0u);
@@ -486,6 +505,7 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.keep_mask = ws->keep_mask;
   a.splat_start = ws->splat_start;
   a.kept_list = ws->kept_list;
+  a.kept_bits = ws->kept_bits;
   a.sp_xy = ws->sp_xy;
   a.sp_conic_o = ws->sp_conic_o;
   a.sp_rgb_d = ws->sp_rgb_d;

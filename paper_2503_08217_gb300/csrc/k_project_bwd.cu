@@ -46,6 +46,7 @@ struct BwdArgs {
   float* pose_dM;          // [n_views][n_inst+1][12]
   s3r_grads g;
   const InstMat* mats;     // from the forward's k_compose (same poses)
+  int overwrite;           // S3R_GRAD_OVERWRITE: write the rows instead of adding to them
 };
 
 // d/d(direction) of sum_k w_k Y_k(d) for the real SH basis of sh_basis<DEG>.
@@ -336,15 +337,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 
     if (a.g.log_scales) {
       float* p = a.g.log_scales + 3 * (size_t)gid;
-      p[0] += g_ls[0]; p[1] += g_ls[1]; p[2] += g_ls[2];
+      if (a.overwrite) {
+        p[0] = g_ls[0]; p[1] = g_ls[1]; p[2] = g_ls[2];
+      } else {
+        p[0] += g_ls[0]; p[1] += g_ls[1]; p[2] += g_ls[2];
+      }
     }
     if (a.g.quats) {
       float4* p = reinterpret_cast<float4*>(a.g.quats) + gid;
-      float4 o = *p;
-      o.x += g_q.x; o.y += g_q.y; o.z += g_q.z; o.w += g_q.w;
-      *p = o;
+      if (a.overwrite) {
+        *p = g_q;
+      } else {
+        float4 o = *p;
+        o.x += g_q.x; o.y += g_q.y; o.z += g_q.z; o.w += g_q.w;
+        *p = o;
+      }
     }
-    if (a.g.opacity_logits) a.g.opacity_logits[gid] += g_ol;
+    if (a.g.opacity_logits) {
+      if (a.overwrite) a.g.opacity_logits[gid] = g_ol;
+      else a.g.opacity_logits[gid] += g_ol;
+    }
 
     // ---- second pass: the colour of each kept view
     m = kmask;
@@ -425,7 +437,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     }
     if (a.g.means) {
       float* p = a.g.means + 3 * (size_t)gid;
-      p[0] += g_mu[0]; p[1] += g_mu[1]; p[2] += g_mu[2];
+      if (a.overwrite) {
+        p[0] = g_mu[0]; p[1] = g_mu[1]; p[2] = g_mu[2];
+      } else {
+        p[0] += g_mu[0]; p[1] += g_mu[1]; p[2] += g_mu[2];
+      }
     }
     }
     // SH adjoints: each lane writes its row over its (consumed) SH row, then
@@ -447,10 +463,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
           const int g = idx / St::kRow, qd = idx - g * St::kRow;
           const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
           if ((live >> g) & 1u) {
-            float4 o = dst[(size_t)gg * St::kRow + qd];
             const float4 d = src[g * St::kPitch + qd];
-            o.x += d.x; o.y += d.y; o.z += d.z; o.w += d.w;
-            dst[(size_t)gg * St::kRow + qd] = o;
+            if (a.overwrite) {
+              dst[(size_t)gg * St::kRow + qd] = d;
+            } else {
+              float4 o = dst[(size_t)gg * St::kRow + qd];
+              o.x += d.x; o.y += d.y; o.z += d.z; o.w += d.w;
+              dst[(size_t)gg * St::kRow + qd] = o;
+            }
           }
         }
       } else {
@@ -459,7 +479,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
           const int idx = it * 32 + (int)lane;
           const int g = idx / St::kRow, qd = idx - g * St::kRow;
           const uint32_t gg = __shfl_sync(0xffffffffu, gid, g);
-          if ((live >> g) & 1u) a.g.sh[(size_t)gg * St::kRow + qd] += my_sh[g * St::kPitch + qd];
+          if ((live >> g) & 1u) {
+            float* q = a.g.sh + (size_t)gg * St::kRow + qd;
+            *q = a.overwrite ? my_sh[g * St::kPitch + qd] : *q + my_sh[g * St::kPitch + qd];
+          }
         }
       }
     }
@@ -475,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
 // dL/dP_k = V_rot^T dL/dW_{v,k} summed over views, then (q, t) of the pose.
 __global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __restrict__ dM,
                              int n_inst, const float4* __restrict__ pose_q, float* g_q,
-                             float* g_t) {
+                             float* g_t, int overwrite) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
   if (k > n_inst) return;
   const int nk = n_inst + 1;
@@ -492,16 +515,57 @@ __global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __
     }
   }
   if (g_t) {
-    g_t[3 * (k - 1)] += dPt[0];
-    g_t[3 * (k - 1) + 1] += dPt[1];
-    g_t[3 * (k - 1) + 2] += dPt[2];
+    float* p = g_t + 3 * (k - 1);
+    for (int c = 0; c < 3; ++c) p[c] = overwrite ? dPt[c] : p[c] + dPt[c];
   }
   if (g_q) {
     const float4 gq = quat_backward(pose_q[k - 1], dPr);
-    g_q[4 * (k - 1)] += gq.x;
-    g_q[4 * (k - 1) + 1] += gq.y;
-    g_q[4 * (k - 1) + 2] += gq.z;
-    g_q[4 * (k - 1) + 3] += gq.w;
+    const float v[4] = {gq.x, gq.y, gq.z, gq.w};
+    float* p = g_q + 4 * (k - 1);
+    for (int c = 0; c < 4; ++c) p[c] = overwrite ? v[c] : p[c] + v[c];
+  }
+}
+
+// Overwrite mode, before k_project_bwd: the arrays of 1-4 floats per
+// Gaussian (means, log-scales, quaternions, opacity logits: 44 bytes) are
+// zeroed whole, with full coalesced stores (k_project_bwd then writes the
+// kept rows again; skipping them here would leave sectors half written), and
+// the SH rows (sector-sized: 192 bytes at degree 3) only where no view kept
+// the Gaussian: one warp per word of the kept bitmap, rows of the warp's 32
+// Gaussians contiguous, float4 stores where a row is whole float4s.
+__device__ __forceinline__ void zero_all(float* p, int64_t count, int64_t i0, int64_t stride) {
+  if (!p) return;
+  for (int64_t i = i0; i < count; i += stride) p[i] = 0.f;
+}
+
+template <int SHF>   // SH floats per Gaussian: 3 (K 1), 12, 27, 48 (K 16)
+__global__ void __launch_bounds__(256) k_zero_overwrite(const uint32_t* __restrict__ kept_bits,
+                                                        int64_t n, s3r_grads g) {
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  zero_all(g.means, 3 * n, t0, nt);
+  zero_all(g.log_scales, 3 * n, t0, nt);
+  zero_all(g.quats, 4 * n, t0, nt);
+  zero_all(g.opacity_logits, n, t0, nt);
+  if (!g.sh) return;
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t n_words = (n + 31) / 32;
+  for (int64_t w = t0 >> 5; w < n_words; w += nt >> 5) {
+    const int64_t g0 = w * 32;
+    const int cnt = (int)min((int64_t)32, n - g0);
+    const uint32_t live = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    const uint32_t zero = ~kept_bits[w] & live;
+    if (!zero) continue;
+    if constexpr (SHF % 4 == 0) {
+      constexpr int W4 = SHF / 4;
+      float4* p = reinterpret_cast<float4*>(g.sh) + g0 * W4;
+      for (int i = (int)lane; i < W4 * cnt; i += 32)
+        if ((zero >> (i / W4)) & 1u) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      float* p = g.sh + g0 * SHF;
+      for (int i = (int)lane; i < SHF * cnt; i += 32)
+        if ((zero >> (i / SHF)) & 1u) p[i] = 0.f;
+    }
   }
 }
 
@@ -561,9 +625,24 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.pose_dM = ws->pose_dM;
   a.g = *g;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
+  a.overwrite = ws->grad_mode == S3R_GRAD_OVERWRITE ? 1 : 0;
   const int nk = ws->n_inst + 1;
   cudaError_t e = launch_zero(ws->pose_dM, 12 * (int64_t)ws->n_views * nk, st);
   if (e != cudaSuccess) return e;
+  if (a.overwrite && ws->n > 0 &&
+      (g->means || g->log_scales || g->quats || g->opacity_logits || g->sh)) {
+    const int64_t words = (ws->n + 31) / 32;
+    int64_t blocks = (words + 7) / 8;
+    if (blocks > (int64_t)ws->num_sms * 8) blocks = (int64_t)ws->num_sms * 8;
+    KernelTimer timer(ws, kKZeroUnkept, st);
+    switch (sc->sh_degree) {
+      case 0: k_zero_overwrite<3><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
+      case 1: k_zero_overwrite<12><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
+      case 2: k_zero_overwrite<27><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
+      default: k_zero_overwrite<48><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   switch (sc->sh_degree) {
     case 0: e = launch_deg<0>(ws, a, st); break;
     case 1: e = launch_deg<1>(ws, a, st); break;
@@ -574,7 +653,8 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   if (ws->n_inst > 0 && (g->inst_quat || g->inst_trans)) {
     KernelTimer timer(ws, kKPoseChain, st);
     k_pose_chain<<<(ws->n_inst + 127) / 128, 128, 0, st>>>(ws->views, ws->pose_dM, ws->n_inst,
-                                                          a.pose_q, g->inst_quat, g->inst_trans);
+                                                          a.pose_q, g->inst_quat, g->inst_trans,
+                                                          a.overwrite);
     e = cudaGetLastError();
   }
   return e;

@@ -156,6 +156,9 @@ cudaError_t launch_zero(void* p, int64_t words, cudaStream_t st) {
 cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, float* grad,
                            float* loss, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  // the blocks add their partial sums to *loss: start it at zero
+  cudaError_t e = launch_zero(loss, 1, st);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (n + 255) / 256;
   if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
   k_l1<<<(unsigned)blocks, 256, 0, st>>>(n, pred, target, grad, loss);

@@ -66,13 +66,13 @@ const char* const kKernelNames[kKCount] = {
     "begin", "temporal_compact", "compose", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
     "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd", "zero_splat_grads",
-    "blend_bwd", "project_bwd", "pose_chain", "tile_order", "splat_tiles"};
+    "blend_bwd", "project_bwd", "pose_chain", "tile_order", "splat_tiles", "zero_unkept_grads"};
 
 void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   void* ptrs[] = {ws->ctr, ws->hist, ws->lookback, ws->selected, ws->frustum_mask,
-                  ws->keep_mask, ws->splat_start, ws->kept_list, ws->sp_xy, ws->sp_conic_o, ws->sp_rgb_d,
+                  ws->keep_mask, ws->splat_start, ws->kept_list, ws->kept_bits, ws->sp_xy, ws->sp_conic_o, ws->sp_rgb_d,
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
@@ -189,6 +189,8 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->keep_mask, N);
   S3R_ALLOC(ws->splat_start, N);
   S3R_ALLOC(ws->kept_list, N);
+  ws->kept_words = (N + 4095) / 4096 * 128;   // whole compaction tiles
+  S3R_ALLOC(ws->kept_bits, ws->kept_words);
   S3R_ALLOC(ws->sp_xy, S);
   S3R_ALLOC(ws->sp_conic_o, S);
   S3R_ALLOC(ws->sp_rgb_d, S);
@@ -409,6 +411,14 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
     ms[i] = t;
   }
+  return S3R_OK;
+}
+
+s3r_status s3r_set_grad_mode(s3r_workspace* ws, int32_t mode) {
+  if (!ws) return fail(S3R_ERR_INVALID, "NULL workspace");
+  if (mode != S3R_GRAD_ACCUMULATE && mode != S3R_GRAD_OVERWRITE)
+    return fail(S3R_ERR_INVALID, "gradient mode %d unknown", mode);
+  ws->grad_mode = mode;
   return S3R_OK;
 }
 

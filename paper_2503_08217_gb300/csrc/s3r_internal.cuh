@@ -97,7 +97,7 @@ constexpr int kDupChunkMin = 1024;   // smallest output chunk of the pair expans
 enum KernelId : int {
   kKBegin = 0, kKCompact, kKCompose, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
   kKTile0, kKTile1, kKTile2, kKTile3, kKTileRanges, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
-  kKProjectBwd, kKPoseChain, kKTileOrder, kKSplatTiles, kKCount
+  kKProjectBwd, kKPoseChain, kKTileOrder, kKSplatTiles, kKZeroUnkept, kKCount
 };
 
 }  // namespace s3r
@@ -117,6 +117,8 @@ struct s3r_workspace {
   uint32_t* keep_mask;      // [N]
   uint32_t* splat_start;    // [N]
   uint2* kept_list;         // [N] (compacted index, Gaussian id) of those kept in >= 1 view (any order)
+  uint32_t* kept_bits;      // [ceil(N / 4096) * 128] bit per Gaussian id: selected and kept in >= 1 view
+  int64_t kept_words;
   float2* sp_xy;            // [S]
   float4* sp_conic_o;       // [S]
   float4* sp_rgb_d;         // [S]
@@ -155,6 +157,7 @@ struct s3r_workspace {
   int tile_passes;
   s3r_lod_params lod;       // mode S3R_LOD_THRESHOLD unless s3r_set_lod said otherwise
   int counting;             // blend kernels count their pairs (s3r_set_counting)
+  int grad_mode;            // S3R_GRAD_ACCUMULATE or S3R_GRAD_OVERWRITE (s3r_set_grad_mode)
   // per-kernel timing hook
   int timing;
   cudaEvent_t ev[2 * s3r::kKCount];

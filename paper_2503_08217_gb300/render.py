@@ -78,6 +78,7 @@ class Renderer:
                                     max_pixels=pixel_count(cams), max_rows=max_rows,
                                     device=device)
         self.graph = None
+        self._grad_mode = binding.GRAD_ACCUMULATE
 
     # ---------------------------------------------------------------- stages
     def forward(self, scene: DeviceScene, inst_quat, inst_trans, cams, t: float, vis_window,
@@ -94,9 +95,15 @@ class Renderer:
         return out
 
     def backward(self, scene: DeviceScene, inst_quat, inst_trans, background, dL, grads: dict,
-                 *, c_scene=None):
+                 *, c_scene=None, overwrite: bool = False):
+        """render_bwd into `grads`: added to them, or with `overwrite` every
+        element written (the buffers need no zeroing)."""
         cs = scene.c_scene() if c_scene is None else c_scene
         poses = binding.make_poses(inst_quat, inst_trans)
+        mode = binding.GRAD_OVERWRITE if overwrite else binding.GRAD_ACCUMULATE
+        if mode != self._grad_mode:
+            self.ws.set_grad_mode(mode)
+            self._grad_mode = mode
         self.ws.render_bwd(cs, poses, background, dL.contiguous(), grads)
 
     def counts(self):
@@ -156,13 +163,14 @@ class S3RRender(torch.autograd.Function):
     def backward(ctx, dout):
         background, means, log_scales, quats, opacity_logits, sh, inst_quat, inst_trans = \
             ctx.saved_tensors
-        grads = {"means": torch.zeros_like(means), "log_scales": torch.zeros_like(log_scales),
-                 "quats": torch.zeros_like(quats), "opacity_logits": torch.zeros_like(opacity_logits),
-                 "sh": torch.zeros_like(sh), "inst_quat": torch.zeros_like(inst_quat),
-                 "inst_trans": torch.zeros_like(inst_trans)}
+        # every element is written by the library (overwrite mode)
+        grads = {"means": torch.empty_like(means), "log_scales": torch.empty_like(log_scales),
+                 "quats": torch.empty_like(quats), "opacity_logits": torch.empty_like(opacity_logits),
+                 "sh": torch.empty_like(sh), "inst_quat": torch.empty_like(inst_quat),
+                 "inst_trans": torch.empty_like(inst_trans)}
         cs = ctx.scene.c_scene(means, log_scales, quats, opacity_logits, sh)
         ctx.renderer.backward(ctx.scene, inst_quat, inst_trans, background, dout.contiguous(), grads,
-                              c_scene=cs)
+                              c_scene=cs, overwrite=True)
         return (None, None, None, None, None, None, None, None, grads["means"], grads["log_scales"],
                 grads["quats"], grads["opacity_logits"], grads["sh"], grads["inst_quat"],
                 grads["inst_trans"])

@@ -164,14 +164,12 @@ class Trainer:
         cams, t = self.cams[k], float(self.times[k])
         out = torch.empty(3 * pixel_count(cams), device=s.scene.means.device)
         dL = torch.empty_like(out)
-        for g in self.grads.values():
-            g.zero_()
-        self.loss.zero_()
         iq, it = s.inst_quat[k], s.inst_trans[k]
         self.renderer.forward(s.scene, iq, it, cams, t, s.vis_window, s.point_life,
                               float(s.lod.get("r", 0.0)), self.background, out=out)
         binding.l1_loss(out, target, dL, self.loss)
-        self.renderer.backward(s.scene, iq, it, self.background, dL, self.grads)
+        # every gradient element is written (overwrite mode): no zeroing
+        self.renderer.backward(s.scene, iq, it, self.background, dL, self.grads, overwrite=True)
         b1, b2 = self.betas
         gate = self.renderer.ws.status_word()
         counters = (s.adam_steps, s.pose_steps[k], s.step)

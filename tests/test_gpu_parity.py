@@ -348,8 +348,8 @@ def test_visibility_modes_match_oracle(built):
     np.testing.assert_array_equal(life.cpu().numpy()[:7], ref[:7])
 
 
-def _rig_crop(seed=1):
-    sc = scenegen.generate("mid", seed=seed, n_static=30_000, n_inst=4, n_steps=12)
+def _rig_crop(seed=1, sh_degree=None):
+    sc = scenegen.generate("mid", seed=seed, n_static=30_000, n_inst=4, n_steps=12, sh_degree=sh_degree)
     # instances near the rig so that dynamic Gaussians are visible
     sc.inst_trans[:, :, 2] = np.linspace(8, 40, 4)[None, :] + sc.inst_trans[:, :, 2] * 0.0 + \
         np.arange(sc.n_steps)[:, None] * 0.5
@@ -481,6 +481,51 @@ def test_stochastic_lod_eq7_rig(built):
                                              "inst_quat", "inst_trans"))
     finally:
         oracle.set_lod(0)
+
+
+@pytest.mark.parametrize("sh_degree", [0, 1, 2, 3])
+def test_gradient_overwrite_equals_accumulation(built, sh_degree):
+    """The overwrite mode of the backward writes every element of every
+    gradient buffer: into buffers filled with NaN it gives what accumulation
+    into zeroed buffers gives (up to the float atomics' summation order), and
+    exactly zero for the Gaussians no view kept (SH rows of 3, 12, 27 and 48
+    floats: the scalar and the vector zeroing)."""
+    import gpu_helpers
+    from paper_2503_08217_gb300.render import DeviceScene
+    sc = _rig_crop(sh_degree=sh_degree)
+    vis, _ = gpu_helpers.sweep_visibility(sc, lod=1.0)
+    step = 6
+    cams = sc.cams[step]
+    dev = DeviceScene.from_host(sc)
+    r = gpu_helpers.Renderer(sc.n, sc.n_inst, cams)
+    iq = torch.from_numpy(sc.inst_quat[step]).cuda()
+    it = torch.from_numpy(sc.inst_trans[step]).cuda()
+    bg = torch.tensor([0.2, 0.1, 0.3], device="cuda")
+    vis_t = torch.from_numpy(vis).cuda()
+    out = r.forward(dev, iq, it, cams, float(sc.times[step]), vis_t, None, 1.0, bg)
+    dL = torch.randn_like(out)
+    shapes = {"means": dev.means, "log_scales": dev.log_scales, "quats": dev.quats,
+              "opacity_logits": dev.opacity_logits, "sh": dev.sh, "inst_quat": iq, "inst_trans": it}
+    acc = {k: torch.zeros_like(v) for k, v in shapes.items()}
+    ovw = {k: torch.full_like(v, float("nan")) for k, v in shapes.items()}
+    r.backward(dev, iq, it, bg, dL, acc)
+    r.backward(dev, iq, it, bg, dL, ovw, overwrite=True)
+    r.backward(dev, iq, it, bg, dL, acc)               # accumulation adds: twice the gradient
+    torch.cuda.synchronize()
+    r.sync_status()
+    keep = r.ws.debug("keep_mask", torch.int32, r.counts()["n_selected"]).cpu().numpy()
+    sel = r.ws.debug("selected", torch.int32, keep.size).cpu().numpy()
+    kept = np.zeros(sc.n, bool)
+    kept[sel[keep != 0]] = True
+    assert 0 < kept.sum() < sc.n
+    for k in shapes:
+        a, b = 0.5 * acc[k].double().cpu().numpy(), ovw[k].double().cpu().numpy()
+        assert not np.isnan(b).any(), k
+        scale = max(np.abs(a).max(), 1e-30)
+        np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-5 * scale, err_msg=k)
+        if k not in ("inst_quat", "inst_trans"):
+            assert (b.reshape(sc.n, -1)[~kept] == 0).all(), k
+            assert (np.abs(b.reshape(sc.n, -1)[kept]).sum(1) > 0).mean() > 0.5, k
 
 
 def test_empty_selection_renders_background(built, tiny):
