@@ -1,6 +1,7 @@
 // Test hook for failure detection: one warp runs the library's two bounded
 // look-back waits (warp_lookback, used by the compaction, splat and pair
-// scans; lookback_prefix, used by the radix passes) as tile 1 against a tile-0
+// scans; lookback_walk, used by the radix passes, through lookback_prefix) as
+// tile 1 against a tile-0
 // word that nothing ever publishes, with a small poll limit. Each wait gives
 // up after max_polls polls, latches kStatusTimeout into the workspace's
 // status word and returns, so the host reads S3R_ERR_TIMEOUT from the next

@@ -61,13 +61,40 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* s_tmp 
   return wbase + incl - x;
 }
 
+// Keys (and values, or their positions) of one radix tile: warp w reads its
+// kWarpKeys consecutive keys as kSortItems coalesced rounds. Slots past the
+// end get key 0xffffffff (digit 255) and are never written out.
+__device__ __forceinline__ void load_tile(const PassArgs& a, int64_t n, int64_t tile, int warp,
+                                          uint32_t lane, uint32_t (&key)[kSortItems],
+                                          uint32_t (&val)[kSortItems]) {
+  const int64_t first = tile * kSortTileKeys + (int64_t)warp * kWarpKeys + lane;
+  // items of this lane below n (one 64-bit compare; the rounds then compare
+  // small constants against it), and one base pointer per array
+  const int64_t left = n - first;
+  const int avail = left <= 0 ? 0 : (left >= (int64_t)kWarpKeys ? kWarpKeys : (int)left);
+  const uint32_t* kp = a.keys_in + first;
+  const uint32_t* vp = a.vals_in ? a.vals_in + first : nullptr;
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const bool valid = r * 32 < avail;
+    key[r] = valid ? __ldcs(kp + r * 32) : 0xffffffffu;
+    val[r] = valid ? (vp ? __ldcs(vp + r * 32) : (uint32_t)(first + r * 32)) : 0u;
+  }
+}
+
+// One LSD pass. Per tile: rank the digits (eight warp ballots per key),
+// publish the tile's digit counts for the look-back, reorder the tile by digit
+// in shared memory, take the next tile and start its loads, then walk the
+// look-back for the global offsets (thread d for digit d, eight predecessors
+// per round trip) while those loads are in flight, and write the reordered
+// tile out.
 __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(PassArgs a) {
   __shared__ uint32_t s_keys[kSortTileKeys];
   __shared__ uint32_t s_vals[kSortTileKeys];
   __shared__ uint32_t s_cnt[kWarps][kRadix];   // per-warp digit counts -> exclusive offsets
   __shared__ uint32_t s_gbase[kRadix];         // exclusive scan of the global histogram
-  __shared__ uint32_t s_dst[kRadix];           // global start of each digit for this tile
   __shared__ uint32_t s_loc[kRadix];           // tile-local start of each digit
+  __shared__ uint32_t s_dst[kRadix];           // global start of each digit minus its local start
   __shared__ uint32_t s_tmp[kWarps];
   __shared__ uint32_t s_tile;
 
@@ -79,32 +106,20 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
   const uint32_t lt = lanemask_lt();
   const int d_me = threadIdx.x;   // the digit this thread scans / looks back on
 
-  s_gbase[d_me] = block_excl_scan(a.hist[d_me], s_tmp, nullptr);
+  if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + a.stage, 1u);
+  s_gbase[d_me] = block_excl_scan(a.hist[d_me], s_tmp, nullptr);   // synchronises
+  int64_t tile = s_tile;
+  uint32_t key[kSortItems], val[kSortItems];
+  if (tile < n_tiles) load_tile(a, n, tile, warp, lane, key, val);
 
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + a.stage, 1u);
+  while (tile < n_tiles) {
     for (int i = lane; i < kRadix; i += 32) s_cnt[warp][i] = 0;
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= n_tiles) break;
-    const int64_t base = tile * kSortTileKeys + (int64_t)warp * kWarpKeys;
-
-    uint32_t key[kSortItems], val[kSortItems];
+    __syncwarp();
     uint32_t rank[kSortItems];
-    // all loads first, so that each thread has 2 x 15 requests in flight
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-      const int64_t idx = base + r * 32 + lane;
-      const bool valid = idx < n;
-      key[r] = valid ? __ldcs(a.keys_in + idx) : 0xffffffffu;
-      val[r] = valid ? (a.vals_in ? __ldcs(a.vals_in + idx) : (uint32_t)idx) : 0u;
-    }
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
       // peers with the same digit: the AND over the digit's eight bits of the
-      // ballot or its complement. Slots past the end hold key 0xffffffff
-      // (digit 255) and are counted with it: they are the tile's last slots,
-      // so they only follow the valid keys of that digit and are never written
+      // ballot or its complement (padding keys rank last within digit 255)
       const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
       uint32_t peers = 0xffffffffu;
 #pragma unroll
@@ -121,7 +136,8 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
     }
     __syncthreads();
 
-    // per digit: exclusive offsets over warps, tile count, look-back
+    // per digit: exclusive offsets over warps and the tile's count, published
+    // at once for the successors' look-back
     uint32_t tile_cnt = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
@@ -129,33 +145,44 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
       s_cnt[w][d_me] = tile_cnt;
       tile_cnt += c;
     }
-    const uint32_t prefix =
-        lookback_prefix(a.lookback + d_me, kRadix, tile, tag, tile_cnt, a.ctr);
-    s_dst[d_me] = s_gbase[d_me] + prefix;
-    s_loc[d_me] = block_excl_scan(tile_cnt, s_tmp, nullptr);
+    lookback_publish(a.lookback + d_me, kRadix, tile, tag, tile == 0 ? 2u : 1u, tile_cnt);
+    const uint32_t loc = block_excl_scan(tile_cnt, s_tmp, nullptr);   // synchronises
+    s_loc[d_me] = loc;
     __syncthreads();
 
     // reorder in shared memory by digit (stable)
+    const int64_t base = tile * kSortTileKeys + (int64_t)warp * kWarpKeys;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-      const int64_t idx = base + r * 32 + lane;
-      if (idx < n) {
+      if (base + r * 32 + lane < n) {
         const uint32_t d = (key[r] >> a.shift) & (kRadix - 1);
         const uint32_t pos = s_loc[d] + s_cnt[warp][d] + rank[r];
         s_keys[pos] = key[r];
         s_vals[pos] = val[r];
       }
     }
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + a.stage, 1u);
     __syncthreads();
-    const int64_t tile_n = min((int64_t)kSortTileKeys, n - tile * kSortTileKeys);
+    const int64_t next = s_tile;
+    // the next tile's loads overlap this tile's look-back and write-out
+    if (next < n_tiles) load_tile(a, n, next, warp, lane, key, val);
+
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      prefix = lookback_walk(a.lookback + d_me, kRadix, tile, tag, a.ctr);
+      lookback_publish(a.lookback + d_me, kRadix, tile, tag, 2u, prefix + tile_cnt);
+    }
+    s_dst[d_me] = s_gbase[d_me] + prefix - loc;
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)kSortTileKeys, n - tile * kSortTileKeys);
     for (int i = threadIdx.x; i < tile_n; i += kSortThreads) {
       const uint32_t k = s_keys[i];
-      const uint32_t d = (k >> a.shift) & (kRadix - 1);
-      const uint32_t dst = s_dst[d] + (uint32_t)i - s_loc[d];
+      const uint32_t dst = s_dst[(k >> a.shift) & (kRadix - 1)] + (uint32_t)i;
       __stcs(a.keys_out + dst, k);
       __stcs(a.vals_out + dst, s_vals[i]);
     }
-    __syncthreads();
+    __syncthreads();   // shared arrays and s_tile are reused
+    tile = next;
   }
 }
 

@@ -76,7 +76,7 @@ struct ViewSet {
 #define S3R_SORT_ITEMS 15
 #endif
 #ifndef S3R_SORT_BLOCKS
-#define S3R_SORT_BLOCKS 3
+#define S3R_SORT_BLOCKS 2
 #endif
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = S3R_SORT_ITEMS;
@@ -242,39 +242,72 @@ __device__ __forceinline__ uint32_t stage_tag(uint32_t epoch, int stage) {
   return ((epoch << 4) | (uint32_t)stage) & 0x3fffffffu;
 }
 
-// Exclusive prefix for `tile` of one running sum (one digit). `words` points
-// at digit d's word of tile 0; consecutive tiles are `stride` words apart.
-// Publishes the inclusive value on exit. Bounded: after max_polls unanswered
-// polls it latches kStatusTimeout into ctr and returns the partial sum.
-__device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, int64_t stride,
-                                                     int64_t tile, uint32_t tag, uint32_t aggregate,
-                                                     uint32_t* ctr, int max_polls = kSpinLimit) {
-  unsigned long long* mine = words + tile * stride;
-  if (tile == 0) {
-    st_relaxed(mine, lb_word(tag, 2, aggregate));
-    return 0;
-  }
-  st_relaxed(mine, lb_word(tag, 1, aggregate));
+// Decoupled look-back over tiles for one running sum (one digit): `words`
+// points at the sum's word of tile 0, consecutive tiles `stride` words apart.
+// A tile first publishes its own aggregate (flag 1, lookback_publish), then
+// walks back over its predecessors, adding aggregates until it meets an
+// inclusive prefix (flag 2), and publishes its own inclusive prefix. The walk
+// reads kLookbackBatch predecessors per round trip (independent loads), so a
+// chain of w unfinished predecessors costs about w / kLookbackBatch dependent
+// loads. Bounded: after max_polls rounds without progress it latches
+// kStatusTimeout into ctr and returns the partial sum.
+constexpr int kLookbackBatch = 8;
+
+__device__ __forceinline__ void lookback_publish(unsigned long long* words, int64_t stride,
+                                                 int64_t tile, uint32_t tag, uint32_t flag,
+                                                 uint32_t value) {
+  st_relaxed(words + tile * stride, lb_word(tag, flag, value));
+}
+
+__device__ __forceinline__ uint32_t lookback_walk(unsigned long long* words, int64_t stride,
+                                                  int64_t tile, uint32_t tag, uint32_t* ctr,
+                                                  int max_polls = kSpinLimit) {
   uint32_t prefix = 0;
   int64_t k = tile - 1;
   int spins = 0;
   while (k >= 0) {
-    unsigned long long w = ld_relaxed(words + k * stride);
-    uint32_t wtag = (uint32_t)(w >> 34);
-    uint32_t flag = (uint32_t)(w >> 32) & 3u;
-    if (wtag != tag || flag == 0) {
+    unsigned long long w[kLookbackBatch];
+#pragma unroll
+    for (int j = 0; j < kLookbackBatch; ++j)
+      w[j] = k - j >= 0 ? ld_relaxed(words + (k - j) * stride) : lb_word(tag, 2u, 0u);
+    uint32_t acc = 0;
+    int used = 0;
+    bool stop = false, done = false;
+#pragma unroll
+    for (int j = 0; j < kLookbackBatch; ++j) {
+      const uint32_t flag = (uint32_t)(w[j] >> 34) == tag ? (uint32_t)(w[j] >> 32) & 3u : 0u;
+      const bool take = !stop && flag != 0u;
+      acc += take ? (uint32_t)w[j] : 0u;
+      used += take ? 1 : 0;
+      done = done || (take && flag == 2u);
+      stop = stop || flag != 1u;
+    }
+    prefix += acc;
+    k -= used;
+    if (done) break;
+    if (used == 0) {
       if (++spins > max_polls) {
         atomicOr(ctr + kCtrStatus, kStatusTimeout);
         break;
       }
       __nanosleep(20);
-      continue;
     }
-    prefix += (uint32_t)w;
-    if (flag == 2) break;
-    --k;
   }
-  st_relaxed(mine, lb_word(tag, 2, prefix + aggregate));
+  return prefix;
+}
+
+// Publish, walk and publish the inclusive value in one call (one thread per
+// running sum); returns the exclusive prefix of `tile`.
+__device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, int64_t stride,
+                                                     int64_t tile, uint32_t tag, uint32_t aggregate,
+                                                     uint32_t* ctr, int max_polls = kSpinLimit) {
+  if (tile == 0) {
+    lookback_publish(words, stride, 0, tag, 2u, aggregate);
+    return 0;
+  }
+  lookback_publish(words, stride, tile, tag, 1u, aggregate);
+  const uint32_t prefix = lookback_walk(words, stride, tile, tag, ctr, max_polls);
+  lookback_publish(words, stride, tile, tag, 2u, prefix + aggregate);
   return prefix;
 }
 
