@@ -254,10 +254,12 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
     kk = (scene.sh_degree + 1) ** 2 * 3 * 4
     geo = 12 + 12 + 16 + 4
     m = {
-        "temporal_compact": ("hbm", 8 * n + 4 * nsel),
-        # masks: ids, geometry, two masks out, the life record where in frustum,
-        # the (index, id) work list; scan: masks in, offsets out; splats: the
-        # work list, mask, offset, geometry and SH in, 53-byte records out
+        # the visibility windows in, the selected ids and the selection bitmap out
+        "temporal_compact": ("hbm", 8 * n + 4 * nsel + n / 8),
+        # masks: ids, geometry, two masks out, the life record where in
+        # frustum, the (index, id) work list; scan: masks in, offsets out;
+        # splats: the work list, mask, offset, geometry and SH in, 53-byte
+        # records out
         "project": ("hbm", nsel * (4 + geo + 8) + 8 * nfr + n_kept_gaussians * 8),
         "splat_scan": ("hbm", nsel * 8),
         "project_splats": ("hbm", n_kept_gaussians * (8 + 4 + 4 + geo + kk)
@@ -274,10 +276,11 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "splat_tiles": ("hbm", S * (8 + 16 + 8 + 1) + S * 32),
         "duplicate": ("hbm", S * (4 + 32) + S * (4 + 32)),
         "duplicate_expand": ("hbm", S * (4 + 32) + K * 8),   # + tile-digit histograms (on chip)
-        # boundary detection: the sorted pair keys in, [start, end) per tile out
-        "tile_ranges": ("hbm", K * 4 + tiles * 8),
-        "zero_splat_grads": ("hbm", S * 48),
-        "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + 2 * (geo + kk)) + S * 48),
+        # per tile: its range and class slot out (the binary searches' reads
+        # are cached); the forward's contributor bits cleared
+        "tile_ranges": ("hbm", tiles * (8 + 4) + K / 8 * 2),
+        # overwrite mode: kept rows written once (no read), the splat adjoints read
+        "project_bwd": ("hbm", n_kept_gaussians * (12 + geo + kk + (geo + kk)) + S * 48),
         # FP32 operations per evaluated (pixel, splat) pair, counted in the code
         # (MUFU ops besides). Forward 17: offset (1, the column's dx shared),
         # quadratic form (5), opacity scale and alpha clamp (2), three tests,
@@ -461,6 +464,16 @@ def run_ours(args, rank, world, local):
                 row.update(bound="alu", ops=int(amount), gops=round(gops, 1),
                            frac=round(gops / alu_peak_gops, 3))
         table[name] = row
+    if "blend_bwd" in table and kmean.get("blend_bwd", 0) > 0:
+        # the backward's CTAs also zero the gradient rows of the overwrite mode
+        # once its tile queue is empty (the 44-byte arrays in full, the SH rows
+        # of the Gaussians no view kept): the kernel's floor is its ALU work at
+        # the ALU peak plus that traffic at the HBM peak
+        kk_b = (scene.sh_degree + 1) ** 2 * 3 * 4
+        zb = 44 * n + kk_b * (n - n_kept_g)
+        floor_ms = (models["blend_bwd"][1] / (alu_peak_gops * 1e9) + zb / (hbm_peak * 1e9)) * 1e3
+        table["blend_bwd"].update(zero_bytes=int(zb),
+                                  frac_alu_plus_hbm=round(floor_ms / kmean["blend_bwd"], 3))
     if "blend_fwd" in table and kmean.get("blend_fwd", 0) > 0:
         # the survey's per-pair estimate of the forward (15 FP32 operations
         # per evaluated pair) beside the 17 counted in the code
@@ -479,10 +492,12 @@ def run_ours(args, rank, world, local):
                         unit="Gop/s (FP32)", frac=table[dom]["frac"],
                         peak_source=f"{n_sms} SMs (queried) x 128 FP32 lanes x max SM clock "
                                     f"{sm_max:.0f} MHz")
-    # the timed kernels, plus untimed ones of ours: the L1 loss and its zeroed
-    # output, the three small zero fills (tile ranges, contributor bits,
-    # pose-adjoint sums) and, for the conventional pipeline, the world transform
-    launches_per_step = len(kmean) + 5 + (1 if args.conventional else 0)
+            if "frac_alu_plus_hbm" in table[dom]:
+                roof.update(fused_zeroing_bytes=table[dom]["zero_bytes"],
+                            frac_alu_plus_hbm=table[dom]["frac_alu_plus_hbm"])
+    # the timed kernels, plus untimed ones of ours: the L1 loss and the zeroing
+    # of its output and, for the conventional pipeline, the world transform
+    launches_per_step = len(kmean) + 2 + (1 if args.conventional else 0)
 
     # --- plain per-view comparator: the same library, one camera per call, eager
     plain = None

@@ -36,6 +36,12 @@
  *     s3r_query_counts) returns S3R_ERR_CAPACITY / S3R_ERR_TIMEOUT and clears it.
  *   - Nothing aborts. s3r_last_error() returns a thread-local message for the
  *     most recent non-OK status of the calling thread.
+ *   - A sequence captured into a CUDA graph for replay starts at s3r_project:
+ *     some set-up of a call is done by the launches of the calls before it
+ *     (the forward clears the per-splat adjoints that the backward after it
+ *     sums into; a backward that does not follow a forward clears them with a
+ *     launch of its own), so a graph of a later call alone would replay
+ *     without it.
  *
  * Camera model: OpenCV pinhole (x right, y down, z forward). Pixel (x, y) is
  * sampled at (x + 0.5, y + 0.5). Tiles are 16x16 pixels. Gaussian i of
@@ -380,6 +386,53 @@ s3r_status s3r_kernel_times(s3r_workspace* ws, float* ms, int32_t n);
 #define S3R_STATIC_MAX_GAUSSIANS (1LL << 26)
 s3r_status s3r_select_visible_static(int64_t n, float t, const float* vis_window, uint32_t* out_idx,
                                      uint32_t* out_count, void* stream);
+
+/* NeuralODE object poses (Sec. 3.2, Eqs. 3-4). Each dynamic instance's state
+ * z(t) = [position (3), rotation vector r (3)] follows dz/dt = f(z, t, c) (Eq. 3),
+ * f(z, t, c) = W3 tanh(W2 tanh(W1 [z, t, c] + b1) + b2) + b3 with hidden width
+ * S3R_ODE_HIDDEN and c the instance's embedding (embed_dim <= S3R_ODE_MAX_EMBED
+ * floats); Eq. 4's integral from z(t0) is taken with classical fourth-order
+ * Runge-Kutta steps, `substeps` equal steps between consecutive output times.
+ * The pose at an output time (the instance pose W_{t,i2g} of s3r_poses) is
+ * the unit quaternion (cos(|r|/2), sin(|r|/2) r/|r|) (w, x, y, z) and the
+ * translation z[0:3]. The paper names neither the network nor the
+ * integrator: these are this library's choices.
+ *   params  device [s3r_ode_param_count(embed_dim)] FP32: W1 (H x (7 + D),
+ *           row-major), b1 (H), W2 (H x H), b2 (H), W3 (6 x H), b3 (6).
+ *   embed   device [n_inst, embed_dim] FP32 (may be NULL when embed_dim = 0). */
+#define S3R_ODE_HIDDEN 64
+#define S3R_ODE_MAX_EMBED 16
+typedef struct {
+  int32_t embed_dim;
+  const float* params;
+  const float* embed;
+} s3r_ode_net;
+int64_t s3r_ode_param_count(int32_t embed_dim);
+
+/* Forward (Eq. 4) for n_inst instances at once:
+ *   z0      device [n_inst, 6] states at times[0];
+ *   times   device [n_times] output times, ascending (n_times >= 1);
+ *   states  device [(n_times - 1) * substeps + 1, n_inst, 6]: the state after
+ *           every Runge-Kutta step (kept for s3r_ode_poses_bwd);
+ *   quat    device [n_times, n_inst, 4] (16-byte aligned), trans [n_times,
+ *           n_inst, 3]: the poses, so that quat + 4 n_inst j and trans +
+ *           3 n_inst j are timestep j's s3r_poses.
+ * S3R_ERR_INVALID on bad sizes or pointers, nothing launched. */
+s3r_status s3r_ode_poses(const s3r_ode_net* net, int32_t n_inst, const float* z0,
+                         const float* times, int32_t n_times, int32_t substeps, float* states,
+                         float* quat, float* trans, void* stream);
+
+/* Reverse mode of s3r_ode_poses (the exact derivative of its Runge-Kutta
+ * steps): given dL/dquat and dL/dtrans at every output time (device, the
+ * layouts of quat and trans; zeros where a time is not used), ADDS dL/dparams
+ * [param_count], dL/dembed [n_inst, embed_dim] and dL/dz0 [n_inst, 6] into
+ * caller-zeroed device buffers. `states` is the forward's output. The pose
+ * adjoints of one timestep are the inst_quat / inst_trans gradients of
+ * s3r_render_bwd. */
+s3r_status s3r_ode_poses_bwd(const s3r_ode_net* net, int32_t n_inst, const float* times,
+                             int32_t n_times, int32_t substeps, const float* states,
+                             const float* g_quat, const float* g_trans, float* g_params,
+                             float* g_embed, float* g_z0, void* stream);
 
 /* Synchronise `stream`, then return the device counts of the last call
  * sequence and the latched device status (which it clears). Tests and logs

@@ -30,7 +30,8 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_version", "s3r_built_arch", "s3r_l1_loss", "s3r_set_timing",
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
            "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
-           "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status", "s3r_set_grad_mode")
+           "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status", "s3r_set_grad_mode",
+           "s3r_ode_param_count", "s3r_ode_poses", "s3r_ode_poses_bwd")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -80,6 +81,10 @@ class AdamTensor(ctypes.Structure):
                 ("exp_avg_sq", ctypes.c_void_p), ("n", ctypes.c_int64)]
 
 
+class OdeNet(ctypes.Structure):
+    _fields_ = [("embed_dim", ctypes.c_int32), ("params", ctypes.c_void_p), ("embed", ctypes.c_void_p)]
+
+
 class Counts(ctypes.Structure):
     _fields_ = [("n_selected", ctypes.c_int64), ("n_splats", ctypes.c_int64),
                 ("n_duplicates", ctypes.c_int64), ("n_frustum", ctypes.c_int64),
@@ -122,6 +127,10 @@ def load(path: str = LIB_PATH):
     L.s3r_set_lod.argtypes = [vp, P(LodParams)]
     L.s3r_set_counting.argtypes = [vp, i32]
     L.s3r_set_grad_mode.argtypes = [vp, i32]
+    L.s3r_ode_param_count.argtypes = [i32]
+    L.s3r_ode_param_count.restype = i64
+    L.s3r_ode_poses.argtypes = [P(OdeNet), i32, vp, vp, i32, i32, vp, vp, vp, vp]
+    L.s3r_ode_poses_bwd.argtypes = [P(OdeNet), i32, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp]
     L.s3r_select_visible_static.argtypes = [i64, f32, vp, vp, vp, vp]
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp, vp]
     L.s3r_device_status.argtypes = [vp]
@@ -144,7 +153,7 @@ def load(path: str = LIB_PATH):
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
                  "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
                  "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout",
-                 "s3r_set_epoch", "s3r_set_grad_mode"):
+                 "s3r_set_epoch", "s3r_set_grad_mode", "s3r_ode_poses", "s3r_ode_poses_bwd"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -384,3 +393,40 @@ def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1:
 def update_visibility(n: int, t: float, mask, point_life, vis_window, mode: int, stream=None):
     _check(load().s3r_update_visibility(int(n), float(t), _ptr(mask), _ptr(point_life),
                                         _ptr(vis_window), int(mode), _stream(stream)))
+
+
+# ---------------------------------------------------------------- NeuralODE poses
+def ode_param_count(embed_dim: int) -> int:
+    n = int(load().s3r_ode_param_count(int(embed_dim)))
+    if n < 0:
+        raise ValueError(f"embed_dim {embed_dim} outside [0, 16]")
+    return n
+
+
+def _ode_net(params, embed) -> OdeNet:
+    d = int(embed.shape[1]) if embed is not None and embed.dim() == 2 else 0
+    return OdeNet(d, _ptr(params), _ptr(embed) if d else None)
+
+
+def ode_poses(params, embed, z0, times, substeps: int, stream=None):
+    """Eq. 4 through the library: returns (states, quat [T, K, 4], trans [T, K, 3])
+    as new device tensors (see s3r_ode_poses)."""
+    K, T = int(z0.shape[0]), int(times.shape[0])
+    dev = z0.device
+    states = torch.empty(((T - 1) * substeps + 1, K, 6), device=dev)
+    quat = torch.empty((T, K, 4), device=dev)
+    trans = torch.empty((T, K, 3), device=dev)
+    net = _ode_net(params, embed)
+    _check(load().s3r_ode_poses(ctypes.byref(net), K, _ptr(z0), _ptr(times), T, int(substeps),
+                                _ptr(states), _ptr(quat), _ptr(trans), _stream(stream)))
+    return states, quat, trans
+
+
+def ode_poses_bwd(params, embed, times, substeps: int, states, g_quat, g_trans, g_params, g_embed,
+                  g_z0, stream=None):
+    """Reverse mode of ode_poses: adds into g_params, g_embed, g_z0."""
+    K, T = int(states.shape[1]), int(times.shape[0])
+    net = _ode_net(params, embed)
+    _check(load().s3r_ode_poses_bwd(ctypes.byref(net), K, _ptr(times), T, int(substeps), _ptr(states),
+                                    _ptr(g_quat), _ptr(g_trans), _ptr(g_params), _ptr(g_embed),
+                                    _ptr(g_z0), _stream(stream)))

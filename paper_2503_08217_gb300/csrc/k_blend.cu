@@ -48,9 +48,39 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
 
+// Persistent tile queue: a launch of (SMs x resident blocks) CTAs takes tiles
+// from an atomic cursor, the longest tile lists first (k_tile_ranges files
+// every tile under class clz(length), class 0 the longest, 32 the empty
+// tiles). The last CTA to leave resets the cursor for the next launch.
+struct TileQueue {
+  uint32_t* cursor;
+  uint32_t* exits;
+  uint32_t* extra;     // a second cursor reset with it (or null)
+};
+
+// Overwrite mode of the backward: once the tile queue is empty, the CTAs of
+// the blend backward zero the caller's gradient arrays in chunks of
+// kZeroChunk Gaussians taken from their own cursor: the arrays of 1-4 floats
+// per Gaussian in full (the projection backward, which runs next, writes the
+// kept rows), the SH rows only of the Gaussians that no view kept. The
+// zeroing, which is bound by memory bandwidth, fills the ALU-bound blend's
+// tail instead of a launch of its own.
+constexpr int kZeroChunk = 2048;   // Gaussians (or splats) per chunk (64 words of the kept bitmap)
+struct GradZero {
+  const uint32_t* kept_bits;
+  int64_t n;                       // 0: nothing to zero (accumulate mode)
+  s3r_grads g;
+  int sh_floats;                   // 3 (K + 1)^2
+  uint32_t* cursor;
+};
+
 struct BlendArgs {
   const uint2* ranges;
-  const uint32_t* tile_order;
+  const uint32_t* class_cnt;    // [kTileClasses] tiles per class
+  const uint32_t* class_list;   // [kTileClasses][tiles] tile ids per class
+  int tiles;
+  TileQueue fwd_queue, bwd_queue;
+  GradZero zero;          // backward only
   const uint32_t* sorted_splats;
   const float2* sp_xy;
   const float4* sp_conic_o;
@@ -60,7 +90,9 @@ struct BlendArgs {
   float* out;             // forward only
   float* final_T;
   uint32_t* n_contrib;
-  float* sp_grad;         // backward only, [S*12]
+  float* sp_grad;         // [S*12]: zeroed by the forward's tail, summed by the backward
+  const uint32_t* ctr;
+  int64_t cap_splats;
   unsigned long long* pairs;     // counting mode: list pairs the forward walked
   unsigned long long* eval_fwd;  // counting mode: pairs the forward evaluated
   unsigned long long* eval_bwd;  // counting mode: pairs the backward evaluated
@@ -78,6 +110,126 @@ __device__ __forceinline__ void or_bits(uint32_t* arr, uint32_t gp, uint32_t bit
 __device__ __forceinline__ uint32_t get_bits(const uint32_t* arr, uint32_t gp) {
   const uint32_t w = gp >> 5, sh = gp & 31u;
   return __funnelshift_r(arr[w], arr[w + 1], sh);
+}
+
+// Class starts of the queue (exclusive scan of the class counts), once per
+// CTA; thread 0 takes the CTA's first queue position.
+__device__ __forceinline__ void queue_init(const BlendArgs& a, const TileQueue& q, uint32_t* s_cstart,
+                                           uint32_t& pending) {
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int c = 0; c < kTileClasses; ++c) {
+      s_cstart[c] = run;
+      run += a.class_cnt[c];
+    }
+    s_cstart[kTileClasses] = run;
+    pending = atomicAdd(q.cursor, 1u);
+  }
+  __syncthreads();
+}
+
+// The CTA's next tile, or -1 when the queue is empty (block-uniform). Thread
+// 0 holds the position taken one tile ahead, so that the atomic's round trip
+// overlaps the current tile's work.
+__device__ __forceinline__ int queue_next(const BlendArgs& a, const TileQueue& q,
+                                          const uint32_t* s_cstart, int* s_tile, uint32_t& pending) {
+  if (threadIdx.x == 0) {
+    const uint32_t i = pending;
+    int t = -1;
+    if (i < s_cstart[kTileClasses]) {
+      pending = atomicAdd(q.cursor, 1u);
+      int c = 0;
+      while (i >= s_cstart[c + 1]) ++c;
+      t = (int)a.class_list[(size_t)c * a.tiles + (i - s_cstart[c])];
+    }
+    *s_tile = t;
+  }
+  __syncthreads();
+  return *s_tile;
+}
+
+// Every CTA has taken its last tile: the last one to leave resets the cursor.
+__device__ __forceinline__ void queue_exit(const TileQueue& q) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(q.exits, 1u) == gridDim.x - 1) {
+      *q.cursor = 0u;
+      if (q.extra) *q.extra = 0u;
+      *q.exits = 0u;
+      __threadfence();
+    }
+  }
+}
+
+__device__ __forceinline__ void zero_span(float* p, int64_t lo, int64_t hi) {
+  if (!p) return;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) p[i] = 0.f;
+}
+
+template <int SHF>
+__device__ __forceinline__ void zero_sh_unkept(const GradZero& z, int64_t w0, int64_t w1) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int nwarps = (int)(blockDim.x >> 5);
+  for (int64_t w = w0 + (threadIdx.x >> 5); w < w1; w += nwarps) {
+    const int64_t g0 = w * 32;
+    const int cnt = (int)min((int64_t)32, z.n - g0);
+    const uint32_t live = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    const uint32_t zero = ~z.kept_bits[w] & live;
+    if (!zero) continue;
+    if constexpr (SHF % 4 == 0) {
+      constexpr int W4 = SHF / 4;
+      float4* p = reinterpret_cast<float4*>(z.g.sh) + g0 * W4;
+      for (int i = (int)lane; i < W4 * cnt; i += 32)
+        if ((zero >> (i / W4)) & 1u) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      float* p = z.g.sh + g0 * SHF;
+      for (int i = (int)lane; i < SHF * cnt; i += 32)
+        if ((zero >> (i / SHF)) & 1u) p[i] = 0.f;
+    }
+  }
+}
+
+// The forward's tail: its CTAs, once the tile queue is empty, zero the
+// per-splat adjoints (12 floats per splat) in chunks, for the backward that
+// sums into them.
+__device__ void splat_grad_zero_chunks(float4* g, const uint32_t* ctr, int64_t cap,
+                                       uint32_t* cursor, int* s_chunk) {
+  const int64_t n = min((int64_t)ctr[kCtrSplats], cap);
+  const int64_t n_chunks = (n + kZeroChunk - 1) / kZeroChunk;
+  for (;;) {
+    if (threadIdx.x == 0) *s_chunk = (int)atomicAdd(cursor, 1u);
+    __syncthreads();
+    const int64_t c = *s_chunk;
+    __syncthreads();
+    if (c >= n_chunks) break;
+    const int64_t lo = 3 * c * kZeroChunk, hi = 3 * min(n, (c + 1) * kZeroChunk);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ void grad_zero_chunks(const GradZero& z, int* s_chunk) {
+  const int64_t n_chunks = (z.n + kZeroChunk - 1) / kZeroChunk;
+  for (;;) {
+    if (threadIdx.x == 0) *s_chunk = (int)atomicAdd(z.cursor, 1u);
+    __syncthreads();
+    const int64_t c = *s_chunk;
+    __syncthreads();
+    if (c >= n_chunks) break;
+    const int64_t g0 = c * kZeroChunk, g1 = min(z.n, g0 + kZeroChunk);
+    zero_span(z.g.means, 3 * g0, 3 * g1);
+    zero_span(z.g.log_scales, 3 * g0, 3 * g1);
+    zero_span(z.g.quats, 4 * g0, 4 * g1);
+    zero_span(z.g.opacity_logits, g0, g1);
+    if (z.g.sh) {
+      const int64_t w0 = g0 / 32, w1 = (g1 + 31) / 32;
+      switch (z.sh_floats) {
+        case 3: zero_sh_unkept<3>(z, w0, w1); break;
+        case 12: zero_sh_unkept<12>(z, w0, w1); break;
+        case 27: zero_sh_unkept<27>(z, w0, w1); break;
+        default: zero_sh_unkept<48>(z, w0, w1); break;
+      }
+    }
+  }
 }
 
 __device__ __forceinline__ int view_of_tile(const ViewSet& vs, int tile) {
@@ -330,130 +482,141 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
   __shared__ float4 s_p3[kBatchFwd];   // b b v v
   __shared__ float2 s_u[kBatchFwd];    // u u
   __shared__ float4 s_box[kBatchFwd];
-  const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
-  const int v = view_of_tile(vs, tile);
-  const ViewInfo& vi = vs.v[v];
-  const int lt = tile - vi.tile_base;
-  const int warp = threadIdx.x >> 5;
-  const uint32_t lane = lane_id();
-  const Band P = band_pixels(vi, lt, warp, lane);
-  const uint2 range = a.ranges[tile];
-  const int n = (int)(range.y - range.x);
-  const f2 FY = pk(P.fy[0], P.fy[1]);
-  const f2 FX[2] = {pk(P.fx[0], P.fx[0]), pk(P.fx[1], P.fx[1])};
-  const f2 ONE = pk(1.f, 1.f);
+  __shared__ uint32_t s_cstart[kTileClasses + 1];
+  __shared__ int s_tile;
+  uint32_t pending = 0;
+  queue_init(a, a.fwd_queue, s_cstart, pending);
+  for (;;) {
+    const int tile = queue_next(a, a.fwd_queue, s_cstart, &s_tile, pending);
+    if (tile < 0) break;
+    const int v = view_of_tile(vs, tile);
+    const ViewInfo& vi = vs.v[v];
+    const int lt = tile - vi.tile_base;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const Band P = band_pixels(vi, lt, warp, lane);
+    const uint2 range = a.ranges[tile];
+    const int n = (int)(range.y - range.x);
+    const f2 FY = pk(P.fy[0], P.fy[1]);
+    const f2 FX[2] = {pk(P.fx[0], P.fx[0]), pk(P.fx[1], P.fx[1])};
+    const f2 ONE = pk(1.f, 1.f);
 
-  // per column c: the pair (row 0, row 1); scalar per-pixel state k = 2c + r
-  f2 T2[2], C2[2][3];
-  int last[kBandPix], endp[kBandPix];
-  bool done[kBandPix];
-  uint32_t n_eval = 0;
-  bool all_done = true;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    T2[c] = ONE;
-    C2[c][0] = C2[c][1] = C2[c][2] = pk(0.f, 0.f);
-#pragma unroll
-    for (int r = 0; r < kBandRows; ++r) {
-      const int k = c * kBandRows + r;
-      last[k] = 0;
-      done[k] = !(P.X0 + 8 * c < vi.width && P.Y0 + 4 * r < vi.height);
-      endp[k] = done[k] ? 0 : n;      // positions walked
-      all_done = all_done && done[k];
-    }
-  }
-  uint32_t* wbits = a.contrib + warp * a.contrib_words;
-  for (int b0 = 0; b0 < n; b0 += kBatchFwd) {
-    if (__syncthreads_count(all_done) == kBandThreads) break;
-    for (int i = threadIdx.x; i < kBatchFwd && b0 + i < n; i += kBandThreads) {
-      const uint32_t s = a.sorted_splats[range.x + b0 + i];
-      const float2 xy = a.sp_xy[s];
-      const float4 co = a.sp_conic_o[s];
-      const float4 rgb = a.sp_rgb_d[s];
-      float4 sa, sb;
-      float sc;
-      stage_splat(xy, co, rgb, sa, sb, sc);
-      s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
-      s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
-      s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
-      s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
-      s_u[i] = make_float2(sa.x, sa.x);
-      s_box[i] = alpha_box(xy, co);
-    }
-    __syncthreads();
-    const int m = min(kBatchFwd, n - b0);
-    for (int c0 = 0; c0 < m; c0 += 32) {
-      if (__all_sync(0xffffffffu, all_done)) break;
-      // which of the next 32 splats can reach alpha >= 1/255 in this warp's band
-      const int jl = c0 + (int)lane;
-      bool reach = false;
-      if (jl < m) {
-        const float4 p0 = s_p0[jl], p1 = s_p1[jl], p3 = s_p3[jl];
-        const float4 ea = make_float4(s_u[jl].x, p3.z, p0.x, p0.z);
-        const float4 eb = make_float4(p1.x, p1.z, 0.f, 0.f);
-        reach = !box_misses(s_box[jl], P) && ellipse_reaches(ea, eb, P);
-      }
-      uint32_t todo = __ballot_sync(0xffffffffu, reach);
-      uint32_t blended = 0;     // splats of this chunk blended into some pixel of the band
-      while (todo) {
-        const int j = c0 + __ffs(todo) - 1;
-        todo &= todo - 1;
-        const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
-        const float2 qu = s_u[j];
-        const int pos = b0 + j + 1;
-        bool any_blend = false;
-        // warp-uniform: every lane walks the same splat
-        if (q1.z > kAlphaMax)
-          fwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
-                                  n_eval, any_blend);
-        else
-          fwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
-                                   n_eval, any_blend);
-        all_done = true;
-#pragma unroll
-        for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
-        if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
-      }
-      if (lane == 0 && blended) or_bits(wbits, range.x + b0 + c0, blended);
-    }
-  }
-  if constexpr (kCount) {
-    // work accounting, one 64-bit atomic per warp and counter
-    unsigned long long walked = 0;
-#pragma unroll
-    for (int k = 0; k < kBandPix; ++k) walked += (unsigned long long)endp[k];
-    unsigned long long evald = n_eval;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      walked += __shfl_xor_sync(0xffffffffu, walked, o);
-      evald += __shfl_xor_sync(0xffffffffu, evald, o);
-    }
-    if (lane == 0 && walked) atomicAdd(a.pairs, walked);
-    if (lane == 0 && evald) atomicAdd(a.eval_fwd, evald);
-  }
-  const int64_t plane = (int64_t)vi.width * vi.height;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    float T[2], Cr[2], Cg[2], Cb[2];
-    upk(T2[c], T[0], T[1]);
-    upk(C2[c][0], Cr[0], Cr[1]);
-    upk(C2[c][1], Cg[0], Cg[1]);
-    upk(C2[c][2], Cb[0], Cb[1]);
-#pragma unroll
-    for (int r = 0; r < kBandRows; ++r) {
-      const int k = c * kBandRows + r;
-      const int px = P.X0 + 8 * c, py = P.Y0 + 4 * r;
-      if (px < vi.width && py < vi.height) {
-        const int64_t pix = (int64_t)py * vi.width + px;
-        float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
-        o[0] = fmaf(T[r], a.bg[0], Cr[r]);
-        o[plane] = fmaf(T[r], a.bg[1], Cg[r]);
-        o[2 * plane] = fmaf(T[r], a.bg[2], Cb[r]);
-        a.final_T[vi.pix_base + pix] = T[r];
-        a.n_contrib[vi.pix_base + pix] = (uint32_t)last[k];
+    // per column c: the pair (row 0, row 1); scalar per-pixel state k = 2c + r
+    f2 T2[2], C2[2][3];
+    int last[kBandPix], endp[kBandPix];
+    bool done[kBandPix];
+    uint32_t n_eval = 0;
+    bool all_done = true;
+  #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      T2[c] = ONE;
+      C2[c][0] = C2[c][1] = C2[c][2] = pk(0.f, 0.f);
+  #pragma unroll
+      for (int r = 0; r < kBandRows; ++r) {
+        const int k = c * kBandRows + r;
+        last[k] = 0;
+        done[k] = !(P.X0 + 8 * c < vi.width && P.Y0 + 4 * r < vi.height);
+        endp[k] = done[k] ? 0 : n;      // positions walked
+        all_done = all_done && done[k];
       }
     }
+    uint32_t* wbits = a.contrib + warp * a.contrib_words;
+    for (int b0 = 0; b0 < n; b0 += kBatchFwd) {
+      if (__syncthreads_count(all_done) == kBandThreads) break;
+      for (int i = threadIdx.x; i < kBatchFwd && b0 + i < n; i += kBandThreads) {
+        const uint32_t s = a.sorted_splats[range.x + b0 + i];
+        const float2 xy = a.sp_xy[s];
+        const float4 co = a.sp_conic_o[s];
+        const float4 rgb = a.sp_rgb_d[s];
+        float4 sa, sb;
+        float sc;
+        stage_splat(xy, co, rgb, sa, sb, sc);
+        s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
+        s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
+        s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
+        s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
+        s_u[i] = make_float2(sa.x, sa.x);
+        s_box[i] = alpha_box(xy, co);
+      }
+      __syncthreads();
+      const int m = min(kBatchFwd, n - b0);
+      for (int c0 = 0; c0 < m; c0 += 32) {
+        if (__all_sync(0xffffffffu, all_done)) break;
+        // which of the next 32 splats can reach alpha >= 1/255 in this warp's band
+        const int jl = c0 + (int)lane;
+        bool reach = false;
+        if (jl < m) {
+          const float4 p0 = s_p0[jl], p1 = s_p1[jl], p3 = s_p3[jl];
+          const float4 ea = make_float4(s_u[jl].x, p3.z, p0.x, p0.z);
+          const float4 eb = make_float4(p1.x, p1.z, 0.f, 0.f);
+          reach = !box_misses(s_box[jl], P) && ellipse_reaches(ea, eb, P);
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, reach);
+        uint32_t blended = 0;     // splats of this chunk blended into some pixel of the band
+        while (todo) {
+          const int j = c0 + __ffs(todo) - 1;
+          todo &= todo - 1;
+          const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
+          const float2 qu = s_u[j];
+          const int pos = b0 + j + 1;
+          bool any_blend = false;
+          // warp-uniform: every lane walks the same splat
+          if (q1.z > kAlphaMax)
+            fwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
+                                    n_eval, any_blend);
+          else
+            fwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
+                                     n_eval, any_blend);
+          all_done = true;
+  #pragma unroll
+          for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
+          if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
+        }
+        if (lane == 0 && blended) or_bits(wbits, range.x + b0 + c0, blended);
+      }
+    }
+    if constexpr (kCount) {
+      // work accounting, one 64-bit atomic per warp and counter
+      unsigned long long walked = 0;
+  #pragma unroll
+      for (int k = 0; k < kBandPix; ++k) walked += (unsigned long long)endp[k];
+      unsigned long long evald = n_eval;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        walked += __shfl_xor_sync(0xffffffffu, walked, o);
+        evald += __shfl_xor_sync(0xffffffffu, evald, o);
+      }
+      if (lane == 0 && walked) atomicAdd(a.pairs, walked);
+      if (lane == 0 && evald) atomicAdd(a.eval_fwd, evald);
+    }
+    const int64_t plane = (int64_t)vi.width * vi.height;
+  #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float T[2], Cr[2], Cg[2], Cb[2];
+      upk(T2[c], T[0], T[1]);
+      upk(C2[c][0], Cr[0], Cr[1]);
+      upk(C2[c][1], Cg[0], Cg[1]);
+      upk(C2[c][2], Cb[0], Cb[1]);
+  #pragma unroll
+      for (int r = 0; r < kBandRows; ++r) {
+        const int k = c * kBandRows + r;
+        const int px = P.X0 + 8 * c, py = P.Y0 + 4 * r;
+        if (px < vi.width && py < vi.height) {
+          const int64_t pix = (int64_t)py * vi.width + px;
+          float* o = a.out + 3 * (int64_t)vi.pix_base + pix;
+          o[0] = fmaf(T[r], a.bg[0], Cr[r]);
+          o[plane] = fmaf(T[r], a.bg[1], Cg[r]);
+          o[2 * plane] = fmaf(T[r], a.bg[2], Cb[r]);
+          a.final_T[vi.pix_base + pix] = T[r];
+          a.n_contrib[vi.pix_base + pix] = (uint32_t)last[k];
+        }
+      }
+    }
+    __syncthreads();   // shared staging is reused by the next tile
   }
+  splat_grad_zero_chunks(reinterpret_cast<float4*>(a.sp_grad), a.ctr, a.cap_splats,
+                         a.fwd_queue.extra, &s_tile);
+  queue_exit(a.fwd_queue);
 }
 
 // a ? x : y as one selp. Written out because the compiler turned the
@@ -649,147 +812,157 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_BWD_BLOCKS) k_blend_bw
   __shared__ float s_g[kBatchBwd][9];
   __shared__ float s_sink[kBandThreads];   // target of the lanes with no sum to add
   __shared__ int s_max;
-  const int tile = (int)a.tile_order[blockIdx.x];   // longest lists first
-  const int v = view_of_tile(vs, tile);
-  const ViewInfo& vi = vs.v[v];
-  const int lt = tile - vi.tile_base;
-  const int warp = threadIdx.x >> 5;
-  const uint32_t lane = lane_id();
-  const int X0 = (lt % vi.gx) * kTile + (int)(lane & 7u);
-  const int Y0 = (lt / vi.gx) * kTile + warp * (kTile / kBandWarps) + (int)(lane >> 3);
-  const uint2 range = a.ranges[tile];
+  __shared__ uint32_t s_cstart[kTileClasses + 1];
+  __shared__ int s_tile;
+  uint32_t pending = 0;
+  queue_init(a, a.bwd_queue, s_cstart, pending);
+  for (;;) {
+    const int tile = queue_next(a, a.bwd_queue, s_cstart, &s_tile, pending);
+    if (tile < 0) break;
+    const int v = view_of_tile(vs, tile);
+    const ViewInfo& vi = vs.v[v];
+    const int lt = tile - vi.tile_base;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const int X0 = (lt % vi.gx) * kTile + (int)(lane & 7u);
+    const int Y0 = (lt / vi.gx) * kTile + warp * (kTile / kBandWarps) + (int)(lane >> 3);
+    const uint2 range = a.ranges[tile];
 
-  float fx[2], fy[kRows];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) fx[c] = (float)(X0 + 8 * c) + 0.5f;
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) fy[r] = (float)(Y0 + 4 * r) + 0.5f;
-  const f2 FY = pk(fy[0], fy[1]);
-  const f2 FX[2] = {pk(fx[0], fx[0]), pk(fx[1], fx[1])};
-  const f2 ONE = pk(1.f, 1.f);
-  // per column c: (row 0, row 1) pairs of T, Bd and dL/dC; scalar last contributor
-  f2 T2[2], Bd2[2], Q0[2], Q1[2], Q2[2];
-  int last[kPix];
-  int wlast = 0;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    BwdPixel qq[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      const int px = X0 + 8 * c, py = Y0 + 4 * r;
-      bwd_init(qq[r], a, vi, px, py, px < vi.width && py < vi.height);
-      last[c * kRows + r] = qq[r].last;
-      wlast = max(wlast, qq[r].last);
+    float fx[2], fy[kRows];
+  #pragma unroll
+    for (int c = 0; c < 2; ++c) fx[c] = (float)(X0 + 8 * c) + 0.5f;
+  #pragma unroll
+    for (int r = 0; r < kRows; ++r) fy[r] = (float)(Y0 + 4 * r) + 0.5f;
+    const f2 FY = pk(fy[0], fy[1]);
+    const f2 FX[2] = {pk(fx[0], fx[0]), pk(fx[1], fx[1])};
+    const f2 ONE = pk(1.f, 1.f);
+    // per column c: (row 0, row 1) pairs of T, Bd and dL/dC; scalar last contributor
+    f2 T2[2], Bd2[2], Q0[2], Q1[2], Q2[2];
+    int last[kPix];
+    int wlast = 0;
+  #pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      BwdPixel qq[kRows];
+  #pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const int px = X0 + 8 * c, py = Y0 + 4 * r;
+        bwd_init(qq[r], a, vi, px, py, px < vi.width && py < vi.height);
+        last[c * kRows + r] = qq[r].last;
+        wlast = max(wlast, qq[r].last);
+      }
+      T2[c] = pk(qq[0].T, qq[1].T);
+      Bd2[c] = pk(qq[0].Bd, qq[1].Bd);
+      Q0[c] = pk(qq[0].d0, qq[1].d0);
+      Q1[c] = pk(qq[0].d1, qq[1].d1);
+      Q2[c] = pk(qq[0].d2, qq[1].d2);
     }
-    T2[c] = pk(qq[0].T, qq[1].T);
-    Bd2[c] = pk(qq[0].Bd, qq[1].Bd);
-    Q0[c] = pk(qq[0].d0, qq[1].d0);
-    Q1[c] = pk(qq[0].d1, qq[1].d1);
-    Q2[c] = pk(qq[0].d2, qq[1].d2);
-  }
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
-  if (lane == 0 && wlast) atomicMax(&s_max, wlast);
-  __syncthreads();
-  const int n = s_max;
-  uint32_t n_eval = 0;   // counting mode: pairs inside their pixel's walk
-  // the forward recorded its contributors per band, with the same bands
-  const uint32_t* wbits = a.contrib + warp * a.contrib_words;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+  #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    if (lane == 0 && wlast) atomicMax(&s_max, wlast);
+    __syncthreads();
+    const int n = s_max;
+    uint32_t n_eval = 0;   // counting mode: pairs inside their pixel's walk
+    // the forward recorded its contributors per band, with the same bands
+    const uint32_t* wbits = a.contrib + warp * a.contrib_words;
 
-  for (int hi = n; hi > 0; hi -= kBatchBwd) {
-    const int lo = max(0, hi - kBatchBwd);
-    const int m = hi - lo;
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kT) {
-      const uint32_t s = a.sorted_splats[range.x + lo + i];
-      s_id[i] = s;
-      const float2 xy = a.sp_xy[s];
-      const float4 co = a.sp_conic_o[s];
-      float4 sa, sb;
-      float sc;
-      stage_splat(xy, co, a.sp_rgb_d[s], sa, sb, sc);
-      s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
-      s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
-      s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
-      s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
-      s_u[i] = make_float2(sa.x, sa.x);
-    }
-    for (int i = threadIdx.x; i < kBatchBwd * 9; i += kT) (&s_g[0][0])[i] = 0.f;
-    __syncthreads();
-    // this warp's splats end at its own last contributor; walk them back to
-    // front, 32 at a time, visiting only the splats the forward blended into
-    // at least one pixel of the band (recorded bits)
-    for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
-      const int c0 = max(0, c1 - 31);
-      uint32_t todo = get_bits(wbits, range.x + lo + c0);
-      const int span = c1 - c0 + 1;
-      if (span < 32) todo &= (1u << span) - 1u;
-      // as a ballot result the mask is warp-uniform to the compiler as well
-      todo = __ballot_sync(0xffffffffu, (todo >> lane) & 1u);
-      while (todo) {
-        const int bit = 31 - __clz(todo);
-        todo &= ~(1u << bit);
-        const int j = c0 + bit;
-        const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
-        const float2 qu = s_u[j];
-        const int pos = lo + j;
-        float g[4];
-        f2 g4, g5, g6, g7, g8;
-        // warp-uniform: every lane walks the same splat
-        if (q1.z > kAlphaMax)
-          bwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
-                                  n_eval, g, g4, g5, g6, g7, g8);
-        else
-          bwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
-                                   n_eval, g, g4, g5, g6, g7, g8);
-        float gs[9] = {g[0], g[1], g[2], g[3], 0.f, 0.f, 0.f, 0.f, 0.f};
-        {
-          float lo4, hi4;
-          upk(g4, lo4, hi4); gs[4] = lo4 + hi4;
-          upk(g5, lo4, hi4); gs[5] = lo4 + hi4;
-          upk(g6, lo4, hi4); gs[6] = lo4 + hi4;
-          upk(g7, lo4, hi4); gs[7] = lo4 + hi4;
-          upk(g8, lo4, hi4); gs[8] = lo4 + hi4;
+    for (int hi = n; hi > 0; hi -= kBatchBwd) {
+      const int lo = max(0, hi - kBatchBwd);
+      const int m = hi - lo;
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += kT) {
+        const uint32_t s = a.sorted_splats[range.x + lo + i];
+        s_id[i] = s;
+        const float2 xy = a.sp_xy[s];
+        const float4 co = a.sp_conic_o[s];
+        float4 sa, sb;
+        float sc;
+        stage_splat(xy, co, a.sp_rgb_d[s], sa, sb, sc);
+        s_p0[i] = make_float4(sa.z, sa.z, sa.w, sa.w);
+        s_p1[i] = make_float4(sb.x, sb.x, sb.y, sb.y);
+        s_p2[i] = make_float4(sb.z, sb.z, sb.w, sb.w);
+        s_p3[i] = make_float4(sc, sc, sa.y, sa.y);
+        s_u[i] = make_float2(sa.x, sa.x);
+      }
+      for (int i = threadIdx.x; i < kBatchBwd * 9; i += kT) (&s_g[0][0])[i] = 0.f;
+      __syncthreads();
+      // this warp's splats end at its own last contributor; walk them back to
+      // front, 32 at a time, visiting only the splats the forward blended into
+      // at least one pixel of the band (recorded bits)
+      for (int c1 = min(m, wlast - lo) - 1; c1 >= 0; c1 -= 32) {
+        const int c0 = max(0, c1 - 31);
+        uint32_t todo = get_bits(wbits, range.x + lo + c0);
+        const int span = c1 - c0 + 1;
+        if (span < 32) todo &= (1u << span) - 1u;
+        // as a ballot result the mask is warp-uniform to the compiler as well
+        todo = __ballot_sync(0xffffffffu, (todo >> lane) & 1u);
+        while (todo) {
+          const int bit = 31 - __clz(todo);
+          todo &= ~(1u << bit);
+          const int j = c0 + bit;
+          const float4 q0 = s_p0[j], q1 = s_p1[j], q2 = s_p2[j], q3 = s_p3[j];
+          const float2 qu = s_u[j];
+          const int pos = lo + j;
+          float g[4];
+          f2 g4, g5, g6, g7, g8;
+          // warp-uniform: every lane walks the same splat
+          if (q1.z > kAlphaMax)
+            bwd_splat<kCount, true>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
+                                    n_eval, g, g4, g5, g6, g7, g8);
+          else
+            bwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, last, T2, Bd2, Q0, Q1, Q2,
+                                     n_eval, g, g4, g5, g6, g7, g8);
+          float gs[9] = {g[0], g[1], g[2], g[3], 0.f, 0.f, 0.f, 0.f, 0.f};
+          {
+            float lo4, hi4;
+            upk(g4, lo4, hi4); gs[4] = lo4 + hi4;
+            upk(g5, lo4, hi4); gs[5] = lo4 + hi4;
+            upk(g6, lo4, hi4); gs[6] = lo4 + hi4;
+            upk(g7, lo4, hi4); gs[7] = lo4 + hi4;
+            upk(g8, lo4, hi4); gs[8] = lo4 + hi4;
+          }
+          const float tot = warp_sum8_transposed(gs, lane);
+          float g8s = gs[8];
+  #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) g8s += __shfl_xor_sync(0xffffffffu, g8s, o);
+          // one shared atomic per warp: lanes 4m add value m, lane 1 the ninth
+          // sum, the rest add to their own sink word. Predicated atomics compiled
+          // to divergent branches (two per splat).
+          const bool own = (lane & 3u) == 0;
+          float* dst = own ? &s_g[j][lane >> 2] : (lane == 1 ? &s_g[j][8] : &s_sink[threadIdx.x]);
+          red_shared(dst, select_f(own, tot, g8s));
         }
-        const float tot = warp_sum8_transposed(gs, lane);
-        float g8s = gs[8];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) g8s += __shfl_xor_sync(0xffffffffu, g8s, o);
-        // one shared atomic per warp: lanes 4m add value m, lane 1 the ninth
-        // sum, the rest add to their own sink word. Predicated atomics compiled
-        // to divergent branches (two per splat).
-        const bool own = (lane & 3u) == 0;
-        float* dst = own ? &s_g[j][lane >> 2] : (lane == 1 ? &s_g[j][8] : &s_sink[threadIdx.x]);
-        red_shared(dst, select_f(own, tot, g8s));
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += kT) {
+        const float* sg = s_g[i];
+        bool any = false;
+  #pragma unroll
+        for (int r = 0; r < 9; ++r) any |= sg[r] != 0.f;
+        if (any) {
+          float* dst = a.sp_grad + 12 * (size_t)s_id[i];
+          // moments -> adjoints: power*log2(e) = dx (A2 dx + B2 dy) + C2 dy^2 with
+          // dx = u - px, so d/du = ln 2 (2 A2 g0 + B2 g1), d/dv = ln 2 (B2 g0 + 2 C2 g1)
+          const float A2 = s_p0[i].x, B2 = s_p0[i].z, C2 = s_p1[i].x;
+          const float gu = kLn2 * fmaf(2.f * A2, sg[0], B2 * sg[1]);
+          const float gv = kLn2 * fmaf(B2, sg[0], 2.f * C2 * sg[1]);
+          red_v4(dst, gu, gv, -0.5f * sg[2], -sg[3]);
+          red_v4(dst + 4, -0.5f * sg[4], sg[5], sg[6], sg[7]);
+          atomicAdd(dst + 8, sg[8]);
+        }
       }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += kT) {
-      const float* sg = s_g[i];
-      bool any = false;
-#pragma unroll
-      for (int r = 0; r < 9; ++r) any |= sg[r] != 0.f;
-      if (any) {
-        float* dst = a.sp_grad + 12 * (size_t)s_id[i];
-        // moments -> adjoints: power*log2(e) = dx (A2 dx + B2 dy) + C2 dy^2 with
-        // dx = u - px, so d/du = ln 2 (2 A2 g0 + B2 g1), d/dv = ln 2 (B2 g0 + 2 C2 g1)
-        const float A2 = s_p0[i].x, B2 = s_p0[i].z, C2 = s_p1[i].x;
-        const float gu = kLn2 * fmaf(2.f * A2, sg[0], B2 * sg[1]);
-        const float gv = kLn2 * fmaf(B2, sg[0], 2.f * C2 * sg[1]);
-        red_v4(dst, gu, gv, -0.5f * sg[2], -sg[3]);
-        red_v4(dst + 4, -0.5f * sg[4], sg[5], sg[6], sg[7]);
-        atomicAdd(dst + 8, sg[8]);
-      }
+    if constexpr (kCount) {
+      unsigned long long evald = n_eval;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) evald += __shfl_xor_sync(0xffffffffu, evald, o);
+      if (lane == 0 && evald) atomicAdd(a.eval_bwd, evald);
     }
+    __syncthreads();   // shared staging is reused by the next tile
   }
-  if constexpr (kCount) {
-    unsigned long long evald = n_eval;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) evald += __shfl_xor_sync(0xffffffffu, evald, o);
-    if (lane == 0 && evald) atomicAdd(a.eval_bwd, evald);
-  }
+  if (a.zero.n > 0) grad_zero_chunks(a.zero, &s_tile);
+  queue_exit(a.bwd_queue);
 }
 
 // Zero the per-splat adjoints of the splats written by the last projection.
@@ -805,7 +978,17 @@ __global__ void k_zero_grads(float4* g, const uint32_t* ctr, int64_t cap) {
 static BlendArgs make_args(s3r_workspace* ws) {
   BlendArgs a;
   a.ranges = ws->ranges;
-  a.tile_order = ws->tile_order;
+  a.class_cnt = ws->tile_class_cnt;
+  a.class_list = ws->tile_class_list;
+  a.tiles = ws->views.total_tiles;
+  a.fwd_queue = TileQueue{ws->ctr + kCtrBlendFwdCursor, ws->ctr + kCtrBlendFwdExits,
+                          ws->ctr + kCtrFwdZeroCursor};
+  a.ctr = ws->ctr;
+  a.cap_splats = ws->cap.max_splats;
+  a.bwd_queue = TileQueue{ws->ctr + kCtrBlendBwdCursor, ws->ctr + kCtrBlendBwdExits,
+                          ws->ctr + kCtrBwdZeroCursor};
+  a.zero = GradZero{nullptr, 0, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}, 0,
+                    ws->ctr + kCtrBwdZeroCursor};
   a.sorted_splats = ws->dup_val[ws->dup_final];
   a.sp_xy = ws->sp_xy;
   a.sp_conic_o = ws->sp_conic_o;
@@ -824,6 +1007,19 @@ static BlendArgs make_args(s3r_workspace* ws) {
   return a;
 }
 
+// Resident CTAs per SM of a blend instantiation, queried once per process.
+template <typename K>
+int blend_blocks_per_sm(K kernel, int* cache) {
+  if (*cache == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBandThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    *cache = per_sm;
+  }
+  return *cache;
+}
+
 cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cudaStream_t st) {
   BlendArgs a = make_args(ws);
   a.bg = bg;
@@ -834,36 +1030,54 @@ cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cu
     // pairs walked and evaluated (two adjacent 64-bit counters)
     if ((e = cudaMemsetAsync(a.pairs, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return e;
   }
-  e = launch_zero(ws->contrib, kBandWarps * ws->contrib_words, st);
-  if (e != cudaSuccess) return e;
+  // the contributor bits were cleared by the sort's tile ranges
+  static thread_local int per_sm[2] = {0, 0};
   KernelTimer timer(ws, kKBlendFwd, st);
-  if (ws->counting)
-    k_blend_fwd<true><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
-  else
-    k_blend_fwd<false><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
+  if (ws->counting) {
+    const int g = ws->num_sms * blend_blocks_per_sm(k_blend_fwd<true>, &per_sm[1]);
+    k_blend_fwd<true><<<g, kBandThreads, 0, st>>>(ws->views, a);
+  } else {
+    const int g = ws->num_sms * blend_blocks_per_sm(k_blend_fwd<false>, &per_sm[0]);
+    k_blend_fwd<false><<<g, kBandThreads, 0, st>>>(ws->views, a);
+  }
+  ws->sp_grad_clean = 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* dL,
-                              cudaStream_t st) {
+                              const s3r_grads* grads, cudaStream_t st) {
   BlendArgs a = make_args(ws);
   a.bg = bg;
   a.dL = dL;
-  {
+  // the splat adjoints start at zero: cleared by the forward's tail, or here
+  // when a backward has used them since
+  if (!ws->sp_grad_clean) {
     KernelTimer timer(ws, kKZeroGrads, st);
     k_zero_grads<<<ws->num_sms * 4, 256, 0, st>>>(reinterpret_cast<float4*>(ws->sp_grad), ws->ctr,
                                                   ws->cap.max_splats);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (ws->views.total_tiles == 0) return cudaSuccess;
+  ws->sp_grad_clean = 0;
+  if (ws->grad_mode == S3R_GRAD_OVERWRITE && ws->n > 0 &&
+      (grads->means || grads->log_scales || grads->quats || grads->opacity_logits || grads->sh)) {
+    a.zero.kept_bits = ws->kept_bits;
+    a.zero.n = ws->n;
+    a.zero.g = *grads;
+    a.zero.sh_floats = 3 * (ws->sh_degree + 1) * (ws->sh_degree + 1);
+  }
+  cudaError_t e;
   if (ws->counting && (e = cudaMemsetAsync(a.eval_bwd, 0, sizeof(unsigned long long), st)) != cudaSuccess)
     return e;
+  static thread_local int per_sm[2] = {0, 0};
   KernelTimer timer(ws, kKBlendBwd, st);
-  if (ws->counting)
-    k_blend_bwd<true><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
-  else
-    k_blend_bwd<false><<<ws->views.total_tiles, kBandThreads, 0, st>>>(ws->views, a);
+  if (ws->counting) {
+    const int g = ws->num_sms * blend_blocks_per_sm(k_blend_bwd<true>, &per_sm[1]);
+    k_blend_bwd<true><<<g, kBandThreads, 0, st>>>(ws->views, a);
+  } else {
+    const int g = ws->num_sms * blend_blocks_per_sm(k_blend_bwd<false>, &per_sm[0]);
+    k_blend_bwd<false><<<g, kBandThreads, 0, st>>>(ws->views, a);
+  }
   return cudaGetLastError();
 }
 

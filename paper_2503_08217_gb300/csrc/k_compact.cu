@@ -10,7 +10,7 @@
 #include <mutex>
 #include <string>
 
-#include "s3r_internal.cuh"
+#include "s3r_math.cuh"
 
 namespace s3r {
 namespace {
@@ -21,23 +21,56 @@ constexpr int kRounds = 8;                            // float4 loads per lane
 constexpr int kWarpSpan = kRounds * 32 * 2;           // Gaussians per warp
 constexpr int kTileSpan = kWarps * kWarpSpan;         // 4096 Gaussians per tile
 
-__global__ void k_begin(uint32_t* ctr, uint32_t* hist, unsigned long long* lookback,
-                        int64_t lookback_words) {
-  // one block: zero the per-call counters and histograms, bump the epoch
-  for (int i = threadIdx.x; i < kHistCount * kRadix; i += blockDim.x) hist[i] = 0;
-  const uint32_t epoch = ctr[kCtrEpoch] + 1;
-  __syncthreads();   // every thread has read the old epoch
-  // the status word, the epoch and the blend pair counts (which describe the
-  // last counted render) survive
-  if (threadIdx.x < kCtrCount && threadIdx.x != kCtrStatus && threadIdx.x != kCtrEpoch &&
-      (threadIdx.x < kCtrPairs || threadIdx.x > kCtrEvalBwd + 1))
-    ctr[threadIdx.x] = 0;
-  if (threadIdx.x == 0) ctr[kCtrEpoch] = epoch;
-  // look-back tags keep the epoch's low 26 bits: when they wrap, words of the
-  // call 2^26 calls ago would carry the current tags, so every word is
-  // cleared (once per 67,108,864 calls)
-  if ((epoch & ((1u << 26) - 1u)) == 0u)
-    for (int64_t i = threadIdx.x; i < lookback_words; i += blockDim.x) lookback[i] = 0ull;
+// W_v * P_k for every segment k of view v (k = 0: identity pose), and the
+// camera centre in the segment's frame, computed in FP64 once per call; the
+// block's threads stride over the segments.
+__device__ __forceinline__ void compose_view(const ViewSet& vs, int v,
+                                             const float4* __restrict__ pose_q,
+                                             const float* __restrict__ pose_t, int n_inst,
+                                             InstMat* __restrict__ out) {
+  const int nk = n_inst + 1;
+  const float* Vf = vs.v[v].V;
+  double V[12];
+  for (int i = 0; i < 12; ++i) V[i] = Vf[i];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[3] = {0, 0, 0};
+    if (k > 0) {
+      const float4 qf = pose_q[k - 1];
+      double w = qf.x, x = qf.y, y = qf.z, z = qf.w;
+      const double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+      w *= inv; x *= inv; y *= inv; z *= inv;
+      R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+      R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+      R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+      for (int r = 0; r < 3; ++r) t[r] = pose_t[3 * (k - 1) + r];
+    }
+    double A[9], b[3];
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c)
+        A[3 * r + c] = V[4 * r] * R[c] + V[4 * r + 1] * R[3 + c] + V[4 * r + 2] * R[6 + c];
+      b[r] = V[4 * r] * t[0] + V[4 * r + 1] * t[1] + V[4 * r + 2] * t[2] + V[4 * r + 3];
+    }
+    // c = -A^{-1} b by cofactors
+    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8],
+                 c02 = A[3] * A[7] - A[4] * A[6];
+    const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    const double Ai[9] = {c00 / det, (A[2] * A[7] - A[1] * A[8]) / det, (A[1] * A[5] - A[2] * A[4]) / det,
+                          c01 / det, (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
+                          c02 / det, (A[1] * A[6] - A[0] * A[7]) / det, (A[0] * A[4] - A[1] * A[3]) / det};
+    InstMat m;
+    for (int r = 0; r < 3; ++r) {
+      for (int c = 0; c < 3; ++c) m.m[4 * r + c] = (float)A[3 * r + c];
+      m.m[4 * r + 3] = (float)b[r];
+      const double cr = -(Ai[3 * r] * b[0] + Ai[3 * r + 1] * b[1] + Ai[3 * r + 2] * b[2]);
+      m.c[r] = (float)cr;
+      m.c_lo[r] = (float)(cr - (double)m.c[r]);
+    }
+    double f2 = 0.0;
+    for (int i = 0; i < 9; ++i) f2 += A[i] * A[i];
+    m.a_frob2 = (float)(f2 * (1.0 + 1e-6));
+    m.pad = 0.f;
+    out[v * nk + k] = m;
+  }
 }
 
 // Bits 2m (even) and 2m + 1 (odd) of a 32-bit word from bit m of the low
@@ -55,25 +88,70 @@ __device__ __forceinline__ uint32_t interleave16(uint32_t even, uint32_t odd) {
   return spread(even) | (spread(odd) << 1);
 }
 
+// The first launch of a call sequence also does the call's set-up, so that
+// it needs no launch of its own: its first CTAs compose the instance
+// matrices of the views (for the projection that follows), and the last CTA
+// to finish zeroes the per-call counters, histograms and tile-class counts,
+// bumps the call counter (epoch) and resets the compaction's tile counter.
+// The compaction's look-back words carry the tag of the new epoch, read by
+// every CTA before the last one finishes.
+struct CallSetup {
+  int n_views;                       // 0: no matrices to compose
+  const float4* pose_q;
+  const float* pose_t;
+  int n_inst;
+  InstMat* mats;
+  uint32_t* hist;                    // null: no histograms
+  uint32_t* tile_class_cnt;          // null: no tile classes
+  int64_t lookback_words;
+};
+
+__device__ void call_setup_last(uint32_t* ctr, unsigned long long* lookback, const CallSetup& c,
+                                int64_t n_tiles) {
+  if (c.hist)
+    for (int i = threadIdx.x; i < kHistCount * kRadix; i += blockDim.x) c.hist[i] = 0;
+  if (c.tile_class_cnt && threadIdx.x < kTileClasses) c.tile_class_cnt[threadIdx.x] = 0;
+  const uint32_t epoch = ctr[kCtrEpoch] + 1;
+  __syncthreads();   // every thread has read the old epoch
+  // kept: the status word, the epoch, the selection count just written, the
+  // blend pair counts (they describe the last counted render)
+  if (threadIdx.x < kCtrCount && threadIdx.x != kCtrStatus && threadIdx.x != kCtrEpoch &&
+      threadIdx.x != kCtrSelected && (threadIdx.x < kCtrPairs || threadIdx.x > kCtrEvalBwd + 1))
+    ctr[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    ctr[kCtrEpoch] = epoch;
+    if (n_tiles == 0) ctr[kCtrSelected] = 0;
+  }
+  // look-back tags keep the epoch's low 26 bits: before the call whose tags
+  // wrap around, every word is cleared (once per 67,108,864 calls)
+  if (((epoch + 1u) & ((1u << 26) - 1u)) == 0u)
+    for (int64_t i = threadIdx.x; i < c.lookback_words; i += blockDim.x) lookback[i] = 0ull;
+}
+
 // sel_bits (may be null): bit i of word i / 32 set iff Gaussian i is
 // selected; every word of every tile is written (zeros past n).
-__global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ vis, int64_t n,
+__global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__ ViewSet vs,
+                                                      const float* __restrict__ vis, int64_t n,
                                                       float t, uint32_t* __restrict__ sel,
                                                       uint32_t* ctr,
                                                       unsigned long long* lookback,
-                                                      uint32_t* __restrict__ sel_bits) {
+                                                      uint32_t* __restrict__ sel_bits,
+                                                      const CallSetup setup) {
   __shared__ uint32_t s_tile;
   __shared__ uint32_t s_warp[kWarps];
   __shared__ uint32_t s_base;
+  __shared__ bool s_last;
+  for (int v = blockIdx.x; v < setup.n_views; v += gridDim.x)
+    compose_view(vs, v, setup.pose_q, setup.pose_t, setup.n_inst, setup.mats);
   const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
-  const uint32_t tag = stage_tag(ctr[kCtrEpoch], kStageCompact);
+  const uint32_t tag = stage_tag(ctr[kCtrEpoch] + 1u, kStageCompact);
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    if (tile >= n_tiles) return;
+    if (tile >= n_tiles) break;
     const int64_t g0 = tile * kTileSpan + (int64_t)warp * kWarpSpan;
 
     uint32_t b0[kRounds], b1[kRounds];
@@ -136,25 +214,39 @@ __global__ void __launch_bounds__(kThreads) k_compact(const float* __restrict__ 
     }
     __syncthreads();  // s_tile / s_warp reuse
   }
+  // the last CTA to finish does the call's set-up for the launches after it
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ctr + kCtrCompactExits, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    call_setup_last(ctr, lookback, setup, n_tiles);
+    if (threadIdx.x == 0) ctr[kCtrCompactExits] = 0u;
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_begin(s3r_workspace* ws, cudaStream_t st) {
-  KernelTimer timer(ws, kKBegin, st);
-  k_begin<<<1, 256, 0, st>>>(ws->ctr, ws->hist, ws->lookback, ws->lookback_words);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float t,
-                           cudaStream_t st) {
+cudaError_t launch_compact(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
+                           const float* vis, float t, cudaStream_t st) {
+  const int64_t n = sc->n;
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
   int64_t grid = (int64_t)ws->num_sms * 8;
   if (grid > n_tiles) grid = n_tiles;
   if (grid < 1) grid = 1;
+  CallSetup c;
+  c.n_views = ws->n_views;
+  c.pose_q = reinterpret_cast<const float4*>(poses ? poses->quat : nullptr);
+  c.pose_t = poses ? poses->trans : nullptr;
+  c.n_inst = sc->n_inst;
+  c.mats = reinterpret_cast<InstMat*>(ws->mats);
+  c.hist = ws->hist;
+  c.tile_class_cnt = ws->tile_class_cnt;
+  c.lookback_words = ws->lookback_words;
   KernelTimer timer(ws, kKCompact, st);
-  k_compact<<<(unsigned)grid, kThreads, 0, st>>>(vis, n, t, ws->selected, ws->ctr, ws->lookback,
-                                                 ws->kept_bits);
+  k_compact<<<(unsigned)grid, kThreads, 0, st>>>(ws->views, vis, n, t, ws->selected, ws->ctr,
+                                                 ws->lookback, ws->kept_bits, c);
   return cudaGetLastError();
 }
 
@@ -178,6 +270,7 @@ struct StaticScratch {
 static __device__ __align__(256) StaticScratch g_static_scratch;
 
 constexpr int kMaxDevices = 64;
+const ViewSet g_no_views = {};   // the selection composes no matrices
 std::mutex g_static_mutex;
 StaticScratch* g_static_ptr[kMaxDevices] = {};
 int g_static_sms[kMaxDevices] = {};
@@ -252,8 +345,9 @@ extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float*
     int64_t grid = (int64_t)sms * 8;
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) grid = 1;
-    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(vis_window, n, t, out_idx, sc->ctr, sc->lookback,
-                                                   nullptr);
+    CallSetup none = {0, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0};
+    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(g_no_views, vis_window, n, t, out_idx, sc->ctr,
+                                                   sc->lookback, nullptr, none);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

@@ -54,57 +54,6 @@ struct ProjArgs {
   const InstMat* mats;      // [n_views][n_inst+1], from k_compose
 };
 
-// W_v * P_k for every view v and segment k (k = 0: identity pose), and the
-// camera centre in the segment's frame, computed in FP64 once per call. One
-// block per view, one thread per segment.
-__global__ void k_compose(const __grid_constant__ ViewSet vs, const float4* __restrict__ pose_q,
-                          const float* __restrict__ pose_t, int n_inst, InstMat* __restrict__ out) {
-  const int v = blockIdx.x;
-  const int nk = n_inst + 1;
-  const float* Vf = vs.v[v].V;
-  double V[12];
-  for (int i = 0; i < 12; ++i) V[i] = Vf[i];
-  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-    double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, t[3] = {0, 0, 0};
-    if (k > 0) {
-      const float4 qf = pose_q[k - 1];
-      double w = qf.x, x = qf.y, y = qf.z, z = qf.w;
-      const double inv = 1.0 / sqrt(w * w + x * x + y * y + z * z);
-      w *= inv; x *= inv; y *= inv; z *= inv;
-      R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-      R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-      R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-      for (int r = 0; r < 3; ++r) t[r] = pose_t[3 * (k - 1) + r];
-    }
-    double A[9], b[3];
-    for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < 3; ++c)
-        A[3 * r + c] = V[4 * r] * R[c] + V[4 * r + 1] * R[3 + c] + V[4 * r + 2] * R[6 + c];
-      b[r] = V[4 * r] * t[0] + V[4 * r + 1] * t[1] + V[4 * r + 2] * t[2] + V[4 * r + 3];
-    }
-    // c = -A^{-1} b by cofactors
-    const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8],
-                 c02 = A[3] * A[7] - A[4] * A[6];
-    const double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-    const double Ai[9] = {c00 / det, (A[2] * A[7] - A[1] * A[8]) / det, (A[1] * A[5] - A[2] * A[4]) / det,
-                          c01 / det, (A[0] * A[8] - A[2] * A[6]) / det, (A[2] * A[3] - A[0] * A[5]) / det,
-                          c02 / det, (A[1] * A[6] - A[0] * A[7]) / det, (A[0] * A[4] - A[1] * A[3]) / det};
-    InstMat m;
-    for (int r = 0; r < 3; ++r) {
-      for (int c = 0; c < 3; ++c) m.m[4 * r + c] = (float)A[3 * r + c];
-      m.m[4 * r + 3] = (float)b[r];
-      const double cr = -(Ai[3 * r] * b[0] + Ai[3 * r + 1] * b[1] + Ai[3 * r + 2] * b[2]);
-      m.c[r] = (float)cr;
-      m.c_lo[r] = (float)(cr - (double)m.c[r]);
-    }
-    double f2 = 0.0;
-    for (int i = 0; i < 9; ++i) f2 += A[i] * A[i];
-    m.a_frob2 = (float)(f2 * (1.0 + 1e-6));
-    m.pad = 0.f;
-    out[v * nk + k] = m;
-  }
-}
-
 // Pass 1: every selected Gaussian against every camera. Writes the frustum
 // and keep masks, applies Eq. 5 to the point life (on the frustum mask, before
 // LOD) and appends Gaussians kept in at least one view to the work list.
@@ -517,13 +466,7 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.lookback = ws->lookback;
   a.cap_splats = ws->cap.max_splats;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
-  {
-    KernelTimer timer(ws, kKCompose, st);
-    k_compose<<<ws->n_views, 128, 0, st>>>(ws->views, a.pose_q, a.pose_t, sc->n_inst,
-                                           reinterpret_cast<InstMat*>(ws->mats));
-  }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  // the instance matrices were composed by the compaction's first CTAs
   switch (sc->sh_degree) {
     case 0: return launch_deg<0>(ws, a, st);
     case 1: return launch_deg<1>(ws, a, st);

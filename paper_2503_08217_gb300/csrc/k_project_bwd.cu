@@ -112,6 +112,39 @@ __device__ __forceinline__ float4 quat_backward(float4 q, const float dR[9]) {
                      (gz - z * dot) * inv);
 }
 
+// dL/dP_k = V_rot^T dL/dW_{v,k} summed over views, then (q, t) of the pose,
+// for instance k (1-based). dM is read past L1 (other CTAs summed it).
+__device__ __forceinline__ void pose_chain_one(const ViewSet& vs, const float* dM, int n_inst, int k,
+                                               const float4* __restrict__ pose_q, float* g_q,
+                                               float* g_t, int overwrite) {
+  const int nk = n_inst + 1;
+  float dPr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dPt[3] = {0.f, 0.f, 0.f};
+  for (int v = 0; v < vs.n_views; ++v) {
+    const float* V = vs.v[v].V;
+    const float* dp = dM + (v * nk + k) * 12;
+    float d[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) d[i] = __ldcg(dp + i);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        dPr[3 * r + c] += V[r] * d[c] + V[4 + r] * d[4 + c] + V[8 + r] * d[8 + c];
+      dPt[r] += V[r] * d[3] + V[4 + r] * d[7] + V[8 + r] * d[11];
+    }
+  }
+  if (g_t) {
+    float* p = g_t + 3 * (k - 1);
+    for (int c = 0; c < 3; ++c) p[c] = overwrite ? dPt[c] : p[c] + dPt[c];
+  }
+  if (g_q) {
+    const float4 gq = quat_backward(pose_q[k - 1], dPr);
+    const float v[4] = {gq.x, gq.y, gq.z, gq.w};
+    float* p = g_q + 4 * (k - 1);
+    for (int c = 0; c < 4; ++c) p[c] = overwrite ? v[c] : p[c] + v[c];
+  }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_constant__ ViewSet vs,
                                                           BwdArgs a) {
@@ -493,78 +526,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
     const int k = (i / 12) % nk;
     if (k > 0 && s_dM[i] != 0.f) atomicAdd(a.pose_dM + i, s_dM[i]);
   }
-}
-
-// dL/dP_k = V_rot^T dL/dW_{v,k} summed over views, then (q, t) of the pose.
-__global__ void k_pose_chain(const __grid_constant__ ViewSet vs, const float* __restrict__ dM,
-                             int n_inst, const float4* __restrict__ pose_q, float* g_q,
-                             float* g_t, int overwrite) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  if (k > n_inst) return;
-  const int nk = n_inst + 1;
-  float dPr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, dPt[3] = {0.f, 0.f, 0.f};
-  for (int v = 0; v < vs.n_views; ++v) {
-    const float* V = vs.v[v].V;
-    const float* d = dM + (v * nk + k) * 12;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        dPr[3 * r + c] += V[r] * d[c] + V[4 + r] * d[4 + c] + V[8 + r] * d[8 + c];
-      dPt[r] += V[r] * d[3] + V[4 + r] * d[7] + V[8 + r] * d[11];
-    }
-  }
-  if (g_t) {
-    float* p = g_t + 3 * (k - 1);
-    for (int c = 0; c < 3; ++c) p[c] = overwrite ? dPt[c] : p[c] + dPt[c];
-  }
-  if (g_q) {
-    const float4 gq = quat_backward(pose_q[k - 1], dPr);
-    const float v[4] = {gq.x, gq.y, gq.z, gq.w};
-    float* p = g_q + 4 * (k - 1);
-    for (int c = 0; c < 4; ++c) p[c] = overwrite ? v[c] : p[c] + v[c];
-  }
-}
-
-// Overwrite mode, before k_project_bwd: the arrays of 1-4 floats per
-// Gaussian (means, log-scales, quaternions, opacity logits: 44 bytes) are
-// zeroed whole, with full coalesced stores (k_project_bwd then writes the
-// kept rows again; skipping them here would leave sectors half written), and
-// the SH rows (sector-sized: 192 bytes at degree 3) only where no view kept
-// the Gaussian: one warp per word of the kept bitmap, rows of the warp's 32
-// Gaussians contiguous, float4 stores where a row is whole float4s.
-__device__ __forceinline__ void zero_all(float* p, int64_t count, int64_t i0, int64_t stride) {
-  if (!p) return;
-  for (int64_t i = i0; i < count; i += stride) p[i] = 0.f;
-}
-
-template <int SHF>   // SH floats per Gaussian: 3 (K 1), 12, 27, 48 (K 16)
-__global__ void __launch_bounds__(256) k_zero_overwrite(const uint32_t* __restrict__ kept_bits,
-                                                        int64_t n, s3r_grads g) {
-  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
-  zero_all(g.means, 3 * n, t0, nt);
-  zero_all(g.log_scales, 3 * n, t0, nt);
-  zero_all(g.quats, 4 * n, t0, nt);
-  zero_all(g.opacity_logits, n, t0, nt);
-  if (!g.sh) return;
-  const uint32_t lane = threadIdx.x & 31u;
-  const int64_t n_words = (n + 31) / 32;
-  for (int64_t w = t0 >> 5; w < n_words; w += nt >> 5) {
-    const int64_t g0 = w * 32;
-    const int cnt = (int)min((int64_t)32, n - g0);
-    const uint32_t live = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
-    const uint32_t zero = ~kept_bits[w] & live;
-    if (!zero) continue;
-    if constexpr (SHF % 4 == 0) {
-      constexpr int W4 = SHF / 4;
-      float4* p = reinterpret_cast<float4*>(g.sh) + g0 * W4;
-      for (int i = (int)lane; i < W4 * cnt; i += 32)
-        if ((zero >> (i / W4)) & 1u) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      float* p = g.sh + g0 * SHF;
-      for (int i = (int)lane; i < SHF * cnt; i += 32)
-        if ((zero >> (i / SHF)) & 1u) p[i] = 0.f;
+  // the last CTA to finish maps the summed matrix adjoints to the poses, then
+  // clears the sums for the next call (they start at zero with the workspace)
+  if (a.n_inst > 0) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.ctr + kCtrProjBwdExits, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (a.g.inst_quat || a.g.inst_trans)
+        for (int k = 1 + (int)threadIdx.x; k <= a.n_inst; k += blockDim.x)
+          pose_chain_one(vs, a.pose_dM, a.n_inst, k, a.pose_q, a.g.inst_quat, a.g.inst_trans,
+                         a.overwrite);
+      __syncthreads();
+      for (int i = threadIdx.x; i < vs.n_views * nk * 12; i += blockDim.x) __stcg(a.pose_dM + i, 0.f);
+      if (threadIdx.x == 0) a.ctr[kCtrProjBwdExits] = 0u;
     }
   }
 }
@@ -626,36 +604,12 @@ cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r
   a.g = *g;
   a.mats = reinterpret_cast<const InstMat*>(ws->mats);
   a.overwrite = ws->grad_mode == S3R_GRAD_OVERWRITE ? 1 : 0;
-  const int nk = ws->n_inst + 1;
-  cudaError_t e = launch_zero(ws->pose_dM, 12 * (int64_t)ws->n_views * nk, st);
-  if (e != cudaSuccess) return e;
-  if (a.overwrite && ws->n > 0 &&
-      (g->means || g->log_scales || g->quats || g->opacity_logits || g->sh)) {
-    const int64_t words = (ws->n + 31) / 32;
-    int64_t blocks = (words + 7) / 8;
-    if (blocks > (int64_t)ws->num_sms * 8) blocks = (int64_t)ws->num_sms * 8;
-    KernelTimer timer(ws, kKZeroUnkept, st);
-    switch (sc->sh_degree) {
-      case 0: k_zero_overwrite<3><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
-      case 1: k_zero_overwrite<12><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
-      case 2: k_zero_overwrite<27><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
-      default: k_zero_overwrite<48><<<(unsigned)blocks, 256, 0, st>>>(ws->kept_bits, ws->n, *g); break;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  cudaError_t e = cudaSuccess;
   switch (sc->sh_degree) {
     case 0: e = launch_deg<0>(ws, a, st); break;
     case 1: e = launch_deg<1>(ws, a, st); break;
     case 2: e = launch_deg<2>(ws, a, st); break;
     default: e = launch_deg<3>(ws, a, st); break;
-  }
-  if (e != cudaSuccess) return e;
-  if (ws->n_inst > 0 && (g->inst_quat || g->inst_trans)) {
-    KernelTimer timer(ws, kKPoseChain, st);
-    k_pose_chain<<<(ws->n_inst + 127) / 128, 128, 0, st>>>(ws->views, ws->pose_dM, ws->n_inst,
-                                                          a.pose_q, g->inst_quat, g->inst_trans,
-                                                          a.overwrite);
-    e = cudaGetLastError();
   }
   return e;
 }

@@ -700,66 +700,63 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_expand(DupArgs a) {
   }
 }
 
-// Tile ranges by boundary detection in the sorted pair keys: the first and
-// one-past-last position of every tile id present; tiles without pairs keep
-// the [0, 0) written by the memset before the sort. Each thread takes
-// kRangeItems consecutive keys plus the one after them.
+// Tile ranges and the blend queue's classes, one thread per tile: the
+// tile's first pair is the lower bound of its id in the sorted pair keys
+// (binary search), its end the next tile's first pair (the neighbouring lane's
+// search). Every tile's [start, end) is written ([0, 0) for a tile without
+// pairs), and the tile is filed under class clz(end - start) (32 for the
+// empty ones): a shared count per class, one global atomic per class and
+// block for the block's slots, then the ids. The same launch clears the
+// forward's contributor bits.
 constexpr int kRangeThreads = 256;
-constexpr int kRangeItems = 8;
 
-__global__ void __launch_bounds__(kRangeThreads) k_tile_ranges(const uint32_t* __restrict__ keys,
-                                                               const uint32_t* ctr, int64_t cap,
-                                                               uint2* __restrict__ ranges) {
-  const int64_t K = min((int64_t)ctr[kCtrDups], cap);
-  const int64_t per = (int64_t)kRangeThreads * kRangeItems;
-  for (int64_t base = (int64_t)blockIdx.x * per; base < K; base += (int64_t)gridDim.x * per) {
-    const int64_t i0 = base + (int64_t)threadIdx.x * kRangeItems;
-    if (i0 >= K) continue;
-    uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
-    uint32_t cur = keys[i0];
-#pragma unroll
-    for (int k = 0; k < kRangeItems; ++k) {
-      const int64_t i = i0 + k;
-      if (i >= K) break;
-      const uint32_t next = i + 1 < K ? keys[i + 1] : 0xffffffffu;
-      if (cur != prev) ranges[cur].x = (uint32_t)i;
-      if (cur != next) ranges[cur].y = (uint32_t)(i + 1);
-      prev = cur;
-      cur = next;
+__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t* __restrict__ keys, uint32_t n,
+                                                    uint32_t v) {
+  uint32_t lo = 0, len = n;
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (__ldg(keys + lo + half) < v) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
     }
   }
+  return lo;
 }
 
-// Blend schedule: the tiles in descending order of their pair count (by
-// power-of-two bucket, any order inside a bucket), so that the longest lists
-// start first and do not trail the launch. One CTA.
-constexpr int kOrderThreads = 1024;
-
-__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const uint2* __restrict__ ranges,
-                                                              int tiles,
-                                                              uint32_t* __restrict__ order) {
-  __shared__ uint32_t s_cnt[33];
-  if (threadIdx.x < 33) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
-    const uint2 r = ranges[t];
-    const uint32_t len = r.y - r.x;
-    atomicAdd(&s_cnt[len ? __clz(len) : 32], 1u);   // bucket 0 = longest
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int b = 0; b < 33; ++b) {
-      const uint32_t c = s_cnt[b];
-      s_cnt[b] = run;
-      run += c;
+__global__ void __launch_bounds__(kRangeThreads) k_tile_ranges(
+    const uint32_t* __restrict__ keys, const uint32_t* ctr, int64_t cap, int tiles,
+    uint2* __restrict__ ranges, uint32_t* class_cnt, uint32_t* __restrict__ class_list,
+    uint32_t* __restrict__ contrib, int64_t contrib_words) {
+  __shared__ uint32_t s_cnt[kTileClasses], s_base[kTileClasses];
+  const uint32_t K = (uint32_t)min((int64_t)ctr[kCtrDups], cap);
+  const uint32_t lane = lane_id();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < contrib_words;
+       i += (int64_t)gridDim.x * blockDim.x)
+    contrib[i] = 0u;
+  for (int base = blockIdx.x * kRangeThreads; base < tiles; base += gridDim.x * kRangeThreads) {
+    if (threadIdx.x < kTileClasses) s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const int t = base + (int)threadIdx.x;
+    const bool live = t < tiles;
+    const uint32_t start = live ? lower_bound_u32(keys, K, (uint32_t)t) : K;
+    uint32_t end = __shfl_down_sync(0xffffffffu, start, 1);
+    if (live && (lane == 31 || t + 1 >= tiles)) end = lower_bound_u32(keys, K, (uint32_t)t + 1u);
+    int cls = 0;
+    uint32_t slot = 0;
+    if (live) {
+      const uint32_t len = end - start;
+      ranges[t] = len ? make_uint2(start, end) : make_uint2(0u, 0u);
+      cls = len ? __clz(len) : 32;
+      slot = atomicAdd(&s_cnt[cls], 1u);
     }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += kOrderThreads) {
-    const uint2 r = ranges[t];
-    const uint32_t len = r.y - r.x;
-    order[atomicAdd(&s_cnt[len ? __clz(len) : 32], 1u)] = (uint32_t)t;
+    __syncthreads();
+    if (threadIdx.x < kTileClasses && s_cnt[threadIdx.x])
+      s_base[threadIdx.x] = atomicAdd(class_cnt + threadIdx.x, s_cnt[threadIdx.x]);
+    __syncthreads();
+    if (live) class_list[(size_t)cls * tiles + s_base[cls] + slot] = (uint32_t)t;
+    __syncthreads();
   }
 }
 
@@ -866,19 +863,17 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   ws->dup_final = ws->tile_passes & 1;
-  // ranges of the tiles present in the sorted pairs; the rest stay [0, 0)
-  if ((e = launch_zero(ws->ranges, 2 * (int64_t)ws->views.total_tiles, st)) != cudaSuccess) return e;
+  // every tile's range and class (the blend queue), and the cleared
+  // contributor bits of the forward
   {
-    static thread_local int range_per_sm = 0;
-    if (!range_per_sm) range_per_sm = per_sm_for((const void*)k_tile_ranges, kRangeThreads);
+    const int tiles = ws->views.total_tiles;
+    int64_t grid = (tiles + kRangeThreads - 1) / kRangeThreads;
+    if (grid > (int64_t)ws->num_sms * 8) grid = (int64_t)ws->num_sms * 8;
+    if (grid < 1) grid = 1;
     KernelTimer timer(ws, kKTileRanges, st);
-    k_tile_ranges<<<ws->num_sms * range_per_sm, kRangeThreads, 0, st>>>(
-        ws->dup_key[ws->dup_final], ws->ctr, ws->cap.max_duplicates, ws->ranges);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  {
-    KernelTimer timer(ws, kKTileOrder, st);
-    k_tile_order<<<1, kOrderThreads, 0, st>>>(ws->ranges, ws->views.total_tiles, ws->tile_order);
+    k_tile_ranges<<<(unsigned)grid, kRangeThreads, 0, st>>>(
+        ws->dup_key[ws->dup_final], ws->ctr, ws->cap.max_duplicates, tiles, ws->ranges,
+        ws->tile_class_cnt, ws->tile_class_list, ws->contrib, 2 * ws->contrib_words);
   }
   return cudaGetLastError();
 }

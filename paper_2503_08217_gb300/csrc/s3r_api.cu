@@ -63,10 +63,10 @@ cudaError_t alloc(s3r_workspace* ws, T** p, int64_t count) {
 }
 
 const char* const kKernelNames[kKCount] = {
-    "begin", "temporal_compact", "compose", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
+    "temporal_compact", "project", "splat_scan", "project_splats", "sort_depth_pass0", "sort_depth_pass1",
     "sort_depth_pass2", "sort_depth_pass3", "duplicate", "sort_tile_pass0", "sort_tile_pass1",
-    "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd", "zero_splat_grads",
-    "blend_bwd", "project_bwd", "pose_chain", "tile_order", "splat_tiles", "zero_unkept_grads"};
+    "sort_tile_pass2", "sort_tile_pass3", "tile_ranges", "duplicate_expand", "blend_fwd",
+    "zero_splat_grads", "blend_bwd", "project_bwd", "splat_tiles"};
 
 void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
@@ -76,7 +76,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_order, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_class_cnt, ws->tile_class_list, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -205,7 +205,8 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->dup_val[0], K);
   S3R_ALLOC(ws->dup_val[1], K);
   S3R_ALLOC(ws->ranges, cap->max_tiles);
-  S3R_ALLOC(ws->tile_order, cap->max_tiles);
+  S3R_ALLOC(ws->tile_class_cnt, 64);
+  S3R_ALLOC(ws->tile_class_list, (int64_t)kTileClasses * cap->max_tiles);
   S3R_ALLOC(ws->final_T, cap->max_pixels);
   S3R_ALLOC(ws->n_contrib, cap->max_pixels);
   S3R_ALLOC(ws->sp_grad, 12 * S);
@@ -230,6 +231,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
     }
   }
   if ((e = cudaMemset(ws->ctr, 0, sizeof(uint32_t) * kCtrCount)) != cudaSuccess ||
+      (e = cudaMemset(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)cap->max_views * nk)) != cudaSuccess ||
       (e = cudaMemset(ws->lookback, 0, sizeof(unsigned long long) * ws->lookback_words)) !=
           cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
@@ -314,8 +316,7 @@ s3r_status s3r_project(s3r_workspace* ws, const s3r_scene* scene, const s3r_pose
   ws->stage_done = 0;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if ((e = launch_begin(ws, s)) != cudaSuccess) return cuda_fail(e, "begin");
-  if ((e = launch_compact(ws, vis_window, scene->n, t, s)) != cudaSuccess)
+  if ((e = launch_compact(ws, scene, poses, vis_window, t, s)) != cudaSuccess)
     return cuda_fail(e, "temporal selection");
   if ((e = launch_project(ws, scene, poses, t, point_life, lod_threshold, s)) != cudaSuccess)
     return cuda_fail(e, "projection");
@@ -363,7 +364,7 @@ s3r_status s3r_render_bwd(s3r_workspace* ws, const s3r_scene* scene, const s3r_p
     return fail(S3R_ERR_INVALID, "quaternion and SH gradients must be 16-byte aligned");
   DeviceGuard g(ws->device);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_render_bwd(ws, background, dL_drgb, s);
+  cudaError_t e = launch_render_bwd(ws, background, dL_drgb, grads, s);
   if (e != cudaSuccess) return cuda_fail(e, "render backward");
   e = launch_project_bwd(ws, scene, poses, grads, s);
   if (e != cudaSuccess) return cuda_fail(e, "projection backward");
@@ -510,6 +511,57 @@ s3r_status s3r_l1_loss(int64_t n, const float* pred, const float* target, float*
     return fail(S3R_ERR_INVALID, "pred, target, dL_dpred and loss_out must be float arrays");
   cudaError_t e = launch_l1_loss(n, pred, target, dL_dpred, loss_out, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "l1 loss");
+  return S3R_OK;
+}
+
+int64_t s3r_ode_param_count(int32_t embed_dim) {
+  if (embed_dim < 0 || embed_dim > S3R_ODE_MAX_EMBED) return -1;
+  return ode_param_count(embed_dim);
+}
+
+static s3r_status check_ode(const s3r_ode_net* net, int32_t n_inst, const float* times,
+                            int32_t n_times, int32_t substeps, const float* states) {
+  if (!net || !net->params || net->embed_dim < 0 || net->embed_dim > S3R_ODE_MAX_EMBED ||
+      (net->embed_dim > 0 && !net->embed))
+    return fail(S3R_ERR_INVALID, "ode: params, and embed when embed_dim > 0, with embed_dim <= %d",
+                S3R_ODE_MAX_EMBED);
+  if (n_inst < 0 || n_times < 1 || substeps < 1 || !times || (n_inst > 0 && !states))
+    return fail(S3R_ERR_INVALID, "ode: n_inst >= 0, n_times >= 1, substeps >= 1, times and states");
+  if ((int64_t)(n_times - 1) * substeps + 1 > 0x7fffffffLL / 6 / (n_inst > 0 ? n_inst : 1))
+    return fail(S3R_ERR_INVALID, "ode: trajectory too long");
+  if (!aligned(net->params, 4) || !aligned(times, 4) || !aligned(states, 4))
+    return fail(S3R_ERR_INVALID, "ode: float arrays required");
+  return S3R_OK;
+}
+
+s3r_status s3r_ode_poses(const s3r_ode_net* net, int32_t n_inst, const float* z0,
+                         const float* times, int32_t n_times, int32_t substeps, float* states,
+                         float* quat, float* trans, void* stream) {
+  s3r_status st = check_ode(net, n_inst, times, n_times, substeps, states);
+  if (st != S3R_OK) return st;
+  if (n_inst == 0) return S3R_OK;
+  if (!z0 || !quat || !trans || !aligned(quat, 16) || !aligned(trans, 4) || !aligned(z0, 4))
+    return fail(S3R_ERR_INVALID, "ode: z0, quat (16-byte aligned) and trans required");
+  cudaError_t e = launch_ode_fwd(net, n_inst, z0, times, n_times, substeps, states, quat, trans,
+                                 (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ode forward");
+  return S3R_OK;
+}
+
+s3r_status s3r_ode_poses_bwd(const s3r_ode_net* net, int32_t n_inst, const float* times,
+                             int32_t n_times, int32_t substeps, const float* states,
+                             const float* g_quat, const float* g_trans, float* g_params,
+                             float* g_embed, float* g_z0, void* stream) {
+  s3r_status st = check_ode(net, n_inst, times, n_times, substeps, states);
+  if (st != S3R_OK) return st;
+  if (n_inst == 0) return S3R_OK;
+  if (!g_quat || !g_trans || !g_params || !g_z0 || (net->embed_dim > 0 && !g_embed) ||
+      !aligned(g_quat, 16) || !aligned(g_trans, 4) || !aligned(g_params, 4) || !aligned(g_z0, 4))
+    return fail(S3R_ERR_INVALID, "ode: the pose adjoints (quaternions 16-byte aligned) and the "
+                                 "gradient buffers are required");
+  cudaError_t e = launch_ode_bwd(net, n_inst, times, n_times, substeps, states, g_quat, g_trans,
+                                 g_params, g_embed, g_z0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ode backward");
   return S3R_OK;
 }
 

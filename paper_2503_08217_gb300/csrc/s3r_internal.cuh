@@ -26,8 +26,19 @@ enum Ctr : int {
   kCtrEvalFwd = 26,   // 64-bit: (pixel, splat) pairs the forward evaluated (counting mode)
   kCtrEvalBwd = 28,   // 64-bit: (pixel, splat) pairs the backward evaluated (counting mode)
   kCtrRows = 30,      // 64-bit: row-table entries requested by the tile counts of the sort
-  kCtrCount = 32
+  kCtrBlendFwdCursor = 32,   // persistent blend queues: next tile, and CTAs that left
+  kCtrBlendFwdExits = 33,
+  kCtrBlendBwdCursor = 34,
+  kCtrBlendBwdExits = 35,
+  kCtrProjBwdExits = 36,     // CTAs of the projection backward that finished
+  kCtrBwdZeroCursor = 37,    // next chunk of the overwrite-mode gradient zeroing
+  kCtrCompactExits = 38,     // CTAs of the compaction that finished
+  kCtrFwdZeroCursor = 39,    // next chunk of the splat-adjoint zeroing in the blend forward
+  kCtrCount = 40
 };
+// Tile classes of the blend queue: class c = clz(pairs) holds the tiles with
+// [2^(31-c), 2^(32-c)) pairs (class 0 the longest lists), class 32 the empty.
+constexpr int kTileClasses = 33;
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
@@ -95,9 +106,9 @@ constexpr int kDupChunkMin = 1024;   // smallest output chunk of the pair expans
 
 // Kernel ids for the per-kernel timing hook.
 enum KernelId : int {
-  kKBegin = 0, kKCompact, kKCompose, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
+  kKCompact = 0, kKProject, kKSplatScan, kKProjectSplats, kKDepth0, kKDepth1, kKDepth2, kKDepth3, kKDuplicate,
   kKTile0, kKTile1, kKTile2, kKTile3, kKTileRanges, kKExpand, kKBlendFwd, kKZeroGrads, kKBlendBwd,
-  kKProjectBwd, kKPoseChain, kKTileOrder, kKSplatTiles, kKZeroUnkept, kKCount
+  kKProjectBwd, kKSplatTiles, kKCount
 };
 
 }  // namespace s3r
@@ -129,11 +140,13 @@ struct s3r_workspace {
   uint32_t* dup_key[2];     // [K]
   uint32_t* dup_val[2];     // [K]
   uint2* ranges;            // [tiles]
-  uint32_t* tile_order;     // [tiles] tiles by descending pair count (power-of-two buckets)
+  uint32_t* tile_class_cnt; // [64] tiles per class of pair count (kTileClasses used)
+  uint32_t* tile_class_list;  // [kTileClasses][max_tiles] tile ids per class
   float* final_T;           // [P]
   uint32_t* n_contrib;      // [P]
-  float* sp_grad;           // [S*12]
-  float* pose_dM;           // [views*(inst+1)*12]
+  float* sp_grad;           // [S*12] per-splat 2D adjoints summed by the blend backward
+  int sp_grad_clean;        // host: the last render_fwd zeroed sp_grad and no backward used it since
+  float* pose_dM;           // [views*(inst+1)*12], zero between backward calls
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
@@ -193,9 +206,8 @@ struct KernelTimer {
 namespace s3r {
 
 // ---- launchers (one translation unit each) ---------------------------------
-cudaError_t launch_begin(s3r_workspace* ws, cudaStream_t st);
-cudaError_t launch_compact(s3r_workspace* ws, const float* vis, int64_t n, float t,
-                           cudaStream_t st);
+cudaError_t launch_compact(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
+                           const float* vis, float t, cudaStream_t st);
 cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                            float t, float* life, float lod, cudaStream_t st);
 cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st);
@@ -203,7 +215,7 @@ cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* 
                             float* quats_out, int num_sms, cudaStream_t st);
 cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cudaStream_t st);
 cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* dL,
-                              cudaStream_t st);
+                              const s3r_grads* grads, cudaStream_t st);
 cudaError_t launch_project_bwd(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                                const s3r_grads* g, cudaStream_t st);
 cudaError_t launch_adam(const s3r_adam_tensor* t, int count, float lr, float b1, float b2,
@@ -219,6 +231,14 @@ cudaError_t launch_l1_loss(int64_t n, const float* pred, const float* target, fl
 cudaError_t launch_visibility(int64_t n, float t, const uint32_t* mask, float* life, float* vis,
                               int mode, cudaStream_t st);
 cudaError_t launch_wait_probe(s3r_workspace* ws, int max_polls, cudaStream_t st);
+int64_t ode_param_count(int embed_dim);
+cudaError_t launch_ode_fwd(const s3r_ode_net* net, int n_inst, const float* z0, const float* times,
+                           int n_times, int substeps, float* states, float* quat, float* trans,
+                           cudaStream_t st);
+cudaError_t launch_ode_bwd(const s3r_ode_net* net, int n_inst, const float* times, int n_times,
+                           int substeps, const float* states, const float* g_quat,
+                           const float* g_trans, float* g_params, float* g_embed, float* g_z0,
+                           cudaStream_t st);
 // Record `msg` as the calling thread's last error and return `st`.
 s3r_status set_last_error(s3r_status st, const char* msg);
 

@@ -323,3 +323,22 @@ def subset(scene: Scene, n_static: int, per_inst: int, seed: int = 0) -> Scene:
 
 def with_cameras(scene: Scene, cams_per_step) -> Scene:
     return dataclasses.replace(scene, cams=cams_per_step)
+
+
+def ode_model(seed: int, n_inst: int, embed_dim: int = 8, scale: float = 0.6,
+              z0_positions=None):
+    """Seeded parameters of the NeuralODE pose model (flat FP32 vector in the
+    library's layout, hidden width 64), instance embeddings [K, D] and initial
+    states [K, 6] (the given positions, or uniform in a 20 m box, and zero
+    rotation). Random draws only."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H = 64
+    n = H * (7 + embed_dim) + H + H * H + H + 6 * H + 6
+    params = (rng.standard_normal(n) * (scale / np.sqrt(H))).astype(np.float32)
+    embed = (rng.standard_normal((n_inst, embed_dim)) * 0.5).astype(np.float32)
+    z0 = np.zeros((n_inst, 6), np.float32)
+    if z0_positions is None:
+        z0[:, :3] = rng.uniform(-10.0, 10.0, (n_inst, 3))
+    else:
+        z0[:, :3] = np.asarray(z0_positions, np.float32)
+    return params, embed, z0

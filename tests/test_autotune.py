@@ -187,7 +187,14 @@ def test_the_binding_loads_the_library_the_environment_names():
 
 def test_recorded_traffic_is_not_claimed_for_a_variant_library(monkeypatch):
     import bench
-    assert bench.measured_traffic("blend_bwd", "rig") is not None
+    # a record taken on the current source of the kernel's file
+    src = "paper_2503_08217_gb300/csrc/k_blend.cu"
+    monkeypatch.setitem(bench.NCU_TRAFFIC, "blend_bwd",
+                        {"bytes": 123, "source": src, "profile": "profiles/x.md",
+                         "code_sha256_16": bench.code_hash(os.path.join(ROOT, src))})
+    monkeypatch.delenv("S3R_LIBRARY", raising=False)
+    assert bench.measured_traffic("blend_bwd", "rig") == 123
+    assert bench.measured_traffic("blend_bwd", "mid") is None
     monkeypatch.setenv("S3R_LIBRARY", libbuild.variant_path({"S3R_BLEND_BWD_BATCH": 32}))
     assert bench.measured_traffic("blend_bwd", "rig") is None
 

@@ -771,8 +771,10 @@ def test_autograd_function_matches_direct_calls(built, tiny, tiny_vis):
     r.backward(dev, iq.detach(), it.detach(), bg, w, grads)
     torch.testing.assert_close(out, out2, rtol=0, atol=0)
     for p, k in zip(params, ("means", "log_scales", "quats", "opacity_logits", "sh")):
-        # the same kernels twice: only the order of float atomics differs
-        torch.testing.assert_close(p.grad, grads[k], rtol=1e-4, atol=1e-5)
+        # the same kernels twice: only the order of float atomics differs, so
+        # entries that cancel may move by rounding relative to the tensor's scale
+        scale = max(float(grads[k].abs().max()), 1e-30)
+        torch.testing.assert_close(p.grad, grads[k], rtol=1e-4, atol=1e-5 * scale)
 
 
 def test_cuda_graph_replay_matches_eager(built, tiny, tiny_vis):
