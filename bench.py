@@ -19,6 +19,7 @@ the public API with host buffers, and the SM clocks seen while timing.
   python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
   python bench.py --conventional ...     # the Fig. 1(a) pipeline (world transform, no LOD)
   python bench.py --sweep scale          # per-view time against scene size
+  python bench.py --workload train       # optimisation steps (forward, backward, Adam)
 """
 from __future__ import annotations
 
@@ -107,6 +108,8 @@ WORKLOADS = {
     "tiny": ("tiny", {}, 0.0, "tiny corridor: 20k static + 2x1k dynamic, SH0, one 320x192 camera"),
     "small-rig": ("rig", {"n_static": 1_500_000, "n_inst": 16, "n_steps": 60}, 1.0,
                   "profiling case: the surround rig on a 1.5M-Gaussian corridor"),
+    "train": ("train", {}, 1.0, "training steps on the 2 km corridor: 16M static + 120 instances of "
+              "U{5k..20k}, SH3, the 7-camera surround rig, Adam on every parameter and pose"),
 }
 
 
@@ -293,6 +296,12 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "blend_fwd": ("alu", counts["n_eval_fwd"] * 17),
         "blend_bwd": ("alu", counts["n_eval_bwd"] * 42),
     }
+    # the world transform of the dynamic rows (Fig. 1(a)): means, quaternions
+    # and SH in and out; its backward reads the parameters and the world-frame
+    # adjoints and writes the object-frame adjoints in place
+    n_dyn = int(scene.inst_offsets[-1] - scene.inst_offsets[1]) if scene.n_inst else 0
+    m["to_world"] = ("hbm", n_dyn * 2 * (12 + 16 + kk))
+    m["to_world_bwd"] = ("hbm", n_dyn * 3 * (12 + 16 + kk))
     for p in range(tile_passes):
         m[f"sort_tile_pass{p}"] = ("hbm", K * 16)
     return m
@@ -363,10 +372,13 @@ def run_ours(args, rank, world, local):
              "inst_trans": torch.zeros_like(it)}
 
     if args.conventional:
-        # Fig. 1(a): the world-frame copy of the scene, rendered without instances
-        mw = torch.empty_like(dev.means)
-        qw = torch.empty_like(dev.quats)
-        cs_w = binding.make_scene(mw, dev.log_scales, qw, dev.opacity_logits, dev.sh,
+        # Fig. 1(a): the world-frame copy of the scene, rendered without
+        # instances; its static rows are copied once (they do not move), its
+        # dynamic rows (means, quaternions, rotated SH) rewritten every step
+        mw = dev.means.clone()
+        qw = dev.quats.clone()
+        shw = dev.sh.clone()
+        cs_w = binding.make_scene(mw, dev.log_scales, qw, dev.opacity_logits, shw,
                                   torch.tensor([0, n], dtype=torch.int64, device=dev_name),
                                   dev.sh_degree)
         no_q = torch.zeros((0, 4), device=dev_name)
@@ -377,10 +389,13 @@ def run_ours(args, rank, world, local):
             # the loss and every gradient element are written by the library
             # (L1 loss and the overwrite mode of the backward): no zero fills
             if args.conventional:
-                binding.to_world(cs, binding.make_poses(iq_, it_), mw, qw)
+                poses_ = binding.make_poses(iq_, it_)
+                binding.to_world(cs, poses_, mw, qw, shw)
                 r.forward(dev, no_q, no_t, cams, t, vis, life, lod, bg, out=out, c_scene=cs_w)
                 binding.l1_loss(out, tgt, dL, loss)
                 r.backward(dev, no_q, no_t, bg, dL, grads, c_scene=cs_w, overwrite=True)
+                # the world-frame adjoints back to the object frame and the poses
+                r.ws.to_world_bwd(cs, poses_, grads)
                 return
             r.forward(dev, iq_, it_, cams, t, vis, life, lod, bg, out=out, c_scene=cs)
             binding.l1_loss(out, tgt, dL, loss)
@@ -416,6 +431,24 @@ def run_ours(args, rank, world, local):
             ktimes.setdefault(name, []).append(ms)
     r.ws.set_timing(False)
     del graph_k
+    if args.conventional:
+        # the world transform and its backward are not kernels of the
+        # workspace's timing hook: timed eagerly here, L2 flushed before each
+        poses_ = binding.make_poses(iq, it)
+        for name, fn in (("to_world", lambda: binding.to_world(cs, poses_, mw, qw, shw)),
+                         ("to_world_bwd", lambda: r.ws.to_world_bwd(cs, poses_, grads))):
+            evs = []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(float(i))
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record()
+                fn()
+                b_.record()
+                evs.append((a_, b_))
+            torch.cuda.synchronize()
+            ktimes[name] = [a_.elapsed_time(b_) for a_, b_ in evs[args.warmup:]]
+        step()                                        # the gradients as one step leaves them
+        torch.cuda.synchronize()
 
     # the timed steps: the step as a user captures it
     graph = r.capture(step)
@@ -496,8 +529,9 @@ def run_ours(args, rank, world, local):
                 roof.update(fused_zeroing_bytes=table[dom]["zero_bytes"],
                             frac_alu_plus_hbm=table[dom]["frac_alu_plus_hbm"])
     # the timed kernels, plus untimed ones of ours: the L1 loss and the zeroing
-    # of its output and, for the conventional pipeline, the world transform
-    launches_per_step = len(kmean) + 2 + (1 if args.conventional else 0)
+    # of its output and, for the conventional pipeline, the world transform and
+    # its backward (two launches)
+    launches_per_step = len(kmean) + 2 + (3 if args.conventional else 0)
 
     # --- plain per-view comparator: the same library, one camera per call, eager
     plain = None
@@ -660,9 +694,10 @@ def run_ours(args, rank, world, local):
                        "sh_degree": scene.sh_degree, "lod_px": lod, "lod": lod_cfg,
                        "temporal_selection": not args.no_temporal,
                        **({"pipeline": "conventional (Fig. 1(a)): dynamic Gaussians moved to the world "
-                                       "frame every step, rendered without instances; gradients "
-                                       "stop at the world-frame parameters (the transform's "
-                                       "backward is not run)"} if args.conventional else {}),
+                                       "frame every step (means, quaternions, SH rotated), rendered "
+                                       "without instances, every Gaussian selected, no LOD; the "
+                                       "backward maps the world-frame adjoints back to the object "
+                                       "frame and the poses"} if args.conventional else {}),
                        "l2": "flushed (512 MiB write) between timed steps, outside the timed events",
                        "graph": "whole step captured as one CUDA graph",
                        "parallelism": f"replicas x{world}, one timestep per rank, no collective"},
@@ -676,6 +711,104 @@ def run_ours(args, rank, world, local):
             "launch_shapes": launch_shapes(),
         }
         print(json.dumps(line), flush=True)
+
+
+def run_train(args, rank, world, local):
+    """Optimisation steps of the training configuration: the 2 km corridor
+    (16M static Gaussians, 120 instances, SH3) seen by the 7-camera rig,
+    each step one timestep (cycling over the sequence) through
+    train.Trainer.step: the batched forward, the L1 loss against a synthetic
+    target, the backward (overwrite mode) to every parameter and to the
+    timestep's poses, and fused Adam on both (gated on the device status, no
+    per-step host synchronisation). The visibility record is the first
+    epoch's (Eq. 5 over every timestep, then Eq. 6). Reports views/s of whole
+    steps, the Adam share, and the peak device memory."""
+    import torch
+    from paper_2503_08217_gb300 import binding, build, train
+    from paper_2503_08217_gb300.render import DeviceScene, pixel_count
+
+    build.build()
+    binding.load()
+    torch.cuda.set_device(local)
+    dev_name = f"cuda:{local}"
+    torch.cuda.reset_peak_memory_stats(dev_name)
+    scene, lod, desc = make_workload("train", args.seed)
+    n, K = scene.n, scene.n_inst
+    dev = DeviceScene.from_host(scene, dev_name)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev_name)   # noqa: E731
+    vis = torch.empty((n, 2), device=dev_name)
+    life = torch.empty((n, 2), device=dev_name)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
+    state = train.TrainState.initial(dev, f(scene.inst_quat), f(scene.inst_trans), vis, life,
+                                     {"mode": "threshold", "r": lod})
+    max_splats = max(4096, int(n * 3))
+    tr = train.Trainer(state, scene.cams, scene.times, lr=1e-4, pose_lr=1e-5, max_splats=max_splats,
+                       max_duplicates=min(2**31 - 1, 6 * max_splats))
+    # first epoch: Eq. 5 over every timestep with every window open, then Eq. 6
+    all_vis = vis.clone()
+    cs = dev.c_scene()
+    for kk in range(scene.n_steps):
+        tr.renderer.ws.project(cs, binding.make_poses(state.inst_quat[kk], state.inst_trans[kk]),
+                               scene.cams[kk], float(scene.times[kk]), all_vis, life, lod)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    del all_vis
+    torch.cuda.synchronize()
+    tr.renderer.counts()
+    P = pixel_count(scene.cams[0])
+    gen = torch.Generator(device=dev_name)
+    gen.manual_seed(99)
+    targets = [torch.rand(3 * P, device=dev_name, generator=gen) for _ in range(4)]
+    order = [(i * 37) % scene.n_steps for i in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        tr.step(order[i], targets[i % 4], check=False)
+    tr.check()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record()
+        for i in range(args.warmup, args.warmup + args.steps):
+            tr.step(order[i], targets[i % 4], check=False)
+        e1.record()
+        torch.cuda.synchronize()
+    tr.check()                                    # raises if any step latched a failure
+    ms = e0.elapsed_time(e1) / args.steps
+    # the optimiser's share: the two Adam launches of a step, timed alone
+    s_ = tr.state
+    k = order[-1]
+    g = [tr.grads[nm] for nm in train.PARAM_NAMES]
+    ae = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    saved = [x.clone() for x in s_.scene.params()]
+    for j in range(5):
+        ae[j][0].record()
+        binding.adam_step(s_.scene.params(), g, s_.exp_avg, s_.exp_avg_sq, 1e-12, s_.adam_steps + 1)
+        ae[j][1].record()
+    torch.cuda.synchronize()
+    for x, y in zip(s_.scene.params(), saved):
+        x.copy_(y)
+    del saved
+    adam_ms = float(np.mean([a.elapsed_time(b) for a, b in ae]))
+    n_par = sum(x.numel() for x in s_.scene.params())
+    peak = torch.cuda.max_memory_allocated(dev_name) + tr.renderer.ws.nbytes
+    views = len(scene.cams[0])
+    if rank == 0:
+        print(json.dumps({
+            "metric": "training steps (fwd+bwd+Adam) views/s, peak HBM", "value": round(views / (ms / 1e3), 3),
+            "unit": "views/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"train: {desc}", "gaussians": n, "instances": K, "cameras": views,
+                       "pixels_per_view_batch": P, "timesteps": scene.n_steps, "lod_px": lod,
+                       "step": "train.Trainer.step: forward, L1, backward (overwrite), Adam on the "
+                               "Gaussians and on the timestep's poses; timesteps cycled; no host sync",
+                       "l2": "not flushed: the step's inputs (2.2 GB of parameters, moments and "
+                             "gradients) exceed L2"},
+            "adam": {"ms": round(adam_ms, 4), "share": round(adam_ms / ms, 3), "parameters": int(n_par),
+                     "gbs": round(28 * n_par / (adam_ms / 1e3) / 1e9, 1)},
+            "peak_hbm_gb": round(peak / 1e9, 3),
+            "peak_hbm_how": "torch.cuda.max_memory_allocated (scene, gradients, moments, record, targets) "
+                            "+ s3r_workspace_bytes",
+            "clocks": clocks.summary(),
+        }), flush=True)
 
 
 def cpu_oracle_sample(scene, k, lod, vis_np):
@@ -836,6 +969,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, rank, world, local)
+        return
+    if args.workload == "train":
+        run_train(args, rank, world, local)
         return
     if world > 1:
         import torch

@@ -274,16 +274,32 @@ const uint32_t* s3r_device_status(const s3r_workspace* ws);
  * instance-specific projection of Sec. 3.3 replaces: every Gaussian of a
  * dynamic instance k is moved to the world frame by its pose at time t,
  *   mu_w = R(q_k/|q_k|) mu + t_k,   q_w = (q_k/|q_k|) (x) (q/|q|)
- * (Hamilton product, so R(q_w) = R(q_k) R(q)); static Gaussians are copied
- * with their quaternion normalised. scene and poses as for s3r_project (only
- * means, quats and inst_offsets are read); means_out [n,3] (4-B aligned) and
- * quats_out [n,4] (16-B aligned) are caller-owned device arrays written on
- * `stream`. A scene of them with no instances (inst_offsets {0, n}) renders
- * the same geometry through s3r_project, with the SH of dynamic Gaussians
- * evaluated on the world-frame view direction. S3R_ERR_INVALID on NULL or
+ * (Hamilton product, so R(q_w) = R(q_k) R(q)), and with sh_out its SH
+ * coefficients are rotated so that the world-frame view direction gives the
+ * colour the object-frame direction gives: band l (1 <= l <= sh_degree)
+ * becomes D_l^T c_l per channel, Y_l(R_k^T d) = D_l Y_l(d) (D_l from an exact
+ * 26-point Lebedev quadrature of the rotated basis against the basis); band
+ * 0 is copied. scene and poses as for s3r_project. Only the rows of the
+ * dynamic Gaussians ([inst_offsets[1], n)) of means_out [n,3] (4-B aligned),
+ * quats_out [n,4] (16-B aligned) and sh_out [n,K,3] (or NULL) are written:
+ * static Gaussians do not move, so the caller fills their rows once (a copy).
+ * A scene of these arrays with no instances (inst_offsets {0, n}) then
+ * renders the same image through s3r_project. S3R_ERR_INVALID on NULL or
  * misaligned arrays, nothing launched. */
 s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* means_out,
-                        float* quats_out, void* stream);
+                        float* quats_out, float* sh_out, void* stream);
+
+/* Backward of s3r_to_world, in place: on entry grads->means, grads->quats and
+ * grads->sh (each may be NULL) hold, at the rows of dynamic Gaussians, the
+ * adjoints of the world-frame means, quaternions and rotated SH (as the
+ * backward of the world-frame render writes them); on return those rows
+ * hold the adjoints of the object-frame parameters (the static rows, whose
+ * transform is the identity, are not touched). grads->inst_quat [n_inst,4]
+ * and grads->inst_trans [n_inst,3] are WRITTEN with the pose adjoints. The
+ * per-instance sums use the workspace (its max_instances bounds n_inst);
+ * calls on one workspace must not overlap on the GPU. */
+s3r_status s3r_to_world_bwd(s3r_workspace* ws, const s3r_scene* scene, const s3r_poses* poses,
+                            const s3r_grads* grads, void* stream);
 
 /* Level of detail (Sec. 3.3 "Adaptive LOD", Eq. 7). In the default
  * S3R_LOD_THRESHOLD mode every in-frustum Gaussian whose projected 2D scale

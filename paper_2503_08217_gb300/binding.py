@@ -31,7 +31,7 @@ EXPORTS = ("s3r_workspace_create", "s3r_workspace_destroy", "s3r_workspace_bytes
            "s3r_kernel_count", "s3r_kernel_name", "s3r_kernel_times", "s3r_select_visible_static",
            "s3r_adam_step", "s3r_set_lod", "s3r_set_counting", "s3r_to_world",
            "s3r_check_wait_timeout", "s3r_set_epoch", "s3r_device_status", "s3r_set_grad_mode",
-           "s3r_ode_param_count", "s3r_ode_poses", "s3r_ode_poses_bwd")
+           "s3r_ode_param_count", "s3r_ode_poses", "s3r_ode_poses_bwd", "s3r_to_world_bwd")
 
 LOD_THRESHOLD = 0
 LOD_STOCHASTIC = 1
@@ -135,7 +135,8 @@ def load(path: str = LIB_PATH):
     L.s3r_adam_step.argtypes = [P(AdamTensor), i32, f32, f32, f32, f32, i32, vp, vp]
     L.s3r_device_status.argtypes = [vp]
     L.s3r_device_status.restype = vp
-    L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp]
+    L.s3r_to_world.argtypes = [P(Scene), P(Poses), vp, vp, vp, vp]
+    L.s3r_to_world_bwd.argtypes = [vp, P(Scene), P(Poses), P(Grads), vp]
     L.s3r_check_wait_timeout.argtypes = [vp, i32, vp]
     L.s3r_set_epoch.argtypes = [vp, ctypes.c_uint32, vp]
     L.s3r_kernel_count.restype = i32
@@ -153,7 +154,7 @@ def load(path: str = LIB_PATH):
                  "s3r_query_counts", "s3r_sync_status", "s3r_l1_loss", "s3r_set_timing",
                  "s3r_kernel_times", "s3r_select_visible_static", "s3r_adam_step", "s3r_set_lod",
                  "s3r_set_counting", "s3r_to_world", "s3r_check_wait_timeout",
-                 "s3r_set_epoch", "s3r_set_grad_mode", "s3r_ode_poses", "s3r_ode_poses_bwd"):
+                 "s3r_set_epoch", "s3r_set_grad_mode", "s3r_ode_poses", "s3r_ode_poses_bwd", "s3r_to_world_bwd"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -306,6 +307,15 @@ class Workspace:
     def sync_status(self, stream=None):
         _check(load().s3r_sync_status(self._h, _stream(stream)))
 
+    def to_world_bwd(self, scene: Scene, poses: Poses, grads: dict, stream=None):
+        """Backward of to_world in place on grads (see s3r_to_world_bwd)."""
+        g = Grads()
+        for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "inst_quat",
+                  "inst_trans"):
+            setattr(g, k, _ptr(grads.get(k)))
+        _check(load().s3r_to_world_bwd(self._h, ctypes.byref(scene), ctypes.byref(poses),
+                                       ctypes.byref(g), _stream(stream)))
+
     def set_grad_mode(self, mode: int):
         """GRAD_ACCUMULATE (default): render_bwd adds to the gradient buffers;
         GRAD_OVERWRITE: it writes every element (zeros where no view kept the
@@ -365,11 +375,12 @@ def select_visible_static(vis_window, t: float, out_idx, out_count, stream=None)
                                             _ptr(out_count), _stream(stream)))
 
 
-def to_world(c_scene, poses, means_out, quats_out, stream=None):
-    """The conventional local-to-world transform (see s3r_to_world): writes
-    the world-frame means [n,3] and unit quaternions [n,4]."""
+def to_world(c_scene, poses, means_out, quats_out, sh_out=None, stream=None):
+    """The conventional local-to-world transform (see s3r_to_world): writes the
+    dynamic rows of the world-frame means [n,3], unit quaternions [n,4] and,
+    with sh_out, rotated SH [n,K,3]; static rows are left as they are."""
     _check(load().s3r_to_world(ctypes.byref(c_scene), ctypes.byref(poses), _ptr(means_out),
-                               _ptr(quats_out), _stream(stream)))
+                               _ptr(quats_out), _ptr(sh_out), _stream(stream)))
 
 
 def adam_step(params, grads, exp_avgs, exp_avg_sqs, lr: float, step: int, beta1: float = 0.9,

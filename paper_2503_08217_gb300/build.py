@@ -28,7 +28,7 @@ LIB = os.path.join(HERE, "libs3r.so")
 ARCH = "103a"
 
 SOURCES = ["s3r_api.cu", "k_compact.cu", "k_project.cu", "k_sort.cu", "k_blend.cu",
-           "k_project_bwd.cu", "k_vis.cu", "k_probe.cu", "k_ode.cu"]
+           "k_project_bwd.cu", "k_vis.cu", "k_probe.cu", "k_ode.cu", "k_world.cu"]
 
 _DEFINE_NAME = re.compile(r"^S3R_[A-Z0-9_]+$")
 

@@ -475,67 +475,4 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   }
 }
 
-namespace {
-
-// The conventional path of Fig. 1(a), the comparator of the instance-matrix
-// projection: every Gaussian of a dynamic instance k is moved to the world
-// frame by its pose, mu_w = R(q_k) mu + t_k and q_w = q_k (x) q/|q| (Hamilton
-// product of unit quaternions, so R(q_w) = R(q_k) R(q)); static Gaussians
-// are copied with their quaternion normalised. One thread per Gaussian; its
-// instance from a binary search of the offsets.
-__global__ void __launch_bounds__(256) k_to_world(int64_t n, const float* __restrict__ means,
-                                                  const float4* __restrict__ quats,
-                                                  const int64_t* __restrict__ inst_off, int n_inst,
-                                                  const float4* __restrict__ pose_q,
-                                                  const float* __restrict__ pose_t,
-                                                  float* __restrict__ out_means,
-                                                  float4* __restrict__ out_quats) {
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n;
-       g += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = n_inst + 1;   // inst_off[lo] <= g < inst_off[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (inst_off[mid] <= g) lo = mid; else hi = mid;
-    }
-    const float m0 = means[3 * g], m1 = means[3 * g + 1], m2 = means[3 * g + 2];
-    const float4 q = quats[g];
-    const float iq = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float w2 = q.x * iq, x2 = q.y * iq, y2 = q.z * iq, z2 = q.w * iq;
-    if (lo == 0) {
-      out_means[3 * g] = m0;
-      out_means[3 * g + 1] = m1;
-      out_means[3 * g + 2] = m2;
-      out_quats[g] = make_float4(w2, x2, y2, z2);
-      continue;
-    }
-    const float4 qp = pose_q[lo - 1];
-    float R[9];
-    quat_to_rot(qp, R);
-    const float* t = pose_t + 3 * (lo - 1);
-    out_means[3 * g] = fmaf(R[0], m0, fmaf(R[1], m1, fmaf(R[2], m2, t[0])));
-    out_means[3 * g + 1] = fmaf(R[3], m0, fmaf(R[4], m1, fmaf(R[5], m2, t[1])));
-    out_means[3 * g + 2] = fmaf(R[6], m0, fmaf(R[7], m1, fmaf(R[8], m2, t[2])));
-    const float ip = rsqrtf(qp.x * qp.x + qp.y * qp.y + qp.z * qp.z + qp.w * qp.w);
-    const float w1 = qp.x * ip, x1 = qp.y * ip, y1 = qp.z * ip, z1 = qp.w * ip;
-    out_quats[g] = make_float4(w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
-                               w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
-                               w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
-                               w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2);
-  }
-}
-
-}  // namespace
-
-cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* means_out,
-                            float* quats_out, int num_sms, cudaStream_t st) {
-  if (sc->n == 0) return cudaSuccess;
-  int64_t blocks = (sc->n + 255) / 256;
-  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
-  k_to_world<<<(unsigned)blocks, 256, 0, st>>>(
-      sc->n, sc->means, reinterpret_cast<const float4*>(sc->quats), sc->inst_offsets, sc->n_inst,
-      reinterpret_cast<const float4*>(poses->quat), poses->trans, means_out,
-      reinterpret_cast<float4*>(quats_out));
-  return cudaGetLastError();
-}
-
 }  // namespace s3r

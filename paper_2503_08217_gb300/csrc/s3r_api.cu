@@ -76,7 +76,7 @@ void free_all(s3r_workspace* ws) {
                   ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
-                  ws->sp_grad, ws->pose_dM, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_class_cnt, ws->tile_class_list, ws->contrib};
+                  ws->sp_grad, ws->pose_dM, ws->world_acc, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_class_cnt, ws->tile_class_list, ws->contrib};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -211,6 +211,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->n_contrib, cap->max_pixels);
   S3R_ALLOC(ws->sp_grad, 12 * S);
   S3R_ALLOC(ws->pose_dM, (int64_t)cap->max_views * nk * 12);
+  S3R_ALLOC(ws->world_acc, (int64_t)nk * world_acc_floats());
   S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
   S3R_ALLOC(ws->dup_excl, S + 1);
   S3R_ALLOC(ws->dup_meta, 8 * S);
@@ -232,6 +233,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   }
   if ((e = cudaMemset(ws->ctr, 0, sizeof(uint32_t) * kCtrCount)) != cudaSuccess ||
       (e = cudaMemset(ws->pose_dM, 0, sizeof(float) * 12 * (size_t)cap->max_views * nk)) != cudaSuccess ||
+      (e = cudaMemset(ws->world_acc, 0, sizeof(float) * (size_t)nk * world_acc_floats())) != cudaSuccess ||
       (e = cudaMemset(ws->lookback, 0, sizeof(unsigned long long) * ws->lookback_words)) !=
           cudaSuccess ||
       (e = cudaDeviceSynchronize()) != cudaSuccess) {
@@ -481,24 +483,45 @@ s3r_status s3r_adam_step(const s3r_adam_tensor* tensors, int32_t count, float lr
 }
 
 s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* means_out,
-                        float* quats_out, void* stream) {
+                        float* quats_out, float* sh_out, void* stream) {
   if (!scene) return fail(S3R_ERR_INVALID, "NULL scene");
   if (scene->n < 0 || scene->n > 0xffffffffLL) return fail(S3R_ERR_INVALID, "n outside [0, 2^32)");
   if (scene->n_inst < 0) return fail(S3R_ERR_INVALID, "n_inst < 0");
+  if (scene->sh_degree < 0 || scene->sh_degree > 3)
+    return fail(S3R_ERR_INVALID, "sh_degree %d outside [0, 3]", scene->sh_degree);
   if (!scene->inst_offsets || !aligned(scene->inst_offsets, 8))
     return fail(S3R_ERR_INVALID, "inst_offsets must be an 8-byte aligned array");
-  if (scene->n == 0) return S3R_OK;
+  if (scene->n == 0 || scene->n_inst == 0) return S3R_OK;
   if (!scene->means || !scene->quats || !means_out || !quats_out)
     return fail(S3R_ERR_INVALID, "means, quats and both outputs are required");
   if (!aligned(scene->means, 4) || !aligned(means_out, 4) || !aligned(scene->quats, 16) ||
       !aligned(quats_out, 16))
     return fail(S3R_ERR_INVALID, "means 4-byte and quaternions 16-byte aligned required");
+  if (sh_out && (!scene->sh || !aligned(sh_out, 4)))
+    return fail(S3R_ERR_INVALID, "sh_out needs the scene's SH");
   s3r_status st = check_poses(scene, poses);
   if (st != S3R_OK) return st;
-  const s3r_poses none = {nullptr, nullptr};
-  cudaError_t e = launch_to_world(scene, poses ? poses : &none, means_out, quats_out, sm_count(),
+  cudaError_t e = launch_to_world(scene, poses, means_out, quats_out, sh_out, scene->n, sm_count(),
                                   (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "to_world");
+  return S3R_OK;
+}
+
+s3r_status s3r_to_world_bwd(s3r_workspace* ws, const s3r_scene* scene, const s3r_poses* poses,
+                            const s3r_grads* grads, void* stream) {
+  if (!ws) return fail(S3R_ERR_INVALID, "workspace is NULL");
+  s3r_status st = check_scene(ws, scene);
+  if (st != S3R_OK) return st;
+  if ((st = check_poses(scene, poses)) != S3R_OK) return st;
+  if (!grads) return fail(S3R_ERR_INVALID, "grads is NULL");
+  if ((grads->quats && !aligned(grads->quats, 16)) || (grads->means && !aligned(grads->means, 4)) ||
+      (grads->sh && !aligned(grads->sh, 4)))
+    return fail(S3R_ERR_INVALID, "quaternion gradients must be 16-byte aligned");
+  if (scene->n == 0 || scene->n_inst == 0) return S3R_OK;
+  DeviceGuard g(ws->device);
+  cudaError_t e = launch_to_world_bwd(scene, poses, grads, ws->world_acc, scene->n, ws->num_sms,
+                                      (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "to_world backward");
   return S3R_OK;
 }
 

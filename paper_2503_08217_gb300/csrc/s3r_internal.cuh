@@ -147,6 +147,7 @@ struct s3r_workspace {
   float* sp_grad;           // [S*12] per-splat 2D adjoints summed by the blend backward
   int sp_grad_clean;        // host: the last render_fwd zeroed sp_grad and no backward used it since
   float* pose_dM;           // [views*(inst+1)*12], zero between backward calls
+  float* world_acc;         // [(inst+1) * world_acc_floats()] pose sums of s3r_to_world_bwd, zero between calls
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
   uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
@@ -212,7 +213,11 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
                            float t, float* life, float lod, cudaStream_t st);
 cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st);
 cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* means_out,
-                            float* quats_out, int num_sms, cudaStream_t st);
+                            float* quats_out, float* sh_out, int64_t n_dynamic, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_to_world_bwd(const s3r_scene* sc, const s3r_poses* poses, const s3r_grads* g,
+                                float* acc, int64_t n_dynamic, int num_sms, cudaStream_t st);
+int world_acc_floats();
 cudaError_t launch_render_fwd(s3r_workspace* ws, const float* bg, float* out, cudaStream_t st);
 cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* dL,
                               const s3r_grads* grads, cudaStream_t st);

@@ -209,6 +209,70 @@ __device__ __forceinline__ void sh_basis(float dx, float dy, float dz, float Y[1
 
 __host__ __device__ constexpr int sh_count(int deg) { return (deg + 1) * (deg + 1); }
 
+// d/d(direction) of sum_k w_k Y_k(d) for the real SH basis of sh_basis<DEG>.
+template <int DEG>
+__device__ __forceinline__ void sh_dir_grad(float x, float y, float z, const float w[16],
+                                            float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if (DEG >= 1) {
+    const float k1 = 0.48860251190291992f;
+    g[1] -= k1 * w[1];
+    g[2] += k1 * w[2];
+    g[0] -= k1 * w[3];
+  }
+  if (DEG >= 2) {
+    const float k2a = 1.0925484305920792f, k2c = 0.31539156525252005f, k2e = 0.54627421529603959f;
+    g[0] += k2a * y * w[4];                    g[1] += k2a * x * w[4];
+    g[1] -= k2a * z * w[5];                    g[2] -= k2a * y * w[5];
+    g[0] -= 2.f * k2c * x * w[6];              g[1] -= 2.f * k2c * y * w[6];
+    g[2] += 4.f * k2c * z * w[6];
+    g[0] -= k2a * z * w[7];                    g[2] -= k2a * x * w[7];
+    g[0] += 2.f * k2e * x * w[8];              g[1] -= 2.f * k2e * y * w[8];
+    if (DEG >= 3) {
+      const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f,
+                  k3c = 0.45704579946446572f, k3d = 0.37317633259011546f,
+                  k3e = 1.4453057213202769f;
+      const float xx = x * x, yy = y * y, zz = z * z;
+      g[0] -= 6.f * k3a * x * y * w[9];
+      g[1] -= k3a * (3.f * xx - 3.f * yy) * w[9];
+      g[0] += k3b * y * z * w[10]; g[1] += k3b * x * z * w[10]; g[2] += k3b * x * y * w[10];
+      g[0] += 2.f * k3c * x * y * w[11];
+      g[1] -= k3c * (4.f * zz - xx - 3.f * yy) * w[11];
+      g[2] -= 8.f * k3c * y * z * w[11];
+      g[0] -= 6.f * k3d * x * z * w[12];
+      g[1] -= 6.f * k3d * y * z * w[12];
+      g[2] += k3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      g[0] -= k3c * (4.f * zz - 3.f * xx - yy) * w[13];
+      g[1] += 2.f * k3c * x * y * w[13];
+      g[2] -= 8.f * k3c * x * z * w[13];
+      g[0] += 2.f * k3e * x * z * w[14];
+      g[1] -= 2.f * k3e * y * z * w[14];
+      g[2] += k3e * (xx - yy) * w[14];
+      g[0] -= k3a * (3.f * xx - 3.f * yy) * w[15];
+      g[1] += 6.f * k3a * x * y * w[15];
+    }
+  }
+}
+
+// Adjoint of the raw quaternion q (w, x, y, z) given dL/dR for R(q/|q|).
+__device__ __forceinline__ float4 quat_backward(float4 q, const float dR[9]) {
+  const float n2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  const float inv = rsqrtf(n2);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  // partials of the nine entries of R w.r.t. the unit quaternion
+  float gw = 2.f * (x * (dR[7] - dR[5]) + y * (dR[2] - dR[6]) + z * (dR[3] - dR[1]));
+  float gx = 2.f * (y * (dR[1] + dR[3]) + z * (dR[2] + dR[6]) + w * (dR[7] - dR[5])) -
+             4.f * x * (dR[4] + dR[8]);
+  float gy = 2.f * (x * (dR[1] + dR[3]) + z * (dR[5] + dR[7]) + w * (dR[2] - dR[6])) -
+             4.f * y * (dR[0] + dR[8]);
+  float gz = 2.f * (x * (dR[2] + dR[6]) + y * (dR[5] + dR[7]) + w * (dR[3] - dR[1])) -
+             4.f * z * (dR[0] + dR[4]);
+  const float dot = gw * w + gx * x + gy * y + gz * z;
+  return make_float4((gw - w * dot) * inv, (gx - x * dot) * inv, (gy - y * dot) * inv,
+                     (gz - z * dot) * inv);
+}
+
+
 // ---- stochastic LOD (Eq. 7) ---------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC 2011): ten rounds of two
 // 32x32 -> 64-bit products by fixed odd multipliers, high halves XORed with

@@ -80,10 +80,17 @@ def test_to_world_rejects_bad_arguments_without_a_gpu():
     sc.n = 10
     sc.n_inst = 1
     poses = binding.Poses()
-    assert L.s3r_to_world(None, ctypes.byref(poses), None, None, None) == 1     # NULL scene
-    assert L.s3r_to_world(ctypes.byref(sc), ctypes.byref(poses), None, None, None) == 1   # no offsets
+    assert L.s3r_to_world(None, ctypes.byref(poses), None, None, None, None) == 1     # NULL scene
+    assert L.s3r_to_world(ctypes.byref(sc), ctypes.byref(poses), None, None, None, None) == 1   # no offsets
     assert b"inst_offsets" in L.s3r_last_error()
     offs = (ctypes.c_int64 * 3)(0, 5, 10)
     sc.inst_offsets = ctypes.cast(offs, ctypes.c_void_p)
-    assert L.s3r_to_world(ctypes.byref(sc), ctypes.byref(poses), None, None, None) == 1   # no arrays
+    assert L.s3r_to_world(ctypes.byref(sc), ctypes.byref(poses), None, None, None, None) == 1   # no arrays
     assert b"required" in L.s3r_last_error()
+
+
+def test_to_world_bwd_rejects_a_null_workspace_without_a_gpu():
+    from paper_2503_08217_gb300 import binding
+    L = binding.load()
+    assert L.s3r_to_world_bwd(None, None, None, None, None) == 1
+    assert b"workspace" in L.s3r_last_error()

@@ -250,3 +250,197 @@ def test_rig_full_size_sampled():
                        pixel_blend_flagged=f"{flagged}/{48 * len(cams)}",
                        sorted_pairs=int(res["sorted_tiles"].size), rectangle_pairs=n_rect,
                        left_out_checked_unreachable=f"{n_checked}/{n_out}")
+
+
+def test_corridor_x4_sampled():
+    """The largest scale of the scene-size sweep (Fig. 4 analogue): the large
+    corridor stretched four times at constant density (36M Gaussians, 320
+    instances, 6 km), one 1920x1280 camera at the middle timestep, every
+    Gaussian selected, LOD 1 px: masks and splat records of 3000 sampled
+    Gaussians, 24 sampled pixels, and the gradient of a loss on those pixels,
+    against the FP64 oracle. Index widths: the splat and pair counts of the
+    sweep's largest scene."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding, build
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer
+    build.build()
+    binding.load()
+    scene = scenegen.generate("large", seed=0, length_scale=4.0)
+    n = scene.n
+    assert n > 35_000_000
+    k = scene.n_steps // 2
+    cams = scene.cams[k]
+    cam = cams[0]
+    lod = 1.0
+    rng = np.random.default_rng(8)
+    vis, _ = oracle.vis_reset(n)
+    sel = np.arange(n)
+    rec = oracle.project(scene, sel, k, cam, lod)
+    bad = gpu_helpers.bad_pixels(cam, rec, np.zeros((cam.height, cam.width), bool))
+    py = rng.integers(0, cam.height, 400)
+    px = rng.integers(0, cam.width, 400)
+    keep = ~bad[py, px]
+    pix = np.unique(np.stack([py[keep], px[keep]], 1), axis=0)
+    pix = pix[rng.permutation(pix.shape[0])][:48]
+    sp = oracle.select_splats(rec)
+    o = oracle.render_pixels(sp, pix[:, 1], pix[:, 0])
+    flagged = int(o["flag"].sum())
+    pix = pix[~o["flag"]][:24]
+    assert pix.shape[0] == 24
+    d = np.zeros((3, cam.height, cam.width))
+    d[:, pix[:, 0], pix[:, 1]] = rng.standard_normal((3, pix.shape[0]))
+
+    max_splats = n
+    r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
+    dev = DeviceScene.from_host(scene)
+    res = gpu_helpers.gpu_step(scene, k, cams, vis, lod=lod, dL=[d], renderer=r, dev=dev)
+    assert res["counts"]["n_selected"] == n and res["counts"]["n_splats"] > 500_000
+
+    gids = gpu_helpers.splat_gids(res)
+    # half of the samples from everywhere (most are outside the one camera's
+    # frustum), half from the Gaussians the oracle keeps
+    picks = np.unique(np.concatenate([rng.choice(n, 1500, replace=False),
+                                      rng.choice(np.nonzero(rec["kept"])[0], 1500, replace=False)]))
+    checked = near_picks = 0
+    for j in picks:
+        if rec["near"][j]:
+            near_picks += 1
+            continue
+        assert int(res["frustum_mask"][j]) == int(rec["infrustum"][j])
+        assert int(res["keep_mask"][j]) == int(rec["kept"][j])
+        if rec["kept"][j]:
+            s = int(res["splat_start"][j])
+            assert gids[s] == j
+            u, vv = rec["uv"][j]
+            assert abs(res["xy"][s, 0] - u) <= 1e-5 * abs(u) + 2e-4
+            assert abs(res["xy"][s, 1] - vv) <= 1e-5 * abs(vv) + 2e-4
+            np.testing.assert_allclose(res["conic_o"][s, :3], rec["conic"][j], rtol=1e-3,
+                                       atol=1e-5 * np.abs(rec["conic"][j]).max())
+            np.testing.assert_allclose(res["rgb_d"][s, :3], rec["rgb"][j], atol=2e-5)
+            np.testing.assert_array_equal(res["rect"][s], rec["rect"][j])
+            checked += 1
+    assert checked > 1000 and near_picks <= 3e-3 * picks.size
+
+    got = res["images"][0][:, pix[:, 0], pix[:, 1]].T
+    o = oracle.render_pixels(sp, pix[:, 1], pix[:, 0])
+    assert np.abs(got - o["rgb"]).max() <= 1e-4
+    grads = oracle.zero_grads(scene)
+    gs = oracle.render_backward_pixels(sp, pix[:, 1], pix[:, 0], d[:, pix[:, 0], pix[:, 1]].T.copy())
+    touched = np.nonzero((np.abs(gs["uv"]).sum(1) + np.abs(gs["rgb"]).sum(1) + np.abs(gs["opacity"])) > 0)[0]
+    kept_idx = np.nonzero(rec["kept"])[0][touched]
+    sub = {key: gs[key][touched] for key in ("uv", "conic", "opacity", "rgb")}
+    oracle.project_backward(scene, sel[kept_idx], k, cam, lod, sub, grads)
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        a = res["grads"][name].reshape(-1)
+        b = grads[name].reshape(-1)
+        assert (np.abs(b) > 0).sum() > 50, name
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 1e-3, (name, rel)
+    gpu_helpers.report("corridor x4 (36M)", gaussians=n, splats=res["counts"]["n_splats"],
+                       pairs=res["counts"]["n_duplicates"],
+                       gaussian_sample_near_threshold=f"{near_picks}/{picks.size}",
+                       pixel_blend_flagged=f"{flagged}/48")
+
+
+
+def test_training_corridor_rig_sampled():
+    """The training configuration's scene (16M static Gaussians over 2 km,
+    120 instances, SH3) seen by the 7-camera rig in one batched call, every
+    Gaussian selected, LOD 1 px: masks and splat records of sampled
+    Gaussians in every view, 16 sampled pixels of each camera, and the
+    gradient of a loss on them, against the FP64 oracle. The oracle keeps
+    one view's full records at a time; the sampled Gaussians' records are
+    projected again on their own (a record depends only on its Gaussian)."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding, build
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer
+    build.build()
+    binding.load()
+    scene = scenegen.generate("train", seed=0)
+    n = scene.n
+    assert n > 16_000_000
+    k = scene.n_steps // 2
+    cams = scene.cams[k]
+    V = len(cams)
+    lod = 1.0
+    rng = np.random.default_rng(21)
+    vis, _ = oracle.vis_reset(n)
+    sel = np.arange(n)
+    kept = np.zeros((V, n), bool)
+    splats, samples, dL, flagged = [], [], [], 0
+    for v, cam in enumerate(cams):
+        rec = oracle.project(scene, sel, k, cam, lod, view=v)
+        kept[v] = rec["kept"]
+        bad = gpu_helpers.bad_pixels(cam, rec, np.zeros((cam.height, cam.width), bool))
+        sp = oracle.select_splats(rec)
+        del rec
+        py = rng.integers(0, cam.height, 300)
+        px = rng.integers(0, cam.width, 300)
+        keep = ~bad[py, px]
+        pix = np.unique(np.stack([py[keep], px[keep]], 1), axis=0)
+        pix = pix[rng.permutation(pix.shape[0])][:32]
+        o = oracle.render_pixels(sp, pix[:, 1], pix[:, 0])
+        flagged += int(o["flag"].sum())
+        pix = pix[~o["flag"]][:16]
+        assert pix.shape[0] == 16
+        splats.append(sp)
+        samples.append((pix[:, 1], pix[:, 0]))
+        d = np.zeros((3, cam.height, cam.width))
+        d[:, pix[:, 0], pix[:, 1]] = rng.standard_normal((3, pix.shape[0]))
+        dL.append(d)
+
+    max_splats = int(n * 3)
+    r = Renderer(n, scene.n_inst, cams, max_splats=max_splats, max_duplicates=min(2**31 - 1, 6 * max_splats))
+    dev = DeviceScene.from_host(scene)
+    res = gpu_helpers.gpu_step(scene, k, cams, vis, lod=lod, dL=dL, renderer=r, dev=dev)
+    assert res["counts"]["n_selected"] == n
+
+    gids = gpu_helpers.splat_gids(res)
+    picks = np.unique(np.concatenate([rng.choice(n, 1000, replace=False),
+                                      rng.choice(np.nonzero(kept.any(0))[0], 2000, replace=False)]))
+    precs = [oracle.project(scene, picks, k, cam, lod, view=v) for v, cam in enumerate(cams)]
+    for v in range(V):
+        assert (precs[v]["kept"] == kept[v, picks]).all()
+    checked = near_picks = 0
+    for i, j in enumerate(picks):
+        if any(pr["near"][i] for pr in precs):
+            near_picks += 1
+            continue
+        fm = sum(int(precs[v]["infrustum"][i]) << v for v in range(V))
+        km = sum(int(precs[v]["kept"][i]) << v for v in range(V))
+        assert int(res["frustum_mask"][j]) == fm and int(res["keep_mask"][j]) == km
+        s = int(res["splat_start"][j])
+        for v in range(V):
+            if not (km >> v) & 1:
+                continue
+            pr = precs[v]
+            assert gids[s] == j and res["view"][s] == v
+            u, vv = pr["uv"][i]
+            assert abs(res["xy"][s, 0] - u) <= 1e-5 * abs(u) + 2e-4
+            assert abs(res["xy"][s, 1] - vv) <= 1e-5 * abs(vv) + 2e-4
+            np.testing.assert_allclose(res["rgb_d"][s, :3], pr["rgb"][i], atol=2e-5)
+            np.testing.assert_array_equal(res["rect"][s], pr["rect"][i])
+            s += 1
+            checked += 1
+    assert checked > 1000 and near_picks <= 3e-3 * V * picks.size
+
+    grads = oracle.zero_grads(scene)
+    for v, cam in enumerate(cams):
+        sp = splats[v]
+        px, py = samples[v]
+        o = oracle.render_pixels(sp, px, py)
+        assert np.abs(res["images"][v][:, py, px].T - o["rgb"]).max() <= 1e-4
+        gs = oracle.render_backward_pixels(sp, px, py, dL[v][:, py, px].T.copy())
+        touched = np.nonzero((np.abs(gs["uv"]).sum(1) + np.abs(gs["rgb"]).sum(1) + np.abs(gs["opacity"])) > 0)[0]
+        sub = {key: gs[key][touched] for key in ("uv", "conic", "opacity", "rgb")}
+        oracle.project_backward(scene, sp["gid"][touched], k, cam, lod, sub, grads)
+    for name in ("means", "log_scales", "quats", "opacity_logits", "sh"):
+        a = res["grads"][name].reshape(-1)
+        b = grads[name].reshape(-1)
+        assert (np.abs(b) > 0).sum() > 50, name
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 1e-3, (name, rel)
+    gpu_helpers.report("training corridor rig (16M+)", gaussians=n, splats=res["counts"]["n_splats"],
+                       pairs=res["counts"]["n_duplicates"],
+                       gaussian_sample_near_threshold=f"{near_picks}/{picks.size}",
+                       pixel_blend_flagged=f"{flagged}/{32 * V}")

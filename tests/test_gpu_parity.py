@@ -617,8 +617,8 @@ def test_conventional_world_transform_matches_oracle(built, tiny, tiny_vis):
     dev = DeviceScene.from_host(tiny)
     iq = torch.from_numpy(np.ascontiguousarray(tiny.inst_quat[step], np.float32)).cuda()
     it = torch.from_numpy(np.ascontiguousarray(tiny.inst_trans[step], np.float32)).cuda()
-    mw = torch.empty_like(dev.means)
-    qw = torch.empty_like(dev.quats)
+    mw = dev.means.clone()          # static rows: the caller's copy (they do not move)
+    qw = dev.quats.clone()
     binding.to_world(dev.c_scene(), binding.make_poses(iq, it), mw, qw)
     torch.cuda.synchronize()
     world = copy.deepcopy(tiny)
@@ -660,6 +660,75 @@ def test_conventional_world_transform_matches_oracle(built, tiny, tiny_vis):
         assert bad.mean() <= MAX_EXCLUDED_FRACTION
         assert rec["near"].sum() <= MAX_NEAR_FRACTION * sel.size
     assert checked > 1000
+
+
+def test_conventional_pipeline_sh3_equals_the_streamlined_one(built):
+    """Fig. 1(a) against Fig. 1(b) at SH degree 3 with moving instances: the
+    world transform with rotated SH coefficients, then the renderer on the
+    world-frame scene without instances, gives the image the oracle's
+    instance-specific path gives; the renderer's backward on the world-frame
+    scene followed by the transform's backward gives the gradients of the
+    object-frame parameters and of the poses that the oracle's
+    instance-specific backward gives (the two pipelines compute the same
+    function of the same parameters)."""
+    import gpu_helpers
+    from paper_2503_08217_gb300 import binding
+    from paper_2503_08217_gb300.render import DeviceScene
+    sc = _rig_crop()
+    # instances yawed, so that their SH rotation is not the identity
+    yaw = np.array([0.4, -0.9, 1.3, 2.2])
+    sc.inst_quat[:, :, 0] = np.cos(yaw / 2)[None, :]
+    sc.inst_quat[:, :, 2] = np.sin(yaw / 2)[None, :]
+    sc.inst_quat[:, :, 1] = 0.0
+    sc.inst_quat[:, :, 3] = 0.0
+    vis, _ = gpu_helpers.sweep_visibility(sc, lod=1.0)
+    step = 6
+    cams = sc.cams[step]
+    bg = (0.2, 0.1, 0.3)
+    f = _oracle_views(sc, step, cams, vis, 1.0, bg=bg)
+    dyn = sc.inst_offsets[1]
+    kept_dyn = sum(int(v["rec"]["kept"][np.searchsorted(f["sel"], dyn):].sum()) for v in f["views"])
+    assert kept_dyn > 100
+
+    dev = DeviceScene.from_host(sc)
+    iq = torch.from_numpy(np.ascontiguousarray(sc.inst_quat[step])).cuda()
+    it = torch.from_numpy(np.ascontiguousarray(sc.inst_trans[step])).cuda()
+    poses = binding.make_poses(iq, it)
+    mw, qw, shw = dev.means.clone(), dev.quats.clone(), dev.sh.clone()
+    binding.to_world(dev.c_scene(), poses, mw, qw, shw)
+    world = DeviceScene(means=mw, log_scales=dev.log_scales, quats=qw, opacity_logits=dev.opacity_logits,
+                        sh=shw, inst_offsets=torch.tensor([0, sc.n], dtype=torch.int64, device="cuda"),
+                        sh_degree=sc.sh_degree)
+    r = gpu_helpers.Renderer(sc.n, sc.n_inst, cams)
+    bg_t = torch.tensor(bg, dtype=torch.float32, device="cuda")
+    no_q, no_t = torch.zeros((0, 4), device="cuda"), torch.zeros((0, 3), device="cuda")
+    out = r.forward(world, no_q, no_t, cams, float(sc.times[step]), torch.from_numpy(vis).cuda(), None,
+                    1.0, bg_t)
+    res = {"images": [v.double().cpu().numpy() for v in gpu_helpers.split_views(out, cams)]}
+    _compare_images(res, f, cams, tag="conventional SH3, rotated SH")
+
+    rng = np.random.default_rng(13)
+    dL = []
+    for v, cam in enumerate(cams):
+        d = rng.standard_normal((3, cam.height, cam.width))
+        view = f["views"][v]
+        d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+        dL.append(d)
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=bg)
+    for v in range(len(cams)):
+        dL[v][:, g_orc["pixel_flags"][v]] = 0.0
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=bg)
+    dL_t = torch.from_numpy(np.concatenate([d.astype(np.float32).reshape(-1) for d in dL])).cuda()
+    grads = {k: torch.full_like(v, float("nan")) for k, v in
+             zip(("means", "log_scales", "quats", "opacity_logits", "sh"), dev.params())}
+    r.backward(world, no_q, no_t, bg_t, dL_t, grads, overwrite=True)
+    grads["inst_quat"] = torch.full_like(iq, float("nan"))
+    grads["inst_trans"] = torch.full_like(it, float("nan"))
+    r.ws.to_world_bwd(dev.c_scene(), poses, grads)
+    torch.cuda.synchronize()
+    r.sync_status()
+    _compare_grads({k: v.double().cpu().numpy() for k, v in grads.items()}, g_orc,
+                   ("means", "log_scales", "quats", "opacity_logits", "sh", "inst_quat", "inst_trans"))
 
 
 def test_capacity_overflow_is_reported(built, tiny, tiny_vis):
