@@ -48,30 +48,29 @@ constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTStop = 1e-4f;
 
-// Persistent tile queue: a launch of (SMs x resident blocks) CTAs takes tiles
-// from an atomic cursor, the longest tile lists first (k_tile_ranges files
-// every tile under class clz(length), class 0 the longest, 32 the empty
-// tiles). The last CTA to leave resets the cursor for the next launch.
+// Persistent tile queue: a launch of (SMs x resident blocks) CTAs takes
+// positions from an atomic cursor. Tiles come longest lists first
+// (k_tile_ranges files every tile under class clz(length), class 0 the
+// longest, 32 the empty tiles). Chunks of memory-bound zeroing are spread
+// evenly between the tiles (position i is a chunk when floor((i+1) C / P)
+// > floor(i C / P), C chunks among P positions), so that their stores run
+// while other CTAs of the SM blend: the forward clears the per-splat adjoints
+// the backward sums into, the backward in overwrite mode clears the caller's
+// gradient arrays. The last CTA to leave resets the cursor for the next launch.
 struct TileQueue {
   uint32_t* cursor;
   uint32_t* exits;
-  uint32_t* extra;     // a second cursor reset with it (or null)
 };
 
-// Overwrite mode of the backward: once the tile queue is empty, the CTAs of
-// the blend backward zero the caller's gradient arrays in chunks of
-// kZeroChunk Gaussians taken from their own cursor: the arrays of 1-4 floats
-// per Gaussian in full (the projection backward, which runs next, writes the
-// kept rows), the SH rows only of the Gaussians that no view kept. The
-// zeroing, which is bound by memory bandwidth, fills the ALU-bound blend's
-// tail instead of a launch of its own.
+// Overwrite mode of the backward: the arrays of 1-4 floats per Gaussian are
+// zeroed in full (the projection backward, which runs next, writes the kept
+// rows), the SH rows only of the Gaussians that no view kept.
 constexpr int kZeroChunk = 2048;   // Gaussians (or splats) per chunk (64 words of the kept bitmap)
 struct GradZero {
   const uint32_t* kept_bits;
   int64_t n;                       // 0: nothing to zero (accumulate mode)
   s3r_grads g;
   int sh_floats;                   // 3 (K + 1)^2
-  uint32_t* cursor;
 };
 
 struct BlendArgs {
@@ -90,7 +89,7 @@ struct BlendArgs {
   float* out;             // forward only
   float* final_T;
   uint32_t* n_contrib;
-  float* sp_grad;         // [S*12]: zeroed by the forward's tail, summed by the backward
+  float* sp_grad;         // [S*12]: zeroed by the forward (chunks in its queue), summed by the backward
   const uint32_t* ctr;
   int64_t cap_splats;
   unsigned long long* pairs;     // counting mode: list pairs the forward walked
@@ -112,10 +111,11 @@ __device__ __forceinline__ uint32_t get_bits(const uint32_t* arr, uint32_t gp) {
   return __funnelshift_r(arr[w], arr[w + 1], sh);
 }
 
-// Class starts of the queue (exclusive scan of the class counts), once per
-// CTA; thread 0 takes the CTA's first queue position.
+// Class starts of the queue (exclusive scan of the class counts) and the
+// number of zeroing chunks, once per CTA; thread 0 takes the CTA's first
+// queue position.
 __device__ __forceinline__ void queue_init(const BlendArgs& a, const TileQueue& q, uint32_t* s_cstart,
-                                           uint32_t& pending) {
+                                           uint32_t n_chunks, uint32_t& pending) {
   if (threadIdx.x == 0) {
     uint32_t run = 0;
     for (int c = 0; c < kTileClasses; ++c) {
@@ -123,24 +123,35 @@ __device__ __forceinline__ void queue_init(const BlendArgs& a, const TileQueue& 
       run += a.class_cnt[c];
     }
     s_cstart[kTileClasses] = run;
+    s_cstart[kTileClasses + 1] = n_chunks;
     pending = atomicAdd(q.cursor, 1u);
   }
   __syncthreads();
 }
 
-// The CTA's next tile, or -1 when the queue is empty (block-uniform). Thread
-// 0 holds the position taken one tile ahead, so that the atomic's round trip
-// overlaps the current tile's work.
+// The CTA's next work item (block-uniform): a tile id (>= 0), a zeroing
+// chunk c as -2 - c, or -1 when the queue is empty. Thread 0 holds the
+// position taken one item ahead, so that the atomic's round trip overlaps
+// the current item's work.
 __device__ __forceinline__ int queue_next(const BlendArgs& a, const TileQueue& q,
                                           const uint32_t* s_cstart, int* s_tile, uint32_t& pending) {
   if (threadIdx.x == 0) {
     const uint32_t i = pending;
+    const uint64_t T = s_cstart[kTileClasses], C = s_cstart[kTileClasses + 1];
+    const uint64_t P = T + C;
     int t = -1;
-    if (i < s_cstart[kTileClasses]) {
+    if (i < P) {
       pending = atomicAdd(q.cursor, 1u);
-      int c = 0;
-      while (i >= s_cstart[c + 1]) ++c;
-      t = (int)a.class_list[(size_t)c * a.tiles + (i - s_cstart[c])];
+      const uint64_t cb = C ? (uint64_t)i * C / P : 0u;              // chunks before position i
+      const uint64_t cb1 = C ? ((uint64_t)i + 1u) * C / P : 0u;
+      if (cb1 > cb) {
+        t = -2 - (int)cb;
+      } else {
+        const uint32_t ti = (uint32_t)(i - cb);                          // tiles before position i
+        int c = 0;
+        while (ti >= s_cstart[c + 1]) ++c;
+        t = (int)a.class_list[(size_t)c * a.tiles + (ti - s_cstart[c])];
+      }
     }
     *s_tile = t;
   }
@@ -148,13 +159,12 @@ __device__ __forceinline__ int queue_next(const BlendArgs& a, const TileQueue& q
   return *s_tile;
 }
 
-// Every CTA has taken its last tile: the last one to leave resets the cursor.
+// Every CTA has taken its last item: the last one to leave resets the cursor.
 __device__ __forceinline__ void queue_exit(const TileQueue& q) {
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(q.exits, 1u) == gridDim.x - 1) {
       *q.cursor = 0u;
-      if (q.extra) *q.extra = 0u;
       *q.exits = 0u;
       __threadfence();
     }
@@ -189,45 +199,36 @@ __device__ __forceinline__ void zero_sh_unkept(const GradZero& z, int64_t w0, in
   }
 }
 
-// The forward's tail: its CTAs, once the tile queue is empty, zero the
-// per-splat adjoints (12 floats per splat) in chunks, for the backward that
-// sums into them.
-__device__ void splat_grad_zero_chunks(float4* g, const uint32_t* ctr, int64_t cap,
-                                       uint32_t* cursor, int* s_chunk) {
-  const int64_t n = min((int64_t)ctr[kCtrSplats], cap);
-  const int64_t n_chunks = (n + kZeroChunk - 1) / kZeroChunk;
-  for (;;) {
-    if (threadIdx.x == 0) *s_chunk = (int)atomicAdd(cursor, 1u);
-    __syncthreads();
-    const int64_t c = *s_chunk;
-    __syncthreads();
-    if (c >= n_chunks) break;
-    const int64_t lo = 3 * c * kZeroChunk, hi = 3 * min(n, (c + 1) * kZeroChunk);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+// Zeroing chunk c of the forward: the per-splat adjoints (12 floats per
+// splat) of splats [c kZeroChunk, (c + 1) kZeroChunk).
+__device__ __forceinline__ uint32_t splat_grad_chunks(const BlendArgs& a) {
+  const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
+  return (uint32_t)((n + kZeroChunk - 1) / kZeroChunk);
+}
+__device__ void splat_grad_zero_chunk(const BlendArgs& a, int64_t c) {
+  const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
+  float4* g = reinterpret_cast<float4*>(a.sp_grad);
+  const int64_t lo = 3 * c * kZeroChunk, hi = 3 * min(n, (c + 1) * kZeroChunk);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__device__ void grad_zero_chunks(const GradZero& z, int* s_chunk) {
-  const int64_t n_chunks = (z.n + kZeroChunk - 1) / kZeroChunk;
-  for (;;) {
-    if (threadIdx.x == 0) *s_chunk = (int)atomicAdd(z.cursor, 1u);
-    __syncthreads();
-    const int64_t c = *s_chunk;
-    __syncthreads();
-    if (c >= n_chunks) break;
-    const int64_t g0 = c * kZeroChunk, g1 = min(z.n, g0 + kZeroChunk);
-    zero_span(z.g.means, 3 * g0, 3 * g1);
-    zero_span(z.g.log_scales, 3 * g0, 3 * g1);
-    zero_span(z.g.quats, 4 * g0, 4 * g1);
-    zero_span(z.g.opacity_logits, g0, g1);
-    if (z.g.sh) {
-      const int64_t w0 = g0 / 32, w1 = (g1 + 31) / 32;
-      switch (z.sh_floats) {
-        case 3: zero_sh_unkept<3>(z, w0, w1); break;
-        case 12: zero_sh_unkept<12>(z, w0, w1); break;
-        case 27: zero_sh_unkept<27>(z, w0, w1); break;
-        default: zero_sh_unkept<48>(z, w0, w1); break;
-      }
+// Zeroing chunk c of the backward: Gaussians [c kZeroChunk, (c + 1) kZeroChunk).
+__device__ __forceinline__ uint32_t grad_chunks(const GradZero& z) {
+  return (uint32_t)((z.n + kZeroChunk - 1) / kZeroChunk);
+}
+__device__ void grad_zero_chunk(const GradZero& z, int64_t c) {
+  const int64_t g0 = c * kZeroChunk, g1 = min(z.n, g0 + kZeroChunk);
+  zero_span(z.g.means, 3 * g0, 3 * g1);
+  zero_span(z.g.log_scales, 3 * g0, 3 * g1);
+  zero_span(z.g.quats, 4 * g0, 4 * g1);
+  zero_span(z.g.opacity_logits, g0, g1);
+  if (z.g.sh) {
+    const int64_t w0 = g0 / 32, w1 = (g1 + 31) / 32;
+    switch (z.sh_floats) {
+      case 3: zero_sh_unkept<3>(z, w0, w1); break;
+      case 12: zero_sh_unkept<12>(z, w0, w1); break;
+      case 27: zero_sh_unkept<27>(z, w0, w1); break;
+      default: zero_sh_unkept<48>(z, w0, w1); break;
     }
   }
 }
@@ -482,13 +483,18 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
   __shared__ float4 s_p3[kBatchFwd];   // b b v v
   __shared__ float2 s_u[kBatchFwd];    // u u
   __shared__ float4 s_box[kBatchFwd];
-  __shared__ uint32_t s_cstart[kTileClasses + 1];
+  __shared__ uint32_t s_cstart[kTileClasses + 2];
   __shared__ int s_tile;
   uint32_t pending = 0;
-  queue_init(a, a.fwd_queue, s_cstart, pending);
+  queue_init(a, a.fwd_queue, s_cstart, threadIdx.x == 0 ? splat_grad_chunks(a) : 0u, pending);
   for (;;) {
     const int tile = queue_next(a, a.fwd_queue, s_cstart, &s_tile, pending);
-    if (tile < 0) break;
+    if (tile == -1) break;
+    if (tile < -1) {
+      splat_grad_zero_chunk(a, -2 - (int64_t)tile);
+      __syncthreads();   // s_tile is rewritten by the next queue_next
+      continue;
+    }
     const int v = view_of_tile(vs, tile);
     const ViewInfo& vi = vs.v[v];
     const int lt = tile - vi.tile_base;
@@ -614,8 +620,6 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
     }
     __syncthreads();   // shared staging is reused by the next tile
   }
-  splat_grad_zero_chunks(reinterpret_cast<float4*>(a.sp_grad), a.ctr, a.cap_splats,
-                         a.fwd_queue.extra, &s_tile);
   queue_exit(a.fwd_queue);
 }
 
@@ -812,13 +816,18 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_BWD_BLOCKS) k_blend_bw
   __shared__ float s_g[kBatchBwd][9];
   __shared__ float s_sink[kBandThreads];   // target of the lanes with no sum to add
   __shared__ int s_max;
-  __shared__ uint32_t s_cstart[kTileClasses + 1];
+  __shared__ uint32_t s_cstart[kTileClasses + 2];
   __shared__ int s_tile;
   uint32_t pending = 0;
-  queue_init(a, a.bwd_queue, s_cstart, pending);
+  queue_init(a, a.bwd_queue, s_cstart, grad_chunks(a.zero), pending);
   for (;;) {
     const int tile = queue_next(a, a.bwd_queue, s_cstart, &s_tile, pending);
-    if (tile < 0) break;
+    if (tile == -1) break;
+    if (tile < -1) {
+      grad_zero_chunk(a.zero, -2 - (int64_t)tile);
+      __syncthreads();   // s_tile is rewritten by the next queue_next
+      continue;
+    }
     const int v = view_of_tile(vs, tile);
     const ViewInfo& vi = vs.v[v];
     const int lt = tile - vi.tile_base;
@@ -961,7 +970,6 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_BWD_BLOCKS) k_blend_bw
     }
     __syncthreads();   // shared staging is reused by the next tile
   }
-  if (a.zero.n > 0) grad_zero_chunks(a.zero, &s_tile);
   queue_exit(a.bwd_queue);
 }
 
@@ -981,14 +989,11 @@ static BlendArgs make_args(s3r_workspace* ws) {
   a.class_cnt = ws->tile_class_cnt;
   a.class_list = ws->tile_class_list;
   a.tiles = ws->views.total_tiles;
-  a.fwd_queue = TileQueue{ws->ctr + kCtrBlendFwdCursor, ws->ctr + kCtrBlendFwdExits,
-                          ws->ctr + kCtrFwdZeroCursor};
+  a.fwd_queue = TileQueue{ws->ctr + kCtrBlendFwdCursor, ws->ctr + kCtrBlendFwdExits};
   a.ctr = ws->ctr;
   a.cap_splats = ws->cap.max_splats;
-  a.bwd_queue = TileQueue{ws->ctr + kCtrBlendBwdCursor, ws->ctr + kCtrBlendBwdExits,
-                          ws->ctr + kCtrBwdZeroCursor};
-  a.zero = GradZero{nullptr, 0, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}, 0,
-                    ws->ctr + kCtrBwdZeroCursor};
+  a.bwd_queue = TileQueue{ws->ctr + kCtrBlendBwdCursor, ws->ctr + kCtrBlendBwdExits};
+  a.zero = GradZero{nullptr, 0, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}, 0};
   a.sorted_splats = ws->dup_val[ws->dup_final];
   a.sp_xy = ws->sp_xy;
   a.sp_conic_o = ws->sp_conic_o;

@@ -31,9 +31,7 @@ enum Ctr : int {
   kCtrBlendBwdCursor = 34,
   kCtrBlendBwdExits = 35,
   kCtrProjBwdExits = 36,     // CTAs of the projection backward that finished
-  kCtrBwdZeroCursor = 37,    // next chunk of the overwrite-mode gradient zeroing
   kCtrCompactExits = 38,     // CTAs of the compaction that finished
-  kCtrFwdZeroCursor = 39,    // next chunk of the splat-adjoint zeroing in the blend forward
   kCtrCount = 40
 };
 // Tile classes of the blend queue: class c = clz(pairs) holds the tiles with
