@@ -19,6 +19,7 @@ the public API with host buffers, and the SM clocks seen while timing.
   python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
   python bench.py --conventional ...     # the Fig. 1(a) pipeline (world transform, no LOD)
   python bench.py --sweep scale          # per-view time against scene size
+  python bench.py --sweep lod            # per-view time against the LOD threshold
   python bench.py --workload train       # optimisation steps (forward, backward, Adam)
 """
 from __future__ import annotations
@@ -138,10 +139,12 @@ def parse():
                    help="the conventional pipeline of Fig. 1(a): every step moves the dynamic "
                         "Gaussians to the world frame (s3r_to_world) and renders the scene without "
                         "instances, every Gaussian selected and no LOD")
-    p.add_argument("--sweep", default=None, choices=("scale",),
+    p.add_argument("--sweep", default=None, choices=("scale", "lod"),
                    help="scale: per-view fwd+bwd time of the large corridor stretched at constant "
-                        "density, with the temporal record and with every Gaussian visible")
+                        "density, with the temporal record and with every Gaussian visible; lod: "
+                        "per-view fwd+bwd time of the large corridor against the LOD threshold")
     p.add_argument("--sweep-scales", default="0.5,1,2,4")
+    p.add_argument("--sweep-lods", default="0,0.5,1,2")
     return p.parse_args()
 
 
@@ -433,20 +436,24 @@ def run_ours(args, rank, world, local):
     del graph_k
     if args.conventional:
         # the world transform and its backward are not kernels of the
-        # workspace's timing hook: timed eagerly here, L2 flushed before each
+        # workspace's timing hook: each is captured in a graph of its own and
+        # timed by events around the replay (L2 flushed before each), so that
+        # no host-side argument marshalling falls inside the events
         poses_ = binding.make_poses(iq, it)
         for name, fn in (("to_world", lambda: binding.to_world(cs, poses_, mw, qw, shw)),
                          ("to_world_bwd", lambda: r.ws.to_world_bwd(cs, poses_, grads))):
+            g_ = r.capture(fn)
             evs = []
             for i in range(args.warmup + args.steps):
                 flush.fill_(float(i))
                 a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a_.record()
-                fn()
+                g_.replay()
                 b_.record()
                 evs.append((a_, b_))
             torch.cuda.synchronize()
             ktimes[name] = [a_.elapsed_time(b_) for a_, b_ in evs[args.warmup:]]
+            del g_
         step()                                        # the gradients as one step leaves them
         torch.cuda.synchronize()
 
@@ -875,6 +882,85 @@ def run_reference(args, rank, world, local):
     }), flush=True)
 
 
+def _sweep_prepare(scene, lod_sweep):
+    """Device scene, renderer and the first-epoch record of a sweep scene:
+    Eq. 5 over every timestep with every window open (at the LOD threshold
+    `lod_sweep`; M_t is taken before LOD, so the record does not depend on
+    it), then Eq. 6. Returns (dev, c_scene, renderer, vis, all_vis)."""
+    import torch
+    from paper_2503_08217_gb300 import binding
+    from paper_2503_08217_gb300.render import DeviceScene, Renderer
+    n = scene.n
+    k = scene.n_steps // 2
+    dev = DeviceScene.from_host(scene)
+    cs = dev.c_scene()
+    max_splats = max(4096, n)
+    r = Renderer(n, scene.n_inst, scene.cams[k], max_splats=max_splats,
+                 max_duplicates=min(2**31 - 1, 6 * max_splats))
+    vis = torch.empty((n, 2), device="cuda")
+    life = torch.empty((n, 2), device="cuda")
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
+    all_vis = vis.clone()
+    for kk in range(scene.n_steps):
+        iq = torch.from_numpy(scene.inst_quat[kk]).cuda()
+        it = torch.from_numpy(scene.inst_trans[kk]).cuda()
+        r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
+                     life, lod_sweep)
+    binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
+    torch.cuda.synchronize()
+    r.counts()
+    return dev, cs, r, vis, all_vis
+
+
+def _sweep_time(args, scene, dev, cs, r, v, lod, flush):
+    """Graph-captured forward + L1 + backward (overwrite) of the middle
+    timestep's cameras with record `v` at LOD threshold `lod`: mean ms per
+    step over args.steps replays (L2 flushed between them) and the counts."""
+    import torch
+    from paper_2503_08217_gb300 import binding
+    from paper_2503_08217_gb300.render import pixel_count
+    k = scene.n_steps // 2
+    cams = scene.cams[k]
+    P = pixel_count(cams)
+    iq = torch.from_numpy(scene.inst_quat[k]).cuda()
+    it = torch.from_numpy(scene.inst_trans[k]).cuda()
+    t = float(scene.times[k])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    target = torch.rand(3 * P, device="cuda", generator=gen)
+    out = torch.empty(3 * P, device="cuda")
+    dL = torch.empty(3 * P, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    bg = torch.zeros(3, device="cuda")
+    grads = {"means": torch.empty_like(dev.means), "log_scales": torch.empty_like(dev.log_scales),
+             "quats": torch.empty_like(dev.quats), "opacity_logits": torch.empty_like(dev.opacity_logits),
+             "sh": torch.empty_like(dev.sh), "inst_quat": torch.empty_like(iq),
+             "inst_trans": torch.empty_like(it)}
+
+    def step():
+        r.forward(dev, iq, it, cams, t, v, None, lod, bg, out=out, c_scene=cs)
+        binding.l1_loss(out, target, dL, loss)
+        r.backward(dev, iq, it, bg, dL, grads, c_scene=cs, overwrite=True)
+    step()
+    torch.cuda.synchronize()
+    c = r.counts()
+    graph = r.capture(step)
+    for _ in range(args.warmup):
+        graph.replay()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        graph.replay()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    r.sync_status()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    del graph
+    return ms, c
+
+
 def run_scale_sweep(args):
     """Per-view forward + backward time as the scene grows (the corridor of
     the 'large' workload stretched at constant density: Gaussians, instances,
@@ -884,7 +970,6 @@ def run_scale_sweep(args):
     the window [-1, 1], so every one is compacted and projected."""
     import torch
     from paper_2503_08217_gb300 import binding, build, scenegen
-    from paper_2503_08217_gb300.render import DeviceScene, Renderer, pixel_count
     build.build()
     binding.load()
     torch.cuda.set_device(0)
@@ -893,79 +978,55 @@ def run_scale_sweep(args):
     for f in [float(x) for x in args.sweep_scales.split(",")]:
         scene = scenegen.generate("large", seed=args.seed, length_scale=f)
         lod = 1.0
-        k = scene.n_steps // 2
-        cams = scene.cams[k]
-        P = pixel_count(cams)
         n = scene.n
-        dev = DeviceScene.from_host(scene)
-        cs = dev.c_scene()
-        max_splats = max(4096, n)
-        r = Renderer(n, scene.n_inst, cams, max_splats=max_splats,
-                     max_duplicates=min(2**31 - 1, 6 * max_splats))
-        vis = torch.empty((n, 2), device="cuda")
-        life = torch.empty((n, 2), device="cuda")
-        binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_RESET)
-        all_vis = vis.clone()
-        for kk in range(scene.n_steps):
-            iq = torch.from_numpy(scene.inst_quat[kk]).cuda()
-            it = torch.from_numpy(scene.inst_trans[kk]).cuda()
-            r.ws.project(cs, binding.make_poses(iq, it), scene.cams[kk], float(scene.times[kk]), all_vis,
-                         life, lod)
-        binding.update_visibility(n, 0.0, None, life, vis, binding.VIS_FINALIZE)
-        torch.cuda.synchronize()
-        r.counts()
-        iq = torch.from_numpy(scene.inst_quat[k]).cuda()
-        it = torch.from_numpy(scene.inst_trans[k]).cuda()
-        t = float(scene.times[k])
-        target = torch.rand(3 * P, device="cuda")
-        out = torch.empty(3 * P, device="cuda")
-        dL = torch.empty(3 * P, device="cuda")
-        loss = torch.zeros(1, device="cuda")
-        bg = torch.zeros(3, device="cuda")
-        grads = {"means": torch.zeros_like(dev.means), "log_scales": torch.zeros_like(dev.log_scales),
-                 "quats": torch.zeros_like(dev.quats), "opacity_logits": torch.zeros_like(dev.opacity_logits),
-                 "sh": torch.zeros_like(dev.sh), "inst_quat": torch.zeros_like(iq),
-                 "inst_trans": torch.zeros_like(it)}
+        dev, cs, r, vis, all_vis = _sweep_prepare(scene, lod)
+        cams = scene.cams[scene.n_steps // 2]
         row = {"length_scale": f, "gaussians": n, "instances": scene.n_inst, "timesteps": scene.n_steps,
                "corridor_m": round(float(scene.means[:, 2].max() - scene.means[:, 2].min()), 1)}
         for mode, v in (("temporal", vis), ("all_visible", all_vis)):
-            def step():
-                r.forward(dev, iq, it, cams, t, v, None, lod, bg, out=out, c_scene=cs)
-                binding.l1_loss(out, target, dL, loss)
-                r.backward(dev, iq, it, bg, dL, grads, c_scene=cs, overwrite=True)
-            step()
-            torch.cuda.synchronize()
-            c = r.counts()
-            graph = r.capture(step)
-            for _ in range(args.warmup):
-                graph.replay()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(args.steps)]
-            for i in range(args.steps):
-                flush.fill_(float(i))
-                ev[i][0].record()
-                graph.replay()
-                ev[i][1].record()
-            torch.cuda.synchronize()
-            r.sync_status()
-            ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            ms, c = _sweep_time(args, scene, dev, cs, r, v, lod, flush)
             row[mode] = {"ms_per_view": round(ms / len(cams), 3), "selected": int(c["n_selected"]),
                          "splats": int(c["n_splats"])}
-            del graph
         rows.append(row)
-        del r, dev, grads, vis, life, all_vis, out, dL, target
+        del r, dev, vis, all_vis
         torch.cuda.empty_cache()
     print(json.dumps({"sweep": "scale", "metric": "fwd+bwd ms per view vs scene scale",
                       "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
                       "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_lod_sweep(args):
+    """Per-view forward + backward time against the adaptive-LOD threshold
+    (Sec. 3.3): the large corridor (8M static + 80 instances, SH3), one
+    1920x1280 camera at the middle timestep, temporal selection after a
+    first-epoch sweep, r in --sweep-lods (pixels of the projected 2D scale
+    below which a Gaussian is culled; r = 0 culls nothing)."""
+    import torch
+    from paper_2503_08217_gb300 import binding, build, scenegen
+    build.build()
+    binding.load()
+    torch.cuda.set_device(0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    scene = scenegen.generate("large", seed=args.seed)
+    dev, cs, r, vis, _ = _sweep_prepare(scene, 0.0)
+    rows = []
+    for lod in [float(x) for x in args.sweep_lods.split(",")]:
+        ms, c = _sweep_time(args, scene, dev, cs, r, vis, lod, flush)
+        rows.append({"lod_px": lod, "ms_per_view": round(ms, 3), "views_per_s": round(1e3 / ms, 1),
+                     "selected": int(c["n_selected"]), "splats": int(c["n_splats"]),
+                     "pairs": int(c["n_duplicates"])})
+    print(json.dumps({"sweep": "lod", "metric": "fwd+bwd ms per view vs LOD threshold",
+                      "unit": "ms", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic", "gaussians": scene.n, "timestep": scene.n_steps // 2,
+                      "camera": "1920x1280, f 960", "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.sweep == "scale":
+    if args.sweep is not None:
         if rank == 0:
-            run_scale_sweep(args)
+            (run_scale_sweep if args.sweep == "scale" else run_lod_sweep)(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world, local)

@@ -281,7 +281,8 @@ const uint32_t* s3r_device_status(const s3r_workspace* ws);
  * 26-point Lebedev quadrature of the rotated basis against the basis); band
  * 0 is copied. scene and poses as for s3r_project. Only the rows of the
  * dynamic Gaussians ([inst_offsets[1], n)) of means_out [n,3] (4-B aligned),
- * quats_out [n,4] (16-B aligned) and sh_out [n,K,3] (or NULL) are written:
+ * quats_out [n,4] (16-B aligned) and sh_out [n,K,3] (16-B aligned, like the
+ * scene's SH; or NULL) are written:
  * static Gaussians do not move, so the caller fills their rows once (a copy).
  * A scene of these arrays with no instances (inst_offsets {0, n}) then
  * renders the same image through s3r_project. S3R_ERR_INVALID on NULL or
@@ -290,7 +291,8 @@ s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* m
                         float* quats_out, float* sh_out, void* stream);
 
 /* Backward of s3r_to_world, in place: on entry grads->means, grads->quats and
- * grads->sh (each may be NULL) hold, at the rows of dynamic Gaussians, the
+ * grads->sh (each may be NULL; quats and sh 16-byte aligned) hold, at the
+ * rows of dynamic Gaussians, the
  * adjoints of the world-frame means, quaternions and rotated SH (as the
  * backward of the world-frame render writes them); on return those rows
  * hold the adjoints of the object-frame parameters (the static rows, whose

@@ -26,10 +26,16 @@
 namespace s3r {
 namespace {
 
-constexpr int kWorldThreads = 256;
+constexpr int kWorldWarps = 2;
+constexpr int kWorldThreads = 32 * kWorldWarps;   // Gaussians per chunk of a CTA
 constexpr int kRotFloats = 9 + 25 + 49;      // D_1, D_2, D_3 row-major
 constexpr int kWorldAcc = 9 + 3 + 4 + kRotFloats;   // dR, dt, dp, dD per instance
 constexpr int kLocalInst = 4;                // instances whose matrices a CTA keeps in shared memory
+
+// entries of D_1..D_deg
+__host__ __device__ constexpr int rot_count(int deg) {
+  return deg <= 0 ? 0 : (deg == 1 ? 9 : (deg == 2 ? 34 : 83));
+}
 
 __device__ __forceinline__ void lebedev26(int m, float d[3], float& w) {
   const float s2 = 0.70710678118654752f, s3 = 0.57735026918962576f;
@@ -109,35 +115,150 @@ struct WorldArgs {
   float* g_pose_t;
 };
 
-// The matrices of the instances that a CTA's chunk of Gaussians touches
-// (usually one), in shared memory: [kLocalInst][kRotFloats]; instances past
-// kLocalInst compute theirs per Gaussian.
+// The SH basis at the 26 Lebedev points, [26][16] (once per CTA).
 template <int DEG>
-__device__ void chunk_rotations(const WorldArgs& a, int k0, int k1, float* s_D) {
-  for (int k = k0 + (int)threadIdx.x; k <= k1 && k - k0 < kLocalInst; k += blockDim.x) {
-    float R[9];
-    quat_to_rot(a.pose_q[k - 1], R);
-    sh_rotation<DEG>(R, s_D + (k - k0) * kRotFloats);
+__device__ void lebedev_basis(float* s_Yd) {
+  constexpr int K = sh_count(DEG);
+  for (int m = threadIdx.x; m < 26; m += blockDim.x) {
+    float d[3], w, Y[16];
+    lebedev26(m, d, w);
+    sh_basis<DEG>(d[0], d[1], d[2], Y);
+    for (int i = 0; i < K; ++i) s_Yd[m * 16 + i] = Y[i];
   }
+}
+
+// D_1..D_DEG of the instances k0 .. min(k1, k0 + kLocalInst - 1) that a
+// chunk of Gaussians touches (usually one), into s_D [kLocalInst][kRotFloats]:
+// first 4 pi w_m Y(R^T d_m) at the 26 points (one thread per point and
+// instance), then one thread per matrix entry for its 26-term sum (the
+// quadrature in the order of sh_rotation). Instances past kLocalInst compute
+// theirs per Gaussian. Synchronises the CTA before returning.
+template <int DEG>
+__device__ void chunk_rotations(const WorldArgs& a, int k0, int k1, const float* s_Yd, float* s_Yu,
+                                float* s_D) {
+  constexpr int K = sh_count(DEG), E = rot_count(DEG);
+  const int ns = min(k1 - k0 + 1, kLocalInst);
+  for (int e = threadIdx.x; e < ns * 26; e += blockDim.x) {
+    const int sl = e / 26, m = e - sl * 26;
+    float R[9], d[3], w, Y[16];
+    quat_to_rot(a.pose_q[k0 + sl - 1], R);
+    lebedev26(m, d, w);
+    sh_basis<DEG>(R[0] * d[0] + R[3] * d[1] + R[6] * d[2], R[1] * d[0] + R[4] * d[1] + R[7] * d[2],
+                  R[2] * d[0] + R[5] * d[1] + R[8] * d[2], Y);
+    const float sw = 12.566370614359172f * w;
+    for (int i = 0; i < K; ++i) s_Yu[e * 16 + i] = sw * Y[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ns * E; e += blockDim.x) {
+    const int sl = e / E, r = e - sl * E;
+    const int l = r < 9 ? 1 : (r < 34 ? 2 : 3);
+    const int nb = 2 * l + 1, idx = r - rot_off(l), i = idx / nb, j = idx - i * nb, b = band_start(l);
+    float acc = 0.f;
+    for (int m = 0; m < 26; ++m) acc = fmaf(s_Yu[(sl * 26 + m) * 16 + b + i], s_Yd[m * 16 + b + j], acc);
+    s_D[sl * kRotFloats + r] = acc;
+  }
+  __syncthreads();
+}
+
+// A lane's own staged SH row (kFloatPitch floats from `row`) to and from
+// registers: as float4s where the rows are (conflict-free across a quarter
+// warp with the odd float4 pitch), else as floats.
+template <int DEG>
+__device__ __forceinline__ void row_get(const float* row, float (&c)[3 * sh_count(DEG)]) {
+  using St = ShStage<DEG>;
+  if constexpr (St::kVec) {
+#pragma unroll
+    for (int q = 0; q < St::kRow; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(row)[q];
+      c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3 * sh_count(DEG); ++q) c[q] = row[q];
+  }
+}
+template <int DEG>
+__device__ __forceinline__ void row_put(float* row, const float (&c)[3 * sh_count(DEG)]) {
+  using St = ShStage<DEG>;
+  if constexpr (St::kVec) {
+#pragma unroll
+    for (int q = 0; q < St::kRow; ++q)
+      reinterpret_cast<float4*>(row)[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 3 * sh_count(DEG); ++q) row[q] = c[q];
+  }
+}
+
+// Coalesced copy of n_here staged rows to the consecutive rows g0.. of `sh`
+// (the inverse of stage_sh_rows for consecutive Gaussians).
+template <int DEG>
+__device__ __forceinline__ void unstage_sh_rows(float* __restrict__ sh, const float* stage, int64_t g0,
+                                                int n_here, uint32_t lane) {
+  using St = ShStage<DEG>;
+  if constexpr (St::kVec) {
+    float4* dst = reinterpret_cast<float4*>(sh) + g0 * St::kRow;
+    const float4* src = reinterpret_cast<const float4*>(stage);
+    for (int idx = (int)lane; idx < n_here * St::kRow; idx += 32) {
+      const int g = idx / St::kRow, q = idx - g * St::kRow;
+      dst[idx] = src[g * St::kPitch + q];
+    }
+  } else {
+    float* dst = sh + g0 * St::kRow;
+    for (int idx = (int)lane; idx < n_here * St::kRow; idx += 32) {
+      const int g = idx / St::kRow, q = idx - g * St::kRow;
+      dst[idx] = stage[g * St::kPitch + q];
+    }
+  }
+}
+
+// The CTA's contiguous range of 64-Gaussian chunks of the dynamic rows, so
+// that consecutive chunks mostly share their instance's matrices.
+struct ChunkRange {
+  int64_t first, begin, end;
+};
+__device__ __forceinline__ ChunkRange chunk_range(const WorldArgs& a) {
+  ChunkRange r;
+  r.first = a.inst_off[1];
+  const int64_t n_chunks = (a.n - r.first + kWorldThreads - 1) / kWorldThreads;
+  const int64_t per = (n_chunks + gridDim.x - 1) / gridDim.x;
+  r.begin = (int64_t)blockIdx.x * per;
+  r.end = min(n_chunks, r.begin + per);
+  return r;
 }
 
 template <int DEG>
 __global__ void __launch_bounds__(kWorldThreads) k_to_world(WorldArgs a) {
+  using St = ShStage<DEG>;
   constexpr int K = sh_count(DEG);
   __shared__ float s_D[kLocalInst * kRotFloats];
-  const int64_t first = a.inst_off[1];
-  for (int64_t base = first + (int64_t)blockIdx.x * kWorldThreads; base < a.n;
-       base += (int64_t)gridDim.x * kWorldThreads) {
+  __shared__ float s_Yd[26 * 16];
+  __shared__ float s_Yu[kLocalInst * 26 * 16];
+  __shared__ __align__(16) float s_rows[kWorldWarps * St::kWords];
+  const ChunkRange cr = chunk_range(a);
+  const uint32_t lane = threadIdx.x & 31u;
+  const int warp = threadIdx.x >> 5;
+  float* rows = s_rows + warp * St::kWords;
+  const bool rotate = DEG > 0 && a.sh_out;
+  if (rotate) lebedev_basis<DEG>(s_Yd);   // read after chunk_rotations' first barrier
+  int kc0 = -1, kc1 = -1;
+  for (int64_t c = cr.begin; c < cr.end; ++c) {
+    const int64_t base = cr.first + c * kWorldThreads;
     const int64_t g = base + threadIdx.x;
     const int k0 = segment_of_gid(a.inst_off, a.n_inst, base);
     const int k1 = segment_of_gid(a.inst_off, a.n_inst, min(a.n, base + kWorldThreads) - 1);
-    if (DEG > 0 && a.sh_out) chunk_rotations<DEG>(a, k0, k1, s_D);
-    __syncthreads();
-    if (g < a.n) {
-      const int k = segment_of_gid(a.inst_off, a.n_inst, g);
-      const float4 qp = a.pose_q[k - 1];
-      float R[9];
-      quat_to_rot(qp, R);
+    if (rotate && (k0 != kc0 || k1 != kc1)) {   // block-uniform
+      __syncthreads();   // the previous chunk's reads of s_D are done
+      chunk_rotations<DEG>(a, k0, k1, s_Yd, s_Yu, s_D);
+      kc0 = k0;
+      kc1 = k1;
+    }
+    const bool live = g < a.n;
+    const int k = live ? segment_of_gid(a.inst_off, a.n_inst, g) : k0;
+    const float4 qp = a.pose_q[k - 1];
+    float R[9];
+    quat_to_rot(qp, R);
+    if (live) {
       const float* t = a.pose_t + 3 * (k - 1);
       const float m0 = a.means[3 * g], m1 = a.means[3 * g + 1], m2 = a.means[3 * g + 2];
       a.means_out[3 * g] = fmaf(R[0], m0, fmaf(R[1], m1, fmaf(R[2], m2, t[0])));
@@ -152,11 +273,19 @@ __global__ void __launch_bounds__(kWorldThreads) k_to_world(WorldArgs a) {
                                    w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
                                    w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
                                    w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2);
-      if (a.sh_out) {
-        const float* c = a.sh + (size_t)K * 3 * g;
-        float* o = a.sh_out + (size_t)K * 3 * g;
-        for (int ch = 0; ch < 3; ++ch) o[ch] = c[ch];          // degree 0 is rotation invariant
-        if (DEG > 0) {
+    }
+    if (a.sh_out) {
+      // the warp's rows through shared memory: coalesced in, rotated per
+      // lane, coalesced out (c'_l = D_l^T c_l per channel; degree 0 as is)
+      const int64_t wbase = base + warp * 32;
+      const int n_here = (int)max((int64_t)0, min((int64_t)32, a.n - wbase));
+      if (n_here > 0) {
+        stage_sh_rows<DEG>(rows, a.sh, (uint32_t)(wbase + lane), n_here, lane);
+        __syncwarp();
+        if (DEG > 0 && live) {
+          float cr_[3 * K], o[3 * K];
+          float* row = rows + lane * St::kFloatPitch;
+          row_get<DEG>(row, cr_);
           float Dl[kRotFloats];
           const float* D = s_D + (k - k0) * kRotFloats;
           if (k - k0 >= kLocalInst) {
@@ -164,19 +293,27 @@ __global__ void __launch_bounds__(kWorldThreads) k_to_world(WorldArgs a) {
             D = Dl;
           }
 #pragma unroll
+          for (int ch = 0; ch < 3; ++ch) o[ch] = cr_[ch];
+#pragma unroll
           for (int l = 1; l <= DEG; ++l) {
             const int nb = 2 * l + 1, b = band_start(l);
+#pragma unroll
             for (int j = 0; j < nb; ++j)
+#pragma unroll
               for (int ch = 0; ch < 3; ++ch) {
                 float v = 0.f;
-                for (int i = 0; i < nb; ++i) v = fmaf(D[rot_off(l) + i * nb + j], c[3 * (b + i) + ch], v);
+#pragma unroll
+                for (int i = 0; i < nb; ++i) v = fmaf(D[rot_off(l) + i * nb + j], cr_[3 * (b + i) + ch], v);
                 o[3 * (b + j) + ch] = v;
               }
           }
+          row_put<DEG>(row, o);
         }
+        __syncwarp();
+        unstage_sh_rows<DEG>(a.sh_out, rows, wbase, n_here, lane);
+        __syncwarp();   // the rows are restaged by the next chunk
       }
     }
-    __syncthreads();
   }
 }
 
@@ -184,111 +321,154 @@ __global__ void __launch_bounds__(kWorldThreads) k_to_world(WorldArgs a) {
 // Gaussian: dmu = R^T dmu_w; dq from q_w = p (x) q^ (dq^ = p* (x) dq_w, then
 // through the normalisation); dc_l = D_l dc'_l. Per instance (summed): dR
 // from the means and dD_l = sum c_l dc'_l^T, dt = sum dmu_w, dp = sum dq_w (x) q^*.
+// The SH rows of the parameters and of the adjoints go through shared memory
+// (coalesced); a warp's dD sums are taken over its staged rows, one matrix
+// entry per lane, before one atomic per entry and instance.
 template <int DEG>
 __global__ void __launch_bounds__(kWorldThreads) k_to_world_bwd(WorldArgs a) {
-  constexpr int K = sh_count(DEG);
-  constexpr int kUsed = 16 + (DEG >= 1 ? 9 : 0) + (DEG >= 2 ? 25 : 0) + (DEG >= 3 ? 49 : 0);
+  using St = ShStage<DEG>;
+  constexpr int K = sh_count(DEG), E = rot_count(DEG);
   __shared__ float s_D[kLocalInst * kRotFloats];
-  const int64_t first = a.inst_off[1];
+  __shared__ float s_Yd[26 * 16];
+  __shared__ float s_Yu[kLocalInst * 26 * 16];
+  __shared__ __align__(16) float s_c[kWorldWarps * St::kWords];
+  __shared__ __align__(16) float s_g[kWorldWarps * St::kWords];
+  __shared__ float s_t[kWorldWarps][32][17];
+  __shared__ int s_k[kWorldWarps][32];
+  const ChunkRange cr = chunk_range(a);
   const uint32_t lane = threadIdx.x & 31u;
-  for (int64_t base = first + (int64_t)blockIdx.x * kWorldThreads; base < a.n;
-       base += (int64_t)gridDim.x * kWorldThreads) {
+  const int warp = threadIdx.x >> 5;
+  float* crow = s_c + warp * St::kWords;
+  float* grow = s_g + warp * St::kWords;
+  const bool rotate = DEG > 0 && a.g_sh;
+  if (rotate) lebedev_basis<DEG>(s_Yd);
+  int kc0 = -1, kc1 = -1;
+  for (int64_t c = cr.begin; c < cr.end; ++c) {
+    const int64_t base = cr.first + c * kWorldThreads;
     const int64_t g = base + threadIdx.x;
     const int k0 = segment_of_gid(a.inst_off, a.n_inst, base);
     const int k1 = segment_of_gid(a.inst_off, a.n_inst, min(a.n, base + kWorldThreads) - 1);
-    if (DEG > 0 && a.g_sh) chunk_rotations<DEG>(a, k0, k1, s_D);
-    __syncthreads();
-    // this Gaussian's terms of its instance's sums: dR (9), dt (3), dp (4), dD
-    float t[kUsed];
+    if (rotate && (k0 != kc0 || k1 != kc1)) {
+      __syncthreads();
+      chunk_rotations<DEG>(a, k0, k1, s_Yd, s_Yu, s_D);
+      kc0 = k0;
+      kc1 = k1;
+    }
+    // this Gaussian's terms of its instance's sums: dR (9), dt (3), dp (4)
+    float t[16];
 #pragma unroll
-    for (int i = 0; i < kUsed; ++i) t[i] = 0.f;
+    for (int i = 0; i < 16; ++i) t[i] = 0.f;
     const bool live = g < a.n;
-    const int k = live ? segment_of_gid(a.inst_off, a.n_inst, g) : k1;
-    if (live) {
-      const float4 qp = a.pose_q[k - 1];
-      float R[9];
-      quat_to_rot(qp, R);
-      if (a.g_means) {
-        float* gm = a.g_means + 3 * g;
-        const float d0 = gm[0], d1 = gm[1], d2 = gm[2];
-        const float m[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
-        gm[0] = R[0] * d0 + R[3] * d1 + R[6] * d2;
-        gm[1] = R[1] * d0 + R[4] * d1 + R[7] * d2;
-        gm[2] = R[2] * d0 + R[5] * d1 + R[8] * d2;
-        const float dw[3] = {d0, d1, d2};
+    const int k = live ? segment_of_gid(a.inst_off, a.n_inst, g) : -1;
+    const float4 qp = a.pose_q[(live ? k : k0) - 1];
+    float R[9];
+    quat_to_rot(qp, R);
+    if (live && a.g_means) {
+      float* gm = a.g_means + 3 * g;
+      const float d0 = gm[0], d1 = gm[1], d2 = gm[2];
+      const float m[3] = {a.means[3 * g], a.means[3 * g + 1], a.means[3 * g + 2]};
+      gm[0] = R[0] * d0 + R[3] * d1 + R[6] * d2;
+      gm[1] = R[1] * d0 + R[4] * d1 + R[7] * d2;
+      gm[2] = R[2] * d0 + R[5] * d1 + R[8] * d2;
+      const float dw[3] = {d0, d1, d2};
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
+      for (int r = 0; r < 3; ++r) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) t[3 * r + c] = dw[r] * m[c];
-          t[9 + r] = dw[r];
-        }
+        for (int cc = 0; cc < 3; ++cc) t[3 * r + cc] = dw[r] * m[cc];
+        t[9 + r] = dw[r];
       }
-      if (a.g_quats) {
-        const float4 q = a.quats[g];
-        const float nq = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-        const float qw = q.x / nq, qx = q.y / nq, qy = q.z / nq, qz = q.w / nq;
-        const float np = sqrtf(qp.x * qp.x + qp.y * qp.y + qp.z * qp.z + qp.w * qp.w);
-        const float pw = qp.x / np, px = qp.y / np, py = qp.z / np, pz = qp.w / np;
-        const float4 G = a.g_quats[g];
-        // dq^ = p* (x) G, then through the normalisation of q
-        const float aw = pw * G.x + px * G.y + py * G.z + pz * G.w;
-        const float ax = pw * G.y - px * G.x - py * G.w + pz * G.z;
-        const float ay = pw * G.z + px * G.w - py * G.x - pz * G.y;
-        const float az = pw * G.w - px * G.z + py * G.y - pz * G.x;
-        const float dot = aw * qw + ax * qx + ay * qy + az * qz;
-        a.g_quats[g] = make_float4((aw - qw * dot) / nq, (ax - qx * dot) / nq, (ay - qy * dot) / nq,
-                                   (az - qz * dot) / nq);
-        // dp^ = G (x) q^*
-        t[12] = G.x * qw + G.y * qx + G.z * qy + G.w * qz;
-        t[13] = -G.x * qx + G.y * qw - G.z * qz + G.w * qy;
-        t[14] = -G.x * qy + G.y * qz + G.z * qw - G.w * qx;
-        t[15] = -G.x * qz - G.y * qy + G.z * qx + G.w * qw;
-      }
-      if (DEG > 0 && a.g_sh) {
-        float* gs = a.g_sh + (size_t)K * 3 * g;
-        const float* c = a.sh + (size_t)K * 3 * g;
-        float Dl[kRotFloats];
-        const float* D = s_D + (k - k0) * kRotFloats;
-        if (k - k0 >= kLocalInst) {
-          sh_rotation<DEG>(R, Dl);
-          D = Dl;
-        }
+    }
+    if (live && a.g_quats) {
+      const float4 q = a.quats[g];
+      const float nq = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+      const float qw = q.x / nq, qx = q.y / nq, qy = q.z / nq, qz = q.w / nq;
+      const float np = sqrtf(qp.x * qp.x + qp.y * qp.y + qp.z * qp.z + qp.w * qp.w);
+      const float pw = qp.x / np, px = qp.y / np, py = qp.z / np, pz = qp.w / np;
+      const float4 G = a.g_quats[g];
+      // dq^ = p* (x) G, then through the normalisation of q
+      const float aw = pw * G.x + px * G.y + py * G.z + pz * G.w;
+      const float ax = pw * G.y - px * G.x - py * G.w + pz * G.z;
+      const float ay = pw * G.z + px * G.w - py * G.x - pz * G.y;
+      const float az = pw * G.w - px * G.z + py * G.y - pz * G.x;
+      const float dot = aw * qw + ax * qx + ay * qy + az * qz;
+      a.g_quats[g] = make_float4((aw - qw * dot) / nq, (ax - qx * dot) / nq, (ay - qy * dot) / nq,
+                                 (az - qz * dot) / nq);
+      // dp^ = G (x) q^*
+      t[12] = G.x * qw + G.y * qx + G.z * qy + G.w * qz;
+      t[13] = -G.x * qx + G.y * qw - G.z * qz + G.w * qy;
+      t[14] = -G.x * qy + G.y * qz + G.z * qw - G.w * qx;
+      t[15] = -G.x * qz - G.y * qy + G.z * qx + G.w * qw;
+    }
 #pragma unroll
-        for (int l = 1; l <= DEG; ++l) {
-          const int nb = 2 * l + 1, b = band_start(l);
-          float gw[7][3];
-          for (int j = 0; j < nb; ++j)
-            for (int ch = 0; ch < 3; ++ch) gw[j][ch] = gs[3 * (b + j) + ch];
-          for (int i = 0; i < nb; ++i) {
-            for (int j = 0; j < nb; ++j)
-              t[16 + rot_off(l) + i * nb + j] =
-                  c[3 * (b + i)] * gw[j][0] + c[3 * (b + i) + 1] * gw[j][1] + c[3 * (b + i) + 2] * gw[j][2];
-            for (int ch = 0; ch < 3; ++ch) {
-              float v = 0.f;
-              for (int j = 0; j < nb; ++j) v = fmaf(D[rot_off(l) + i * nb + j], gw[j][ch], v);
-              gs[3 * (b + i) + ch] = v;
+    for (int i = 0; i < 16; ++i) s_t[warp][lane][i] = t[i];
+    s_k[warp][lane] = k;
+    const int64_t wbase = base + warp * 32;
+    const int n_here = (int)max((int64_t)0, min((int64_t)32, a.n - wbase));
+    __syncwarp();
+    if (n_here > 0) {   // warp-uniform
+      const int k_lo = s_k[warp][0], k_hi = s_k[warp][n_here - 1];
+      if (rotate) {
+        stage_sh_rows<DEG>(crow, a.sh, (uint32_t)(wbase + lane), n_here, lane);
+        stage_sh_rows<DEG>(grow, a.g_sh, (uint32_t)(wbase + lane), n_here, lane);
+        __syncwarp();
+        // dD_l[i][j] = sum over the instance's Gaussians and channels of c_{b+i} dc'_{b+j}
+        for (int kk = k_lo; kk <= k_hi; ++kk) {
+          for (int e = (int)lane; e < E; e += 32) {
+            const int l = e < 9 ? 1 : (e < 34 ? 2 : 3);
+            const int nb = 2 * l + 1, idx = e - rot_off(l), i = idx / nb, j = idx - i * nb;
+            const int ci = 3 * (band_start(l) + i), cj = 3 * (band_start(l) + j);
+            float acc = 0.f;
+            for (int g2 = 0; g2 < n_here; ++g2) {
+              if (s_k[warp][g2] != kk) continue;
+              const float* cg = crow + g2 * St::kFloatPitch;
+              const float* gg = grow + g2 * St::kFloatPitch;
+              acc = fmaf(cg[ci], gg[cj], fmaf(cg[ci + 1], gg[cj + 1], fmaf(cg[ci + 2], gg[cj + 2], acc)));
             }
+            if (acc != 0.f) atomicAdd(a.acc + (size_t)kk * kWorldAcc + 16 + e, acc);
           }
         }
+        __syncwarp();
+        if (live) {
+          float gw[3 * K], o[3 * K];
+          float* row = grow + lane * St::kFloatPitch;
+          row_get<DEG>(row, gw);
+          float Dl[kRotFloats];
+          const float* D = s_D + (k - k0) * kRotFloats;
+          if (k - k0 >= kLocalInst) {
+            sh_rotation<DEG>(R, Dl);
+            D = Dl;
+          }
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) o[ch] = gw[ch];
+#pragma unroll
+          for (int l = 1; l <= DEG; ++l) {
+            const int nb = 2 * l + 1, b = band_start(l);
+#pragma unroll
+            for (int i = 0; i < nb; ++i)
+#pragma unroll
+              for (int ch = 0; ch < 3; ++ch) {
+                float v = 0.f;
+#pragma unroll
+                for (int j = 0; j < nb; ++j) v = fmaf(D[rot_off(l) + i * nb + j], gw[3 * (b + j) + ch], v);
+                o[3 * (b + i) + ch] = v;
+              }
+          }
+          row_put<DEG>(row, o);
+        }
+        __syncwarp();
+        unstage_sh_rows<DEG>(a.g_sh, grow, wbase, n_here, lane);
+      }
+      // dR, dt, dp: one lane per term, summed over the warp's Gaussians of each instance
+      for (int kk = k_lo; kk <= k_hi; ++kk) {
+        if (lane < 16) {
+          float v = 0.f;
+          for (int g2 = 0; g2 < n_here; ++g2)
+            if (s_k[warp][g2] == kk) v += s_t[warp][g2][lane];
+          if (v != 0.f) atomicAdd(a.acc + (size_t)kk * kWorldAcc + lane, v);
+        }
       }
     }
-    // sums over the warp where all its lanes belong to one instance (the
-    // common case: instances are contiguous runs of thousands), else per lane
-    const int k_lane0 = __shfl_sync(0xffffffffu, k, 0);
-    const bool uniform = __all_sync(0xffffffffu, k == k_lane0);
-    float* acc = a.acc + (size_t)k * kWorldAcc;
-#pragma unroll
-    for (int i = 0; i < kUsed; ++i) {
-      if (uniform) {
-        float v = t[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && v != 0.f) atomicAdd(acc + i, v);
-      } else if (live && t[i] != 0.f) {
-        atomicAdd(acc + i, t[i]);
-      }
-    }
-    __syncthreads();
+    __syncwarp();   // s_t, s_k and the staged rows are rewritten by the next chunk
   }
 }
 
@@ -356,6 +536,20 @@ __global__ void k_world_pose(WorldArgs a) {
 
 int world_acc_floats() { return kWorldAcc; }
 
+namespace {
+// CTAs of a world-transform launch: one resident wave (each CTA takes a
+// contiguous range of chunks), fewer for a small scene. The occupancy of each
+// kernel is queried once.
+int64_t world_grid(const void* fn, int* cache, int64_t n_rows, int num_sms) {
+  if (*cache == 0 &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(cache, fn, kWorldThreads, 0) != cudaSuccess || *cache < 1))
+    *cache = 1;
+  int64_t blocks = (n_rows + kWorldThreads - 1) / kWorldThreads;
+  if (blocks > (int64_t)num_sms * *cache) blocks = (int64_t)num_sms * *cache;
+  return blocks < 1 ? 1 : blocks;
+}
+}  // namespace
+
 cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* means_out,
                             float* quats_out, float* sh_out, int64_t n_dynamic, int num_sms,
                             cudaStream_t st) {
@@ -372,13 +566,24 @@ cudaError_t launch_to_world(const s3r_scene* sc, const s3r_poses* poses, float* 
   a.means_out = means_out;
   a.quats_out = reinterpret_cast<float4*>(quats_out);
   a.sh_out = sh_out;
-  int64_t blocks = (n_dynamic + kWorldThreads - 1) / kWorldThreads;
-  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+  static thread_local int occ[4] = {0, 0, 0, 0};
   switch (sc->sh_degree) {
-    case 0: k_to_world<0><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a); break;
-    case 1: k_to_world<1><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a); break;
-    case 2: k_to_world<2><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a); break;
-    default: k_to_world<3><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a); break;
+    case 0:
+      k_to_world<0><<<(unsigned)world_grid((const void*)k_to_world<0>, &occ[0], n_dynamic, num_sms),
+                      kWorldThreads, 0, st>>>(a);
+      break;
+    case 1:
+      k_to_world<1><<<(unsigned)world_grid((const void*)k_to_world<1>, &occ[1], n_dynamic, num_sms),
+                      kWorldThreads, 0, st>>>(a);
+      break;
+    case 2:
+      k_to_world<2><<<(unsigned)world_grid((const void*)k_to_world<2>, &occ[2], n_dynamic, num_sms),
+                      kWorldThreads, 0, st>>>(a);
+      break;
+    default:
+      k_to_world<3><<<(unsigned)world_grid((const void*)k_to_world<3>, &occ[3], n_dynamic, num_sms),
+                      kWorldThreads, 0, st>>>(a);
+      break;
   }
   return cudaGetLastError();
 }
@@ -401,25 +606,27 @@ cudaError_t launch_to_world_bwd(const s3r_scene* sc, const s3r_poses* poses, con
   a.acc = acc;
   a.g_pose_q = g->inst_quat;
   a.g_pose_t = g->inst_trans;
-  int64_t blocks = (n_dynamic + kWorldThreads - 1) / kWorldThreads;
-  if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
-  if (blocks < 1) blocks = 1;
   const unsigned pose_blocks = (unsigned)((sc->n_inst + 127) / 128);
+  static thread_local int occ[4] = {0, 0, 0, 0};
   switch (sc->sh_degree) {
     case 0:
-      k_to_world_bwd<0><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a);
+      k_to_world_bwd<0><<<(unsigned)world_grid((const void*)k_to_world_bwd<0>, &occ[0], n_dynamic, num_sms),
+                          kWorldThreads, 0, st>>>(a);
       k_world_pose<0><<<pose_blocks, 128, 0, st>>>(a);
       break;
     case 1:
-      k_to_world_bwd<1><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a);
+      k_to_world_bwd<1><<<(unsigned)world_grid((const void*)k_to_world_bwd<1>, &occ[1], n_dynamic, num_sms),
+                          kWorldThreads, 0, st>>>(a);
       k_world_pose<1><<<pose_blocks, 128, 0, st>>>(a);
       break;
     case 2:
-      k_to_world_bwd<2><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a);
+      k_to_world_bwd<2><<<(unsigned)world_grid((const void*)k_to_world_bwd<2>, &occ[2], n_dynamic, num_sms),
+                          kWorldThreads, 0, st>>>(a);
       k_world_pose<2><<<pose_blocks, 128, 0, st>>>(a);
       break;
     default:
-      k_to_world_bwd<3><<<(unsigned)blocks, kWorldThreads, 0, st>>>(a);
+      k_to_world_bwd<3><<<(unsigned)world_grid((const void*)k_to_world_bwd<3>, &occ[3], n_dynamic, num_sms),
+                          kWorldThreads, 0, st>>>(a);
       k_world_pose<3><<<pose_blocks, 128, 0, st>>>(a);
       break;
   }

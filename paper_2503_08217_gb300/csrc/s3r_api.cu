@@ -497,8 +497,8 @@ s3r_status s3r_to_world(const s3r_scene* scene, const s3r_poses* poses, float* m
   if (!aligned(scene->means, 4) || !aligned(means_out, 4) || !aligned(scene->quats, 16) ||
       !aligned(quats_out, 16))
     return fail(S3R_ERR_INVALID, "means 4-byte and quaternions 16-byte aligned required");
-  if (sh_out && (!scene->sh || !aligned(sh_out, 4)))
-    return fail(S3R_ERR_INVALID, "sh_out needs the scene's SH");
+  if (sh_out && (!scene->sh || !aligned(sh_out, 16) || !aligned(scene->sh, 16)))
+    return fail(S3R_ERR_INVALID, "sh_out needs the scene's SH, both 16-byte aligned");
   s3r_status st = check_poses(scene, poses);
   if (st != S3R_OK) return st;
   cudaError_t e = launch_to_world(scene, poses, means_out, quats_out, sh_out, scene->n, sm_count(),
@@ -515,8 +515,8 @@ s3r_status s3r_to_world_bwd(s3r_workspace* ws, const s3r_scene* scene, const s3r
   if ((st = check_poses(scene, poses)) != S3R_OK) return st;
   if (!grads) return fail(S3R_ERR_INVALID, "grads is NULL");
   if ((grads->quats && !aligned(grads->quats, 16)) || (grads->means && !aligned(grads->means, 4)) ||
-      (grads->sh && !aligned(grads->sh, 4)))
-    return fail(S3R_ERR_INVALID, "quaternion gradients must be 16-byte aligned");
+      (grads->sh && !aligned(grads->sh, 16)))
+    return fail(S3R_ERR_INVALID, "quaternion and SH gradients must be 16-byte aligned");
   if (scene->n == 0 || scene->n_inst == 0) return S3R_OK;
   DeviceGuard g(ws->device);
   cudaError_t e = launch_to_world_bwd(scene, poses, grads, ws->world_acc, scene->n, ws->num_sms,
