@@ -56,6 +56,7 @@ PARAMS = (
     Param("S3R_BLEND_BWD_BLOCKS", "k_blend.cu", (12, 16, 20), "resident blocks per SM, blend backward"),
     Param("S3R_SORT_ITEMS", "s3r_internal.cuh", (11, 15, 18), "keys per thread of a radix tile"),
     Param("S3R_SORT_BLOCKS", "s3r_internal.cuh", (2, 3, 4), "resident onesweep blocks per SM"),
+    Param("S3R_SORT_LOOKBACK", "k_sort.cu", (4, 8, 16), "look-back words read per round trip, onesweep"),
     Param("S3R_DUP_EXPAND_ITEMS", "k_sort.cu", (4, 8, 12), "pairs written per thread, expansion"),
     Param("S3R_PROJECT_MASK_BLOCKS", "k_project.cu", (4, 6, 8), "resident blocks per SM, projection mask"),
 )

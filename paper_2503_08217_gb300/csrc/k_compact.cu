@@ -147,27 +147,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
   const uint32_t lane = lane_id();
   const uint32_t tag = stage_tag(ctr[kCtrEpoch] + 1u, kStageCompact);
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= n_tiles) break;
+  // the windows of a tile: lane reads Gaussians 2 (32 r + lane) + {0, 1} of
+  // its warp's span, round r (one float4 per round)
+  auto load = [&](int64_t tile, float4 (&w)[kRounds]) {
     const int64_t g0 = tile * kTileSpan + (int64_t)warp * kWarpSpan;
-
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+      const int64_t g = g0 + 2 * (r * 32 + (int64_t)lane);
+      w[r] = make_float4(1.f, -1.f, 1.f, -1.f);  // empty windows
+      if (g + 1 < n) {
+        w[r] = __ldcs(reinterpret_cast<const float4*>(vis + 2 * g));
+      } else if (g < n) {
+        const float2 h = __ldcs(reinterpret_cast<const float2*>(vis + 2 * g));
+        w[r].x = h.x;
+        w[r].y = h.y;
+      }
+    }
+  };
+  if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
+  __syncthreads();
+  int64_t tile = s_tile;
+  float4 w[kRounds];
+  if (tile < n_tiles) load(tile, w);
+  // Per tile: ballots of the windows loaded, then the next tile's loads are
+  // issued before this tile's look-back and write-out, so that their latency
+  // overlaps them.
+  while (tile < n_tiles) {
+    const int64_t g0 = tile * kTileSpan + (int64_t)warp * kWarpSpan;
     uint32_t b0[kRounds], b1[kRounds];
     uint32_t count = 0;
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
-      const int64_t g = g0 + 2 * (r * 32 + (int64_t)lane);
-      float4 w = make_float4(1.f, -1.f, 1.f, -1.f);  // empty windows
-      if (g + 1 < n) {
-        w = __ldcs(reinterpret_cast<const float4*>(vis + 2 * g));
-      } else if (g < n) {
-        const float2 h = __ldcs(reinterpret_cast<const float2*>(vis + 2 * g));
-        w.x = h.x; w.y = h.y;
-      }
-      const bool f0 = (w.x <= t) && (t <= w.y);
-      const bool f1 = (w.z <= t) && (t <= w.w);
+      const bool f0 = (w[r].x <= t) && (t <= w[r].y);
+      const bool f1 = (w[r].z <= t) && (t <= w[r].w);
       b0[r] = __ballot_sync(0xffffffffu, f0);
       b1[r] = __ballot_sync(0xffffffffu, f1);
       count += __popc(b0[r]) + __popc(b1[r]);
@@ -182,7 +194,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
       sel_bits[(g0 >> 5) + lane] = interleave16(e >> sh, o >> sh);
     }
     if (lane == 0) s_warp[warp] = count;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
     __syncthreads();
+    const int64_t next = s_tile;
+    if (next < n_tiles) load(next, w);
     if (warp == 0) {
       const uint32_t c = lane < kWarps ? s_warp[lane] : 0u;
       uint32_t incl = c;
@@ -212,7 +227,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
       if (f1) sel[out + before + (f0 ? 1u : 0u)] = (uint32_t)(g + 1);
       out += __popc(b0[r]) + __popc(b1[r]);
     }
-    __syncthreads();  // s_tile / s_warp reuse
+    __syncthreads();  // s_tile / s_warp / s_base reuse
+    tile = next;
   }
   // the last CTA to finish does the call's set-up for the launches after it
   __threadfence();

@@ -186,6 +186,8 @@ __global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_m
 
 // First splat of every selected Gaussian: an exclusive scan of the kept-view
 // counts popc(keep_mask) in 4096-Gaussian tiles (block scan + warp look-back).
+// A thread owns 16 consecutive masks (four 128-bit loads and stores); the
+// next tile's masks are loaded before this tile's look-back.
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kThreads * kScanItems;
 
@@ -200,16 +202,31 @@ __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restr
   const uint32_t tag = stage_tag(ctr[kCtrEpoch], kStageProject);
   const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= n_tiles) break;
+  auto load = [&](int64_t tile, uint32_t (&m)[kScanItems]) {
+    const int64_t j0 = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    if (j0 + kScanItems <= (int64_t)n_sel) {
+      const uint4* p = reinterpret_cast<const uint4*>(keep_mask + j0);
+#pragma unroll
+      for (int q = 0; q < kScanItems / 4; ++q) {
+        const uint4 v = __ldg(p + q);
+        m[4 * q] = v.x; m[4 * q + 1] = v.y; m[4 * q + 2] = v.z; m[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kScanItems; ++i) m[i] = (j0 + i < (int64_t)n_sel) ? keep_mask[j0 + i] : 0u;
+    }
+  };
+  if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
+  __syncthreads();
+  int64_t tile = s_tile;
+  uint32_t m[kScanItems];
+  if (tile < n_tiles) load(tile, m);
+  while (tile < n_tiles) {
     const int64_t j0 = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t c[kScanItems], run = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-      c[i] = (j0 + i < (int64_t)n_sel) ? (uint32_t)__popc(keep_mask[j0 + i]) : 0u;
+      c[i] = (uint32_t)__popc(m[i]);
       run += c[i];
     }
     uint32_t incl = run;
@@ -219,7 +236,10 @@ __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restr
       if (lane >= (uint32_t)o) incl += y;
     }
     if (lane == 31) s_warp[warp] = incl;
+    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
     __syncthreads();
+    const int64_t next = s_tile;
+    if (next < n_tiles) load(next, m);
     if (warp == 0) {
       const uint32_t wc = lane < kWarps ? s_warp[lane] : 0u;
       uint32_t wi = wc;
@@ -238,12 +258,23 @@ __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restr
     }
     __syncthreads();
     uint32_t off = s_base + s_warp[warp] + incl - run;
+    uint32_t o[kScanItems];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-      if (j0 + i < (int64_t)n_sel) splat_start[j0 + i] = off;
+      o[i] = off;
       off += c[i];
     }
+    if (j0 + kScanItems <= (int64_t)n_sel) {
+      uint4* p = reinterpret_cast<uint4*>(splat_start + j0);
+#pragma unroll
+      for (int q = 0; q < kScanItems / 4; ++q) p[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kScanItems; ++i)
+        if (j0 + i < (int64_t)n_sel) splat_start[j0 + i] = o[i];
+    }
     __syncthreads();
+    tile = next;
   }
 }
 

@@ -21,6 +21,13 @@ namespace {
 
 constexpr int kWarps = kSortThreads / 32;
 constexpr int kWarpKeys = kSortItems * 32;   // keys per warp per tile
+// Predecessor words a digit's look-back reads per round trip (build-time
+// define the autotuner varies).
+#ifndef S3R_SORT_LOOKBACK
+#define S3R_SORT_LOOKBACK 8
+#endif
+constexpr int kSortLookback = S3R_SORT_LOOKBACK;
+static_assert(kSortLookback >= 1 && kSortLookback <= 64, "look-back batch of 1..64 words");
 
 struct PassArgs {
   const uint32_t* keys_in;
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
 
     uint32_t prefix = 0;
     if (tile > 0) {
-      prefix = lookback_walk(a.lookback + d_me, kRadix, tile, tag, a.ctr);
+      prefix = lookback_walk<kSortLookback>(a.lookback + d_me, kRadix, tile, tag, a.ctr);
       lookback_publish(a.lookback + d_me, kRadix, tile, tag, 2u, prefix + tile_cnt);
     }
     s_dst[d_me] = s_gbase[d_me] + prefix - loc;
@@ -476,21 +483,28 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
   const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
   const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
-  for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
-    __syncthreads();
-    const int64_t tile = s_tile;
-    if (tile >= n_tiles) break;
+  // a tile's sorted splat ids and their tile records (gathered by id)
+  uint32_t sp[kDupPer];
+  uint4 r0[kDupPer], r1[kDupPer];
+  auto load = [&](int64_t tile) {
     const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
-    uint32_t sp[kDupPer], cnt[kDupPer], run = 0;
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) sp[k] = i0 + k < n ? a.sorted_splats[i0 + k] : 0u;
-    uint4 r0[kDupPer], r1[kDupPer];
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
       r0[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k]] : make_uint4(0u, 0u, 0u, 0u);
       r1[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k] + 1] : make_uint4(0u, 0u, 0u, 0u);
     }
+  };
+  if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
+  __syncthreads();
+  int64_t tile = s_tile;
+  if (tile < n_tiles) load(tile);
+  // per tile: the records in depth order and the counts, then the next
+  // tile's gathers are issued before this tile's scan and look-back
+  while (tile < n_tiles) {
+    const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
+    uint32_t cnt[kDupPer], run = 0;
 #pragma unroll
     for (int k = 0; k < kDupPer; ++k) {
       cnt[k] = min(r0[k].x, kSat);
@@ -500,8 +514,11 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
         a.dup_meta[2 * (i0 + k) + 1] = r1[k];
       }
     }
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
     uint32_t total;
-    uint32_t ex = block_excl_scan_sat(run, s_tmp, &total);
+    uint32_t ex = block_excl_scan_sat(run, s_tmp, &total);   // synchronises
+    const int64_t next = s_tile;
+    if (next < n_tiles) load(next);
     if (threadIdx.x < 32) {
       const uint32_t prefix = warp_lookback<true>(a.lookback, tile, tag, total, a.ctr);
       if (threadIdx.x == 0) {
@@ -534,6 +551,7 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
       a.dup_chunk[(tot + kExpChunk - 1) / kExpChunk] = (uint32_t)(n - 1);
     }
     __syncthreads();
+    tile = next;
   }
 }
 

@@ -282,6 +282,7 @@ __device__ __forceinline__ void lookback_publish(unsigned long long* words, int6
   st_relaxed(words + tile * stride, lb_word(tag, flag, value));
 }
 
+template <int kBatch = kLookbackBatch>
 __device__ __forceinline__ uint32_t lookback_walk(unsigned long long* words, int64_t stride,
                                                   int64_t tile, uint32_t tag, uint32_t* ctr,
                                                   int max_polls = kSpinLimit) {
@@ -289,15 +290,15 @@ __device__ __forceinline__ uint32_t lookback_walk(unsigned long long* words, int
   int64_t k = tile - 1;
   int spins = 0;
   while (k >= 0) {
-    unsigned long long w[kLookbackBatch];
+    unsigned long long w[kBatch];
 #pragma unroll
-    for (int j = 0; j < kLookbackBatch; ++j)
+    for (int j = 0; j < kBatch; ++j)
       w[j] = k - j >= 0 ? ld_relaxed(words + (k - j) * stride) : lb_word(tag, 2u, 0u);
     uint32_t acc = 0;
     int used = 0;
     bool stop = false, done = false;
 #pragma unroll
-    for (int j = 0; j < kLookbackBatch; ++j) {
+    for (int j = 0; j < kBatch; ++j) {
       const uint32_t flag = (uint32_t)(w[j] >> 34) == tag ? (uint32_t)(w[j] >> 32) & 3u : 0u;
       const bool take = !stop && flag != 0u;
       acc += take ? (uint32_t)w[j] : 0u;
