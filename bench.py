@@ -109,6 +109,8 @@ WORKLOADS = {
     "tiny": ("tiny", {}, 0.0, "tiny corridor: 20k static + 2x1k dynamic, SH0, one 320x192 camera"),
     "small-rig": ("rig", {"n_static": 1_500_000, "n_inst": 16, "n_steps": 60}, 1.0,
                   "profiling case: the surround rig on a 1.5M-Gaussian corridor"),
+    "ode": ("train", {}, 1.0, "NeuralODE poses of the training corridor's 120 instances over its "
+            "400 timesteps (embedding width 8, RK4 with 2 substeps): forward and reverse mode"),
     "train": ("train", {}, 1.0, "training steps on the 2 km corridor: 16M static + 120 instances of "
               "U{5k..20k}, SH3, the 7-camera surround rig, Adam on every parameter and pose"),
 }
@@ -818,6 +820,81 @@ def run_train(args, rank, world, local):
         }), flush=True)
 
 
+def run_ode(args):
+    """NeuralODE object poses (Sec. 3.2, Eqs. 3-4) at the training
+    configuration's size: 120 instances, 400 output times, embedding width 8,
+    two RK4 substeps per interval (798 steps per instance). One step = the
+    forward (states, quaternions, translations at every output time) and the
+    reverse mode from synthetic pose adjoints, graph-captured; the forward is
+    also timed alone. The FP32 operation count is the three matrix products
+    of f per stage (FMA = 2 operations) times four stages per step; the
+    reverse mode recomputes each step's stages and back-propagates through
+    them (about three times the forward's products). One warp per instance
+    walks its steps in sequence, so the work is latency-bound, not ALU-bound."""
+    import torch
+    from paper_2503_08217_gb300 import binding, build, scenegen
+    build.build()
+    binding.load()
+    torch.cuda.set_device(0)
+    K, D, T, S, H = 120, 8, 400, 2, 64
+    params, embed, z0 = scenegen.ode_model(args.seed, K, D)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+    params, embed, z0 = cu(params), cu(embed), cu(z0)
+    times = torch.linspace(-1.0, 1.0, T, device="cuda")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    gq = torch.randn((T, K, 4), device="cuda", generator=gen)
+    gt = torch.randn((T, K, 3), device="cuda", generator=gen)
+    g_p = torch.zeros_like(params)
+    g_e = torch.zeros_like(embed)
+    g_z = torch.zeros_like(z0)
+    out = {}
+
+    def fwd():
+        out["s"] = binding.ode_poses(params, embed, z0, times, S)
+
+    def both():
+        fwd()
+        binding.ode_poses_bwd(params, embed, times, S, out["s"][0], gq, gt, g_p, g_e, g_z)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a_, b_ in ev:
+            a_.record()
+            g.replay()
+            b_.record()
+        torch.cuda.synchronize()
+        return float(np.mean([a_.elapsed_time(b_) for a_, b_ in ev]))
+
+    ms_fwd = timed(fwd)
+    ms_both = timed(both)
+    steps = (T - 1) * S
+    f_ops = 2 * (H * (7 + D) + H * H + 6 * H)          # FP32 operations of one evaluation of f
+    fwd_ops = K * steps * 4 * f_ops
+    ops = 4 * fwd_ops                                    # forward + reverse (recompute + adjoint)
+    peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * measured_peaks()[2] * 1e6
+    print(json.dumps({
+        "metric": "NeuralODE poses fwd+bwd ms (Eqs. 3-4)", "value": round(ms_both, 4), "unit": "ms",
+        "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "data": "synthetic", "forward_ms": round(ms_fwd, 4),
+        "config": {"workload": "ode: " + WORKLOADS["ode"][3], "instances": K, "output_times": T,
+                   "substeps": S, "rk4_steps_per_instance": steps, "hidden": H, "embed_dim": D},
+        "roofline": {"bound": "latency (one warp per instance, sequential steps)",
+                     "achieved_gops": round(ops / (ms_both / 1e3) / 1e9, 1),
+                     "alu_peak_gops": round(peak / 1e9, 1),
+                     "frac": round(ops / (ms_both / 1e3) / peak, 4)},
+    }), flush=True)
+
+
 def cpu_oracle_sample(scene, k, lod, vis_np):
     """The FP64 oracle, as it stands, on a bounded sample of the same
     workload: one camera (the smallest of the rig) at the same timestep over
@@ -1033,6 +1110,10 @@ def main():
         return
     if args.workload == "train":
         run_train(args, rank, world, local)
+        return
+    if args.workload == "ode":
+        if rank == 0:
+            run_ode(args)
         return
     if world > 1:
         import torch

@@ -422,6 +422,9 @@ __device__ __forceinline__ void fwd_splat(const float4 q0, const float4 q1, cons
                                           f2 (&C2)[2][3], int (&last)[kBandPix],
                                           int (&endp)[kBandPix], bool (&done)[kBandPix],
                                           uint32_t& n_eval, bool& any_blend) {
+  // a blended pixel takes alpha >= 1/255 > 0, a skipped one 0: the splat was
+  // blended somewhere in the lane's pixels iff the applied alphas sum above 0
+  f2 ab_sum = pk(0.f, 0.f);
   const f2 A2 = pk(q0.x, q0.y), B2 = pk(q0.z, q0.w), C2c = pk(q1.x, q1.y), O2 = pk(q1.z, q1.w);
   const f2 R2 = pk(q2.x, q2.y), G2 = pk(q2.z, q2.w), Bl2 = pk(q3.x, q3.y), V2 = pk(q3.z, q3.w);
   const f2 U2 = pk(qu.x, qu.y);
@@ -460,15 +463,18 @@ __device__ __forceinline__ void fwd_splat(const float4 q0, const float4 q1, cons
       last[k] = blend[r] ? pos : last[k];
       if constexpr (kCount) endp[k] = stop ? pos : endp[k];
       done[k] = done[k] || stop;
-      any_blend = any_blend || blend[r];
     }
     const f2 AB = pk(ab[0], ab[1]);
+    ab_sum = add2(ab_sum, AB);
     const f2 w = mul2(AB, T2[c]);
     C2[c][0] = fma2(R2, w, C2[c][0]);
     C2[c][1] = fma2(G2, w, C2[c][1]);
     C2[c][2] = fma2(Bl2, w, C2[c][2]);
     T2[c] = mul2(T2[c], sub2(ONE, AB));
   }
+  float s0, s1;
+  upk(ab_sum, s0, s1);
+  any_blend = s0 + s1 > 0.f;
 }
 
 // S3R_BLEND_FWD_BLOCKS: 20 blocks per SM (48 registers, a small spill)
@@ -528,6 +534,9 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
     }
     uint32_t* wbits = a.contrib + warp * a.contrib_words;
     for (int b0 = 0; b0 < n; b0 += kBatchFwd) {
+      // the pixels' done flags are folded once per chunk and batch, not per splat
+  #pragma unroll
+      for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
       if (__syncthreads_count(all_done) == kBandThreads) break;
       for (int i = threadIdx.x; i < kBatchFwd && b0 + i < n; i += kBandThreads) {
         const uint32_t s = a.sorted_splats[range.x + b0 + i];
@@ -547,6 +556,9 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
       __syncthreads();
       const int m = min(kBatchFwd, n - b0);
       for (int c0 = 0; c0 < m; c0 += 32) {
+        all_done = true;
+  #pragma unroll
+        for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
         if (__all_sync(0xffffffffu, all_done)) break;
         // which of the next 32 splats can reach alpha >= 1/255 in this warp's band
         const int jl = c0 + (int)lane;
@@ -573,9 +585,6 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
           else
             fwd_splat<kCount, false>(q0, q1, q2, q3, qu, FY, FX, ONE, pos, T2, C2, last, endp, done,
                                      n_eval, any_blend);
-          all_done = true;
-  #pragma unroll
-          for (int k = 0; k < kBandPix; ++k) all_done = all_done && done[k];
           if (__any_sync(0xffffffffu, any_blend)) blended |= 1u << (j - c0);
         }
         if (lane == 0 && blended) or_bits(wbits, range.x + b0 + c0, blended);

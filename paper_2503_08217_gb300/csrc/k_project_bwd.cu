@@ -115,36 +115,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_project_bwd(const __grid_consta
   // consecutive work-list entries
   const uint32_t n_kept = a.ctr[kCtrKept];
   const uint32_t epoch = a.ctr[kCtrEpoch];
-  for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < (int64_t)n_kept;
-       base += (int64_t)gridDim.x * kThreads) {
+  // software pipeline over the warp's batches: the next batch's work-list
+  // entry is loaded one batch ahead, and a batch's mask, splat offset and
+  // geometry loads are issued together with its SH staging
+  const int64_t stride = (int64_t)gridDim.x * kThreads;
+  int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32;
+  uint2 kept_next = base + lane < (int64_t)n_kept ? a.kept_list[base + lane] : make_uint2(0u, 0u);
+  for (; base < (int64_t)n_kept; base += stride) {
     const int n_here = (int)min((int64_t)32, (int64_t)n_kept - base);
     const bool valid = lane < (uint32_t)n_here;
-    const uint2 kept = valid ? a.kept_list[base + lane] : make_uint2(0u, 0u);
+    const uint2 kept = kept_next;
+    kept_next = base + stride + lane < (int64_t)n_kept ? a.kept_list[base + stride + lane]
+                                                       : make_uint2(0u, 0u);
     const uint32_t j = kept.x, gid = kept.y;
+    uint32_t kmask = 0u, s0 = 0u;
+    float mu[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, ol = 0.f;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (valid) {
+      kmask = a.keep_mask[j];
+      s0 = a.splat_start[j];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        mu[c] = a.means[3 * (size_t)gid + c];
+        ls[c] = a.log_scales[3 * (size_t)gid + c];
+      }
+      q = a.quats[gid];
+      ol = a.opac_logits[gid];
+    }
     stage_sh_rows<DEG>(my_sh, a.sh_f, gid, n_here, lane);
     __syncwarp();
-    const uint32_t kmask = valid ? a.keep_mask[j] : 0u;
     float g_sh[K * 3];
 #pragma unroll
     for (int i = 0; i < K * 3; ++i) g_sh[i] = 0.f;
     if (kmask) {
     const int k = segment_of(s_off, a.n_inst, gid);
-    const uint32_t s0 = a.splat_start[j];
     uint32_t s = s0;
 
-    const float mu[3] = {a.means[3 * (size_t)gid], a.means[3 * (size_t)gid + 1],
-                         a.means[3 * (size_t)gid + 2]};
-    const float sc[3] = {__expf(a.log_scales[3 * (size_t)gid]),
-                         __expf(a.log_scales[3 * (size_t)gid + 1]),
-                         __expf(a.log_scales[3 * (size_t)gid + 2])};
-    const float4 q = a.quats[gid];
+    const float sc[3] = {__expf(ls[0]), __expf(ls[1]), __expf(ls[2])};
     float R[9], RS[9];
     quat_to_rot(q, R);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) RS[3 * r + c] = R[3 * r + c] * sc[c];
-    const float opac = 1.f / (1.f + __expf(-a.opac_logits[gid]));
+    const float opac = 1.f / (1.f + __expf(-ol));
     const volatile float* sh = row_sh;   // re-read per use: keeps 48 values out of registers
 
     float g_mu[3] = {0.f, 0.f, 0.f}, g_RS[9];
