@@ -1063,7 +1063,7 @@ cudaError_t launch_render_bwd(s3r_workspace* ws, const float* bg, const float* d
   BlendArgs a = make_args(ws);
   a.bg = bg;
   a.dL = dL;
-  // the splat adjoints start at zero: cleared by the forward's tail, or here
+  // the splat adjoints start at zero: cleared by the forward (chunks in its queue), or here
   // when a backward has used them since
   if (!ws->sp_grad_clean) {
     KernelTimer timer(ws, kKZeroGrads, st);
