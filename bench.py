@@ -46,8 +46,8 @@ METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM r
 # hash), so that a comment edit keeps the figure and any code edit drops it
 # (the roofline line then reports traffic null).
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 1983652608, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
-                  "code_sha256_16": "329d0bb78f3fc65b", "profile": "profiles/blend_bwd_traffic_rig.md"},
+    "blend_bwd": {"bytes": 1982031104, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
+                  "code_sha256_16": "67c2b83145c2647f", "profile": "profiles/blend_bwd_traffic_rig.md"},
 }
 
 

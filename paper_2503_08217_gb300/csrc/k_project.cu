@@ -4,13 +4,15 @@
 // "Adaptive LOD"), SH colour, and the compaction of the kept (Gaussian, view)
 // pairs ("splats") into a dense, ordered array.
 //
-// One persistent CTA per SM slot. Each CTA first composes all instance
-// matrices W_t W_{t,i2g} of all views into shared memory (a few hundred 3x4
-// products), then loops over tiles of 256 selected Gaussians taken from an
-// atomic counter. Per Gaussian (one thread) the 44 geometry bytes are read
-// once for all views; pass 1 computes the frustum/keep masks, a block scan
-// plus decoupled look-back gives the splat offsets, pass 2 recomputes the kept
-// views, loads the SH coefficients (16-B vector loads) and writes the splats.
+// Three kernels. The mask pass: one thread per selected Gaussian reads its 44
+// geometry bytes once and tests every camera (a conservative pre-test, then
+// the full projection for the candidates) through the composed matrices W_t
+// W_{t,i2g} (written by the compaction's first CTAs, read through L1); it
+// writes the frustum and keep masks, applies Eq. 5 and appends the kept
+// Gaussians to a work list. The splat-offset scan: block scan plus decoupled
+// look-back over the kept-view counts. The splat writer: per kept Gaussian,
+// its kept views again, SH colour (the warp's SH rows staged through shared
+// memory with coalesced 16-B loads) and the splat records.
 #include "s3r_math.cuh"
 
 namespace s3r {
@@ -51,7 +53,7 @@ struct ProjArgs {
   uint32_t* ctr;
   unsigned long long* lookback;
   int64_t cap_splats;
-  const InstMat* mats;      // [n_views][n_inst+1], from k_compose
+  const InstMat* mats;      // [n_views][n_inst+1], composed by the compaction
 };
 
 // Pass 1: every selected Gaussian against every camera. Writes the frustum

@@ -13,8 +13,8 @@
 // read, and their adjoints added, through shared memory with coalesced
 // accesses of the whole warp.
 // Adjoints of the composed 3x4 matrices are summed per (view, instance) in
-// shared memory and flushed once per CTA; a tiny kernel then maps them to the
-// pose: dP = V_rot^T dW, and through R(q) to (dq, dt).
+// shared memory and flushed once per CTA; the last CTA to finish then maps
+// them to the pose: dP = V_rot^T dW, and through R(q) to (dq, dt).
 #include "s3r_math.cuh"
 
 namespace s3r {
@@ -45,7 +45,7 @@ struct BwdArgs {
   uint32_t* ctr;
   float* pose_dM;          // [n_views][n_inst+1][12]
   s3r_grads g;
-  const InstMat* mats;     // from the forward's k_compose (same poses)
+  const InstMat* mats;     // composed by the forward's compaction (same poses)
   int overwrite;           // S3R_GRAD_OVERWRITE: write the rows instead of adding to them
 };
 

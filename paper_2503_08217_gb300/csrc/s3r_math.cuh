@@ -10,7 +10,7 @@ namespace s3r {
 // Composed instance matrix W_{t,i} = W_t W_{t,i2g} (3x4, row-major, rows
 // [A | b]) and the camera centre in the instance's frame, c = -A^{-1} b, as an
 // unevaluated sum c_hi + c_lo of two floats. Both are computed in FP64 once per
-// call (k_compose). Camera-space positions are evaluated as
+// call (by the compaction's first CTAs). Camera-space positions are evaluated as
 // A ((mu - c_hi) - c_lo): for Gaussians near the camera mu - c_hi is exact
 // (Sterbenz), so positions far from the world origin do not lose their
 // camera-relative precision the way A mu + b does.
@@ -65,13 +65,6 @@ __device__ __forceinline__ void cam_pos(const InstMat& M, const float d[3], floa
   x = fmaf(M.m[0], d[0], fmaf(M.m[1], d[1], M.m[2] * d[2]));
   y = fmaf(M.m[4], d[0], fmaf(M.m[5], d[1], M.m[6] * d[2]));
   z = fmaf(M.m[8], d[0], fmaf(M.m[9], d[1], M.m[10] * d[2]));
-}
-
-// Copy the composed matrices of the call from global to shared memory.
-__device__ __forceinline__ void load_mats(const InstMat* __restrict__ g, InstMat* s, int count) {
-  const float4* src = reinterpret_cast<const float4*>(g);
-  float4* dst = reinterpret_cast<float4*>(s);
-  for (int i = threadIdx.x; i < count * (int)(sizeof(InstMat) / 16); i += blockDim.x) dst[i] = src[i];
 }
 
 // Segment (0 = static, k = instance k) of Gaussian `gid` from the offsets.
