@@ -106,15 +106,22 @@ __device__ __forceinline__ void eval_f(const SW& w, int I, const float (&z)[6], 
     for (int d = 0; d < D; ++d) a = fmaf(w.W1t[(7 + d) * kH + u], c[d], a);
     h1[q] = tanhf(a);
   }
-  float a0 = w.b2[lane], a1 = w.b2[lane + 32];
-#pragma unroll 8
-  for (int j = 0; j < kH; ++j) {
-    const float hj = __shfl_sync(0xffffffffu, h1[j >> 5], j & 31);
-    a0 = fmaf(w.W2t[j * kH + lane], hj, a0);
-    a1 = fmaf(w.W2t[j * kH + lane + 32], hj, a1);
+  // four partial sums per output (inputs j = 4 i + p), so that the chain of
+  // dependent FMAs is 16 long instead of 64: the products are latency-bound
+  // (one warp per instance walks its steps in sequence)
+  float a0[4] = {w.b2[lane], 0.f, 0.f, 0.f}, a1[4] = {w.b2[lane + 32], 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int i = 0; i < kH / 4; ++i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * i + q;
+      const float hj = __shfl_sync(0xffffffffu, h1[j >> 5], j & 31);
+      a0[q] = fmaf(w.W2t[j * kH + lane], hj, a0[q]);
+      a1[q] = fmaf(w.W2t[j * kH + lane + 32], hj, a1[q]);
+    }
   }
-  h2[0] = tanhf(a0);
-  h2[1] = tanhf(a1);
+  h2[0] = tanhf((a0[0] + a0[1]) + (a0[2] + a0[3]));
+  h2[1] = tanhf((a1[0] + a1[1]) + (a1[2] + a1[3]));
 #pragma unroll
   for (int o = 0; o < 6; ++o)
     out[o] = w.b3[o] + warp_sum(fmaf(w.W3[o * kH + lane], h2[0], w.W3[o * kH + lane + 32] * h2[1]));
@@ -281,16 +288,23 @@ __device__ __forceinline__ void vjp_f(const SW& w, const Acc& g, int I, const fl
   g.b2[lane + 32] += p2[1];
   // dW2[u][j] += p2[u] h1[j] (lane owns rows u = l, l + 32); hb1[j] = sum_u W2[u][j] p2[u]
   // (lane owns columns j = l, l + 32)
-  float hb1[2] = {0.f, 0.f};
-#pragma unroll 8
-  for (int m = 0; m < kH; ++m) {
-    const float h1m = __shfl_sync(0xffffffffu, h1[m >> 5], m & 31);
-    const float p2m = __shfl_sync(0xffffffffu, p2[m >> 5], m & 31);
-    g.W2t[m * kH + lane] += p2[0] * h1m;
-    g.W2t[m * kH + lane + 32] += p2[1] * h1m;
-    hb1[0] = fmaf(w.W2[m * kH + lane], p2m, hb1[0]);
-    hb1[1] = fmaf(w.W2[m * kH + lane + 32], p2m, hb1[1]);
+  // (four partial sums per column, as in eval_f, to shorten the FMA chain)
+  float hb1a[4] = {0.f, 0.f, 0.f, 0.f}, hb1b[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+  for (int i = 0; i < kH / 4; ++i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = 4 * i + q;
+      const float h1m = __shfl_sync(0xffffffffu, h1[m >> 5], m & 31);
+      const float p2m = __shfl_sync(0xffffffffu, p2[m >> 5], m & 31);
+      g.W2t[m * kH + lane] += p2[0] * h1m;
+      g.W2t[m * kH + lane + 32] += p2[1] * h1m;
+      hb1a[q] = fmaf(w.W2[m * kH + lane], p2m, hb1a[q]);
+      hb1b[q] = fmaf(w.W2[m * kH + lane + 32], p2m, hb1b[q]);
+    }
   }
+  const float hb1[2] = {(hb1a[0] + hb1a[1]) + (hb1a[2] + hb1a[3]),
+                        (hb1b[0] + hb1b[1]) + (hb1b[2] + hb1b[3])};
   const float p1[2] = {hb1[0] * (1.f - h1[0] * h1[0]), hb1[1] * (1.f - h1[1] * h1[1])};
   g.b1[lane] += p1[0];
   g.b1[lane + 32] += p1[1];
