@@ -522,7 +522,11 @@ def test_gradient_overwrite_equals_accumulation(built, sh_degree):
         a, b = 0.5 * acc[k].double().cpu().numpy(), ovw[k].double().cpu().numpy()
         assert not np.isnan(b).any(), k
         scale = max(np.abs(a).max(), 1e-30)
-        np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-5 * scale, err_msg=k)
+        # the per-splat sums are float atomics in a different order in each
+        # call: a large splat's rotation gradient sums thousands of per-tile
+        # terms that cancel, so its rounding is relative to the buffer's
+        # scale, not to the element
+        np.testing.assert_allclose(b, a, rtol=1e-4, atol=5e-5 * scale, err_msg=k)
         if k not in ("inst_quat", "inst_trans"):
             assert (b.reshape(sc.n, -1)[~kept] == 0).all(), k
             assert (np.abs(b.reshape(sc.n, -1)[kept]).sum(1) > 0).mean() > 0.5, k
