@@ -464,7 +464,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_sat(uint32_t x, uint32_t* s_
   __syncthreads();
   uint32_t wbase = 0, tot = 0;
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
+  for (int w = 0; w < kDupThreads / 32; ++w) {
     const uint32_t c = s_tmp[w];
     if (w < warp) wbase = sat_add(wbase, c);
     tot = sat_add(tot, c);
@@ -478,7 +478,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_sat(uint32_t x, uint32_t* s_
 // real pair count of 2^32 or more cannot wrap into a small one: it latches
 // the capacity status like any other overflow.
 __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
-  __shared__ uint32_t s_tmp[8];
+  __shared__ uint32_t s_tmp[kDupThreads / 32];
   __shared__ uint32_t s_tile, s_base;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
   const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
