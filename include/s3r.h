@@ -356,7 +356,7 @@ s3r_status s3r_set_counting(s3r_workspace* ws, int32_t enable);
  * give-up latches a timeout into the workspace status instead of hanging.
  * This call makes both look-back waits run out on purpose: one warp waits,
  * as tile 1, on a tile-0 word that nothing publishes, giving up after
- * `max_polls` polls (1 .. S3R_MAX_PROBE_POLLS; each poll sleeps ~20-30 ns, so
+ * `max_polls` polls (1 .. S3R_MAX_PROBE_POLLS; each poll sleeps ~20-40 ns, so
  * at most a few tens of milliseconds). Asynchronous on `stream`; the next
  * s3r_sync_status returns S3R_ERR_TIMEOUT and clears the status, and the
  * workspace stays usable (the hook writes only four look-back words that no

@@ -2,11 +2,13 @@
 // Gaussians whose visibility window [v_s, v_e] contains t, as one streaming
 // pass over the record.
 //
-// Each warp owns 512 consecutive Gaussians and reads them as 8 rounds of
-// 128-bit loads (one float4 = two (v_s, v_e) pairs per lane). A warp ballot
-// per round gives every selected Gaussian its rank; a block scan over the 8
-// warps and a single-pass decoupled look-back over tiles give the global
-// offset, so the output is written once, in order, coalesced.
+// A tile is 4096 consecutive Gaussians; each warp owns 512 of them and reads
+// them as 8 rounds of 128-bit loads (one float4 = two (v_s, v_e) pairs per
+// lane). A warp ballot per round gives every selected Gaussian its rank. A
+// CTA takes a chunk of consecutive tiles, keeps their ballots in shared
+// memory, and gets the chunk's global offset from the counts that all earlier
+// chunks published (chunk_prefix), so the output is written once, in order,
+// coalesced.
 #include <mutex>
 #include <string>
 
@@ -20,6 +22,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRounds = 8;                            // float4 loads per lane
 constexpr int kWarpSpan = kRounds * 32 * 2;           // Gaussians per warp
 constexpr int kTileSpan = kWarps * kWarpSpan;         // 4096 Gaussians per tile
+constexpr int kChunkTiles = kThreads / kWarps;        // tiles a CTA holds (one offset per thread)
 
 // W_v * P_k for every segment k of view v (k = 0: identity pose), and the
 // camera centre in the segment's frame, computed in FP64 once per call; the
@@ -128,18 +131,29 @@ __device__ void call_setup_last(uint32_t* ctr, unsigned long long* lookback, con
     for (int64_t i = threadIdx.x; i < c.lookback_words; i += blockDim.x) lookback[i] = 0ull;
 }
 
+// The tiles are dealt out in chunks of `per` consecutive tiles, one chunk per
+// claim of the CTA counter. A CTA streams its chunk's windows, keeping the
+// ballots (one bit per Gaussian) in shared memory, publishes the chunk's
+// count, sums the counts of ALL earlier chunks at once (its 256 threads read
+// them in parallel: one round trip, where a walk back over the tiles in
+// flight took one dependent round trip per 32 tiles) and then writes its
+// indices from the ballots. A chunk only waits for chunks claimed before it,
+// whose CTAs are running, so no residency assumption is needed.
+//
 // sel_bits (may be null): bit i of word i / 32 set iff Gaussian i is
 // selected; every word of every tile is written (zeros past n).
 __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__ ViewSet vs,
                                                       const float* __restrict__ vis, int64_t n,
-                                                      float t, uint32_t* __restrict__ sel,
+                                                      float t, int per,
+                                                      uint32_t* __restrict__ sel,
                                                       uint32_t* ctr,
                                                       unsigned long long* lookback,
                                                       uint32_t* __restrict__ sel_bits,
                                                       const CallSetup setup) {
-  __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_warp[kWarps];
-  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_bits[kChunkTiles][kWarps][2 * kRounds];   // ballots of the chunk
+  __shared__ uint32_t s_off[kChunkTiles * kWarps];   // per (tile, warp): count -> offset in chunk
+  __shared__ uint32_t s_tmp[kWarps];
+  __shared__ uint32_t s_chunk;
   __shared__ bool s_last;
   for (int v = blockIdx.x; v < setup.n_views; v += gridDim.x)
     compose_view(vs, v, setup.pose_q, setup.pose_t, setup.n_inst, setup.mats);
@@ -147,6 +161,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
   const uint32_t lane = lane_id();
   const uint32_t tag = stage_tag(ctr[kCtrEpoch] + 1u, kStageCompact);
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
+  const int64_t n_chunks = (n_tiles + per - 1) / per;
   // the windows of a tile: lane reads Gaussians 2 (32 r + lane) + {0, 1} of
   // its warp's span, round r (one float4 per round)
   auto load = [&](int64_t tile, float4 (&w)[kRounds]) {
@@ -164,71 +179,87 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
       }
     }
   };
-  if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
-  __syncthreads();
-  int64_t tile = s_tile;
-  float4 w[kRounds];
-  if (tile < n_tiles) load(tile, w);
-  // Per tile: ballots of the windows loaded, then the next tile's loads are
-  // issued before this tile's look-back and write-out, so that their latency
-  // overlaps them.
-  while (tile < n_tiles) {
-    const int64_t g0 = tile * kTileSpan + (int64_t)warp * kWarpSpan;
-    uint32_t b0[kRounds], b1[kRounds];
-    uint32_t count = 0;
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-      const bool f0 = (w[r].x <= t) && (t <= w[r].y);
-      const bool f1 = (w[r].z <= t) && (t <= w[r].w);
-      b0[r] = __ballot_sync(0xffffffffu, f0);
-      b1[r] = __ballot_sync(0xffffffffu, f1);
-      count += __popc(b0[r]) + __popc(b1[r]);
-    }
-    if (sel_bits && lane < 2 * kRounds) {
-      // round r covers Gaussians g0 + 64 r .. + 63: two words, lanes 2r and 2r + 1
-      uint32_t e = 0, o = 0;
-#pragma unroll
-      for (int r = 0; r < kRounds; ++r)
-        if ((int)(lane >> 1) == r) { e = b0[r]; o = b1[r]; }
-      const uint32_t sh = (lane & 1u) * 16u;
-      sel_bits[(g0 >> 5) + lane] = interleave16(e >> sh, o >> sh);
-    }
-    if (lane == 0) s_warp[warp] = count;
-    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ctr + kCtrTileBase + kStageCompact, 1u);
     __syncthreads();
-    const int64_t next = s_tile;
-    if (next < n_tiles) load(next, w);
-    if (warp == 0) {
-      const uint32_t c = lane < kWarps ? s_warp[lane] : 0u;
-      uint32_t incl = c;
+    const int64_t chunk = s_chunk;
+    if (chunk >= n_chunks) break;
+    const int64_t t0 = chunk * per;
+    const int nt = (int)min((int64_t)per, n_tiles - t0);
+    // 1. ballots of the chunk's tiles (the next tile's loads issued first)
+    float4 w[kRounds];
+    load(t0, w);
+    for (int i = 0; i < nt; ++i) {
+      uint32_t b[2 * kRounds];
+      uint32_t count = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
+      for (int r = 0; r < kRounds; ++r) {
+        b[r] = __ballot_sync(0xffffffffu, (w[r].x <= t) && (t <= w[r].y));
+        b[kRounds + r] = __ballot_sync(0xffffffffu, (w[r].z <= t) && (t <= w[r].w));
+        count += __popc(b[r]) + __popc(b[kRounds + r]);
       }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      const uint32_t prefix = warp_lookback(lookback, tile, tag, total, ctr);
-      if (lane < kWarps) s_warp[lane] = incl - c;
-      if (lane == 0) {
-        s_base = prefix;
-        if (tile == n_tiles - 1) ctr[kCtrSelected] = prefix + total;
+      if (i + 1 < nt) load(t0 + i + 1, w);
+      // lane m < 16 keeps ballot m (rounds' even Gaussians, then odd ones)
+      uint32_t mine = 0;
+#pragma unroll
+      for (int m = 0; m < 2 * kRounds; ++m)
+        if ((int)lane == m) mine = b[m];
+      if (lane < 2 * kRounds) s_bits[i][warp][lane] = mine;
+      if (sel_bits && lane < 2 * kRounds) {
+        // round r covers Gaussians g0 + 64 r .. + 63: two words, lanes 2r and 2r + 1
+        const int r = (int)(lane >> 1);
+        uint32_t e = 0, o = 0;
+#pragma unroll
+        for (int q = 0; q < kRounds; ++q)
+          if (r == q) { e = b[q]; o = b[kRounds + q]; }
+        const uint32_t sh = (lane & 1u) * 16u;
+        const int64_t g0 = (t0 + i) * kTileSpan + (int64_t)warp * kWarpSpan;
+        sel_bits[(g0 >> 5) + lane] = interleave16(e >> sh, o >> sh);
       }
+      if (lane == 0) s_off[i * kWarps + warp] = count;
     }
     __syncthreads();
-    uint32_t out = s_base + s_warp[warp];
+    // 2. offsets of the (tile, warp) spans within the chunk: one entry per
+    //    thread (per * kWarps <= kThreads)
+    const uint32_t c = threadIdx.x < nt * kWarps ? s_off[threadIdx.x] : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      const uint32_t y = s_tmp[q];
+      if (q < warp) wbase += y;
+      total += y;
+    }
+    if (threadIdx.x < nt * kWarps) s_off[threadIdx.x] = wbase + incl - c;
+    // 3. publish the chunk's count and sum every earlier chunk's count
+    if (threadIdx.x == 0) lookback_publish(lookback, 1, chunk, tag, 1u, total);
+    const uint32_t prefix = chunk_prefix<kWarps>(lookback, chunk, tag, ctr, s_tmp);
+    if (threadIdx.x == 0 && chunk == n_chunks - 1) ctr[kCtrSelected] = prefix + total;
+    // 4. the chunk's indices, in order, from the ballots
     const uint32_t lt = lanemask_lt();
+    for (int i = 0; i < nt; ++i) {
+      const int64_t g0 = (t0 + i) * kTileSpan + (int64_t)warp * kWarpSpan;
+      uint32_t out = prefix + s_off[i * kWarps + warp];
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-      const int64_t g = g0 + 2 * (r * 32 + (int64_t)lane);
-      const uint32_t before = __popc(b0[r] & lt) + __popc(b1[r] & lt);
-      const bool f0 = (b0[r] >> lane) & 1u;
-      const bool f1 = (b1[r] >> lane) & 1u;
-      if (f0) sel[out + before] = (uint32_t)g;
-      if (f1) sel[out + before + (f0 ? 1u : 0u)] = (uint32_t)(g + 1);
-      out += __popc(b0[r]) + __popc(b1[r]);
+      for (int r = 0; r < kRounds; ++r) {
+        const uint32_t b0 = s_bits[i][warp][r], b1 = s_bits[i][warp][kRounds + r];
+        const int64_t g = g0 + 2 * (r * 32 + (int64_t)lane);
+        const uint32_t before = __popc(b0 & lt) + __popc(b1 & lt);
+        const bool f0 = (b0 >> lane) & 1u;
+        const bool f1 = (b1 >> lane) & 1u;
+        if (f0) sel[out + before] = (uint32_t)g;
+        if (f1) sel[out + before + (f0 ? 1u : 0u)] = (uint32_t)(g + 1);
+        out += __popc(b0) + __popc(b1);
+      }
     }
-    __syncthreads();  // s_tile / s_warp / s_base reuse
-    tile = next;
+    __syncthreads();   // s_chunk / s_bits / s_off reuse
   }
   // the last CTA to finish does the call's set-up for the launches after it
   __threadfence();
@@ -242,15 +273,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_compact(const __grid_constant__
   }
 }
 
+// Chunk length and grid for n Gaussians on `sms` SMs: one chunk per resident
+// CTA where a chunk of at most kChunkTiles tiles allows it, else as many
+// chunks of kChunkTiles tiles as needed (the CTAs then take several).
+struct CompactGrid {
+  int per;
+  unsigned grid;
+};
+CompactGrid compact_grid(int64_t n, int sms) {
+  // occupancy is queried once (outside any graph capture: the first call)
+  static int per_sm = 0;
+  if (!per_sm) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_compact, kThreads, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm = b;
+  }
+  const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
+  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * per_sm;
+  int64_t per = (n_tiles + resident - 1) / resident;
+  per = per < 1 ? 1 : (per > kChunkTiles ? kChunkTiles : per);
+  const int64_t n_chunks = (n_tiles + per - 1) / per;
+  int64_t grid = n_chunks < resident ? n_chunks : resident;
+  if (grid < 1) grid = 1;
+  return {(int)per, (unsigned)grid};
+}
+
 }  // namespace
 
 cudaError_t launch_compact(s3r_workspace* ws, const s3r_scene* sc, const s3r_poses* poses,
                            const float* vis, float t, cudaStream_t st) {
   const int64_t n = sc->n;
-  const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
-  int64_t grid = (int64_t)ws->num_sms * 8;
-  if (grid > n_tiles) grid = n_tiles;
-  if (grid < 1) grid = 1;
+  const CompactGrid cg = compact_grid(n, ws->num_sms);
   CallSetup c;
   c.n_views = ws->n_views;
   c.pose_q = reinterpret_cast<const float4*>(poses ? poses->quat : nullptr);
@@ -261,8 +316,8 @@ cudaError_t launch_compact(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   c.tile_class_cnt = ws->tile_class_cnt;
   c.lookback_words = ws->lookback_words;
   KernelTimer timer(ws, kKCompact, st);
-  k_compact<<<(unsigned)grid, kThreads, 0, st>>>(ws->views, vis, n, t, ws->selected, ws->ctr,
-                                                 ws->lookback, ws->kept_bits, c);
+  k_compact<<<cg.grid, kThreads, 0, st>>>(ws->views, vis, n, t, cg.per, ws->selected, ws->ctr,
+                                          ws->lookback, ws->kept_bits, c);
   return cudaGetLastError();
 }
 
@@ -358,12 +413,10 @@ extern "C" s3r_status s3r_select_visible_static(int64_t n, float t, const float*
   if (e == cudaSuccess && n_tiles > 0)
     e = cudaMemsetAsync(sc->lookback, 0, sizeof(unsigned long long) * (size_t)n_tiles, s);
   if (e == cudaSuccess) {
-    int64_t grid = (int64_t)sms * 8;
-    if (grid > n_tiles) grid = n_tiles;
-    if (grid < 1) grid = 1;
+    const CompactGrid cg = compact_grid(n, sms);
     CallSetup none = {0, nullptr, nullptr, 0, nullptr, nullptr, nullptr, 0};
-    k_compact<<<(unsigned)grid, kThreads, 0, s>>>(g_no_views, vis_window, n, t, out_idx, sc->ctr,
-                                                   sc->lookback, nullptr, none);
+    k_compact<<<cg.grid, kThreads, 0, s>>>(g_no_views, vis_window, n, t, cg.per, out_idx, sc->ctr,
+                                            sc->lookback, nullptr, none);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

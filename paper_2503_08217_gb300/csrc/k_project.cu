@@ -187,20 +187,29 @@ __global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_m
 }
 
 // First splat of every selected Gaussian: an exclusive scan of the kept-view
-// counts popc(keep_mask) in 4096-Gaussian tiles (block scan + warp look-back).
-// A thread owns 16 consecutive masks (four 128-bit loads and stores); the
-// next tile's masks are loaded before this tile's look-back.
+// counts popc(keep_mask) in 4096-Gaussian tiles. A thread owns 16 consecutive
+// masks (four 128-bit loads and stores). A CTA takes a chunk of consecutive
+// tiles, scans each tile in the block, gets the chunk's global offset from
+// the counts that all earlier chunks published (chunk_prefix), and then reads
+// its masks again (from L2) to write the offsets.
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kThreads * kScanItems;
+constexpr int kScanChunkTiles = 16;   // tiles a CTA's shared memory holds the offsets of
 
 __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restrict__ keep_mask,
                                                          uint32_t* __restrict__ splat_start,
                                                          uint32_t* ctr,
                                                          unsigned long long* lookback) {
-  __shared__ uint32_t s_tile, s_base;
-  __shared__ uint32_t s_warp[kWarps];
+  __shared__ uint32_t s_ex[kScanChunkTiles][kThreads];   // thread's offset within the chunk
+  __shared__ uint32_t s_tmp[kWarps];
+  __shared__ uint32_t s_chunk;
   const uint32_t n_sel = ctr[kCtrSelected];
   const int64_t n_tiles = ((int64_t)n_sel + kScanTile - 1) / kScanTile;
+  // one chunk per CTA of the grid where kScanChunkTiles tiles allow it (the
+  // count is on the device, so every CTA derives the same chunk length)
+  const int per = (int)max((int64_t)1, min((int64_t)kScanChunkTiles,
+                                           (n_tiles + gridDim.x - 1) / (int64_t)gridDim.x));
+  const int64_t n_chunks = (n_tiles + per - 1) / per;
   const uint32_t tag = stage_tag(ctr[kCtrEpoch], kStageProject);
   const int warp = threadIdx.x >> 5;
   const uint32_t lane = lane_id();
@@ -218,65 +227,73 @@ __global__ void __launch_bounds__(kThreads) k_splat_scan(const uint32_t* __restr
       for (int i = 0; i < kScanItems; ++i) m[i] = (j0 + i < (int64_t)n_sel) ? keep_mask[j0 + i] : 0u;
     }
   };
-  if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
-  __syncthreads();
-  int64_t tile = s_tile;
-  uint32_t m[kScanItems];
-  if (tile < n_tiles) load(tile, m);
-  while (tile < n_tiles) {
-    const int64_t j0 = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t c[kScanItems], run = 0;
+  auto run_of = [](const uint32_t (&m)[kScanItems]) {
+    uint32_t run = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      c[i] = (uint32_t)__popc(m[i]);
-      run += c[i];
-    }
-    uint32_t incl = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= (uint32_t)o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    if (threadIdx.x == 0) s_tile = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
+    for (int i = 0; i < kScanItems; ++i) run += (uint32_t)__popc(m[i]);
+    return run;
+  };
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(ctr + kCtrTileBase + kStageProject, 1u);
     __syncthreads();
-    const int64_t next = s_tile;
-    if (next < n_tiles) load(next, m);
-    if (warp == 0) {
-      const uint32_t wc = lane < kWarps ? s_warp[lane] : 0u;
-      uint32_t wi = wc;
+    const int64_t chunk = s_chunk;
+    if (chunk >= n_chunks) break;
+    const int64_t t0 = chunk * per;
+    const int nt = (int)min((int64_t)per, n_tiles - t0);
+    // 1. per tile: the threads' kept-view counts, scanned over the block and
+    //    carried over the chunk's tiles (the next tile's loads issued first)
+    uint32_t m[kScanItems];
+    load(t0, m);
+    uint32_t carry = 0;
+    for (int i = 0; i < nt; ++i) {
+      const uint32_t run = run_of(m);
+      if (i + 1 < nt) load(t0 + i + 1, m);
+      uint32_t incl = run;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= (uint32_t)o) wi += y;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
       }
-      const uint32_t total = __shfl_sync(0xffffffffu, wi, 31);
-      const uint32_t prefix = warp_lookback(lookback, tile, tag, total, ctr);
-      if (lane < kWarps) s_warp[lane] = wi - wc;
-      if (lane == 0) {
-        s_base = prefix;
-        if (tile == n_tiles - 1) ctr[kCtrSplats] = prefix + total;
+      if (lane == 31) s_tmp[warp] = incl;
+      __syncthreads();
+      uint32_t wbase = 0, tot = 0;
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) {
+        const uint32_t y = s_tmp[q];
+        if (q < warp) wbase += y;
+        tot += y;
+      }
+      s_ex[i][threadIdx.x] = carry + wbase + incl - run;
+      carry += tot;
+      __syncthreads();   // s_tmp is rewritten by the next tile
+    }
+    // 2. the chunk's count, published, and every earlier chunk's count
+    if (threadIdx.x == 0) lookback_publish(lookback, 1, chunk, tag, 1u, carry);
+    const uint32_t prefix = chunk_prefix<kWarps>(lookback, chunk, tag, ctr, s_tmp);
+    if (threadIdx.x == 0 && chunk == n_chunks - 1) ctr[kCtrSplats] = prefix + carry;
+    // 3. the offsets, from the masks read again
+    load(t0, m);
+    for (int i = 0; i < nt; ++i) {
+      const int64_t j0 = (t0 + i) * kScanTile + (int64_t)threadIdx.x * kScanItems;
+      uint32_t o[kScanItems];
+      uint32_t off = prefix + s_ex[i][threadIdx.x];
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k) {
+        o[k] = off;
+        off += (uint32_t)__popc(m[k]);
+      }
+      if (i + 1 < nt) load(t0 + i + 1, m);
+      if (j0 + kScanItems <= (int64_t)n_sel) {
+        uint4* p = reinterpret_cast<uint4*>(splat_start + j0);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) p[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+          if (j0 + k < (int64_t)n_sel) splat_start[j0 + k] = o[k];
       }
     }
-    __syncthreads();
-    uint32_t off = s_base + s_warp[warp] + incl - run;
-    uint32_t o[kScanItems];
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-      o[i] = off;
-      off += c[i];
-    }
-    if (j0 + kScanItems <= (int64_t)n_sel) {
-      uint4* p = reinterpret_cast<uint4*>(splat_start + j0);
-#pragma unroll
-      for (int q = 0; q < kScanItems / 4; ++q) p[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kScanItems; ++i)
-        if (j0 + i < (int64_t)n_sel) splat_start[j0 + i] = o[i];
-    }
-    __syncthreads();
-    tile = next;
+    __syncthreads();   // s_chunk / s_ex reuse
   }
 }
 

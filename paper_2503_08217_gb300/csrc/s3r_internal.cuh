@@ -404,6 +404,45 @@ __device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int
   return prefix;
 }
 
+// Chunked single-pass scan: once a block has published its chunk's aggregate
+// (flag 1, lookback_publish at stride 1), it sums the aggregates of ALL
+// earlier chunks, its threads reading them in parallel (one round trip, where
+// a walk back over the chunks in flight takes one per batch of
+// predecessors). Chunks are claimed in order from a counter, so a chunk only
+// waits for chunks whose blocks are running. Every thread of the block calls
+// it (it synchronises twice); returns the exclusive prefix in every thread.
+// s_red: kWarpsB words. Bounded like lookback_walk. kSaturate: sat_add sums.
+template <int kWarpsB, bool kSaturate = false>
+__device__ __forceinline__ uint32_t chunk_prefix(const unsigned long long* words, int64_t chunk,
+                                                 uint32_t tag, uint32_t* ctr, uint32_t* s_red,
+                                                 int max_polls = kSpinLimit) {
+  auto add = [](uint32_t a, uint32_t b) { return kSaturate ? sat_add(a, b) : a + b; };
+  uint32_t part = 0;
+  for (int64_t k = threadIdx.x; k < chunk; k += kWarpsB * 32) {
+    unsigned long long x = ld_relaxed(words + k);
+    int spins = 0;
+    while ((uint32_t)(x >> 34) != tag) {
+      if (++spins > max_polls) {
+        atomicOr(ctr + kCtrStatus, kStatusTimeout);
+        x = 0;
+        break;
+      }
+      __nanosleep(32);
+      x = ld_relaxed(words + k);
+    }
+    part = add(part, (uint32_t)x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part = add(part, __shfl_xor_sync(0xffffffffu, part, o));
+  __syncthreads();   // s_red may still be read by the caller's previous step
+  if ((threadIdx.x & 31u) == 0) s_red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  uint32_t prefix = 0;
+#pragma unroll
+  for (int w = 0; w < kWarpsB; ++w) prefix = add(prefix, s_red[w]);
+  return prefix;
+}
+
 __device__ __forceinline__ uint32_t lane_id() {
   uint32_t l;
   asm("mov.u32 %0, %%laneid;" : "=r"(l));
