@@ -276,13 +276,13 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "sort_depth_pass1": ("hbm", S * 16),
         "sort_depth_pass2": ("hbm", S * 16),
         "sort_depth_pass3": ("hbm", S * 16),
-        # duplication: per splat, its (u, v), conic, rect and view in, its
-        # 32-byte tile record out (row-table entries beyond three rows not
-        # counted); the scan reads each sorted splat's id and record and
-        # writes its offset and the record in depth order; the expansion reads
+        # duplication: per splat in depth order, its sorted id, (u, v),
+        # conic, rect and view in, its tile count and 32-byte expansion
+        # record out (row-table entries beyond three rows not counted); the
+        # scan reads the counts and writes the offsets; the expansion reads
         # offsets and records and writes the pairs
-        "splat_tiles": ("hbm", S * (8 + 16 + 8 + 1) + S * 32),
-        "duplicate": ("hbm", S * (4 + 32) + S * (4 + 32)),
+        "splat_tiles": ("hbm", S * (4 + 8 + 16 + 8 + 1) + S * (4 + 32)),
+        "duplicate": ("hbm", S * (4 + 4)),
         "duplicate_expand": ("hbm", S * (4 + 32) + K * 8),   # + tile-digit histograms (on chip)
         # per tile: its range and class slot out (the binary searches' reads
         # are cached); the forward's contributor bits cleared

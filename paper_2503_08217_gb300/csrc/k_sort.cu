@@ -216,22 +216,23 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
 // and reciprocals are the hardware approximations (errors of about 1 ulp, far
 // inside the margins), deterministic like the rest of the arithmetic.
 //
-//  k_splat_tiles: per splat (by id, in any order), a 32-byte record: its
-//                tile count (one interval per row of its rectangle), the tile
-//                id of the rectangle's corner, grid and rectangle widths,
-//                rectangle height, and its rows: the first kInlineRows in the
-//                record, the others 4 bytes each in a row table (offsets from
-//                a warp-aggregated bump counter; the warp computes a tall
-//                splat's rows together, one per lane). A splat that no
-//                longer fits the table stores its region (32 bytes) instead,
-//                and the expansion recomputes its later rows from it with the
-//                same function. Outside the scan below, whose look-back chain
-//                would otherwise wait on the few splats with tens of rows.
-//  k_dup_scan:   per sorted splat, the count from its record and a copy of
-//                the record in depth order (the count replaced by the splat
-//                id), so that the expansion reads most splats' rows without a
-//                dependent load; a block scan + decoupled look-back over
-//                1024-splat tiles gives every splat its first output.
+//  k_splat_tiles: per splat, in depth order (its data gathered by the sorted
+//                id), its tile count (one interval per row of its
+//                rectangle) and a 32-byte record for the expansion: the splat
+//                id, the tile id of the rectangle's corner, grid and
+//                rectangle widths, rectangle height, and its rows: the first
+//                kInlineRows in the record, the others 4 bytes each in a row
+//                table (offsets from a warp-aggregated bump counter; the warp
+//                computes a tall splat's rows together, one per lane), so
+//                that the expansion reads most splats' rows without a
+//                dependent load. A splat that no longer fits the table
+//                stores its region (32 bytes, by splat id) instead, and the
+//                expansion recomputes its later rows from it with the same
+//                function. Outside the scan below, which would otherwise
+//                wait on the few splats with tens of rows.
+//  k_dup_scan:   the exclusive scan of the counts (saturating) gives every
+//                splat its first output, and every expansion chunk its first
+//                splat.
 //  k_dup_expand: persistent CTAs take fixed chunks of 256 * kExpItems outputs
 //                (2048 at 8); each thread expands kExpItems consecutive
 //                outputs (binary search of the chunk's splat offsets in
@@ -239,8 +240,6 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
 //                one, then an incremental cursor over rows and splats); the
 //                pairs are staged in shared memory and written coalesced.
 constexpr int kDupThreads = 256;
-constexpr int kDupPer = 4;                            // splats per thread in the scan
-constexpr int kDupSplats = kDupThreads * kDupPer;     // 1024 per scan tile
 #ifndef S3R_DUP_EXPAND_ITEMS
 #define S3R_DUP_EXPAND_ITEMS 8   // build-time define the autotuner varies
 #endif
@@ -336,7 +335,7 @@ struct DupArgs {
   const uint32_t* sorted_splats;
   const uint2* sp_rect;
   const uint8_t* sp_view;
-  const uint4* sp_tiles;       // [S][2] records of k_splat_tiles, by splat id
+  const uint32_t* sp_cnt;      // [S] tiles each splat reaches, by depth position
   const uint32_t* row_spans;   // per row of a rectangle: first | end << 16 (columns)
   const float4* sp_region;     // [S][2] region, by splat id, where sp_rowoff is kNoRows
   uint32_t* dup_key;
@@ -355,16 +354,18 @@ constexpr uint32_t kNoRows = 0xffffffffu;
 constexpr int kInlineRows = 3;
 
 struct TilesArgs {
+  const uint32_t* sorted;   // depth order -> splat id
   const float2* xy;
   const float4* co;
   const uint2* rect;
   const uint8_t* view;
   uint32_t* ctr;
   int64_t cap;
-  uint4* rec;
+  uint32_t* cnt;            // [S] tiles reached, by depth position
+  uint4* meta;              // [S][2] expansion records, by depth position
   uint32_t* row_spans;
   int64_t rows_cap;
-  float4* region;
+  float4* region;           // [S][2] by splat id
 };
 
 __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_constant__ ViewSet vs,
@@ -373,9 +374,10 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
   const uint32_t lane = lane_id();
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n;
        base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
+    const int64_t i = base + threadIdx.x;   // depth position
     const bool live = i < n;
-    const uint2 rc = live ? a.rect[i] : make_uint2(0u, 0u);
+    const uint32_t sp = live ? a.sorted[i] : 0u;
+    const uint2 rc = live ? a.rect[sp] : make_uint2(0u, 0u);
     const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16;
     const uint32_t w = (rc.y & 0xffffu) - x0, h = (rc.y >> 16) - y0;
     // table entries for the rows past the inline ones, one atomic per warp
@@ -394,7 +396,7 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
     const uint64_t off = wbase + incl - need;
     const bool table = off + need <= (uint64_t)a.rows_cap;
     Region g = {};
-    if (live) g = region_of(a.xy[i], a.co[i], x0, y0);
+    if (live) g = region_of(a.xy[sp], a.co[sp], x0, y0);
     // each lane: the inline rows of its own splat
     uint32_t cnt = 0;
     uint32_t head[kInlineRows] = {0u, 0u, 0u};
@@ -436,13 +438,14 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
       if (lane == (uint32_t)b) cnt += part;
     }
     if (!live) continue;
-    const ViewInfo& vi = vs.v[a.view[i] & 0x7f];   // bit 7: Eq. 7 moved
+    const ViewInfo& vi = vs.v[a.view[sp] & 0x7f];   // bit 7: Eq. 7 moved
     const uint32_t corner = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
     // a rectangle without columns (an Eq. 7 splat moved out of the frustum)
     // has no rows either for the expansion, which then reads no row table
-    a.rec[2 * i] = make_uint4(cnt, corner, (uint32_t)vi.gx | (w << 16), w != 0 ? h : 0u);
-    a.rec[2 * i + 1] = make_uint4(table ? (uint32_t)off : kNoRows, head[0], head[1], head[2]);
-    if (!table) region_store(g, a.region + 2 * i);
+    a.cnt[i] = cnt;
+    a.meta[2 * i] = make_uint4(sp, corner, (uint32_t)vi.gx | (w << 16), w != 0 ? h : 0u);
+    a.meta[2 * i + 1] = make_uint4(table ? (uint32_t)off : kNoRows, head[0], head[1], head[2]);
+    if (!table) region_store(g, a.region + 2 * sp);
   }
 }
 
@@ -477,81 +480,111 @@ __device__ __forceinline__ uint32_t block_excl_scan_sat(uint32_t x, uint32_t* s_
 // Pair offsets saturate at kSat (above every capacity, which is < 2^31), so a
 // real pair count of 2^32 or more cannot wrap into a small one: it latches
 // the capacity status like any other overflow.
+//
+// The counts are in depth order already (k_splat_tiles), so this is a plain
+// scan: 4096-count tiles, 16 consecutive counts per thread (128-bit loads and
+// stores); a CTA scans the tiles of its chunk in the block, gets the chunk's
+// offset from the counts all earlier chunks published (chunk_prefix), and
+// reads its counts again (from L2) to write the offsets and the expansion
+// chunks' first splats.
+constexpr int kDupScanItems = 16;
+constexpr int kDupScanTile = kDupThreads * kDupScanItems;   // 4096
+constexpr int kDupScanChunkTiles = 16;
+
 __global__ void __launch_bounds__(kDupThreads) k_dup_scan(DupArgs a) {
+  __shared__ uint32_t s_ex[kDupScanChunkTiles][kDupThreads];   // thread's offset within the chunk
   __shared__ uint32_t s_tmp[kDupThreads / 32];
-  __shared__ uint32_t s_tile, s_base;
+  __shared__ uint32_t s_chunk;
   const int64_t n = min((int64_t)a.ctr[kCtrSplats], a.cap_splats);
-  const int64_t n_tiles = (n + kDupSplats - 1) / kDupSplats;
+  const int64_t n_tiles = (n + kDupScanTile - 1) / kDupScanTile;
+  // one chunk per CTA of the grid where kDupScanChunkTiles tiles allow it (the
+  // count is on the device, so every CTA derives the same chunk length)
+  const int per = (int)max((int64_t)1, min((int64_t)kDupScanChunkTiles,
+                                           (n_tiles + gridDim.x - 1) / (int64_t)gridDim.x));
+  const int64_t n_chunks = (n_tiles + per - 1) / per;
   const uint32_t tag = stage_tag(a.ctr[kCtrEpoch], kStageDup);
-  // a tile's sorted splat ids and their tile records (gathered by id)
-  uint32_t sp[kDupPer];
-  uint4 r0[kDupPer], r1[kDupPer];
-  auto load = [&](int64_t tile) {
-    const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
+  auto load = [&](int64_t tile, uint32_t (&c)[kDupScanItems]) {
+    const int64_t i0 = tile * kDupScanTile + (int64_t)threadIdx.x * kDupScanItems;
+    if (i0 + kDupScanItems <= n) {
+      const uint4* p = reinterpret_cast<const uint4*>(a.sp_cnt + i0);
 #pragma unroll
-    for (int k = 0; k < kDupPer; ++k) sp[k] = i0 + k < n ? a.sorted_splats[i0 + k] : 0u;
+      for (int q = 0; q < kDupScanItems / 4; ++q) {
+        const uint4 v = p[q];
+        c[4 * q] = v.x; c[4 * q + 1] = v.y; c[4 * q + 2] = v.z; c[4 * q + 3] = v.w;
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < kDupPer; ++k) {
-      r0[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k]] : make_uint4(0u, 0u, 0u, 0u);
-      r1[k] = i0 + k < n ? a.sp_tiles[2 * (size_t)sp[k] + 1] : make_uint4(0u, 0u, 0u, 0u);
+      for (int k = 0; k < kDupScanItems; ++k) c[k] = i0 + k < n ? a.sp_cnt[i0 + k] : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kDupScanItems; ++k) c[k] = min(c[k], kSat);
   };
-  if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
-  __syncthreads();
-  int64_t tile = s_tile;
-  if (tile < n_tiles) load(tile);
-  // per tile: the records in depth order and the counts, then the next
-  // tile's gathers are issued before this tile's scan and look-back
-  while (tile < n_tiles) {
-    const int64_t i0 = tile * kDupSplats + (int64_t)threadIdx.x * kDupPer;
-    uint32_t cnt[kDupPer], run = 0;
-#pragma unroll
-    for (int k = 0; k < kDupPer; ++k) {
-      cnt[k] = min(r0[k].x, kSat);
-      run = sat_add(run, cnt[k]);
-      if (i0 + k < n) {
-        a.dup_meta[2 * (i0 + k)] = make_uint4(sp[k], r0[k].y, r0[k].z, r0[k].w);
-        a.dup_meta[2 * (i0 + k) + 1] = r1[k];
-      }
-    }
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
-    uint32_t total;
-    uint32_t ex = block_excl_scan_sat(run, s_tmp, &total);   // synchronises
-    const int64_t next = s_tile;
-    if (next < n_tiles) load(next);
-    if (threadIdx.x < 32) {
-      const uint32_t prefix = warp_lookback<true>(a.lookback, tile, tag, total, a.ctr);
-      if (threadIdx.x == 0) {
-        s_base = prefix;
-        if (tile == n_tiles - 1) {
-          const uint32_t all = sat_add(prefix, total);
-          a.ctr[kCtrDups] = all;
-          a.dup_excl[n] = all;                          // sentinel
-          if ((int64_t)all > a.cap_dups) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
-        }
-      }
-    }
+  for (;;) {
+    if (threadIdx.x == 0) s_chunk = atomicAdd(a.ctr + kCtrTileBase + kStageDup, 1u);
     __syncthreads();
-    ex = sat_add(ex, s_base);
+    const int64_t chunk = s_chunk;
+    if (chunk >= n_chunks) break;
+    const int64_t t0 = chunk * per;
+    const int nt = (int)min((int64_t)per, n_tiles - t0);
+    // 1. per tile: the threads' sums, scanned over the block and carried over
+    //    the chunk (the next tile's loads issued first)
+    uint32_t c[kDupScanItems];
+    load(t0, c);
+    uint32_t carry = 0;
+    for (int i = 0; i < nt; ++i) {
+      uint32_t run = 0;
 #pragma unroll
-    for (int k = 0; k < kDupPer; ++k) {
-      if (i0 + k < n) {
-        a.dup_excl[i0 + k] = ex;
-        // every chunk boundary inside this splat's outputs [ex, ex + cnt)
-        // (below capacity) starts with this splat
-        const uint64_t e1 = min((uint64_t)ex + cnt[k], (uint64_t)a.cap_dups);
-        for (uint64_t c = ((uint64_t)ex + kExpChunk - 1) / kExpChunk; c * kExpChunk < e1; ++c)
-          a.dup_chunk[c] = (uint32_t)(i0 + k);
-      }
-      ex = sat_add(ex, cnt[k]);
+      for (int k = 0; k < kDupScanItems; ++k) run = sat_add(run, c[k]);
+      if (i + 1 < nt) load(t0 + i + 1, c);
+      uint32_t total;
+      const uint32_t ex = block_excl_scan_sat(run, s_tmp, &total);   // synchronises
+      s_ex[i][threadIdx.x] = sat_add(carry, ex);
+      carry = sat_add(carry, total);
     }
-    if (tile == n_tiles - 1 && threadIdx.x == 0) {
+    // 2. the chunk's count, published, and every earlier chunk's count
+    if (threadIdx.x == 0) lookback_publish(a.lookback, 1, chunk, tag, 1u, carry);
+    const uint32_t prefix =
+        chunk_prefix<kDupThreads / 32, true>(a.lookback, chunk, tag, a.ctr, s_tmp);
+    if (threadIdx.x == 0 && chunk == n_chunks - 1) {
+      const uint32_t all = sat_add(prefix, carry);
+      a.ctr[kCtrDups] = all;
+      a.dup_excl[n] = all;                          // sentinel
+      if ((int64_t)all > a.cap_dups) atomicOr(a.ctr + kCtrStatus, kStatusCapacity);
       // after the last chunk: the last splat (chunks end at an inclusive splat bound)
-      const uint64_t tot = min((uint64_t)sat_add(s_base, total), (uint64_t)a.cap_dups);
+      const uint64_t tot = min((uint64_t)all, (uint64_t)a.cap_dups);
       a.dup_chunk[(tot + kExpChunk - 1) / kExpChunk] = (uint32_t)(n - 1);
     }
-    __syncthreads();
-    tile = next;
+    // 3. every splat's first output, and the expansion chunks starting in it
+    load(t0, c);
+    for (int i = 0; i < nt; ++i) {
+      const int64_t i0 = (t0 + i) * kDupScanTile + (int64_t)threadIdx.x * kDupScanItems;
+      uint32_t o[kDupScanItems];
+      uint32_t ex = sat_add(prefix, s_ex[i][threadIdx.x]);
+#pragma unroll
+      for (int k = 0; k < kDupScanItems; ++k) {
+        o[k] = ex;
+        if (i0 + k < n) {
+          // every chunk boundary inside this splat's outputs [ex, ex + c)
+          // (below capacity) starts with this splat
+          const uint64_t e1 = min((uint64_t)ex + c[k], (uint64_t)a.cap_dups);
+          for (uint64_t q = ((uint64_t)ex + kExpChunk - 1) / kExpChunk; q * kExpChunk < e1; ++q)
+            a.dup_chunk[q] = (uint32_t)(i0 + k);
+        }
+        ex = sat_add(ex, c[k]);
+      }
+      if (i + 1 < nt) load(t0 + i + 1, c);
+      if (i0 + kDupScanItems <= n) {
+        uint4* p = reinterpret_cast<uint4*>(a.dup_excl + i0);
+#pragma unroll
+        for (int q = 0; q < kDupScanItems / 4; ++q)
+          p[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < kDupScanItems; ++k)
+          if (i0 + k < n) a.dup_excl[i0 + k] = o[k];
+      }
+    }
+    __syncthreads();   // s_chunk / s_ex reuse
   }
 }
 
@@ -820,7 +853,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   d.sorted_splats = ws->depth_val[0];
   d.sp_rect = ws->sp_rect;
   d.sp_view = ws->sp_view;
-  d.sp_tiles = reinterpret_cast<const uint4*>(ws->sp_tiles);
+  d.sp_cnt = ws->sp_tiles;
   d.row_spans = ws->row_spans;
   d.sp_region = reinterpret_cast<const float4*>(ws->sp_region);
   d.dup_key = ws->dup_key[0];
@@ -845,7 +878,9 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     t.view = ws->sp_view;
     t.ctr = ws->ctr;
     t.cap = ws->cap.max_splats;
-    t.rec = reinterpret_cast<uint4*>(ws->sp_tiles);
+    t.sorted = ws->depth_val[0];
+    t.cnt = ws->sp_tiles;
+    t.meta = reinterpret_cast<uint4*>(ws->dup_meta);
     t.row_spans = ws->row_spans;
     t.rows_cap = ws->rows_cap;
     t.region = reinterpret_cast<float4*>(ws->sp_region);

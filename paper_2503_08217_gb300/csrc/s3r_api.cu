@@ -215,7 +215,7 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->mats, (int64_t)cap->max_views * nk * 20);
   S3R_ALLOC(ws->dup_excl, S + 1);
   S3R_ALLOC(ws->dup_meta, 8 * S);
-  S3R_ALLOC(ws->sp_tiles, 8 * S);
+  S3R_ALLOC(ws->sp_tiles, S);
   S3R_ALLOC(ws->sp_region, 8 * S);
   // about 2.5 rows per splat at 1 px LOD; past the table, rows are recomputed
   ws->rows_cap = std::min<int64_t>(cap->max_rows > 0 ? cap->max_rows : 4 * S, 0xfffffff0LL);

@@ -148,8 +148,8 @@ struct s3r_workspace {
   float* world_acc;         // [(inst+1) * world_acc_floats()] pose sums of s3r_to_world_bwd, zero between calls
   float* mats;              // composed matrices [views*(inst+1)] x 20 floats
   uint32_t* dup_excl;       // [S+1] first pair of each depth-sorted splat
-  uint32_t* dup_meta;       // [S] x 4: expansion descriptor of each sorted splat
-  uint32_t* sp_tiles;       // [S] x 8: tiles of its rectangle a splat's alpha region reaches, rows
+  uint32_t* dup_meta;       // [S] x 8: expansion record of each splat, depth order
+  uint32_t* sp_tiles;       // [S] tiles of its rectangle a splat's alpha region reaches, depth order
   float* sp_region;         // [S] x 8: that region, where the row table had no room
   uint32_t* row_spans;      // [rows_cap] column interval of one rectangle row
   int64_t rows_cap;
