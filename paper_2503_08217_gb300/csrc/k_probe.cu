@@ -1,9 +1,9 @@
-// Test hook for failure detection: one warp runs the library's three bounded
-// look-back waits (chunk_prefix, used by the compaction and the splat scan;
-// warp_lookback, used by the pair scan; lookback_walk, used by the radix
-// passes, through lookback_prefix) as chunk/tile 1 against a word 0 that
-// nothing ever publishes, with a small poll limit. Each wait gives up after
-// max_polls polls, latches
+// Test hook for failure detection: one warp runs the library's two bounded
+// look-back waits (chunk_prefix, used by the compaction and the splat and
+// pair scans; lookback_walk, used by the radix passes, through
+// lookback_prefix) as chunk/tile 1 against a word 0 that nothing ever
+// publishes, with a small poll limit. Each wait gives up after max_polls
+// polls, latches
 // kStatusTimeout into the workspace's status word and returns, so the host
 // reads S3R_ERR_TIMEOUT from the next s3r_sync_status and the context stays
 // usable. The hook writes four words at the end of the look-back array,
@@ -24,7 +24,6 @@ __global__ void __launch_bounds__(32) k_wait_probe(unsigned long long* words, ui
   }
   __syncthreads();
   chunk_prefix<1>(words, 1, tag, ctr, s_red, max_polls);            // reads words[0]
-  warp_lookback(words, 1, tag, 1u, ctr, max_polls);                  // writes words[1]
   if (threadIdx.x == 0) lookback_prefix(words + 2, 1, 1, tag, 1u, ctr, max_polls);   // words[3]
 }
 

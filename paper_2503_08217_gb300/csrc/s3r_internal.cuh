@@ -335,12 +335,6 @@ __device__ __forceinline__ uint32_t lookback_prefix(unsigned long long* words, i
   return prefix;
 }
 
-__device__ __forceinline__ uint32_t lane_id_() {
-  uint32_t l;
-  asm("mov.u32 %0, %%laneid;" : "=r"(l));
-  return l;
-}
-
 // Saturating sum for running sums that may pass 2^32 (the pair offsets):
 // values at or above kSat mean "more than any capacity" and stay there. For
 // operands <= kSat the 64-bit sum cannot wrap, and min(a + b, kSat) is
@@ -349,59 +343,6 @@ constexpr uint32_t kSat = 0x80000000u;
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
   const unsigned long long s = (unsigned long long)a + b;
   return s > kSat ? kSat : (uint32_t)s;
-}
-
-// Warp-cooperative form of lookback_prefix for one running sum over tiles at
-// stride 1: all 32 lanes of ONE warp call it with the same arguments. Each
-// step reads 32 predecessors at once and stops at the nearest one that has
-// published its inclusive prefix, so a walk over w unfinished predecessors
-// takes ceil(w/32) dependent loads instead of w. Returns the exclusive
-// prefix in every lane; lane 0 publishes the inclusive value. Bounded like
-// lookback_prefix. kSaturate: every sum is sat_add (aggregates <= kSat).
-template <bool kSaturate = false>
-__device__ __forceinline__ uint32_t warp_lookback(unsigned long long* words, int64_t tile,
-                                                  uint32_t tag, uint32_t aggregate, uint32_t* ctr,
-                                                  int max_polls = kSpinLimit) {
-  const uint32_t lane = lane_id_();
-  if (lane == 0) st_relaxed(words + tile, lb_word(tag, tile == 0 ? 2u : 1u, aggregate));
-  if (tile == 0) return 0;
-  uint32_t prefix = 0;
-  int64_t base = tile - 1;
-  int spins = 0;
-  for (;;) {
-    const int64_t k = base - (int64_t)lane;
-    uint32_t flag = 2, val = 0;   // before tile 0: an inclusive zero
-    if (k >= 0) {
-      const unsigned long long w = ld_relaxed(words + k);
-      const bool ok = (uint32_t)(w >> 34) == tag;
-      flag = ok ? (uint32_t)(w >> 32) & 3u : 0u;
-      val = (uint32_t)w;
-    }
-    const uint32_t incl = __ballot_sync(0xffffffffu, flag == 2u);
-    const uint32_t waiting = __ballot_sync(0xffffffffu, flag == 0u);
-    const int first = incl ? __ffs(incl) - 1 : 32;          // nearest inclusive
-    const uint32_t need = first == 32 ? 0xffffffffu : (0xffffffffu >> (31 - first));
-    if (waiting & need) {
-      if (++spins > max_polls) {
-        if (lane == 0) atomicOr(ctr + kCtrStatus, kStatusTimeout);
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    uint32_t part = ((int)lane <= first) ? val : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint32_t y = __shfl_xor_sync(0xffffffffu, part, o);
-      part = kSaturate ? sat_add(part, y) : part + y;
-    }
-    prefix = kSaturate ? sat_add(prefix, part) : prefix + part;
-    if (first < 32) break;
-    base -= 32;
-  }
-  if (lane == 0)
-    st_relaxed(words + tile, lb_word(tag, 2u, kSaturate ? sat_add(prefix, aggregate) : prefix + aggregate));
-  return prefix;
 }
 
 // Chunked single-pass scan: once a block has published its chunk's aggregate
