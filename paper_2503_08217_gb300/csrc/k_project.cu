@@ -76,11 +76,19 @@ __global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_m
   __shared__ uint32_t s_wcount[kWarps];
   // per-lane view indices differ: camera records are read from shared memory
   __shared__ ViewInfo s_views[S3R_MAX_VIEWS];
+  // the static segment's matrix for every view, staged in shared memory for
+  // the pre-tests (the instances' matrices, and the candidates' full
+  // projections, read them through L1)
+  __shared__ InstMat s_static[S3R_MAX_VIEWS];
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(vs.v);
     uint32_t* dst = reinterpret_cast<uint32_t*>(s_views);
     const int words = vs.n_views * (int)(sizeof(ViewInfo) / 4);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    constexpr int kMatWords = (int)(sizeof(InstMat) / 4);
+    float* mdst = reinterpret_cast<float*>(s_static);
+    for (int i = threadIdx.x; i < vs.n_views * kMatWords; i += blockDim.x)
+      mdst[i] = reinterpret_cast<const float*>(mats + (i / kMatWords) * nk)[i % kMatWords];
   }
   for (int i = threadIdx.x; i < nk + 1; i += blockDim.x) s_off[i] = (uint32_t)a.inst_off[i];
   if (threadIdx.x == 0) s_frustum = 0;
@@ -115,8 +123,13 @@ __global__ void __launch_bounds__(kThreads, S3R_PROJECT_MASK_BLOCKS) k_project_m
       // the candidates (each lane walks its own; the loop runs max-over-lanes times)
       const float smax = fmaxf(s0, fmaxf(s1, s2));
       uint32_t cand = 0;
-      for (int v = 0; v < vs.n_views; ++v)
-        if (may_touch_view(mats[v * nk + k], mu, smax * smax, s_views[v])) cand |= 1u << v;
+      if (k == 0) {
+        for (int v = 0; v < vs.n_views; ++v)
+          if (may_touch_view(s_static[v], mu, smax * smax, s_views[v])) cand |= 1u << v;
+      } else {
+        for (int v = 0; v < vs.n_views; ++v)
+          if (may_touch_view(mats[v * nk + k], mu, smax * smax, s_views[v])) cand |= 1u << v;
+      }
       while (cand) {
         const int v = __ffs(cand) - 1;
         cand &= cand - 1;
