@@ -7,10 +7,11 @@
 // Three kernels. The mask pass: one thread per selected Gaussian reads its 44
 // geometry bytes once and tests every camera (a conservative pre-test, then
 // the full projection for the candidates) through the composed matrices W_t
-// W_{t,i2g} (written by the compaction's first CTAs, read through L1); it
+// W_{t,i2g} (written by the compaction's first CTAs; the static segment's
+// staged in shared memory for the pre-tests, the others read through L1); it
 // writes the frustum and keep masks, applies Eq. 5 and appends the kept
-// Gaussians to a work list. The splat-offset scan: block scan plus decoupled
-// look-back over the kept-view counts. The splat writer: per kept Gaussian,
+// Gaussians to a work list. The splat-offset scan: block scans over chunks of
+// tiles plus the chunk prefix over the kept-view counts. The splat writer: per kept Gaussian,
 // its kept views again, SH colour (the warp's SH rows staged through shared
 // memory with coalesced 16-B loads) and the splat records.
 #include "s3r_math.cuh"
