@@ -291,7 +291,7 @@ CompactGrid compact_grid(int64_t n, int sms) {
     per_sm = b;
   }
   const int64_t n_tiles = (n + kTileSpan - 1) / kTileSpan;
-  const int64_t resident = (int64_t)(sms > 0 ? sms : 1) * per_sm;
+  const int64_t resident = scan_ctas((int64_t)(sms > 0 ? sms : 1) * per_sm);
   int64_t per = (n_tiles + resident - 1) / resident;
   per = per < 1 ? 1 : (per > kChunkTiles ? kChunkTiles : per);
   const int64_t n_chunks = (n_tiles + per - 1) / per;

@@ -478,7 +478,7 @@ cudaError_t launch_deg(s3r_workspace* ws, const ProjArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   {
     KernelTimer timer(ws, kKSplatScan, st);
-    k_splat_scan<<<ws->num_sms * per_scan, kThreads, 0, st>>>(a.keep_mask, a.splat_start, a.ctr,
+    k_splat_scan<<<(unsigned)scan_ctas((int64_t)ws->num_sms * per_scan), kThreads, 0, st>>>(a.keep_mask, a.splat_start, a.ctr,
                                                               a.lookback);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -889,7 +889,7 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {
     KernelTimer timer(ws, kKDuplicate, st);
-    k_dup_scan<<<ws->num_sms * dup_per_sm, kDupThreads, 0, st>>>(d);
+    k_dup_scan<<<(unsigned)scan_ctas((int64_t)ws->num_sms * dup_per_sm), kDupThreads, 0, st>>>(d);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   {

@@ -77,6 +77,19 @@ struct ViewSet {
   ViewInfo v[S3R_MAX_VIEWS];
 };
 
+// ---- chunked scans ----------------------------------------------------------
+// S3R_SCAN_CTAS: at most this many CTAs run the chunked scans (compaction,
+// splat offsets, pair offsets); 0, the default, means every resident CTA. A
+// small value makes every chunk span many tiles and every CTA take several
+// chunks, a launch shape the parity tests also run.
+#ifndef S3R_SCAN_CTAS
+#define S3R_SCAN_CTAS 0
+#endif
+static_assert(S3R_SCAN_CTAS >= 0, "a CTA cap, or 0 for none");
+inline int64_t scan_ctas(int64_t resident) {
+  return (S3R_SCAN_CTAS > 0 && resident > S3R_SCAN_CTAS) ? (int64_t)S3R_SCAN_CTAS : resident;
+}
+
 // ---- radix sort geometry ----------------------------------------------------
 // S3R_SORT_ITEMS (keys per thread per tile) and S3R_SORT_BLOCKS (resident
 // onesweep blocks per SM) are build-time defines the autotuner varies; the

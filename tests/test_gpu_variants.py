@@ -7,7 +7,9 @@ sizes). The tests run in a child pytest with S3R_LIBRARY naming the variant,
 so this process's loaded library is not replaced. The larger batches stage
 two Gaussians per thread (a loop the 64-Gaussian default takes once), the
 smaller radix tiles and expansion chunks multiply the look-back tiles and
-chunk-map entries.
+chunk-map entries. A third library caps the chunked scans (compaction, splat
+and pair offsets) at two CTAs, so that on these small inputs a chunk spans
+many tiles and each CTA takes several chunks.
 """
 from __future__ import annotations
 
@@ -40,10 +42,7 @@ LOW = _shapes(min)
 HIGH = _shapes(max)
 
 
-@pytest.mark.parametrize("defines", [LOW, HIGH], ids=["below_defaults", "above_defaults"])
-def test_off_default_launch_shapes_pass_parity(defines):
-    d = autotune.source_defaults()
-    assert all(defines[k] != d[k] for k in d)
+def _parity_with(defines):
     lib = libbuild.build(defines=defines)
     env = dict(os.environ, S3R_LIBRARY=lib)
     cmd = [sys.executable, "-m", "pytest", "tests/test_gpu_parity.py", "-m", "gpu", "-x", "-q",
@@ -51,3 +50,14 @@ def test_off_default_launch_shapes_pass_parity(defines):
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
     assert f"{N_PARITY} passed" in r.stdout, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("defines", [LOW, HIGH], ids=["below_defaults", "above_defaults"])
+def test_off_default_launch_shapes_pass_parity(defines):
+    d = autotune.source_defaults()
+    assert all(defines[k] != d[k] for k in d)
+    _parity_with(defines)
+
+
+def test_two_scan_ctas_pass_parity():
+    _parity_with({"S3R_SCAN_CTAS": 2})
