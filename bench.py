@@ -46,8 +46,8 @@ METRIC = "fwd+bwd views/s and Mpix/s vs plain per-view path, same GB300; % HBM r
 # hash), so that a comment edit keeps the figure and any code edit drops it
 # (the roofline line then reports traffic null).
 NCU_TRAFFIC = {
-    "blend_bwd": {"bytes": 1982031104, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
-                  "code_sha256_16": "67c2b83145c2647f", "profile": "profiles/blend_bwd_traffic_rig.md"},
+    "blend_bwd": {"bytes": 1983235328, "source": "paper_2503_08217_gb300/csrc/k_blend.cu",
+                  "code_sha256_16": "9d5f105faa34333b", "profile": "profiles/blend_bwd_traffic_rig.md"},
 }
 
 
@@ -266,22 +266,23 @@ def kernel_models(counts, scene, n_kept_gaussians: int, n_pixels: int, tiles: in
         "temporal_compact": ("hbm", 8 * n + 4 * nsel + n / 8),
         # masks: ids, geometry, two masks out, the life record where in
         # frustum, the (index, id) work list; scan: masks in, offsets out;
-        # splats: the work list, mask, offset, geometry and SH in, 53-byte
-        # records out
+        # splats: the work list, mask, offset, geometry and SH in, 61-byte
+        # records out (the 32-byte packed record, colour and depth, the
+        # rectangle and view, the depth key)
         "project": ("hbm", nsel * (4 + geo + 8) + 8 * nfr + n_kept_gaussians * 8),
         "splat_scan": ("hbm", nsel * 8),
         "project_splats": ("hbm", n_kept_gaussians * (8 + 4 + 4 + geo + kk)
-                           + S * (8 + 16 + 16 + 8 + 1 + 4)),
+                           + S * (32 + 16 + 8 + 1 + 4)),
         "sort_depth_pass0": ("hbm", S * (4 + 8)),
         "sort_depth_pass1": ("hbm", S * 16),
         "sort_depth_pass2": ("hbm", S * 16),
         "sort_depth_pass3": ("hbm", S * 16),
-        # duplication: per splat in depth order, its sorted id, (u, v),
-        # conic, rect and view in, its tile count and 32-byte expansion
-        # record out (row-table entries beyond three rows not counted); the
+        # duplication: per splat in depth order, its sorted id and packed
+        # 32-byte record in, its tile count and 32-byte expansion record out
+        # (row-table entries beyond three rows not counted); the
         # scan reads the counts and writes the offsets; the expansion reads
         # offsets and records and writes the pairs
-        "splat_tiles": ("hbm", S * (4 + 8 + 16 + 8 + 1) + S * (4 + 32)),
+        "splat_tiles": ("hbm", S * (4 + 32) + S * (4 + 32)),
         "duplicate": ("hbm", S * (4 + 4)),
         "duplicate_expand": ("hbm", S * (4 + 32) + K * 8),   # + tile-digit histograms (on chip)
         # per tile: its range and class slot out (the binary searches' reads

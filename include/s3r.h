@@ -474,8 +474,11 @@ s3r_status s3r_set_epoch(s3r_workspace* ws, uint32_t epoch, void* stream);
  *         "frustum_mask" u32[n_selected] bit v = inside camera v's frustum;
  *         "keep_mask" u32[n_selected] bit v = kept (frustum and LOD) in v;
  *         "splat_start" u32[n_selected] first splat of each selected Gaussian;
- *         "splat_xy" float2[n_splats]; "splat_conic_opacity" float4;
- *         "splat_rgb_depth" float4; "splat_rect" uint2 (x0|y0<<16, x1|y1<<16,
+ *         "splat_record" 8 x 32-bit [n_splats]: float u, v, conic a, b, c
+ *         (power = -0.5 (a dx^2 + c dy^2) - b dx dy), opacity, then x0|y0<<16
+ *         and w|h<<13|view<<26|moved<<31 (all ones for views of more than
+ *         8190 tiles in x or y); "splat_rgb_depth" float4;
+ *         "splat_rect" uint2 (x0|y0<<16, x1|y1<<16,
  *         tiles, half-open); "splat_view" uint8;
  *         "sorted_splats" u32[n_duplicates] splat id per pair in key order;
  *         "sorted_tiles" u32[n_duplicates] view-tile id per pair;

@@ -81,8 +81,7 @@ struct BlendArgs {
   TileQueue fwd_queue, bwd_queue;
   GradZero zero;          // backward only
   const uint32_t* sorted_splats;
-  const float2* sp_xy;
-  const float4* sp_conic_o;
+  const uint4* sp_tin;     // [S][2] packed splat record: (u, v, conic a, b), (conic c, opacity, ..)
   const float4* sp_rgb_d;
   const float* bg;
   const float* dL;        // backward only
@@ -540,8 +539,10 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_FWD_BLOCKS) k_blend_fw
       if (__syncthreads_count(all_done) == kBandThreads) break;
       for (int i = threadIdx.x; i < kBatchFwd && b0 + i < n; i += kBandThreads) {
         const uint32_t s = a.sorted_splats[range.x + b0 + i];
-        const float2 xy = a.sp_xy[s];
-        const float4 co = a.sp_conic_o[s];
+        const uint4 t0 = a.sp_tin[2 * (size_t)s], t1 = a.sp_tin[2 * (size_t)s + 1];
+        const float2 xy = make_float2(__uint_as_float(t0.x), __uint_as_float(t0.y));
+        const float4 co = make_float4(__uint_as_float(t0.z), __uint_as_float(t0.w),
+                                      __uint_as_float(t1.x), __uint_as_float(t1.y));
         const float4 rgb = a.sp_rgb_d[s];
         float4 sa, sb;
         float sc;
@@ -892,8 +893,10 @@ __global__ void __launch_bounds__(kBandThreads, S3R_BLEND_BWD_BLOCKS) k_blend_bw
       for (int i = threadIdx.x; i < m; i += kT) {
         const uint32_t s = a.sorted_splats[range.x + lo + i];
         s_id[i] = s;
-        const float2 xy = a.sp_xy[s];
-        const float4 co = a.sp_conic_o[s];
+        const uint4 t0 = a.sp_tin[2 * (size_t)s], t1 = a.sp_tin[2 * (size_t)s + 1];
+        const float2 xy = make_float2(__uint_as_float(t0.x), __uint_as_float(t0.y));
+        const float4 co = make_float4(__uint_as_float(t0.z), __uint_as_float(t0.w),
+                                      __uint_as_float(t1.x), __uint_as_float(t1.y));
         float4 sa, sb;
         float sc;
         stage_splat(xy, co, a.sp_rgb_d[s], sa, sb, sc);
@@ -1004,8 +1007,7 @@ static BlendArgs make_args(s3r_workspace* ws) {
   a.bwd_queue = TileQueue{ws->ctr + kCtrBlendBwdCursor, ws->ctr + kCtrBlendBwdExits};
   a.zero = GradZero{nullptr, 0, {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}, 0};
   a.sorted_splats = ws->dup_val[ws->dup_final];
-  a.sp_xy = ws->sp_xy;
-  a.sp_conic_o = ws->sp_conic_o;
+  a.sp_tin = reinterpret_cast<const uint4*>(ws->sp_tin);
   a.sp_rgb_d = ws->sp_rgb_d;
   a.final_T = ws->final_T;
   a.n_contrib = ws->n_contrib;

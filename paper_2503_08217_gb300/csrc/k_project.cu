@@ -44,11 +44,10 @@ struct ProjArgs {
   uint32_t* splat_start;
   uint2* kept_list;
   uint32_t* kept_bits;      // selection bitmap from the compaction; unkept bits cleared here
-  float2* sp_xy;
-  float4* sp_conic_o;
   float4* sp_rgb_d;
   uint2* sp_rect;
   uint8_t* sp_view;
+  uint4* sp_tin;            // [S][2] packed splat record (position, conic, opacity, extent)
   uint32_t* depth_key;
   uint32_t* hist;
   uint32_t* ctr;
@@ -415,12 +414,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_project_splats(const __grid_con
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.f);
         if ((int64_t)s < a.cap_splats) {
-          a.sp_xy[s] = make_float2(p.u, p.v);
-          a.sp_conic_o[s] = make_float4(p.ca, p.cb, p.cc, opac);
           a.sp_rgb_d[s] = make_float4(rgb[0], rgb[1], rgb[2], p.z);
           a.sp_rect[s] = make_uint2((uint32_t)p.x0 | ((uint32_t)p.y0 << 16),
                                     (uint32_t)p.x1 | ((uint32_t)p.y1 << 16));
           a.sp_view[s] = (uint8_t)v | (moved ? kSplatMoved : (uint8_t)0);
+          const bool fits = vi.gx <= kTinMaxGrid && vi.gy <= kTinMaxGrid;
+          const uint32_t ext = (uint32_t)(p.x1 - p.x0) | ((uint32_t)(p.y1 - p.y0) << 13) |
+                               ((uint32_t)v << 26) | (moved ? 0x80000000u : 0u);
+          a.sp_tin[2 * (size_t)s] = make_uint4(__float_as_uint(p.u), __float_as_uint(p.v),
+                                               __float_as_uint(p.ca), __float_as_uint(p.cb));
+          a.sp_tin[2 * (size_t)s + 1] =
+              make_uint4(__float_as_uint(p.cc), __float_as_uint(opac),
+                         (uint32_t)p.x0 | ((uint32_t)p.y0 << 16), fits ? ext : kTinFallback);
           // a splat without tiles (an Eq. 7 splat moved out of the frustum)
           // sorts after every real one (+inf), so that no expansion chunk
           // meets it between splats that have pairs
@@ -519,11 +524,10 @@ cudaError_t launch_project(s3r_workspace* ws, const s3r_scene* sc, const s3r_pos
   a.splat_start = ws->splat_start;
   a.kept_list = ws->kept_list;
   a.kept_bits = ws->kept_bits;
-  a.sp_xy = ws->sp_xy;
-  a.sp_conic_o = ws->sp_conic_o;
   a.sp_rgb_d = ws->sp_rgb_d;
   a.sp_rect = ws->sp_rect;
   a.sp_view = ws->sp_view;
+  a.sp_tin = reinterpret_cast<uint4*>(ws->sp_tin);
   a.depth_key = ws->depth_key[0];
   a.hist = ws->hist;
   a.ctr = ws->ctr;

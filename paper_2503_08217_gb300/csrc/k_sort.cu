@@ -355,8 +355,7 @@ constexpr int kInlineRows = 3;
 
 struct TilesArgs {
   const uint32_t* sorted;   // depth order -> splat id
-  const float2* xy;
-  const float4* co;
+  const uint4* tin;         // [S][2] packed splat records (rect and view below: fallback)
   const uint2* rect;
   const uint8_t* view;
   uint32_t* ctr;
@@ -377,9 +376,26 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
     const int64_t i = base + threadIdx.x;   // depth position
     const bool live = i < n;
     const uint32_t sp = live ? a.sorted[i] : 0u;
-    const uint2 rc = live ? a.rect[sp] : make_uint2(0u, 0u);
-    const uint32_t x0 = rc.x & 0xffffu, y0 = rc.x >> 16;
-    const uint32_t w = (rc.y & 0xffffu) - x0, h = (rc.y >> 16) - y0;
+    // the packed inputs: one 32-byte sector per splat
+    uint4 t0 = make_uint4(0u, 0u, 0u, 0u), t1 = make_uint4(0u, 0u, 0u, 0u);
+    if (live) {
+      t0 = a.tin[2 * (size_t)sp];
+      t1 = a.tin[2 * (size_t)sp + 1];
+    }
+    const float2 sxy = make_float2(__uint_as_float(t0.x), __uint_as_float(t0.y));
+    const float4 sco = make_float4(__uint_as_float(t0.z), __uint_as_float(t0.w),
+                                   __uint_as_float(t1.x), __uint_as_float(t1.y));
+    uint32_t x0 = t1.z & 0xffffu, y0 = t1.z >> 16;
+    uint32_t w = t1.w & 0x1fffu, h = (t1.w >> 13) & 0x1fffu;
+    uint32_t sview = ((t1.w >> 26) & 0x1fu) | ((t1.w >> 31) ? 0x80u : 0u);   // bit 7: moved
+    if (live && t1.w == kTinFallback) {   // a view too large for the packed extent
+      const uint2 rc = a.rect[sp];
+      x0 = rc.x & 0xffffu;
+      y0 = rc.x >> 16;
+      w = (rc.y & 0xffffu) - x0;
+      h = (rc.y >> 16) - y0;
+      sview = a.view[sp];
+    }
     // table entries for the rows past the inline ones, one atomic per warp
     const uint32_t need = (live && w != 0 && h > kInlineRows) ? h - kInlineRows : 0u;
     uint32_t incl = need;
@@ -396,7 +412,7 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
     const uint64_t off = wbase + incl - need;
     const bool table = off + need <= (uint64_t)a.rows_cap;
     Region g = {};
-    if (live) g = region_of(a.xy[sp], a.co[sp], x0, y0);
+    if (live) g = region_of(sxy, sco, x0, y0);
     // each lane: the inline rows of its own splat
     uint32_t cnt = 0;
     uint32_t head[kInlineRows] = {0u, 0u, 0u};
@@ -438,7 +454,7 @@ __global__ void __launch_bounds__(kTilesThreads) k_splat_tiles(const __grid_cons
       if (lane == (uint32_t)b) cnt += part;
     }
     if (!live) continue;
-    const ViewInfo& vi = vs.v[a.view[sp] & 0x7f];   // bit 7: Eq. 7 moved
+    const ViewInfo& vi = vs.v[sview & 0x7f];   // bit 7: Eq. 7 moved
     const uint32_t corner = (uint32_t)vi.tile_base + y0 * (uint32_t)vi.gx + x0;
     // a rectangle without columns (an Eq. 7 splat moved out of the frustum)
     // has no rows either for the expansion, which then reads no row table
@@ -872,13 +888,12 @@ cudaError_t launch_sort(s3r_workspace* ws, cudaStream_t st) {
     if (!tiles_per_sm) tiles_per_sm = per_sm_for((const void*)k_splat_tiles, kTilesThreads);
     KernelTimer timer(ws, kKSplatTiles, st);
     TilesArgs t;
-    t.xy = ws->sp_xy;
-    t.co = ws->sp_conic_o;
     t.rect = ws->sp_rect;
     t.view = ws->sp_view;
     t.ctr = ws->ctr;
     t.cap = ws->cap.max_splats;
     t.sorted = ws->depth_val[0];
+    t.tin = reinterpret_cast<const uint4*>(ws->sp_tin);
     t.cnt = ws->sp_tiles;
     t.meta = reinterpret_cast<uint4*>(ws->dup_meta);
     t.row_spans = ws->row_spans;

@@ -72,8 +72,8 @@ void free_all(s3r_workspace* ws) {
   for (int i = 0; i < 2 * kKCount; ++i)
     if (ws->ev[i]) cudaEventDestroy(ws->ev[i]);
   void* ptrs[] = {ws->ctr, ws->hist, ws->lookback, ws->selected, ws->frustum_mask,
-                  ws->keep_mask, ws->splat_start, ws->kept_list, ws->kept_bits, ws->sp_xy, ws->sp_conic_o, ws->sp_rgb_d,
-                  ws->sp_rect, ws->sp_view, ws->depth_key[0], ws->depth_key[1],
+                  ws->keep_mask, ws->splat_start, ws->kept_list, ws->kept_bits, ws->sp_rgb_d,
+                  ws->sp_rect, ws->sp_view, ws->sp_tin, ws->depth_key[0], ws->depth_key[1],
                   ws->depth_val[0], ws->depth_val[1], ws->dup_key[0], ws->dup_key[1],
                   ws->dup_val[0], ws->dup_val[1], ws->ranges, ws->final_T, ws->n_contrib,
                   ws->sp_grad, ws->pose_dM, ws->world_acc, ws->mats, ws->dup_excl, ws->dup_meta, ws->sp_tiles, ws->sp_region, ws->row_spans, ws->dup_chunk, ws->tile_class_cnt, ws->tile_class_list, ws->contrib};
@@ -191,11 +191,10 @@ s3r_status s3r_workspace_create(const s3r_capacity* cap, int device, s3r_workspa
   S3R_ALLOC(ws->kept_list, N);
   ws->kept_words = (N + 4095) / 4096 * 128;   // whole compaction tiles
   S3R_ALLOC(ws->kept_bits, ws->kept_words);
-  S3R_ALLOC(ws->sp_xy, S);
-  S3R_ALLOC(ws->sp_conic_o, S);
   S3R_ALLOC(ws->sp_rgb_d, S);
   S3R_ALLOC(ws->sp_rect, S);
   S3R_ALLOC(ws->sp_view, S);
+  S3R_ALLOC(ws->sp_tin, 8 * S);
   S3R_ALLOC(ws->depth_key[0], S);
   S3R_ALLOC(ws->depth_key[1], S);
   S3R_ALLOC(ws->depth_val[0], S);
@@ -653,8 +652,7 @@ const void* s3r_debug_buffer(const s3r_workspace* ws, const char* name) {
       {"frustum_mask", ws->frustum_mask},
       {"keep_mask", ws->keep_mask},
       {"splat_start", ws->splat_start},
-      {"splat_xy", ws->sp_xy},
-      {"splat_conic_opacity", ws->sp_conic_o},
+      {"splat_record", ws->sp_tin},
       {"splat_rgb_depth", ws->sp_rgb_d},
       {"splat_rect", ws->sp_rect},
       {"splat_view", ws->sp_view},

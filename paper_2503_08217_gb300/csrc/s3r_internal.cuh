@@ -77,6 +77,24 @@ struct ViewSet {
   ViewInfo v[S3R_MAX_VIEWS];
 };
 
+// ---- packed splat record ----------------------------------------------------
+// A splat's position, conic, opacity and tile extent in one 32-byte record,
+// written by the splat writer: (u, v, conic a, conic b), (conic c, opacity,
+// x0 | y0 << 16, w | h << 13 | view << 26 | moved << 31), with w, h the
+// rectangle's tile extent. The tile-count kernel, which visits the splats in
+// depth order, and the blend's staging, which visits them in each tile's
+// order, gather one sector per splat for all of it. Views whose tile grid is wider or higher than S3R_TIN_MAX_GRID
+// (8190, the most the 13-bit fields hold without ever giving the all-ones
+// word) do not fit that last word; it is then all ones and the kernel reads
+// the separate arrays. A build with S3R_TIN_MAX_GRID 0 takes that path for
+// every view (a variant the parity tests run).
+#ifndef S3R_TIN_MAX_GRID
+#define S3R_TIN_MAX_GRID 8190
+#endif
+static_assert(S3R_TIN_MAX_GRID >= 0 && S3R_TIN_MAX_GRID <= 8190, "13-bit tile extents");
+constexpr uint32_t kTinFallback = 0xffffffffu;
+constexpr int kTinMaxGrid = S3R_TIN_MAX_GRID;
+
 // ---- chunked scans ----------------------------------------------------------
 // S3R_SCAN_CTAS: at most this many CTAs run the chunked scans (compaction,
 // splat offsets, pair offsets); 0, the default, means every resident CTA. A
@@ -141,11 +159,10 @@ struct s3r_workspace {
   uint2* kept_list;         // [N] (compacted index, Gaussian id) of those kept in >= 1 view (any order)
   uint32_t* kept_bits;      // [ceil(N / 4096) * 128] bit per Gaussian id: selected and kept in >= 1 view
   int64_t kept_words;
-  float2* sp_xy;            // [S]
-  float4* sp_conic_o;       // [S]
   float4* sp_rgb_d;         // [S]
   uint2* sp_rect;           // [S]
   uint8_t* sp_view;         // [S]
+  uint32_t* sp_tin;         // [S] x 8: position, conic, opacity and tile extent (one 32-byte record)
   uint32_t* depth_key[2];   // [S]
   uint32_t* depth_val[2];   // [S]
   uint32_t* dup_key[2];     // [K]

@@ -46,8 +46,10 @@ def gpu_step(scene, step, cams, vis, life=None, lod=0.0, bg=(0.0, 0.0, 0.0), dL=
     res["keep_mask"] = ws.debug("keep_mask", torch.int32, n_sel).cpu().numpy().view(np.uint32)
     res["splat_start"] = ws.debug("splat_start", torch.int32, n_sel).cpu().numpy().view(np.uint32)
     sp = min(n_sp, r.ws.capacity.max_splats)
-    res["xy"] = ws.debug("splat_xy", torch.float32, 2 * sp).cpu().numpy().reshape(-1, 2)
-    res["conic_o"] = ws.debug("splat_conic_opacity", torch.float32, 4 * sp).cpu().numpy().reshape(-1, 4)
+    rec = ws.debug("splat_record", torch.float32, 8 * sp).cpu().numpy().reshape(-1, 8)
+    res["xy"] = rec[:, 0:2].copy()
+    res["conic_o"] = rec[:, 2:6].copy()
+    res["record_ext"] = rec[:, 6:8].copy().view(np.uint32)   # x0 | y0 << 16, w | h << 13 | view << 26 | moved << 31
     res["rgb_d"] = ws.debug("splat_rgb_depth", torch.float32, 4 * sp).cpu().numpy().reshape(-1, 4)
     rect = ws.debug("splat_rect", torch.int32, 2 * sp).cpu().numpy().view(np.uint32).reshape(-1, 2)
     res["rect"] = np.stack([rect[:, 0] & 0xFFFF, rect[:, 0] >> 16, rect[:, 1] & 0xFFFF, rect[:, 1] >> 16],
@@ -55,6 +57,16 @@ def gpu_step(scene, step, cams, vis, life=None, lod=0.0, bg=(0.0, 0.0, 0.0), dL=
     vb = ws.debug("splat_view", torch.uint8, sp).cpu().numpy().astype(np.int32)
     res["view"] = vb & 0x7F
     res["moved"] = (vb >> 7).astype(bool)          # Eq. 7: rendered at its noisy mean
+    # the packed record repeats the rectangle, view and Eq. 7 flag (its last
+    # word is all ones for views too large to pack: then the arrays serve)
+    ext, r4 = res["record_ext"], res["rect"].astype(np.uint32)
+    packed = ext[:, 1] != 0xFFFFFFFF
+    same = ((ext[:, 0] == (r4[:, 0] | (r4[:, 1] << 16)))
+            & ((ext[:, 1] & 0x1FFF) == r4[:, 2] - r4[:, 0])
+            & (((ext[:, 1] >> 13) & 0x1FFF) == r4[:, 3] - r4[:, 1])
+            & (((ext[:, 1] >> 26) & 0x1F) == res["view"])
+            & (((ext[:, 1] >> 31) & 1).astype(bool) == res["moved"]))
+    assert (same | ~packed).all(), "packed splat record disagrees with the rect/view arrays"
     nd = min(n_dup, r.ws.capacity.max_duplicates)
     res["sorted_splats"] = ws.debug("sorted_splats", torch.int32, nd).cpu().numpy().view(np.uint32)
     res["sorted_tiles"] = ws.debug("sorted_tiles", torch.int32, nd).cpu().numpy().view(np.uint32)

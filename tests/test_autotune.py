@@ -28,14 +28,14 @@ def test_every_tuned_define_has_a_source_default_among_its_candidates():
 def test_every_overridable_launch_shape_is_in_the_tuner():
     """Each `#ifndef S3R_X / #define S3R_X <int>` default in the CUDA sources is
     a launch shape the tuner searches (S3R_ARCH, the build's target, and
-    S3R_SCAN_CTAS, a cap on the chunked scans' CTAs that only the variant
-    parity test sets, aside)."""
+    S3R_SCAN_CTAS and S3R_TIN_MAX_GRID, which only the variant parity test
+    sets, aside)."""
     import re
     found = set()
     for path in sorted(os.listdir(libbuild.CSRC)):
         with open(os.path.join(libbuild.CSRC, path)) as f:
             found |= set(re.findall(r"^#ifndef (S3R_\w+)\n#define \1 \d+\b", f.read(), re.M))
-    assert found - {"S3R_ARCH", "S3R_SCAN_CTAS"} == {p.name for p in autotune.PARAMS}
+    assert found - {"S3R_ARCH", "S3R_SCAN_CTAS", "S3R_TIN_MAX_GRID"} == {p.name for p in autotune.PARAMS}
 
 
 def test_defines_reach_only_the_units_that_see_them():

@@ -7,9 +7,11 @@ sizes). The tests run in a child pytest with S3R_LIBRARY naming the variant,
 so this process's loaded library is not replaced. The larger batches stage
 two Gaussians per thread (a loop the 64-Gaussian default takes once), the
 smaller radix tiles and expansion chunks multiply the look-back tiles and
-chunk-map entries. A third library caps the chunked scans (compaction, splat
-and pair offsets) at two CTAs, so that on these small inputs a chunk spans
-many tiles and each CTA takes several chunks.
+chunk-map entries. Two more libraries set shapes the tuner does not search:
+one caps the chunked scans (compaction, splat and pair offsets) at two CTAs,
+so that on these small inputs a chunk spans many tiles and each CTA takes
+several chunks; one sends every view of the tile-count kernel down the path
+for views too large for the packed splat record (the separate arrays).
 """
 from __future__ import annotations
 
@@ -59,5 +61,7 @@ def test_off_default_launch_shapes_pass_parity(defines):
     _parity_with(defines)
 
 
-def test_two_scan_ctas_pass_parity():
-    _parity_with({"S3R_SCAN_CTAS": 2})
+@pytest.mark.parametrize("defines", [{"S3R_SCAN_CTAS": 2}, {"S3R_TIN_MAX_GRID": 0}],
+                         ids=["two_scan_ctas", "unpacked_tile_inputs"])
+def test_untuned_shapes_pass_parity(defines):
+    _parity_with(defines)
