@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kSortThreads, S3R_SORT_BLOCKS) k_onesweep(Pass
 // and reciprocals are the hardware approximations (errors of about 1 ulp, far
 // inside the margins), deterministic like the rest of the arithmetic.
 //
-//  k_splat_tiles: per splat, in depth order (its data gathered by the sorted
-//                id), its tile count (one interval per row of its
+//  k_splat_tiles: per splat, in depth order (its packed 32-byte record
+//                gathered by the sorted id), its tile count (one interval per row of its
 //                rectangle) and a 32-byte record for the expansion: the splat
 //                id, the tile id of the rectangle's corner, grid and
 //                rectangle widths, rectangle height, and its rows: the first
