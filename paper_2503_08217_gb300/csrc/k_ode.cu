@@ -22,7 +22,6 @@ namespace {
 
 constexpr int kH = S3R_ODE_HIDDEN;     // hidden width
 constexpr int kMaxD = S3R_ODE_MAX_EMBED;
-constexpr int kMaxI = 7 + kMaxD;       // network input: z (6), t, c (D)
 constexpr int kOdeWarps = 4;           // instances per CTA
 static_assert(kH == 64, "lanes hold hidden units l and l + 32");
 

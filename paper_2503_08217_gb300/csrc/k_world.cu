@@ -149,8 +149,9 @@ __device__ void chunk_rotations(const WorldArgs& a, int k0, int k1, const float*
     for (int i = 0; i < K; ++i) s_Yu[e * 16 + i] = sw * Y[i];
   }
   __syncthreads();
+  constexpr int kE = E > 0 ? E : 1;   // degree 0 has no rotation entries (the loop runs 0 times)
   for (int e = threadIdx.x; e < ns * E; e += blockDim.x) {
-    const int sl = e / E, r = e - sl * E;
+    const int sl = e / kE, r = e - sl * kE;
     const int l = r < 9 ? 1 : (r < 34 ? 2 : 3);
     const int nb = 2 * l + 1, idx = r - rot_off(l), i = idx / nb, j = idx - i * nb, b = band_start(l);
     float acc = 0.f;

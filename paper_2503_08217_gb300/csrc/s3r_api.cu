@@ -629,7 +629,7 @@ const uint32_t* s3r_device_status(const s3r_workspace* ws) {
 }
 
 s3r_status s3r_sync_status(s3r_workspace* ws, void* stream) {
-  s3r_counts c;
+  s3r_counts c = {};
   s3r_status st = s3r_query_counts(ws, stream, &c);
   if (st != S3R_OK) return st;
   if (c.device_status & kStatusTimeout)
