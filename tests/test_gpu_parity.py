@@ -394,6 +394,54 @@ def test_multiview_rig_sh3_lod(built):
                                          "inst_quat", "inst_trans"))
 
 
+def _max_views_crop(seed=2):
+    """The rig crop seen by the most cameras one call takes (S3R_MAX_VIEWS =
+    32): small images of uneven size all around the rig, so that view index
+    31 (the masks' top bit, the packed splat record's view field) and 32
+    tile bases are in use."""
+    sc = _rig_crop(seed=seed)
+    cams = []
+    for k in range(sc.n_steps):
+        pos = (0.0, 0.0, 6.0 + 0.5 * k)
+        cams.append([make_camera(48 + 8 * (i % 3), 32 + 4 * (i % 2), 28.0 + i, pos, 2.0 * np.pi * i / 32)
+                     for i in range(32)])
+    return scenegen.with_cameras(sc, cams)
+
+
+def test_max_views_match_oracle(built):
+    """32 cameras in one call (the maximum): forward stages, images and
+    gradients against the oracle."""
+    import gpu_helpers
+    sc = _max_views_crop()
+    vis, _ = gpu_helpers.sweep_visibility(sc, lod=1.0)
+    step = 5
+    cams = sc.cams[step]
+    assert len(cams) == 32
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3))
+    f = _oracle_views(sc, step, cams, vis, 1.0, bg=(0.2, 0.1, 0.3))
+    _compare_selection_and_masks(res, f, len(cams))
+    # the last camera sees splats (view index 31 is exercised)
+    assert (res["view"] == 31).any() and (res["keep_mask"] >> 31).any()
+    assert _compare_splats(res, f, sc, cams) > 500
+    _stage_isolated_sort(res, cams)
+    _stage_isolated_blend(res, cams, bg=(0.2, 0.1, 0.3))
+    _compare_images(res, f, cams, tag="32 cameras")
+    rng = np.random.default_rng(12)
+    dL = []
+    for v, cam in enumerate(cams):
+        d = rng.standard_normal((3, cam.height, cam.width))
+        view = f["views"][v]
+        d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+        dL.append(d)
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=(0.2, 0.1, 0.3))
+    for v in range(len(cams)):
+        dL[v][:, g_orc["pixel_flags"][v]] = 0.0
+    g_orc = oracle.step_backward(sc, step, f, dL, 1.0, cams=cams, bg=(0.2, 0.1, 0.3))
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, lod=1.0, bg=(0.2, 0.1, 0.3), dL=dL)
+    _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                         "inst_quat", "inst_trans"))
+
+
 def _wide_crop(seed=4):
     """A 60k-Gaussian crop of the mid corridor (SH3, four instances in front of
     the camera) seen by one 1920x1080 camera: 8,160 tiles, so view-tile ids
