@@ -625,6 +625,24 @@ def test_single_gaussian_and_ragged_sizes(built):
     np.testing.assert_allclose(res["images"][0], f["views"][0]["image"], atol=1e-5)
 
 
+def test_one_tile_camera_needs_no_tile_pass(built, tiny, tiny_vis):
+    """A 16x12 camera is one tile: the pair sort runs no tile-digit pass (every
+    key is tile 0) and the tile's range is all the pairs; stages and image
+    against the oracle."""
+    import gpu_helpers
+    vis, _ = tiny_vis
+    cams = [make_camera(16, 12, 14.0, (0.0, 0.0, 0.0), 0.0)]
+    sc = scenegen.with_cameras(tiny, [cams] * tiny.n_steps)
+    step = 3
+    res = gpu_helpers.gpu_step(sc, step, cams, vis)
+    f = _oracle_views(sc, step, cams, vis, 0.0)
+    assert res["counts"]["n_duplicates"] > 100
+    assert (res["ranges"][0] == [0, res["counts"]["n_duplicates"]]).all()
+    _stage_isolated_sort(res, cams)
+    _stage_isolated_blend(res, cams)
+    _compare_images(res, f, cams, tag="one-tile camera")
+
+
 def test_needle_splats_keep_their_rectangles(built, tiny, tiny_vis):
     """Splats whose conic eigenvalue ratio exceeds 3e4 (where the FP32
     per-pixel test's own rounding grows past the cull margins) keep every tile
