@@ -290,6 +290,36 @@ def test_tiny_gradients(built, tiny, tiny_vis):
                                          "inst_quat", "inst_trans"))
 
 
+def test_instances_only_scene(built):
+    """A scene with no static Gaussians (segment 0 empty: every Gaussian is
+    an instance's): stages, image and gradients, pose adjoints included."""
+    import gpu_helpers
+    sc = scenegen.generate("tiny", seed=5, n_static=0)
+    assert sc.inst_offsets[1] == 0 and sc.n > 0
+    vis, _ = gpu_helpers.sweep_visibility(sc)
+    step = 4
+    cams = sc.cams[step]
+    res = gpu_helpers.gpu_step(sc, step, cams, vis)
+    f = _oracle_views(sc, step, cams, vis, 0.0)
+    _compare_selection_and_masks(res, f, len(cams))
+    assert _compare_splats(res, f, sc, cams) > 100
+    _compare_images(res, f, cams, tag="instances only")
+    rng = np.random.default_rng(9)
+    dL = []
+    for v, cam in enumerate(cams):
+        d = rng.standard_normal((3, cam.height, cam.width))
+        view = f["views"][v]
+        d[:, gpu_helpers.bad_pixels(cam, view["rec"], view["flag"])] = 0.0
+        dL.append(d)
+    g_orc = oracle.step_backward(sc, step, f, dL, 0.0, cams=cams)
+    for v in range(len(cams)):
+        dL[v][:, g_orc["pixel_flags"][v]] = 0.0
+    g_orc = oracle.step_backward(sc, step, f, dL, 0.0, cams=cams)
+    res = gpu_helpers.gpu_step(sc, step, cams, vis, dL=dL)
+    _compare_grads(res["grads"], g_orc, ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                         "inst_quat", "inst_trans"))
+
+
 def test_temporal_sweep_record_matches(built, tiny):
     """Eq. 5 over all timesteps then Eq. 6 on the GPU equals the oracle's
     record (the same first-epoch sweep)."""
