@@ -518,7 +518,7 @@ def run_ours(args, rank, world, local):
         table["blend_bwd"].update(zero_bytes=int(zb),
                                   frac_alu_plus_hbm=round(floor_ms / kmean["blend_bwd"], 3))
     if "blend_fwd" in table and kmean.get("blend_fwd", 0) > 0:
-        # the survey's per-pair estimate of the forward (15 FP32 operations
+        # the usual per-pair estimate of a 3DGS forward (15 FP32 operations
         # per evaluated pair) beside the 17 counted in the code
         g15 = counts["n_eval_fwd"] * 15 / (kmean["blend_fwd"] / 1e3) / 1e9
         table["blend_fwd"]["frac_at_15_ops"] = round(g15 / alu_peak_gops, 3)
